@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark: PPPM force evaluations per second on the 216,576-atom + 72,192-WC
+water system (72,192 molecules, cubic 129.3 A box, order 5, beta 0.4 1/A,
+FP32), over a 1,000-step random walk of the positions (0.01 A Gaussian noise
+per coordinate and step, cumulative).
+
+One step = one full force evaluation (bin/sort, spread, forward FFT,
+influence with energy/virial, three ik inverse FFTs, gather) on that step's
+positions.  Inputs of all 1,000 frames are resident in HBM before timing; L2
+is flushed (256 MiB write) between timed steps, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mesh 128|160] [--impl ours|reference]
+
+Rank 0 prints one JSON line.  With N > 1 (torchrun) every rank runs an
+independent replica (the single-box path does not shard): weak scaling.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "PPPM force evals/sec at 216,576 atoms+WCs"
+UNIT = "evals/s"
+N_FRAMES = 1000
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--mesh", type=int, default=128, choices=[128, 160])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--profile-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(mesh):
+    return f"water72192_m{mesh}"
+
+
+def workload_config(mesh, n):
+    return {
+        "workload": f"water72192: 216,576 atoms + 72,192 WCs = {n} sites, cubic 129.3 A, mesh {mesh}^3, "
+                    f"order 5, beta 0.4/A, FP32, {N_FRAMES}-step 0.01 A random walk",
+        "n_sites": n,
+        "mesh": [mesh, mesh, mesh],
+        "order": 5,
+        "beta": 0.4,
+        "frames": N_FRAMES,
+        "l2": "flushed between timed steps (256 MiB write, outside the events)",
+    }
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_index_for(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+# --------------------------------------------------------------------- bytes
+def algorithmic_bytes(n: int, mesh: int) -> dict:
+    """Bytes each kernel must move at minimum (FP32): inputs read once, outputs
+    written once.  Sites are 16 B in (position + charge), forces 12 B out."""
+    N = mesh ** 3
+    NH = mesh * mesh * (mesh // 2 + 1)
+    return {
+        "spread": 16 * n + 4 * N,
+        "gather": 12 * N + 16 * n + 12 * n,
+        "fft_z_r2c": 4 * N + 8 * NH,
+        "fft_y": 16 * NH,
+        "fft_x_influence": 8 * NH + 4 * NH + 16 * NH,
+        "fft_y_inverse3": 16 * NH + 24 * NH,
+        "fft_z_c2r": 24 * NH + 12 * N,
+        "bin": 16 * n + 28 * n,
+        "scatter": 28 * n + 24 * n,
+        "fold": 8 * N,
+        "scan": 0,
+    }
+
+
+def step_algorithmic_bytes(n: int, mesh: int) -> int:
+    """The whole step as the method needs it: spread, one forward FFT pass,
+    influence, three inverse FFT passes, gather."""
+    N = mesh ** 3
+    NH = mesh * mesh * (mesh // 2 + 1)
+    return (16 * n + 4 * N) + (4 * N + 8 * NH) + (8 * NH + 4 * NH) + 3 * (8 * NH + 4 * N) + (12 * N + 28 * n)
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------- oracle (CPU)
+def oracle_time(wb, w, frames_fn, max_evals: int, budget_s: float):
+    """Time the FP64 CPU oracle (plan-time influence function excluded) on up to
+    max_evals frames, stopping once budget_s is spent.  Returns (evals/s, evals,
+    first result)."""
+    from oracle.pppm import OraclePPPM
+    o = OraclePPPM(wb.box, w["mesh"], w["order"], w["beta"])
+    t_total, done, first = 0.0, 0, None
+    for k in range(max_evals):
+        pos = frames_fn(k)
+        t0 = time.perf_counter()
+        r = o.compute(pos, wb.q)
+        t_total += time.perf_counter() - t0
+        done += 1
+        if first is None:
+            first = r
+        if t_total >= budget_s:
+            break
+    return done / t_total, done, first
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def run_reference(args):
+    from workloads.water import NOISE_SEED_1000_STEPS, NOISE_SIGMA_1000_STEPS, make_workload
+    wb, w = make_workload(workload_name(args.mesh))
+    rng = np.random.default_rng(NOISE_SEED_1000_STEPS)
+    cur = [wb.pos.astype(np.float32).astype(np.float64)]
+
+    def frame(k):
+        if k > 0:
+            cur[0] = (cur[0] + rng.normal(0.0, NOISE_SIGMA_1000_STEPS, size=cur[0].shape)).astype(np.float32).astype(np.float64)
+        return cur[0]
+
+    # warmup: at most one evaluation; timed: the first of K or a 120 s budget
+    budget = 120.0
+    if args.warmup > 0:
+        oracle_time(wb, w, frame, 1, 0.0)
+    val, done, _ = oracle_time(wb, w, frame, max(1, args.steps), budget)
+    sample = (f"{done} full FP64 evaluation(s) of successive frames of the workload (of {args.steps} requested; "
+              f"capped at {budget:.0f} s), plan-time influence function excluded")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": done, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 / val, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.mesh, wb.n),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model()},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2504_15508_gb300.pppm import Plan
+    from workloads.water import NOISE_SEED_1000_STEPS, NOISE_SIGMA_1000_STEPS, make_workload
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    wb, w = make_workload(workload_name(args.mesh))
+    n = wb.n
+    # frames: cumulative Gaussian random walk, generated on the device once (seeded)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(NOISE_SEED_1000_STEPS)
+    base = torch.tensor(wb.pos, dtype=torch.float64, device=dev)
+    frames = torch.empty((N_FRAMES, n, 3), dtype=torch.float32, device=dev)
+    cur = base.clone()
+    for k in range(N_FRAMES):
+        if k > 0:
+            cur += NOISE_SIGMA_1000_STEPS * torch.randn(cur.shape, generator=gen, dtype=torch.float64, device=dev)
+        frames[k] = cur.float()
+    del cur, base
+    q = torch.tensor(wb.q, dtype=torch.float32, device=dev)
+
+    plan = Plan(wb.box, w["mesh"], w["order"], w["beta"], precision="fp32")
+    plan.reserve(n)
+    energy = torch.empty(1, dtype=torch.float64, device=dev)
+    forces = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    virial = torch.empty(6, dtype=torch.float64, device=dev)
+    out = (energy, forces, virial)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        plan.compute(frames[k % N_FRAMES], q, out=out, stream=stream)
+
+    for k in range(args.warmup):
+        flush.fill_(float(k))
+        step(k)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sampler = ClockSampler(gpu_index_for(local))
+    time.sleep(0.05)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_(float(k))
+        ev_s[k].record(stream)
+        step(k)
+        ev_e[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(K)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * K / (total_ms * 1e-3)
+
+    # per-kernel breakdown: a second timed loop with event brackets around each launch
+    P = min(K, args.profile_steps)
+    plan.profile(True)
+    for k in range(P):
+        flush.fill_(float(k))
+        step(k)
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile(False)
+    kernels = {name: {"ms_per_launch": ms / c if c else None, "launches": c} for name, (ms, c) in prof.items()}
+    launches_per_step = sum(1 for name, (ms, c) in prof.items() if c)
+
+    peak, peak_kind = read_peaks()
+    alg = algorithmic_bytes(n, args.mesh)
+    dom = max((nm for nm in prof if prof[nm][1]), key=lambda nm: prof[nm][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "algorithmic_bytes": alg[dom]}
+    per_kernel_frac = {nm: (alg[nm] / (kernels[nm]["ms_per_launch"] * 1e-3) / 1e9) / peak
+                       for nm in kernels if kernels[nm]["launches"] and alg.get(nm)}
+    step_bytes = step_algorithmic_bytes(n, args.mesh)
+    ms_per_step = total_ms / K
+
+    # end to end through the host-pointer C ABI call (copies inside the timed region)
+    E = min(args.e2e_steps, N_FRAMES)
+    host_frames = frames[:E].cpu().pin_memory()
+    host_q = q.cpu().pin_memory()
+    hq = host_q.numpy()
+    for k in range(min(3, E)):
+        plan.compute_host(host_frames[k].numpy(), hq)
+    t0 = time.perf_counter()
+    for k in range(E):
+        e_h, f_h, v_h = plan.compute_host(host_frames[k].numpy(), hq)
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * E / e2e_s if world == 1 else E / e2e_s * world
+    e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 12 * n + 56,
+           "steps": E, "host_memory": "pinned"}
+
+    # parity of frame 0 and the CPU baseline (rank 0, N = 1 only)
+    parity, cpu = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        f0 = frames[0].double().cpu().numpy()
+        e_g, f_g, v_g = plan.compute(frames[0], q)
+        torch.cuda.synchronize()
+        cpu_val, cpu_n, ref = oracle_time(wb, w, lambda k: f0, 1, 0.0)
+        fg = f_g.double().cpu().numpy()
+        parity = {"force_rms_rel_err": float(np.linalg.norm(fg - ref["forces"]) / np.linalg.norm(ref["forces"])),
+                  "energy_rel_err": abs(e_g.item() - ref["energy"]) / abs(ref["energy"]),
+                  "virial_rel_err": float(np.linalg.norm(v_g.cpu().numpy() - ref["virial"]) /
+                                          np.linalg.norm(ref["virial"])),
+                  "vs": "FP64 CPU oracle, frame 0"}
+        cpu = {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one full FP64 evaluation of frame 0 (numpy, single thread), plan-time influence "
+                         "function excluded", "cpu": cpu_model()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": workload_config(args.mesh, n),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches_per_step * K,
+        "kernels": kernels, "kernel_hbm_frac": per_kernel_frac,
+        "step_roofline": {"algorithmic_bytes": step_bytes,
+                          "achieved_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
+                          "frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
+        "parity": parity, "wall_s_timed_loop": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

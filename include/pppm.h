@@ -1,0 +1,166 @@
+/*
+ * pppm.h -- C ABI of a single-GPU (sm_103a) PPPM solver for the long-range
+ * Gaussian-charge electrostatics of Deep Potential Long-Range (DPLR).
+ *
+ * What is computed (arXiv 2504.15508, Section 2.1):
+ *   E_Gt = 1/(2 pi V) sum_{m != 0} exp(-pi^2 m^2 / beta^2) / m^2 |S(m)|^2   (Eq. DPLR:EGt)
+ *   S(m) = sum_sites q_j exp(-2 pi i m . r_j)                               (Eq. DPLR:Sm)
+ * over ionic sites and Wannier centroids alike (Eq. DPLR:Wn gives the WC
+ * positions; to this library every site is a plain charged point), together
+ * with the forces -dE_Gt/dr_j (the E_Gt terms of Eq. DPLR:F_inter) and the
+ * virial.  The solver is PPPM with ik differentiation ("Poisson-ik", Section
+ * 3.1: one forward and three inverse 3D FFTs): order-p B-spline charge
+ * assignment, a real-to-complex 3D FFT, a multiply by the optimal influence
+ * function with energy and virial reduction, ik-differentiated inverse FFTs,
+ * and B-spline interpolation of the field back to every site.
+ *
+ * Units and conventions
+ *   Lengths in Angstrom, charges in e.  beta is the splitting parameter (an
+ *   inverse length): a pair of sites interacts as erf(beta r) / r.  E is in
+ *   q^2/Angstrom times `prefactor` (default 1; 14.399645 gives eV).  The box is
+ *   orthorhombic with edges box[0..2]; the k = 0 term is dropped and the
+ *   boundary is conducting.  Virial order: xx, yy, zz, xy, xz, yz, with
+ *   Pi_ab = -dE/d(eps_ab) under affine strain.
+ *   Positions are AoS n x 3 (x, y, z of site 0, then site 1, ...); they need
+ *   not lie inside the box.  Forces are AoS n x 3 in the caller's site order.
+ *
+ * Memory and streams
+ *   Unless an entry point says "host", every array argument is a DEVICE
+ *   pointer, owned by the caller, on the device that was current when the
+ *   plan was created.  The plan owns its workspace (meshes, influence table,
+ *   sort buffers).  Compute calls are asynchronous on the given stream
+ *   (a cudaStream_t passed as void*, NULL = legacy default stream) and write
+ *   energy and virial to device memory, so a call can be captured in a CUDA
+ *   graph once the plan's site capacity covers n (pppm_reserve).
+ *   A plan is not thread-safe: one compute at a time per plan.
+ *
+ * Errors
+ *   Every call returns PPPM_OK (0) or a negative PPPM_ERR_* code; nothing
+ *   aborts or traps.  Invalid positions (NaN, Inf, or farther than ~10^6 box
+ *   lengths from the origin) are detected on the device: the affected sites
+ *   are placed at the origin so that every access stays in bounds, and the
+ *   plan's status word records PPPM_ERR_NONFINITE; pppm_status() reads and
+ *   clears it (it synchronizes the stream).
+ */
+#ifndef PPPM_H
+#define PPPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PPPM_OK = 0,
+    PPPM_ERR_INVALID_ARG = -1,  /* NULL pointer, n < 0, beta <= 0, bad precision */
+    PPPM_ERR_BAD_MESH = -2,     /* a mesh edge is not 2^a 3^b 5^c, is < order, or > 2048 */
+    PPPM_ERR_BAD_ORDER = -3,    /* order outside [2, 7] */
+    PPPM_ERR_BAD_BOX = -4,      /* an edge <= 0 or not finite */
+    PPPM_ERR_CUDA = -5,         /* a CUDA runtime call failed (no device, out of memory, ...) */
+    PPPM_ERR_TIMEOUT = -6,      /* a bounded device-side wait ran out */
+    PPPM_ERR_NONFINITE = -7,    /* non-finite or far-away positions were seen */
+    PPPM_ERR_TOO_LARGE = -8     /* n or the mesh exceeds what the entry point supports */
+};
+
+enum { PPPM_FP32 = 1, PPPM_FP64 = 2 };
+
+typedef struct pppm_plan pppm_plan;
+
+typedef struct {
+    double prefactor;   /* multiplies E, forces and virial (default 1.0) */
+    int alias;          /* alias range a of the influence-function numerator, n in [-a,a]^3 (default 2) */
+    int tile;           /* edge of the spread/gather tiles in mesh cells, 0 = automatic (default 0) */
+} pppm_options;
+
+/* Default options. */
+int pppm_default_options(pppm_options *opt);
+
+/*
+ * Create a plan for one orthorhombic box.
+ *   box[3]    edge lengths (Angstrom), host array
+ *   mesh[3]   mesh points per edge, each 2^a 3^b 5^c, >= order, <= 2048
+ *   order     B-spline assignment order p in [2, 7] (p^3 stencil points)
+ *   beta      splitting parameter of Eq. DPLR:EGt (inverse Angstrom), > 0
+ *   precision PPPM_FP32 (spread/FFT/gather in FP32, compensated FP32 energy and
+ *             virial partials with an FP64 final sum) or PPPM_FP64
+ * The influence function (computed in FP64 on the device) and the FFT twiddles
+ * are built here.  The current CUDA device is used and recorded.
+ */
+int pppm_create(const double box[3], const int mesh[3], int order, double beta,
+                int precision, pppm_plan **out);
+int pppm_set_options(pppm_plan *plan, const pppm_options *opt); /* rebuilds G if alias changed */
+int pppm_get_options(const pppm_plan *plan, pppm_options *opt);
+/* Grow the per-site workspace to at least n sites (compute calls grow it on demand). */
+int pppm_reserve(pppm_plan *plan, int64_t n);
+void pppm_destroy(pppm_plan *plan);
+const char *pppm_strerror(int code);
+/* Read and clear the device status word (synchronizes the plan's last stream). */
+int pppm_status(pppm_plan *plan);
+
+/*
+ * One force evaluation (Eqs. DPLR:EGt, DPLR:Sm and the E_Gt part of
+ * DPLR:F_inter) over n sites, asynchronous on `stream`.
+ *   pos     n x 3 positions        (device; double for pppm_compute, float for _f32)
+ *   q       n charges              (device; same type as pos)
+ *   energy  1 double               (device)
+ *   forces  n x 3                  (device; same type as pos; overwritten)
+ *   virial  6 doubles              (device)
+ * Works with plans of either precision; the plan's precision sets the
+ * arithmetic.  n = 0 gives zero energy and virial.
+ */
+int pppm_compute(pppm_plan *plan, void *stream, const double *pos, const double *q, int64_t n,
+                 double *energy, double *forces, double *virial);
+int pppm_compute_f32(pppm_plan *plan, void *stream, const float *pos, const float *q, int64_t n,
+                     double *energy, float *forces, double *virial);
+
+/*
+ * The same evaluation from HOST arrays (pinned or pageable): copies the
+ * inputs to plan-owned device buffers, computes, copies energy, forces and
+ * virial back and synchronizes before returning.  Returns the device status
+ * too (PPPM_ERR_NONFINITE if bad positions were seen).
+ */
+int pppm_compute_host(pppm_plan *plan, const double *pos, const double *q, int64_t n,
+                      double *energy, double *forces, double *virial);
+int pppm_compute_host_f32(pppm_plan *plan, const float *pos, const float *q, int64_t n,
+                          double *energy, float *forces, double *virial);
+
+/*
+ * Stages of the path, exposed for testing each one on its own.  Mesh arrays
+ * are in the plan's precision (float or double), row-major with z fastest:
+ * real meshes Nx x Ny x Nz, complex half spectra Nx x Ny x (Nz/2+1) of
+ * interleaved (re, im) pairs.
+ *
+ * pppm_spread     charge density rho_p = sum_i q_i W W W / (hx hy hz)
+ *                 (order-p B-spline assignment, periodic) into rho.
+ * pppm_fft_r2c    unnormalised forward 3D DFT of a real mesh: out(k) = sum_p in_p e^{-i k.x_p}.
+ * pppm_fft_c2r    unnormalised inverse 3D DFT of a Hermitian half spectrum
+ *                 (imaginary parts of the kz = 0 and kz = Nz/2 planes are ignored).
+ * pppm_influence  copy the optimal influence function G (half spectrum,
+ *                 Nx x Ny x (Nz/2+1) doubles, FP64 as computed) to `G`.
+ * pppm_fields     the three field meshes E_x, E_y, E_z (3 consecutive real
+ *                 meshes) that the force interpolation reads.
+ */
+int pppm_spread(pppm_plan *plan, void *stream, const double *pos, const double *q, int64_t n, void *rho);
+int pppm_fft_r2c(pppm_plan *plan, void *stream, const void *in, void *out);
+int pppm_fft_c2r(pppm_plan *plan, void *stream, const void *in, void *out);
+int pppm_influence(pppm_plan *plan, double *G);
+int pppm_fields(pppm_plan *plan, void *stream, const double *pos, const double *q, int64_t n, void *fields);
+
+/*
+ * Per-kernel timing (for benchmarks).  While enabled, every kernel launch of a
+ * compute call is bracketed by CUDA events on the compute stream.
+ * pppm_profile_read synchronizes, writes for each kernel slot i < cap the
+ * accumulated milliseconds ms[i] and launch count calls[i] (host arrays, may
+ * be NULL), resets the accumulators and returns the number of slots.
+ * pppm_profile_name(i) names slot i (static string, "" if out of range).
+ */
+int pppm_profile_enable(pppm_plan *plan, int on);
+int pppm_profile_read(pppm_plan *plan, double *ms, int64_t *calls, int cap);
+const char *pppm_profile_name(int slot);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPPM_H */

@@ -1,0 +1,95 @@
+"""ctypes binding of ``libpppm.so`` (the C ABI declared in include/pppm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  If the library is missing the import of the functions fails loudly;
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpppm.so")
+
+PPPM_OK = 0
+PPPM_ERR_INVALID_ARG = -1
+PPPM_ERR_BAD_MESH = -2
+PPPM_ERR_BAD_ORDER = -3
+PPPM_ERR_BAD_BOX = -4
+PPPM_ERR_CUDA = -5
+PPPM_ERR_TIMEOUT = -6
+PPPM_ERR_NONFINITE = -7
+PPPM_ERR_TOO_LARGE = -8
+PPPM_FP32 = 1
+PPPM_FP64 = 2
+
+
+class PPPMError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = strerror(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} (code {code})" if what else f"{msg} (code {code})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("prefactor", ctypes.c_double), ("alias", ctypes.c_int), ("tile", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+vp = ctypes.c_void_p
+i64 = ctypes.c_int64
+dbl = ctypes.c_double
+cint = ctypes.c_int
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "pppm_default_options": (cint, [ctypes.POINTER(Options)]),
+    "pppm_create": (cint, [ctypes.POINTER(dbl), ctypes.POINTER(cint), cint, dbl, cint, ctypes.POINTER(vp)]),
+    "pppm_set_options": (cint, [vp, ctypes.POINTER(Options)]),
+    "pppm_get_options": (cint, [vp, ctypes.POINTER(Options)]),
+    "pppm_reserve": (cint, [vp, i64]),
+    "pppm_destroy": (None, [vp]),
+    "pppm_strerror": (ctypes.c_char_p, [cint]),
+    "pppm_status": (cint, [vp]),
+    "pppm_compute": (cint, [vp, vp, vp, vp, i64, vp, vp, vp]),
+    "pppm_compute_f32": (cint, [vp, vp, vp, vp, i64, vp, vp, vp]),
+    "pppm_compute_host": (cint, [vp, vp, vp, i64, vp, vp, vp]),
+    "pppm_compute_host_f32": (cint, [vp, vp, vp, i64, vp, vp, vp]),
+    "pppm_spread": (cint, [vp, vp, vp, vp, i64, vp]),
+    "pppm_fft_r2c": (cint, [vp, vp, vp, vp]),
+    "pppm_fft_c2r": (cint, [vp, vp, vp, vp]),
+    "pppm_influence": (cint, [vp, vp]),
+    "pppm_fields": (cint, [vp, vp, vp, vp, i64, vp]),
+    "pppm_profile_enable": (cint, [vp, cint]),
+    "pppm_profile_read": (cint, [vp, vp, vp, cint]),
+    "pppm_profile_name": (ctypes.c_char_p, [cint]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} not found: build it with paper_2504_15508_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().pppm_strerror(int(code)).decode()
+
+
+def check(code: int, what: str = "") -> None:
+    if code != PPPM_OK:
+        raise PPPMError(code, what)

@@ -1,0 +1,678 @@
+// C ABI of the PPPM library (include/pppm.h): plan creation, workspace, and the
+// orchestration of the kernels of one force evaluation on a CUDA stream.
+//
+// One evaluation (Poisson-ik PPPM, Section 3.1 of the paper, over the sites of
+// Eqs. DPLR:EGt and DPLR:Sm):
+//   bin -> scan -> scatter      sites sorted by mesh tile
+//   spread -> fold              charge mesh Q = sum q W W W (atomics-free)
+//   z R2C -> y FFT              forward FFT of the mesh (x happens next)
+//   x FFT + G + x IFFT          influence multiply, energy and virial
+//   y IFFT (3 outputs)          ik fields, still complex along z
+//   z C2R (3 fields)            E_x, E_y, E_z on the mesh
+//   gather                      F_i = q_i sum W W W E
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace pppm;
+
+struct pppm_plan {
+    int precision = PPPM_FP32;
+    int device = 0;
+    double box[3] = {0, 0, 0};
+    int mesh[3] = {0, 0, 0};
+    int order = 5;
+    double beta = 0.0;
+    pppm_options opt{};
+    Geo g{};
+    Radix rad[3]{};
+    Bundle bd{};
+    size_t esz = 4;  // sizeof(real)
+    // mesh workspace
+    double* G64 = nullptr;
+    void* G = nullptr;
+    void* tw[3] = {nullptr, nullptr, nullptr};
+    void* rho = nullptr;
+    void* cx[3] = {nullptr, nullptr, nullptr};
+    void* fields = nullptr;
+    void* partial = nullptr;
+    unsigned int* counter = nullptr;
+    int* status = nullptr;
+    // tiles
+    int tileT = 0;
+    void* patch = nullptr;
+    int* cov_off = nullptr;
+    int2* cov_ent = nullptr;
+    int* tile_count = nullptr;
+    int* tile_start = nullptr;
+    // sites
+    int64_t cap = 0;
+    int* tile_of = nullptr;
+    int* slot_of = nullptr;
+    void* rec = nullptr;
+    int* cell = nullptr;
+    void* srec = nullptr;
+    int* scell = nullptr;
+    int* sorig = nullptr;
+    // host-API staging
+    cudaStream_t own = nullptr;
+    void* h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    cudaStream_t last = nullptr;
+    // optional per-kernel timing with CUDA events (pppm_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> pend_slot;
+    std::vector<cudaEvent_t> pend_a, pend_b;
+    double prof_ms[16] = {};
+    int64_t prof_calls[16] = {};
+};
+
+namespace {
+
+enum Slot { K_BIN, K_SCAN, K_SCATTER, K_SPREAD, K_FOLD, K_FFT_Z_R2C, K_FFT_Y, K_FFT_X_INFLUENCE, K_FFT_Y_INV3,
+            K_FFT_Z_C2R, K_GATHER, K_NSLOTS };
+const char* kSlotNames[K_NSLOTS] = {"bin", "scan", "scatter", "spread", "fold", "fft_z_r2c", "fft_y",
+                                    "fft_x_influence", "fft_y_inverse3", "fft_z_c2r", "gather"};
+
+cudaEvent_t prof_event(pppm_plan* P) {
+    if (!P->ev_pool.empty()) {
+        cudaEvent_t e = P->ev_pool.back();
+        P->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one launch with events when profiling is on.
+struct Prof {
+    pppm_plan* P;
+    cudaStream_t s;
+    int slot;
+    cudaEvent_t a = nullptr;
+    Prof(pppm_plan* P_, cudaStream_t s_, int slot_) : P(P_), s(s_), slot(slot_) {
+        if (P->prof_on) {
+            a = prof_event(P);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~Prof() {
+        if (a) {
+            cudaEvent_t b = prof_event(P);
+            cudaEventRecord(b, s);
+            P->pend_slot.push_back(slot);
+            P->pend_a.push_back(a);
+            P->pend_b.push_back(b);
+        }
+    }
+};
+#define PROF(slot) Prof prof_##slot(P, s, slot)
+
+bool smooth235(int n) {
+    if (n < 1) return false;
+    for (int r : {2, 3, 5})
+        while (n % r == 0) n /= r;
+    return n == 1;
+}
+
+Radix make_radix(int L) {
+    Radix r{};
+    r.L = L;
+    int m = L;
+    for (int f : {4, 2, 3, 5})
+        while (m % f == 0) {
+            r.r[r.n++] = f;
+            m /= f;
+        }
+    return r;
+}
+
+#define CK(x)                                         \
+    do {                                              \
+        cudaError_t e_ = (x);                         \
+        if (e_ != cudaSuccess) return PPPM_ERR_CUDA;  \
+    } while (0)
+
+template <typename P>
+int dalloc(P** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    return e == cudaSuccess ? PPPM_OK : PPPM_ERR_CUDA;
+}
+
+template <typename P>
+void dfree(P*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+int64_t mesh_points(const pppm_plan* P) { return (int64_t)P->mesh[0] * P->mesh[1] * P->mesh[2]; }
+int64_t half_points(const pppm_plan* P) { return (int64_t)P->mesh[0] * P->mesh[1] * P->g.Hz; }
+size_t csz(const pppm_plan* P) { return 2 * P->esz; }
+
+// Tile edge for n sites: 8 cells unless that puts more than ~160 sites in an
+// average tile, then 4.
+int choose_tile(const pppm_plan* P, int64_t n) {
+    if (P->opt.tile > 0) return P->opt.tile;
+    double density = (double)n / (double)mesh_points(P);
+    return density * 512.0 <= 160.0 ? 8 : 4;
+}
+
+// (Re)build the tile geometry, the patch scratch and the fold cover lists.
+int setup_tiles(pppm_plan* P, int T) {
+    if (T == P->tileT && P->patch) return PPPM_OK;
+    Geo& g = P->g;
+    const int p = P->order;
+    g.T = T;
+    g.ntiles = 1;
+    for (int d = 0; d < 3; ++d) {
+        g.Tt[d] = T < g.N[d] ? T : g.N[d];
+        g.nt[d] = (g.N[d] + T - 1) / T;
+        g.E[d] = g.Tt[d] + p - 1;
+        g.ntiles *= g.nt[d];
+    }
+    g.Pz = g.E[2] | 1;
+    dfree(P->patch);
+    dfree(P->cov_off);
+    dfree(P->cov_ent);
+    dfree(P->tile_count);
+    dfree(P->tile_start);
+    const size_t psz = (size_t)g.E[0] * g.E[1] * g.E[2];
+    int rc;
+    if ((rc = dalloc(&P->patch, (size_t)g.ntiles * psz * P->esz)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->tile_count, sizeof(int) * (size_t)g.ntiles)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->tile_start, sizeof(int) * ((size_t)g.ntiles + 1))) != PPPM_OK) return rc;
+    // cover lists: for each axis and mesh index, the (tile, patch coordinate) pairs mapping to it
+    int nmax = g.N[0];
+    if (g.N[1] > nmax) nmax = g.N[1];
+    if (g.N[2] > nmax) nmax = g.N[2];
+    const int nmax1 = nmax + 1;
+    std::vector<int> off(3 * (size_t)nmax1, 0);
+    std::vector<int2> ent;
+    for (int d = 0; d < 3; ++d) {
+        const int N = g.N[d];
+        std::vector<std::vector<int2>> lists(N);
+        for (int t = 0; t < g.nt[d]; ++t) {
+            int cells = N - t * T;
+            if (cells > g.Tt[d]) cells = g.Tt[d];
+            for (int c = 0; c < cells + p - 1; ++c) {
+                int m = (t * T + g.kmin + c) % N;
+                if (m < 0) m += N;
+                lists[m].push_back(make_int2(t, c));
+            }
+        }
+        for (int m = 0; m < N; ++m) {
+            off[(size_t)d * nmax1 + m] = (int)ent.size();
+            for (const int2& e : lists[m]) ent.push_back(e);
+        }
+        off[(size_t)d * nmax1 + N] = (int)ent.size();
+    }
+    if ((rc = dalloc(&P->cov_off, sizeof(int) * off.size())) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->cov_ent, sizeof(int2) * ent.size())) != PPPM_OK) return rc;
+    CK(cudaMemcpy(P->cov_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->cov_ent, ent.data(), sizeof(int2) * ent.size(), cudaMemcpyHostToDevice));
+    P->tileT = T;
+    return PPPM_OK;
+}
+
+int reserve_sites(pppm_plan* P, int64_t n) {
+    if (n <= P->cap) return PPPM_OK;
+    if (n > (int64_t)1 << 30) return PPPM_ERR_TOO_LARGE;
+    dfree(P->tile_of);
+    dfree(P->slot_of);
+    dfree(P->rec);
+    dfree(P->cell);
+    dfree(P->srec);
+    dfree(P->scell);
+    dfree(P->sorig);
+    P->cap = 0;
+    const size_t rs = 4 * P->esz;
+    int rc;
+    if ((rc = dalloc(&P->tile_of, sizeof(int) * n)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->slot_of, sizeof(int) * n)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->rec, rs * n)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->cell, sizeof(int) * n)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->srec, rs * n)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->scell, sizeof(int) * n)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->sorig, sizeof(int) * n)) != PPPM_OK) return rc;
+    P->cap = n;
+    return PPPM_OK;
+}
+
+int build_influence(pppm_plan* P) {
+    cudaStream_t s = P->own;
+    CK(launch_influence(s, P->g, P->beta, P->opt.alias, P->G64));
+    if (P->precision == PPPM_FP32) CK(launch_convert<float>(s, P->G64, (float*)P->G, half_points(P)));
+    CK(cudaStreamSynchronize(s));
+    return PPPM_OK;
+}
+
+// ---------------------------------------------------------------- the path
+template <typename T, typename In>
+int run_sites_to_mesh(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_t n, T* rho_out, T scale) {
+    Geo& g = P->g;
+    CK(cudaMemsetAsync(P->tile_count, 0, sizeof(int) * (size_t)g.ntiles, s));
+    { PROF(K_BIN);
+      CK((launch_bin<T, In>(s, g, pos, q, (int)n, P->tile_count, P->tile_of, P->slot_of, (Rec<T>*)P->rec, P->cell,
+                            P->status))); }
+    { PROF(K_SCAN); CK(launch_scan(s, P->tile_count, g.ntiles, P->tile_start)); }
+    { PROF(K_SCATTER);
+      CK(launch_scatter<T>(s, (int)n, P->tile_of, P->slot_of, P->tile_start, (const Rec<T>*)P->rec, P->cell,
+                           (Rec<T>*)P->srec, P->scell, P->sorig)); }
+    { PROF(K_SPREAD);
+      CK(launch_spread<T>(s, g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig, (T*)P->patch)); }
+    { PROF(K_FOLD); CK(launch_fold<T>(s, g, (const T*)P->patch, P->cov_off, P->cov_ent, scale, rho_out)); }
+    return PPPM_OK;
+}
+
+template <typename T>
+int run_solve(pppm_plan* P, cudaStream_t s, double* energy, double* virial, T* fields_out) {
+    typedef typename Cx<T>::t C;
+    Geo& g = P->g;
+    const double h3 = (g.L[0] / g.N[0]) * (g.L[1] / g.N[1]) * (g.L[2] / g.N[2]);
+    const double Ntot = (double)mesh_points(P);
+    const double e_scale = 1.0 / (2.0 * Ntot * h3);  // V / (2 N^2 h^6)
+    const double c_field = 1.0 / (Ntot * h3);
+    C* c0 = (C*)P->cx[0];
+    C* c1 = (C*)P->cx[1];
+    C* c2 = (C*)P->cx[2];
+    { PROF(K_FFT_Z_R2C); CK(launch_fft_z_r2c<T>(s, g, P->rad[2], (const C*)P->tw[2], (const T*)P->rho, c0)); }
+    { PROF(K_FFT_Y); CK(launch_fft_bundle<T>(s, g, 1, -1, P->rad[1], P->bd, (const C*)P->tw[1], c0)); }
+    { PROF(K_FFT_X_INFLUENCE);
+      CK(launch_fft_x_influence<T>(s, g, P->rad[0], P->bd, (const C*)P->tw[0], (const T*)P->G, P->beta, e_scale,
+                                   c_field, c0, c1, (T*)P->partial, P->counter, P->opt.prefactor, energy, virial)); }
+    { PROF(K_FFT_Y_INV3); CK(launch_fft_y_inverse3<T>(s, g, P->rad[1], P->bd, (const C*)P->tw[1], c0, c1, c2)); }
+    const int64_t N3 = mesh_points(P);
+    const C* src[3] = {c1, c2, c0};
+    const int mk[3] = {0, 0, 1};
+    T* out[3] = {fields_out, fields_out + N3, fields_out + 2 * N3};
+    { PROF(K_FFT_Z_C2R); CK(launch_fft_z_c2r<T>(s, g, P->rad[2], (const C*)P->tw[2], 3, src, mk, out)); }
+    return PPPM_OK;
+}
+
+template <typename T, typename In>
+int run_compute(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_t n, double* energy, In* forces,
+                double* virial, T* fields_out) {
+    int rc;
+    if ((rc = setup_tiles(P, choose_tile(P, n))) != PPPM_OK) return rc;
+    if ((rc = reserve_sites(P, n)) != PPPM_OK) return rc;
+    P->last = s;
+    if ((rc = run_sites_to_mesh<T, In>(P, s, pos, q, n, (T*)P->rho, T(1))) != PPPM_OK) return rc;
+    T* fl = fields_out ? fields_out : (T*)P->fields;
+    if ((rc = run_solve<T>(P, s, energy, virial, fl)) != PPPM_OK) return rc;
+    if (forces && n > 0) {
+        PROF(K_GATHER);
+        CK((launch_gather<T, In>(s, P->g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig, fl,
+                                 P->opt.prefactor, forces)));
+    }
+    return PPPM_OK;
+}
+
+template <typename In>
+int compute_dispatch(pppm_plan* P, void* stream, const In* pos, const In* q, int64_t n, double* energy, In* forces,
+                     double* virial) {
+    if (!P || n < 0 || !energy || !virial) return PPPM_ERR_INVALID_ARG;
+    if (n > 0 && (!pos || !q || !forces)) return PPPM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(P->device));
+    if (P->precision == PPPM_FP32) return run_compute<float, In>(P, s, pos, q, n, energy, forces, virial, nullptr);
+    return run_compute<double, In>(P, s, pos, q, n, energy, forces, virial, nullptr);
+}
+
+template <typename In>
+int compute_host(pppm_plan* P, const In* pos, const In* q, int64_t n, double* energy, In* forces, double* virial) {
+    if (!P || n < 0 || !energy || !virial) return PPPM_ERR_INVALID_ARG;
+    if (n > 0 && (!pos || !q || !forces)) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    const size_t need = sizeof(In) * (size_t)(7 * n) + 8 * sizeof(double) + 256;
+    if (need > P->h_stage_bytes) {
+        dfree(P->h_stage);
+        P->h_stage_bytes = 0;
+        int rc;
+        if ((rc = dalloc(&P->h_stage, need)) != PPPM_OK) return rc;
+        P->h_stage_bytes = need;
+    }
+    double* d_e = (double*)P->h_stage;
+    double* d_v = d_e + 1;
+    In* d_pos = (In*)(d_e + 8);
+    In* d_q = d_pos + 3 * n;
+    In* d_f = d_q + n;
+    cudaStream_t s = P->own;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(d_pos, pos, sizeof(In) * 3 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_q, q, sizeof(In) * n, cudaMemcpyHostToDevice, s));
+    }
+    int rc = compute_dispatch<In>(P, s, d_pos, d_q, n, d_e, d_f, d_v);
+    if (rc != PPPM_OK) return rc;
+    CK(cudaMemcpyAsync(energy, d_e, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(virial, d_v, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (n > 0) CK(cudaMemcpyAsync(forces, d_f, sizeof(In) * 3 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return pppm_status(P);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+int pppm_default_options(pppm_options* opt) {
+    if (!opt) return PPPM_ERR_INVALID_ARG;
+    opt->prefactor = 1.0;
+    opt->alias = 2;
+    opt->tile = 0;
+    return PPPM_OK;
+}
+
+const char* pppm_strerror(int code) {
+    switch (code) {
+        case PPPM_OK: return "ok";
+        case PPPM_ERR_INVALID_ARG: return "invalid argument";
+        case PPPM_ERR_BAD_MESH: return "mesh edge must be 2^a 3^b 5^c, >= order and <= 2048";
+        case PPPM_ERR_BAD_ORDER: return "order must be in [2, 7]";
+        case PPPM_ERR_BAD_BOX: return "box edges must be finite and > 0";
+        case PPPM_ERR_CUDA: return "CUDA runtime error";
+        case PPPM_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+        case PPPM_ERR_NONFINITE: return "non-finite or far-away positions or charges";
+        case PPPM_ERR_TOO_LARGE: return "size exceeds what the entry point supports";
+    }
+    return "unknown error";
+}
+
+int pppm_create(const double box[3], const int mesh[3], int order, double beta, int precision, pppm_plan** out) {
+    if (!out) return PPPM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!box || !mesh) return PPPM_ERR_INVALID_ARG;
+    if (precision != PPPM_FP32 && precision != PPPM_FP64) return PPPM_ERR_INVALID_ARG;
+    if (!(beta > 0.0) || !std::isfinite(beta)) return PPPM_ERR_INVALID_ARG;
+    if (order < 2 || order > kMaxOrder) return PPPM_ERR_BAD_ORDER;
+    for (int d = 0; d < 3; ++d) {
+        if (!(box[d] > 0.0) || !std::isfinite(box[d])) return PPPM_ERR_BAD_BOX;
+        if (!smooth235(mesh[d]) || mesh[d] < order || mesh[d] > kMaxMesh) return PPPM_ERR_BAD_MESH;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return PPPM_ERR_CUDA;
+    pppm_plan* P = new (std::nothrow) pppm_plan();
+    if (!P) return PPPM_ERR_CUDA;
+    cudaGetDevice(&P->device);
+    P->precision = precision;
+    P->esz = precision == PPPM_FP32 ? 4 : 8;
+    P->order = order;
+    P->beta = beta;
+    pppm_default_options(&P->opt);
+    Geo& g = P->g;
+    for (int d = 0; d < 3; ++d) {
+        P->box[d] = box[d];
+        P->mesh[d] = mesh[d];
+        g.N[d] = mesh[d];
+        g.L[d] = box[d];
+        g.s[d] = (double)mesh[d] / box[d];
+        g.s_hi[d] = (float)g.s[d];
+        g.s_lo[d] = (float)(g.s[d] - (double)g.s_hi[d]);
+        g.kfac_d[d] = 6.283185307179586476925 / box[d];
+        g.kfac_f[d] = (float)g.kfac_d[d];
+        P->rad[d] = make_radix(mesh[d]);
+    }
+    g.Hz = mesh[2] / 2 + 1;
+    g.order = order;
+    g.kmin = (order % 2) ? -(order - 1) / 2 : -order / 2 + 1;
+    // bundle: about 16 kz columns per block, fewer if shared memory would not hold 6 line buffers
+    {
+        const int Lmax = mesh[0] > mesh[1] ? mesh[0] : mesh[1];
+        int bmax = (int)((200 * 1024) / (6 * (size_t)Lmax * 2 * P->esz));
+        if (bmax < 1) bmax = 1;
+        if (bmax > 16) bmax = 16;
+        int nb = (g.Hz + bmax - 1) / bmax;
+        P->bd.B = (g.Hz + nb - 1) / nb;
+        P->bd.nb = (g.Hz + P->bd.B - 1) / P->bd.B;  // no empty bundle
+    }
+    int rc = PPPM_OK;
+    auto fail = [&](int code) {
+        pppm_destroy(P);
+        return code;
+    };
+    if (cudaStreamCreateWithFlags(&P->own, cudaStreamNonBlocking) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    upload_bspline_coefficients();
+    const int64_t N3 = mesh_points(P), NH = half_points(P);
+    if ((rc = dalloc(&P->G64, sizeof(double) * NH)) != PPPM_OK) return fail(rc);
+    if (precision == PPPM_FP32) {
+        if ((rc = dalloc(&P->G, sizeof(float) * NH)) != PPPM_OK) return fail(rc);
+    } else {
+        P->G = P->G64;
+    }
+    for (int d = 0; d < 3; ++d)
+        if ((rc = dalloc(&P->tw[d], csz(P) * mesh[d])) != PPPM_OK) return fail(rc);
+    if ((rc = dalloc(&P->rho, P->esz * N3)) != PPPM_OK) return fail(rc);
+    for (int c = 0; c < 3; ++c)
+        if ((rc = dalloc(&P->cx[c], csz(P) * NH)) != PPPM_OK) return fail(rc);
+    if ((rc = dalloc(&P->fields, 3 * P->esz * N3)) != PPPM_OK) return fail(rc);
+    const int nblk = x_influence_blocks(g, P->bd);
+    if ((rc = dalloc(&P->partial, 14 * P->esz * (size_t)nblk)) != PPPM_OK) return fail(rc);
+    if ((rc = dalloc(&P->counter, sizeof(unsigned int))) != PPPM_OK) return fail(rc);
+    if ((rc = dalloc(&P->status, sizeof(int))) != PPPM_OK) return fail(rc);
+    if (cudaMemset(P->counter, 0, sizeof(unsigned int)) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    if (cudaMemset(P->status, 0, sizeof(int)) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    for (int d = 0; d < 3; ++d) {
+        cudaError_t e = precision == PPPM_FP32 ? launch_twiddles<float>(P->own, mesh[d], (float2*)P->tw[d])
+                                               : launch_twiddles<double>(P->own, mesh[d], (double2*)P->tw[d]);
+        if (e != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    }
+    if ((rc = build_influence(P)) != PPPM_OK) return fail(rc);
+    if ((rc = setup_tiles(P, 8)) != PPPM_OK) return fail(rc);
+    P->last = P->own;
+    *out = P;
+    return PPPM_OK;
+}
+
+int pppm_set_options(pppm_plan* P, const pppm_options* opt) {
+    if (!P || !opt) return PPPM_ERR_INVALID_ARG;
+    if (!std::isfinite(opt->prefactor) || opt->alias < 0 || opt->alias > 8 || opt->tile < 0 || opt->tile > 16 ||
+        (opt->tile != 0 && opt->tile != 4 && opt->tile != 8 && opt->tile != 16))
+        return PPPM_ERR_INVALID_ARG;
+    if (P->precision == PPPM_FP64 && opt->tile == 16) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    const bool rebuild = opt->alias != P->opt.alias;
+    P->opt = *opt;
+    if (rebuild) return build_influence(P);
+    return PPPM_OK;
+}
+
+int pppm_get_options(const pppm_plan* P, pppm_options* opt) {
+    if (!P || !opt) return PPPM_ERR_INVALID_ARG;
+    *opt = P->opt;
+    return PPPM_OK;
+}
+
+int pppm_reserve(pppm_plan* P, int64_t n) {
+    if (!P || n < 0) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    int rc = setup_tiles(P, choose_tile(P, n));
+    if (rc != PPPM_OK) return rc;
+    return reserve_sites(P, n);
+}
+
+void pppm_destroy(pppm_plan* P) {
+    if (!P) return;
+    cudaSetDevice(P->device);
+    if (P->own) cudaStreamSynchronize(P->own);
+    if (P->G != P->G64) dfree(P->G);
+    P->G = nullptr;
+    dfree(P->G64);
+    for (int d = 0; d < 3; ++d) dfree(P->tw[d]);
+    dfree(P->rho);
+    for (int c = 0; c < 3; ++c) dfree(P->cx[c]);
+    dfree(P->fields);
+    dfree(P->partial);
+    dfree(P->counter);
+    dfree(P->status);
+    dfree(P->patch);
+    dfree(P->cov_off);
+    dfree(P->cov_ent);
+    dfree(P->tile_count);
+    dfree(P->tile_start);
+    dfree(P->tile_of);
+    dfree(P->slot_of);
+    dfree(P->rec);
+    dfree(P->cell);
+    dfree(P->srec);
+    dfree(P->scell);
+    dfree(P->sorig);
+    dfree(P->h_stage);
+    for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : P->pend_a) cudaEventDestroy(e);
+    for (cudaEvent_t e : P->pend_b) cudaEventDestroy(e);
+    if (P->own) cudaStreamDestroy(P->own);
+    delete P;
+}
+
+int pppm_profile_enable(pppm_plan* P, int on) {
+    if (!P) return PPPM_ERR_INVALID_ARG;
+    P->prof_on = on != 0;
+    return PPPM_OK;
+}
+
+int pppm_profile_read(pppm_plan* P, double* ms, int64_t* calls, int cap) {
+    if (!P) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    for (size_t i = 0; i < P->pend_slot.size(); ++i) {
+        float t = 0.f;
+        CK(cudaEventSynchronize(P->pend_b[i]));
+        CK(cudaEventElapsedTime(&t, P->pend_a[i], P->pend_b[i]));
+        P->prof_ms[P->pend_slot[i]] += t;
+        P->prof_calls[P->pend_slot[i]] += 1;
+        P->ev_pool.push_back(P->pend_a[i]);
+        P->ev_pool.push_back(P->pend_b[i]);
+    }
+    P->pend_slot.clear();
+    P->pend_a.clear();
+    P->pend_b.clear();
+    for (int i = 0; i < cap && i < K_NSLOTS; ++i) {
+        if (ms) ms[i] = P->prof_ms[i];
+        if (calls) calls[i] = P->prof_calls[i];
+        P->prof_ms[i] = 0.0;
+        P->prof_calls[i] = 0;
+    }
+    return K_NSLOTS;
+}
+
+const char* pppm_profile_name(int slot) { return (slot >= 0 && slot < K_NSLOTS) ? kSlotNames[slot] : ""; }
+
+int pppm_status(pppm_plan* P) {
+    if (!P) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    CK(cudaStreamSynchronize(P->last));
+    int st = 0;
+    CK(cudaMemcpy(&st, P->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) CK(cudaMemset(P->status, 0, sizeof(int)));
+    return st ? PPPM_ERR_NONFINITE : PPPM_OK;
+}
+
+int pppm_compute(pppm_plan* P, void* stream, const double* pos, const double* q, int64_t n, double* energy,
+                 double* forces, double* virial) {
+    return compute_dispatch<double>(P, stream, pos, q, n, energy, forces, virial);
+}
+
+int pppm_compute_f32(pppm_plan* P, void* stream, const float* pos, const float* q, int64_t n, double* energy,
+                     float* forces, double* virial) {
+    return compute_dispatch<float>(P, stream, pos, q, n, energy, forces, virial);
+}
+
+int pppm_compute_host(pppm_plan* P, const double* pos, const double* q, int64_t n, double* energy, double* forces,
+                      double* virial) {
+    return compute_host<double>(P, pos, q, n, energy, forces, virial);
+}
+
+int pppm_compute_host_f32(pppm_plan* P, const float* pos, const float* q, int64_t n, double* energy, float* forces,
+                          double* virial) {
+    return compute_host<float>(P, pos, q, n, energy, forces, virial);
+}
+
+int pppm_spread(pppm_plan* P, void* stream, const double* pos, const double* q, int64_t n, void* rho) {
+    if (!P || n < 0 || !rho || (n > 0 && (!pos || !q))) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = setup_tiles(P, choose_tile(P, n))) != PPPM_OK) return rc;
+    if ((rc = reserve_sites(P, n)) != PPPM_OK) return rc;
+    P->last = s;
+    const Geo& g = P->g;
+    const double h3 = (g.L[0] / g.N[0]) * (g.L[1] / g.N[1]) * (g.L[2] / g.N[2]);
+    if (P->precision == PPPM_FP32) return run_sites_to_mesh<float, double>(P, s, pos, q, n, (float*)rho, (float)(1.0 / h3));
+    return run_sites_to_mesh<double, double>(P, s, pos, q, n, (double*)rho, 1.0 / h3);
+}
+
+int pppm_fft_r2c(pppm_plan* P, void* stream, const void* in, void* out) {
+    if (!P || !in || !out) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    P->last = s;
+    if (P->precision == PPPM_FP32) {
+        CK(launch_fft_z_r2c<float>(s, P->g, P->rad[2], (const float2*)P->tw[2], (const float*)in, (float2*)out));
+        CK(launch_fft_bundle<float>(s, P->g, 1, -1, P->rad[1], P->bd, (const float2*)P->tw[1], (float2*)out));
+        CK(launch_fft_bundle<float>(s, P->g, 0, -1, P->rad[0], P->bd, (const float2*)P->tw[0], (float2*)out));
+    } else {
+        CK(launch_fft_z_r2c<double>(s, P->g, P->rad[2], (const double2*)P->tw[2], (const double*)in, (double2*)out));
+        CK(launch_fft_bundle<double>(s, P->g, 1, -1, P->rad[1], P->bd, (const double2*)P->tw[1], (double2*)out));
+        CK(launch_fft_bundle<double>(s, P->g, 0, -1, P->rad[0], P->bd, (const double2*)P->tw[0], (double2*)out));
+    }
+    return PPPM_OK;
+}
+
+int pppm_fft_c2r(pppm_plan* P, void* stream, const void* in, void* out) {
+    if (!P || !in || !out) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    P->last = s;
+    CK(cudaMemcpyAsync(P->cx[0], in, csz(P) * half_points(P), cudaMemcpyDeviceToDevice, s));
+    const int mk[1] = {0};
+    if (P->precision == PPPM_FP32) {
+        float2* c0 = (float2*)P->cx[0];
+        CK(launch_fft_bundle<float>(s, P->g, 0, 1, P->rad[0], P->bd, (const float2*)P->tw[0], c0));
+        CK(launch_fft_bundle<float>(s, P->g, 1, 1, P->rad[1], P->bd, (const float2*)P->tw[1], c0));
+        const float2* src[1] = {c0};
+        float* o[1] = {(float*)out};
+        CK(launch_fft_z_c2r<float>(s, P->g, P->rad[2], (const float2*)P->tw[2], 1, src, mk, o));
+    } else {
+        double2* c0 = (double2*)P->cx[0];
+        CK(launch_fft_bundle<double>(s, P->g, 0, 1, P->rad[0], P->bd, (const double2*)P->tw[0], c0));
+        CK(launch_fft_bundle<double>(s, P->g, 1, 1, P->rad[1], P->bd, (const double2*)P->tw[1], c0));
+        const double2* src[1] = {c0};
+        double* o[1] = {(double*)out};
+        CK(launch_fft_z_c2r<double>(s, P->g, P->rad[2], (const double2*)P->tw[2], 1, src, mk, o));
+    }
+    return PPPM_OK;
+}
+
+int pppm_influence(pppm_plan* P, double* G) {
+    if (!P || !G) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    CK(cudaMemcpy(G, P->G64, sizeof(double) * half_points(P), cudaMemcpyDeviceToDevice));
+    return PPPM_OK;
+}
+
+int pppm_fields(pppm_plan* P, void* stream, const double* pos, const double* q, int64_t n, void* fields) {
+    if (!P || n < 0 || !fields || (n > 0 && (!pos || !q))) return PPPM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(P->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // energy and virial of this debug call go to a temporary device buffer
+    double* ev = nullptr;
+    int rc;
+    if ((rc = dalloc(&ev, 8 * sizeof(double))) != PPPM_OK) return rc;
+    if (P->precision == PPPM_FP32)
+        rc = run_compute<float, double>(P, s, pos, q, n, ev, nullptr, ev + 1, (float*)fields);
+    else
+        rc = run_compute<double, double>(P, s, pos, q, n, ev, nullptr, ev + 1, (double*)fields);
+    cudaStreamSynchronize(s);
+    dfree(ev);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Order-p cardinal B-spline charge-assignment weights.
+//
+// For a site at mesh coordinate u (position / h) the p stencil points are the
+// mesh points nearest to u: base g = floor(u + 1/2) for odd p, g = floor(u) for
+// even p, points g + kmin + j for j = 0..p-1 (kmin = -(p-1)/2 for odd p,
+// -p/2 + 1 for even p).  Point j gets M_p(g + kmin + j - u) with M_p the centred
+// cardinal B-spline of order p.  Writing x0 = g + kmin - u + p/2, which lies in
+// (0, 1], that weight is N_p(x0 + j), where N_p is the uniform B-spline on
+// [0, p).  On x0 in [0, 1] each N_p(x0 + j) is one polynomial piece of degree
+// p-1; the pieces' coefficients are built on the host by the recursion
+// N_m(t) = (t N_{m-1}(t) + (m - t) N_{m-1}(t - 1)) / (m - 1) applied to
+// polynomials, and evaluated here with Horner's rule.
+#pragma once
+
+#include "internal.cuh"
+
+namespace pppm {
+
+// c_bsp[p][j][m]: coefficient of x0^m in piece j of the order-p B-spline
+// (this header is included by one translation unit only, which fills them).
+__constant__ double c_bsp_d[kMaxOrder + 1][kMaxOrder][kMaxOrder];
+__constant__ float c_bsp_f[kMaxOrder + 1][kMaxOrder][kMaxOrder];
+
+template <typename T> __device__ __forceinline__ T bsp_coef(int p, int j, int m);
+template <> __device__ __forceinline__ float bsp_coef<float>(int p, int j, int m) { return c_bsp_f[p][j][m]; }
+template <> __device__ __forceinline__ double bsp_coef<double>(int p, int j, int m) { return c_bsp_d[p][j][m]; }
+
+// Coefficients of all P pieces in registers (uniform across the warp).
+template <typename T, int P>
+struct BspCoef {
+    T c[P][P];
+    __device__ __forceinline__ void load() {
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+#pragma unroll
+            for (int m = 0; m < P; ++m) c[j][m] = bsp_coef<T>(P, j, m);
+    }
+    __device__ __forceinline__ T piece(int j, T x) const {
+        T r = c[j][P - 1];
+#pragma unroll
+        for (int m = P - 2; m >= 0; --m) r = r * x + c[j][m];
+        return r;
+    }
+    __device__ __forceinline__ void all(T x, T w[P]) const {
+#pragma unroll
+        for (int j = 0; j < P; ++j) w[j] = piece(j, x);
+    }
+};
+
+// One piece with its coefficients in registers (piece index fixed per thread).
+template <typename T, int P>
+struct BspPiece {
+    T c[P];
+    __device__ __forceinline__ void load(int j) {
+#pragma unroll
+        for (int m = 0; m < P; ++m) c[m] = bsp_coef<T>(P, j, m);
+    }
+    __device__ __forceinline__ T eval(T x) const {
+        T r = c[P - 1];
+#pragma unroll
+        for (int m = P - 2; m >= 0; --m) r = r * x + c[m];
+        return r;
+    }
+};
+
+}  // namespace pppm

@@ -1,0 +1,541 @@
+// Mixed-radix (2, 3, 4, 5) 3D FFT passes of the PPPM path, and the fused
+// influence-function pass.
+//
+// Layout: real meshes are Nx x Ny x Nz (z fastest); spectra are half spectra
+// Nx x Ny x Hz complex, Hz = Nz/2 + 1, in the same order.
+//
+// Every pass moves a batch of 1D lines into shared memory, transforms them
+// with a self-sorting (Stockham) mixed-radix FFT between two shared buffers,
+// and writes them back:
+//   z forward   real rows, two per complex FFT (a + i b), unpacked to two half rows;
+//   y, x        strided lines, a bundle of B adjacent kz columns per block;
+//   x + G       forward x FFT, multiply by the influence function with the
+//               energy/virial reduction, and the inverse x FFTs of G rho and
+//               -i kx G rho in one block (Poisson-ik, Section 3.1 of the paper);
+//   y inverse   of G rho and -i ky G rho (after x) and of -i kx G rho;
+//   z inverse   Hermitian half rows of two rows (or two fields) packed as a + i b.
+// Twiddles come from a table of e^{-2 pi i t / L} built on the device in FP64
+// with sincospi and rounded to the mesh precision.
+#include "internal.cuh"
+
+namespace pppm {
+
+// ------------------------------------------------------------------ complex helpers
+template <typename R> struct CT;
+template <> struct CT<float> {
+    typedef float2 C;
+    static __device__ __forceinline__ C mk(float a, float b) { return make_float2(a, b); }
+};
+template <> struct CT<double> {
+    typedef double2 C;
+    static __device__ __forceinline__ C mk(double a, double b) { return make_double2(a, b); }
+};
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { C r; r.x = a.x * s; r.y = a.y * s; return r; }
+// multiply by i * s (s = +-1)
+template <typename C, typename R> __device__ __forceinline__ C cmul_is(C a, R s) { C r; r.x = -s * a.y; r.y = s * a.x; return r; }
+template <typename C> __device__ __forceinline__ C cconj(C a) { C r; r.x = a.x; r.y = -a.y; return r; }
+
+// Small DFT of size Rdx in registers; s = -1 forward, +1 inverse.
+template <typename C, typename R>
+__device__ __forceinline__ void butterfly(C* v, int Rdx, R s) {
+    if (Rdx == 2) {
+        C a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (Rdx == 4) {
+        C a02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        C a13 = cadd(v[1], v[3]), t = cmul_is(csub(v[1], v[3]), s);
+        v[0] = cadd(a02, a13);
+        v[2] = csub(a02, a13);
+        v[1] = cadd(d02, t);
+        v[3] = csub(d02, t);
+    } else if (Rdx == 3) {
+        const R c1 = R(-0.5), s1 = R(0.86602540378443864676);  // cos, sin of 2 pi / 3
+        C t1 = cadd(v[1], v[2]);
+        C t2 = cmul_is(csub(v[1], v[2]), s * s1);
+        C m = cadd(v[0], cscale(t1, c1));
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(m, t2);
+        v[2] = csub(m, t2);
+    } else {  // 5
+        const R c1 = R(0.30901699437494742410), c2 = R(-0.80901699437494742410);  // cos 2pi/5, cos 4pi/5
+        const R s1 = R(0.95105651629515357212), s2 = R(0.58778525229247312917);   // sin 2pi/5, sin 4pi/5
+        C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+        C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+        C m1 = cadd(v[0], cadd(cscale(a1, c1), cscale(a2, c2)));
+        C m2 = cadd(v[0], cadd(cscale(a1, c2), cscale(a2, c1)));
+        C n1 = cmul_is(cadd(cscale(b1, s1), cscale(b2, s2)), s);
+        C n2 = cmul_is(csub(cscale(b1, s2), cscale(b2, s1)), s);
+        v[0] = cadd(v[0], cadd(a1, a2));
+        v[1] = cadd(m1, n1);
+        v[4] = csub(m1, n1);
+        v[2] = cadd(m2, n2);
+        v[3] = csub(m2, n2);
+    }
+}
+
+// Stockham FFT of `nl` lines of length rp.L held in shared buffer `a`
+// (element t of line l at a[l * ls + t * ps]); `b` is the scratch partner.
+// Returns the buffer holding the result.  line_fast picks which index the
+// consecutive threads walk (the one with unit stride).
+template <typename R>
+__device__ typename CT<R>::C* stockham(typename CT<R>::C* a, typename CT<R>::C* b, int nl, int ls, int ps,
+                                       const Radix& rp, const typename CT<R>::C* __restrict__ tw, R s,
+                                       bool line_fast) {
+    typedef typename CT<R>::C C;
+    C* src = a;
+    C* dst = b;
+    const int L = rp.L;
+    int Ns = 1;
+    for (int st = 0; st < rp.n; ++st) {
+        const int Rdx = rp.r[st];
+        const int nbf = L / Rdx;
+        const int total = nbf * nl;
+        const int tstep = L / (Ns * Rdx);
+        for (int it = threadIdx.x; it < total; it += blockDim.x) {
+            int line, j;
+            if (line_fast) { line = it % nl; j = it / nl; } else { j = it % nbf; line = it / nbf; }
+            const int k = j % Ns;
+            C v[5];
+            const C* sp = src + line * ls;
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < Rdx) v[r] = sp[(j + r * nbf) * ps];
+            if (k != 0) {
+#pragma unroll
+                for (int r = 1; r < 5; ++r)
+                    if (r < Rdx) {
+                        C w = __ldg(&tw[k * r * tstep]);
+                        if (s > R(0)) w.y = -w.y;
+                        v[r] = cmul(v[r], w);
+                    }
+            }
+            butterfly<C, R>(v, Rdx, s);
+            const int d0 = (j / Ns) * Ns * Rdx + k;
+            C* dp = dst + line * ls;
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < Rdx) dp[(d0 + r * Ns) * ps] = v[r];
+        }
+        __syncthreads();
+        C* t = src; src = dst; dst = t;
+        Ns *= Rdx;
+    }
+    return src;
+}
+
+constexpr int kFftThreads = 256;
+
+// ------------------------------------------------------------------ z forward (R2C)
+template <typename R>
+__global__ void __launch_bounds__(kFftThreads)
+k_fft_z_r2c(Geo g, Radix rz, const typename CT<R>::C* __restrict__ tw, const R* __restrict__ in,
+            typename CT<R>::C* __restrict__ out, int rows, int pairs) {
+    typedef typename CT<R>::C C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Nz = g.N[2], Hz = g.Hz;
+    C* a = reinterpret_cast<C*>(smem_raw);
+    C* b = a + pairs * Nz;
+    const int pair0 = blockIdx.x * pairs;
+    const int npairs_total = (rows + 1) / 2;
+    const int np = min(pairs, npairs_total - pair0);
+    for (int i = threadIdx.x; i < np * Nz; i += blockDim.x) {
+        const int p = i / Nz, t = i - p * Nz;
+        const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
+        const R va = in[(int64_t)r0 * Nz + t];
+        const R vb = r1 < rows ? in[(int64_t)r1 * Nz + t] : R(0);
+        a[p * Nz + t] = CT<R>::mk(va, vb);
+    }
+    __syncthreads();
+    C* res = stockham<R>(a, b, np, Nz, 1, rz, tw, R(-1), false);
+    for (int i = threadIdx.x; i < np * Hz; i += blockDim.x) {
+        const int p = i / Hz, k = i - p * Hz;
+        const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
+        const C z = res[p * Nz + k];
+        const C zc = cconj(res[p * Nz + (k == 0 ? 0 : Nz - k)]);
+        const C x0 = cscale(cadd(z, zc), R(0.5));
+        const C d = csub(z, zc);  // = 2 i X1
+        out[(int64_t)r0 * Hz + k] = x0;
+        if (r1 < rows) out[(int64_t)r1 * Hz + k] = CT<R>::mk(R(0.5) * d.y, R(-0.5) * d.x);
+    }
+}
+
+template <typename T>
+cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw,
+                             const T* in, typename Cx<T>::t* out) {
+    const int rows = g.N[0] * g.N[1];
+    int pairs = (int)((32 * 1024) / (2 * g.N[2] * sizeof(typename Cx<T>::t)));
+    pairs = pairs < 1 ? 1 : (pairs > 16 ? 16 : pairs);
+    const int npairs = (rows + 1) / 2;
+    size_t smem = 2ull * pairs * g.N[2] * sizeof(typename Cx<T>::t);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_z_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fft_z_r2c<T><<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, rz, tw, in, out, rows, pairs);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ strided-line C2C
+// axis 1: lines along y (outer index x); axis 0: lines along x (outer index y).
+template <typename R>
+__global__ void __launch_bounds__(kFftThreads)
+k_fft_bundle(Geo g, int axis, R sgn, Radix rp, Bundle bd, const typename CT<R>::C* __restrict__ tw,
+             typename CT<R>::C* __restrict__ data) {
+    typedef typename CT<R>::C C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Hz = g.Hz, L = rp.L, B = bd.B;
+    const int outer = blockIdx.x / bd.nb, bi = blockIdx.x % bd.nb;
+    const int kz0 = bi * B;
+    const int nl = min(B, Hz - kz0);
+    const int64_t es = axis == 1 ? (int64_t)Hz : (int64_t)g.N[1] * Hz;
+    const int64_t os = axis == 1 ? (int64_t)g.N[1] * Hz : (int64_t)Hz;
+    C* a = reinterpret_cast<C*>(smem_raw);
+    C* b = a + L * B;
+    C* base = data + outer * os + kz0;
+    for (int i = threadIdx.x; i < L * nl; i += blockDim.x) {
+        const int t = i / nl, l = i - t * nl;
+        a[t * B + l] = base[t * es + l];
+    }
+    __syncthreads();
+    C* res = stockham<R>(a, b, nl, 1, B, rp, tw, sgn, true);
+    for (int i = threadIdx.x; i < L * nl; i += blockDim.x) {
+        const int t = i / nl, l = i - t * nl;
+        base[t * es + l] = res[t * B + l];
+    }
+}
+
+template <typename T>
+cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, const Radix& r, const Bundle& bd,
+                              const typename Cx<T>::t* tw, typename Cx<T>::t* data) {
+    const int outer = axis == 1 ? g.N[0] : g.N[1];
+    size_t smem = 2ull * r.L * bd.B * sizeof(typename Cx<T>::t);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_bundle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fft_bundle<T><<<outer * bd.nb, kFftThreads, smem, s>>>(g, axis, (T)sign, r, bd, tw, data);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ x + influence
+//
+// Per block: one y index and B adjacent kz columns, lines along x.
+//   1. forward FFT along x  -> rho_hat(k) up to the 1/h^3 factor;
+//   2. per mode: G, the energy term e = w G |rho_hat|^2 V/(2 N^2) and the virial
+//      terms e (delta_ab - 2 (1 + k^2/(4 beta^2)) k_a k_b / k^2), accumulated per
+//      thread with compensated (TwoSum) sums, reduced per block;
+//   3. P = G rho_hat / (N h^3) and -i kx' P (kx' = 0 on the Nyquist index);
+//   4. inverse FFT along x of both; P -> S (in place), -i kx' P -> Bx.
+// The last block to finish sums the per-block partials in FP64 in block order.
+//
+// Half-spectrum weights: w = 1 on the kz = 0 plane (and kz = Nz/2 for even Nz),
+// 2 elsewhere, standing for the mirror mode -k.  For the off-diagonal virial a
+// mirrored mode whose x (or y) index is the Nyquist index keeps that component's
+// sign (the index maps to itself, m = +N/2), so a product k_a k_b survives the
+// pairing only when both or neither of its components flip sign.
+template <typename R>
+__device__ __forceinline__ void two_sum_acc(R& hi, R& lo, R v) {
+    R s = hi + v;
+    R bp = s - hi;
+    R err = (hi - (s - bp)) + (v - bp);
+    hi = s;
+    lo += err;
+}
+
+// (h, l) += (h2, l2) with the rounding error of h + h2 carried into l
+template <typename R>
+__device__ __forceinline__ void two_sum_pair(R& h, R& l, R h2, R l2) {
+    R s = h + h2;
+    R bp = s - h;
+    R err = (h - (s - bp)) + (h2 - bp);
+    h = s;
+    l = l + l2 + err;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kFftThreads)
+k_fft_x_influence(Geo g, Radix rx, Bundle bd, const typename CT<R>::C* __restrict__ tw, const R* __restrict__ G,
+                  R beta, R e_scale, R c_field, typename CT<R>::C* __restrict__ S,
+                  typename CT<R>::C* __restrict__ Bx, R* __restrict__ partial,
+                  unsigned int* __restrict__ counter, double prefactor, double* __restrict__ energy,
+                  double* __restrict__ virial) {
+    typedef typename CT<R>::C C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ R red[kFftThreads / 32][14];
+    __shared__ bool is_last;
+    const int Nx = g.N[0], Ny = g.N[1], Nz = g.N[2], Hz = g.Hz, B = bd.B;
+    const int y = blockIdx.x / bd.nb, bi = blockIdx.x % bd.nb;
+    const int kz0 = bi * B;
+    const int nl = min(B, Hz - kz0);
+    const int64_t es = (int64_t)Ny * Hz;
+    C* a0 = reinterpret_cast<C*>(smem_raw);
+    C* a1 = a0 + Nx * B;
+    C* b0 = a1 + Nx * B;
+    C* b1 = b0 + Nx * B;
+    C* base = S + (int64_t)y * Hz + kz0;
+    for (int i = threadIdx.x; i < Nx * nl; i += blockDim.x) {
+        const int t = i / nl, l = i - t * nl;
+        a0[t * B + l] = base[t * es + l];
+    }
+    __syncthreads();
+    C* rh = stockham<R>(a0, a1, nl, 1, B, rx, tw, R(-1), true);
+    C* pbuf = (rh == a0) ? a1 : a0;  // free partner of the result buffer
+
+    const int my = y <= Ny / 2 ? y : y - Ny;
+    const R ky = kfac<R>(g, 1) * my;
+    const bool nyq_y = (Ny % 2 == 0) && (y == Ny / 2);
+    const R inv4b2 = R(1) / (R(4) * beta * beta);
+    R acc_hi[7], acc_lo[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) { acc_hi[q] = R(0); acc_lo[q] = R(0); }
+    for (int i = threadIdx.x; i < Nx * nl; i += blockDim.x) {
+        const int t = i / nl, l = i - t * nl;
+        const int kz = kz0 + l;
+        const int mx = t <= Nx / 2 ? t : t - Nx;
+        const R kx = kfac<R>(g, 0) * mx;
+        const R kzv = kfac<R>(g, 2) * kz;
+        const bool nyq_x = (Nx % 2 == 0) && (t == Nx / 2);
+        const R gk = G[((int64_t)t * Ny + y) * Hz + kz];
+        const C v = rh[t * B + l];
+        const bool plane1 = (kz == 0) || ((Nz % 2 == 0) && (kz == Nz / 2));
+        const R w = plane1 ? R(1) : R(2);
+        const R k2 = kx * kx + ky * ky + kzv * kzv;
+        if (k2 > R(0)) {
+            const R e = w * e_scale * gk * (v.x * v.x + v.y * v.y);
+            const R c = R(2) * (R(1) + k2 * inv4b2) / k2;
+            const R fxy = (plane1 || (nyq_x == nyq_y)) ? R(1) : R(0);
+            const R fxz = (plane1 || !nyq_x) ? R(1) : R(0);
+            const R fyz = (plane1 || !nyq_y) ? R(1) : R(0);
+            two_sum_acc(acc_hi[0], acc_lo[0], e);
+            two_sum_acc(acc_hi[1], acc_lo[1], e * (R(1) - c * kx * kx));
+            two_sum_acc(acc_hi[2], acc_lo[2], e * (R(1) - c * ky * ky));
+            two_sum_acc(acc_hi[3], acc_lo[3], e * (R(1) - c * kzv * kzv));
+            two_sum_acc(acc_hi[4], acc_lo[4], -e * c * kx * ky * fxy);
+            two_sum_acc(acc_hi[5], acc_lo[5], -e * c * kx * kzv * fxz);
+            two_sum_acc(acc_hi[6], acc_lo[6], -e * c * ky * kzv * fyz);
+        }
+        const C P = cscale(v, gk * c_field);
+        const R kxd = nyq_x ? R(0) : kx;
+        pbuf[t * B + l] = P;
+        b0[t * B + l] = CT<R>::mk(kxd * P.y, -kxd * P.x);  // -i kx' P
+    }
+    __syncthreads();
+    C* rA = stockham<R>(pbuf, rh, nl, 1, B, rx, tw, R(1), true);
+    C* rB = stockham<R>(b0, b1, nl, 1, B, rx, tw, R(1), true);
+    C* obx = Bx + (int64_t)y * Hz + kz0;
+    for (int i = threadIdx.x; i < Nx * nl; i += blockDim.x) {
+        const int t = i / nl, l = i - t * nl;
+        base[t * es + l] = rA[t * B + l];
+        obx[t * es + l] = rB[t * B + l];
+    }
+
+    // block reduction of the 7 compensated sums: (hi, lo) pairs combined with TwoSum
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        R h = acc_hi[q], lo = acc_lo[q];
+        for (int off = 16; off > 0; off >>= 1) {
+            const R h2 = __shfl_down_sync(0xffffffffu, h, off);
+            const R l2 = __shfl_down_sync(0xffffffffu, lo, off);
+            two_sum_pair(h, lo, h2, l2);
+        }
+        if (lane == 0) { red[warp][2 * q] = h; red[warp][2 * q + 1] = lo; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        const int q = threadIdx.x;
+        R h = red[0][2 * q], lo = red[0][2 * q + 1];
+        for (int w = 1; w < kFftThreads / 32; ++w) two_sum_pair(h, lo, red[w][2 * q], red[w][2 * q + 1]);
+        partial[(int64_t)blockIdx.x * 14 + 2 * q] = h;
+        partial[(int64_t)blockIdx.x * 14 + 2 * q + 1] = lo;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int done = atomicAdd(counter, 1u);
+        is_last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        if (warp < 7) {  // warp q sums quantity q over all blocks, then the FP64 final sum
+            const int q = warp;
+            R h = R(0), lo = R(0);
+            for (unsigned int b = lane; b < gridDim.x; b += 32) {
+                two_sum_pair(h, lo, __ldcg(&partial[(int64_t)b * 14 + 2 * q]), __ldcg(&partial[(int64_t)b * 14 + 2 * q + 1]));
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const R h2 = __shfl_down_sync(0xffffffffu, h, off);
+                const R l2 = __shfl_down_sync(0xffffffffu, lo, off);
+                two_sum_pair(h, lo, h2, l2);
+            }
+            if (lane == 0) {
+                const double sum = ((double)h + (double)lo) * prefactor;
+                if (q == 0) energy[0] = sum;
+                else virial[q - 1] = sum;
+            }
+        }
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
+int x_influence_blocks(const Geo& g, const Bundle& bd) { return g.N[1] * bd.nb; }
+
+template <typename T>
+cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx, const Bundle& bd,
+                                   const typename Cx<T>::t* tw, const T* G, double beta, double e_scale,
+                                   double c_field, typename Cx<T>::t* S, typename Cx<T>::t* Bx, T* partial,
+                                   unsigned int* counter, double prefactor, double* energy, double* virial) {
+    size_t smem = 4ull * g.N[0] * bd.B * sizeof(typename Cx<T>::t);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fft_x_influence<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fft_x_influence<T><<<x_influence_blocks(g, bd), kFftThreads, smem, s>>>(
+        g, rx, bd, tw, G, (T)beta, (T)e_scale, (T)c_field, S, Bx, partial, counter, prefactor, energy, virial);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ y inverse, three outputs
+// C = IFFT_y(A), D = IFFT_y(-i ky' A), Ex' = IFFT_y(Bx); C overwrites A, Ex' overwrites Bx.
+template <typename R>
+__global__ void __launch_bounds__(kFftThreads)
+k_fft_y_inverse3(Geo g, Radix ry, Bundle bd, const typename CT<R>::C* __restrict__ tw,
+                 typename CT<R>::C* __restrict__ A, typename CT<R>::C* __restrict__ Bx,
+                 typename CT<R>::C* __restrict__ D) {
+    typedef typename CT<R>::C C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ny = g.N[1], Hz = g.Hz, B = bd.B;
+    const int x = blockIdx.x / bd.nb, bi = blockIdx.x % bd.nb;
+    const int kz0 = bi * B;
+    const int nl = min(B, Hz - kz0);
+    const int64_t off = (int64_t)x * Ny * Hz + kz0;
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int sz = Ny * B;
+    for (int i = threadIdx.x; i < Ny * nl; i += blockDim.x) {
+        const int t = i / nl, l = i - t * nl;
+        const C va = A[off + (int64_t)t * Hz + l];
+        const int my = t <= Ny / 2 ? t : t - Ny;
+        const R kyd = ((Ny % 2 == 0) && (t == Ny / 2)) ? R(0) : kfac<R>(g, 1) * my;
+        buf[t * B + l] = va;
+        buf[2 * sz + t * B + l] = CT<R>::mk(kyd * va.y, -kyd * va.x);
+        buf[4 * sz + t * B + l] = Bx[off + (int64_t)t * Hz + l];
+    }
+    __syncthreads();
+    C* rC = stockham<R>(buf, buf + sz, nl, 1, B, ry, tw, R(1), true);
+    C* rD = stockham<R>(buf + 2 * sz, buf + 3 * sz, nl, 1, B, ry, tw, R(1), true);
+    C* rE = stockham<R>(buf + 4 * sz, buf + 5 * sz, nl, 1, B, ry, tw, R(1), true);
+    for (int i = threadIdx.x; i < Ny * nl; i += blockDim.x) {
+        const int t = i / nl, l = i - t * nl;
+        A[off + (int64_t)t * Hz + l] = rC[t * B + l];
+        D[off + (int64_t)t * Hz + l] = rD[t * B + l];
+        Bx[off + (int64_t)t * Hz + l] = rE[t * B + l];
+    }
+}
+
+template <typename T>
+cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry, const Bundle& bd,
+                                  const typename Cx<T>::t* tw, typename Cx<T>::t* A, typename Cx<T>::t* Bx,
+                                  typename Cx<T>::t* D) {
+    size_t smem = 6ull * g.N[1] * bd.B * sizeof(typename Cx<T>::t);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_y_inverse3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fft_y_inverse3<T><<<g.N[0] * bd.nb, kFftThreads, smem, s>>>(g, ry, bd, tw, A, Bx, D);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ z inverse (C2R)
+struct ZOut {
+    const void* src[3];
+    void* out[3];
+    int mulkz[3];
+    int nf;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kFftThreads)
+k_fft_z_c2r(Geo g, Radix rz, const typename CT<R>::C* __restrict__ tw, ZOut zo, int rows, int pairs) {
+    typedef typename CT<R>::C C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Nz = g.N[2], Hz = g.Hz;
+    const int nf = zo.nf;
+    C* a = reinterpret_cast<C*>(smem_raw);
+    C* b = a + nf * pairs * Nz;
+    const int pair0 = blockIdx.x * pairs;
+    const int npairs_total = (rows + 1) / 2;
+    const int np = min(pairs, npairs_total - pair0);
+    const int nlines = nf * np;
+    const bool even = (Nz % 2) == 0;
+    for (int i = threadIdx.x; i < nlines * Nz; i += blockDim.x) {
+        const int line = i / Nz, t = i - line * Nz;
+        const int f = line / np, p = line - f * np;
+        const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
+        const C* src = reinterpret_cast<const C*>(zo.src[f]);
+        // Hermitian extension: t < Hz reads the half row, t >= Hz the conjugate of Nz - t
+        const int kk = t < Hz ? t : Nz - t;
+        const bool cj = t >= Hz;
+        const bool realonly = (kk == 0) || (even && kk == Nz / 2);
+        R kzd = R(0);
+        if (zo.mulkz[f] && !(even && kk == Nz / 2)) kzd = kfac<R>(g, 2) * kk;
+        C h0 = src[(int64_t)r0 * Hz + kk];
+        C h1 = r1 < rows ? src[(int64_t)r1 * Hz + kk] : CT<R>::mk(R(0), R(0));
+        if (zo.mulkz[f]) {  // -i kz' h
+            h0 = CT<R>::mk(kzd * h0.y, -kzd * h0.x);
+            h1 = CT<R>::mk(kzd * h1.y, -kzd * h1.x);
+        }
+        if (realonly) { h0.y = R(0); h1.y = R(0); }
+        if (cj) { h0.y = -h0.y; h1.y = -h1.y; }
+        a[line * Nz + t] = CT<R>::mk(h0.x - h1.y, h0.y + h1.x);  // h0 + i h1
+    }
+    __syncthreads();
+    C* res = stockham<R>(a, b, nlines, Nz, 1, rz, tw, R(1), false);
+    for (int i = threadIdx.x; i < nlines * Nz; i += blockDim.x) {
+        const int line = i / Nz, t = i - line * Nz;
+        const int f = line / np, p = line - f * np;
+        const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
+        R* out = reinterpret_cast<R*>(zo.out[f]);
+        const C z = res[line * Nz + t];
+        out[(int64_t)r0 * Nz + t] = z.x;
+        if (r1 < rows) out[(int64_t)r1 * Nz + t] = z.y;
+    }
+}
+
+template <typename T>
+cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw, int nf,
+                             const typename Cx<T>::t* const* src, const int* mulkz, T* const* out) {
+    ZOut zo;
+    zo.nf = nf;
+    for (int f = 0; f < 3; ++f) {
+        zo.src[f] = f < nf ? src[f] : nullptr;
+        zo.out[f] = f < nf ? out[f] : nullptr;
+        zo.mulkz[f] = f < nf ? mulkz[f] : 0;
+    }
+    const int rows = g.N[0] * g.N[1];
+    int pairs = (int)((48 * 1024) / (2 * nf * g.N[2] * sizeof(typename Cx<T>::t)));
+    pairs = pairs < 1 ? 1 : (pairs > 8 ? 8 : pairs);
+    const int npairs = (rows + 1) / 2;
+    size_t smem = 2ull * nf * pairs * g.N[2] * sizeof(typename Cx<T>::t);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_z_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fft_z_c2r<T><<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, rz, tw, zo, rows, pairs);
+    return cudaGetLastError();
+}
+
+#define PPPM_INST_FFT(T)                                                                                           \
+    template cudaError_t launch_fft_z_r2c<T>(cudaStream_t, const Geo&, const Radix&, const Cx<T>::t*, const T*,    \
+                                             Cx<T>::t*);                                                           \
+    template cudaError_t launch_fft_bundle<T>(cudaStream_t, const Geo&, int, int, const Radix&, const Bundle&,     \
+                                              const Cx<T>::t*, Cx<T>::t*);                                         \
+    template cudaError_t launch_fft_x_influence<T>(cudaStream_t, const Geo&, const Radix&, const Bundle&,          \
+                                                   const Cx<T>::t*, const T*, double, double, double, Cx<T>::t*,   \
+                                                   Cx<T>::t*, T*, unsigned int*, double, double*, double*);        \
+    template cudaError_t launch_fft_y_inverse3<T>(cudaStream_t, const Geo&, const Radix&, const Bundle&,           \
+                                                  const Cx<T>::t*, Cx<T>::t*, Cx<T>::t*, Cx<T>::t*);               \
+    template cudaError_t launch_fft_z_c2r<T>(cudaStream_t, const Geo&, const Radix&, const Cx<T>::t*, int,         \
+                                             const Cx<T>::t* const*, const int*, T* const*);
+PPPM_INST_FFT(float)
+PPPM_INST_FFT(double)
+
+}  // namespace pppm

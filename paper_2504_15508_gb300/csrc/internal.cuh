@@ -1,0 +1,113 @@
+// Internal declarations shared by the CUDA translation units of the PPPM
+// library: element types, the geometry block passed to kernels by value, the
+// FFT radix plan, and the host-side launchers each .cu file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pppm.h"
+
+namespace pppm {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { typedef float2 t; };
+template <> struct Cx<double> { typedef double2 t; };
+
+// Sorted per-site record: x0 of the three axes (the B-spline argument, see
+// bspline.cuh) and the charge.
+template <typename T> struct __align__(4 * sizeof(T)) Rec { T x0[3]; T q; };
+
+constexpr int kMaxOrder = 7;
+constexpr int kMaxRadixStages = 16;
+constexpr int kSortCap = 1024;       // sites per tile sorted by index in the spread
+constexpr int kMaxMesh = 2048;
+
+// Radix plan of one FFT length: L = prod(r[0..n-1]), each r in {2, 3, 4, 5, 8}.
+struct Radix {
+    int L;
+    int n;
+    int r[kMaxRadixStages];
+};
+
+// Geometry of one box, passed to every kernel by value.
+struct Geo {
+    int N[3];        // mesh points per axis
+    int Hz;          // Nz/2 + 1, complex points along z of the half spectrum
+    float s_hi[3];   // N/L as a double-float pair (FP32 site location)
+    float s_lo[3];
+    double s[3];     // N/L in double
+    double L[3];     // box edges
+    float kfac_f[3]; // 2 pi / L, wavevector per index step
+    double kfac_d[3];
+    int order;       // B-spline order p
+    int kmin;        // offset of the first stencil point from the base point
+    int T;           // tile edge in cells (same on every axis, clamped to N per axis)
+    int Tt[3];       // tile edge per axis after clamping
+    int nt[3];       // tiles per axis
+    int ntiles;
+    int E[3];        // patch extent per axis = Tt + p - 1
+    int Pz;          // padded z pitch of the spread patch in shared memory
+};
+
+template <typename R> __host__ __device__ __forceinline__ R kfac(const Geo& g, int d);
+template <> __host__ __device__ __forceinline__ float kfac<float>(const Geo& g, int d) { return g.kfac_f[d]; }
+template <> __host__ __device__ __forceinline__ double kfac<double>(const Geo& g, int d) { return g.kfac_d[d]; }
+
+// Bundle shape of a strided-line FFT pass (lines along y or x, B adjacent kz
+// columns per block).
+struct Bundle {
+    int B;           // lines per block
+    int nb;          // bundles per outer index = ceil(Hz / B)
+};
+
+// ------------------------------------------------------------------ launchers
+// site_kernels.cu
+template <typename T, typename In>
+cudaError_t launch_bin(cudaStream_t s, const Geo& g, const In* pos, const In* q, int n, int* tile_count,
+                       int* tile_of, int* slot_of, Rec<T>* rec, int* cell, int* status);
+cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int* start);
+template <typename T>
+cudaError_t launch_scatter(cudaStream_t s, int n, const int* tile_of, const int* slot_of, const int* tile_start,
+                           const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell, int* sorig);
+template <typename T>
+cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+                          const int* scell, const int* sorig, T* patch);
+template <typename T>
+cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
+                        T scale, T* rho);
+template <typename T, typename Out>
+cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+                          const int* scell, const int* sorig, const T* fields, double prefactor, Out* forces);
+void upload_bspline_coefficients();
+
+// fft_kernels.cu
+template <typename T>
+cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw,
+                             const T* in, typename Cx<T>::t* out);
+template <typename T>
+cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, const Radix& r, const Bundle& bd,
+                              const typename Cx<T>::t* tw, typename Cx<T>::t* data);
+template <typename T>
+cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx, const Bundle& bd,
+                                   const typename Cx<T>::t* tw, const T* G, double beta, double e_scale,
+                                   double c_field, typename Cx<T>::t* S, typename Cx<T>::t* Bx, T* partial,
+                                   unsigned int* counter, double prefactor, double* energy, double* virial);
+template <typename T>
+cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry, const Bundle& bd,
+                                  const typename Cx<T>::t* tw, typename Cx<T>::t* A, typename Cx<T>::t* Bx,
+                                  typename Cx<T>::t* D);
+// nf fields: out[f] = C2R_z(src[f] * (mulkz[f] ? -i kz' : 1)); src/out arrays of nf pointers
+template <typename T>
+cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw, int nf,
+                             const typename Cx<T>::t* const* src, const int* mulkz, T* const* out);
+int x_influence_blocks(const Geo& g, const Bundle& bd);
+
+// influence.cu
+cudaError_t launch_influence(cudaStream_t s, const Geo& g, double beta, int alias, double* G);
+template <typename T>
+cudaError_t launch_convert(cudaStream_t s, const double* in, T* out, int64_t n);
+template <typename T>
+cudaError_t launch_twiddles(cudaStream_t s, int L, typename Cx<T>::t* tw);
+
+}  // namespace pppm

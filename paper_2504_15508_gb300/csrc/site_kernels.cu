@@ -1,0 +1,467 @@
+// Per-site kernels of the PPPM path: binning and sort of the sites by mesh
+// tile, the atomics-free charge spread, the fold of the tile patches into the
+// mesh, and the force interpolation (gather).
+//
+// Charge assignment and force interpolation use the same order-p B-spline
+// stencil (bspline.cuh); the spread is the transpose of the gather.
+#include <climits>
+
+#include "bspline.cuh"
+#include "internal.cuh"
+
+namespace pppm {
+
+// Piece coefficients of N_p on [0, 1] for p = 1..7, from the Cox-de Boor
+// recursion carried out on polynomials in x0 (FP64 on the host).
+void upload_bspline_coefficients() {
+    static bool done = false;
+    if (done) return;
+    double cd[kMaxOrder + 1][kMaxOrder][kMaxOrder] = {};
+    float cf[kMaxOrder + 1][kMaxOrder][kMaxOrder] = {};
+    // piece j of N_m as a polynomial in x0: poly[j][k] = coefficient of x0^k, for t = x0 + j.
+    double poly[kMaxOrder][kMaxOrder] = {};
+    poly[0][0] = 1.0;  // N_1(x0) = 1 on [0, 1]
+    for (int p = 1; p <= kMaxOrder; ++p) {
+        if (p > 1) {
+            double nxt[kMaxOrder][kMaxOrder] = {};
+            for (int j = 0; j < p; ++j) {
+                // N_p(x0 + j) = ((x0 + j) N_{p-1}(x0 + j) + (p - x0 - j) N_{p-1}(x0 + j - 1)) / (p - 1)
+                for (int k = 0; k < p - 1; ++k) {
+                    double a = (j < p - 1) ? poly[j][k] : 0.0;      // N_{p-1}(x0 + j)
+                    double b = (j >= 1) ? poly[j - 1][k] : 0.0;     // N_{p-1}(x0 + j - 1)
+                    nxt[j][k + 1] += a - b;                          // x0 * (a - b)
+                    nxt[j][k] += j * a + (p - j) * b;
+                }
+                for (int k = 0; k < p; ++k) nxt[j][k] /= (p - 1);
+            }
+            for (int j = 0; j < kMaxOrder; ++j)
+                for (int k = 0; k < kMaxOrder; ++k) poly[j][k] = nxt[j][k];
+        }
+        for (int j = 0; j < p; ++j)
+            for (int k = 0; k < p; ++k) {
+                cd[p][j][k] = poly[j][k];
+                cf[p][j][k] = (float)poly[j][k];
+            }
+    }
+    cudaMemcpyToSymbol(c_bsp_d, cd, sizeof(cd));
+    cudaMemcpyToSymbol(c_bsp_f, cf, sizeof(cf));
+    done = true;
+}
+
+// ------------------------------------------------------------------ binning
+
+// Locate one coordinate in FP32 from a float position: u = x N / L with N/L held
+// as a double-float pair (the product is then accurate to ~1e-12 cells, where a
+// plain FP32 product would be off by ~1e-5 cells at 129 A), base point g and
+// B-spline argument x0 (see bspline.cuh).  Returns false for a non-finite or
+// absurdly distant coordinate, which is then placed at the origin.
+__device__ __forceinline__ bool locate(float x, float s_hi, float s_lo, double /*s*/, int N, bool odd, int& g,
+                                       float& x0) {
+    float u = x * s_hi;
+    float e = fmaf(x, s_hi, -u);
+    float ul = fmaf(x, s_lo, e);
+    bool ok = fabsf(u) < 4.0e6f;
+    if (!ok) { u = 0.f; ul = 0.f; }
+    float gf = odd ? floorf(u + 0.5f) : floorf(u);
+    float d = (u - gf) + ul;
+    if (odd) {
+        if (d >= 0.5f) { gf += 1.f; d -= 1.f; } else if (d < -0.5f) { gf -= 1.f; d += 1.f; }
+        x0 = 0.5f - d;
+    } else {
+        if (d >= 1.f) { gf += 1.f; d -= 1.f; } else if (d < 0.f) { gf -= 1.f; d += 1.f; }
+        x0 = 1.f - d;
+    }
+    int gi = (int)gf % N;
+    g = gi < 0 ? gi + N : gi;
+    return ok;
+}
+
+// FP64 location (FP64 plans, and FP32 plans fed double positions).
+template <typename T>
+__device__ __forceinline__ bool locate(double x, float, float, double s, int N, bool odd, int& g, T& x0) {
+    double u = x * s;
+    bool ok = fabs(u) < 1.0e12;
+    if (!ok) u = 0.0;
+    double gd = odd ? floor(u + 0.5) : floor(u);
+    double d = u - gd;
+    x0 = (T)(odd ? 0.5 - d : 1.0 - d);
+    long long gi = (long long)gd % N;
+    g = (int)(gi < 0 ? gi + N : gi);
+    return ok;
+}
+
+template <typename T, typename In>
+__global__ void k_bin(Geo g, const In* __restrict__ pos, const In* __restrict__ q, int n,
+                      int* __restrict__ tile_count, int* __restrict__ tile_of, int* __restrict__ slot_of,
+                      Rec<T>* __restrict__ rec, int* __restrict__ cell, int* __restrict__ status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool odd = (g.order & 1) != 0;
+    Rec<T> r;
+    int gc[3];
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        T x0;
+        if constexpr (sizeof(T) == 4 && sizeof(In) == 4) {
+            float xf;
+            ok &= locate((float)pos[3 * i + d], g.s_hi[d], g.s_lo[d], g.s[d], g.N[d], odd, gc[d], xf);
+            x0 = xf;
+        } else {
+            ok &= locate<T>((double)pos[3 * i + d], 0.f, 0.f, g.s[d], g.N[d], odd, gc[d], x0);
+        }
+        r.x0[d] = x0;
+    }
+    T qi = (T)q[i];
+    if (!isfinite((double)qi)) { ok = false; qi = (T)0; }
+    r.q = qi;
+    if (!ok) atomicOr(status, 1);
+    int tx = gc[0] / g.T, ty = gc[1] / g.T, tz = gc[2] / g.T;
+    int t = (tx * g.nt[1] + ty) * g.nt[2] + tz;
+    int lx = gc[0] - tx * g.T, ly = gc[1] - ty * g.T, lz = gc[2] - tz * g.T;
+    tile_of[i] = t;
+    slot_of[i] = atomicAdd(&tile_count[t], 1);
+    rec[i] = r;
+    cell[i] = lx | (ly << 8) | (lz << 16);
+}
+
+template <typename T, typename In>
+cudaError_t launch_bin(cudaStream_t s, const Geo& g, const In* pos, const In* q, int n, int* tile_count,
+                       int* tile_of, int* slot_of, Rec<T>* rec, int* cell, int* status) {
+    if (n == 0) return cudaSuccess;
+    k_bin<T, In><<<(n + 255) / 256, 256, 0, s>>>(g, pos, q, n, tile_count, tile_of, slot_of, rec, cell, status);
+    return cudaGetLastError();
+}
+
+// Exclusive scan of the per-tile counts by one block: start[0..ntiles].
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, int ntiles, int* __restrict__ start) {
+    __shared__ int part[1024];
+    const int tid = threadIdx.x;
+    const int chunk = (ntiles + 1023) / 1024;
+    const int b = tid * chunk, e = min(b + chunk, ntiles);
+    int sum = 0;
+    for (int i = b; i < e; ++i) sum += count[i];
+    part[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int v = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int run = part[tid] - sum;
+    for (int i = b; i < e; ++i) {
+        start[i] = run;
+        run += count[i];
+    }
+    if (tid == 1023) start[ntiles] = part[1023];
+}
+
+cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int* start) {
+    k_scan<<<1, 1024, 0, s>>>(count, ntiles, start);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_scatter(int n, const int* __restrict__ tile_of, const int* __restrict__ slot_of,
+                          const int* __restrict__ tile_start, const Rec<T>* __restrict__ rec,
+                          const int* __restrict__ cell, Rec<T>* __restrict__ srec, int* __restrict__ scell,
+                          int* __restrict__ sorig) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int dst = tile_start[tile_of[i]] + slot_of[i];
+    srec[dst] = rec[i];
+    scell[dst] = cell[i];
+    sorig[dst] = i;
+}
+
+template <typename T>
+cudaError_t launch_scatter(cudaStream_t s, int n, const int* tile_of, const int* slot_of, const int* tile_start,
+                           const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell, int* sorig) {
+    if (n == 0) return cudaSuccess;
+    k_scatter<T><<<(n + 255) / 256, 256, 0, s>>>(n, tile_of, slot_of, tile_start, rec, cell, srec, scell, sorig);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ spread
+//
+// One warp per tile of T^3 cells.  The warp accumulates the p^3 contributions
+// of every site whose base point lies in the tile into a private shared-memory
+// patch covering the tile plus the stencil halo, one site after another, in
+// the order of the sites' original indices (so the result does not depend on
+// the order the binning produced).  Lane (iy, iz) adds the p values along x of
+// its stencil row (orders 6 and 7 give a lane two rows); no two lanes touch
+// the same point, and consecutive sites are separated by __syncwarp, so no
+// atomics are needed.  The patch is then
+// written to global scratch; k_fold sums overlapping patches.
+constexpr int kSpreadWarps = 4;
+constexpr int kSpreadCap = 512;
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kSpreadWarps * 32)
+k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
+         const int* __restrict__ scell, const int* __restrict__ sorig, T* __restrict__ patch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * kSpreadWarps + warp;
+    const int Ex = g.E[0], Ey = g.E[1], Ez = g.E[2], Pz = g.Pz;
+    const int plane = Ey * Pz;
+    const int psize = Ex * plane;
+    T* pt = reinterpret_cast<T*>(smem_raw) + warp * psize;
+    int2* keys = reinterpret_cast<int2*>(reinterpret_cast<T*>(smem_raw) + kSpreadWarps * psize) + warp * kSpreadCap;
+    if (tile >= g.ntiles) return;  // whole warp; no block-level barrier below
+
+    for (int i = lane; i < psize; i += 32) pt[i] = T(0);
+    const int s0 = tile_start[tile];
+    const int c = tile_start[tile + 1] - s0;
+    const bool sorted = c > 1 && c <= kSpreadCap;
+    if (sorted) {
+        int cp = 2;
+        while (cp < c) cp <<= 1;
+        for (int i = lane; i < cp; i += 32) keys[i] = i < c ? make_int2(sorig[s0 + i], s0 + i) : make_int2(INT_MAX, -1);
+        __syncwarp();
+        for (int k = 2; k <= cp; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < cp; i += 32) {
+                    int ixj = i ^ j;
+                    if (ixj > i) {
+                        int2 a = keys[i], b = keys[ixj];
+                        bool up = (i & k) == 0;
+                        if ((a.x > b.x) == up) { keys[i] = b; keys[ixj] = a; }
+                    }
+                }
+                __syncwarp();
+            }
+    }
+    __syncwarp();
+
+    // lane -> stencil rows (iy, iz); orders above 5 have more rows than lanes
+    constexpr int NR = (P * P + 31) / 32;
+    BspCoef<T, P> cx;
+    cx.load();
+    BspPiece<T, P> py[NR], pz[NR];
+    int roff[NR];
+    bool ract[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const int row = lane + 32 * j;
+        ract[j] = row < P * P;
+        const int iy = ract[j] ? row / P : 0, iz = ract[j] ? row % P : 0;
+        py[j].load(iy);
+        pz[j].load(iz);
+        roff[j] = iy * Pz + iz;
+    }
+    for (int t = 0; t < c; ++t) {
+        const int s = sorted ? keys[t].y : s0 + t;
+        const Rec<T> r = srec[s];
+        const int cl = scell[s];
+        const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+        T wx[P];
+        cx.all(r.x0[0], wx);
+        T* base0 = pt + lx * plane + ly * Pz + lz;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const T wyz = py[j].eval(r.x0[1]) * pz[j].eval(r.x0[2]) * r.q;
+            if (ract[j]) {
+                T* base = base0 + roff[j];
+#pragma unroll
+                for (int a = 0; a < P; ++a) base[a * plane] += wx[a] * wyz;
+            }
+        }
+        __syncwarp();
+    }
+    T* dst = patch + (size_t)tile * (Ex * Ey * Ez);
+    const int eyz = Ey * Ez;
+    for (int i = lane; i < Ex * eyz; i += 32) {
+        int x = i / eyz, rem = i - x * eyz, y = rem / Ez, z = rem - y * Ez;
+        dst[i] = pt[x * plane + y * Pz + z];
+    }
+}
+
+template <typename T, int P>
+static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+                            const int* scell, const int* sorig, T* patch) {
+    const int psize = g.E[0] * g.E[1] * g.Pz;
+    size_t smem = (size_t)kSpreadWarps * psize * sizeof(T) + (size_t)kSpreadWarps * kSpreadCap * sizeof(int2);
+    cudaError_t e = cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
+    k_spread<T, P><<<blocks, kSpreadWarps * 32, smem, s>>>(g, tile_start, srec, scell, sorig, patch);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+                          const int* scell, const int* sorig, T* patch) {
+    switch (g.order) {
+        case 2: return spread_p<T, 2>(s, g, tile_start, srec, scell, sorig, patch);
+        case 3: return spread_p<T, 3>(s, g, tile_start, srec, scell, sorig, patch);
+        case 4: return spread_p<T, 4>(s, g, tile_start, srec, scell, sorig, patch);
+        case 5: return spread_p<T, 5>(s, g, tile_start, srec, scell, sorig, patch);
+        case 6: return spread_p<T, 6>(s, g, tile_start, srec, scell, sorig, patch);
+        case 7: return spread_p<T, 7>(s, g, tile_start, srec, scell, sorig, patch);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ fold
+//
+// Each mesh point sums, in a fixed order, the patch entries that cover it.
+// cov_off/cov_ent hold per axis the list of (tile index, patch coordinate)
+// pairs covering each mesh index (CSR, built on the host with the periodic
+// wrap); the three axes' lists are concatenated, axis d starting at
+// cov_off[d * (Nmax + 1)] with Nmax = max N.
+template <typename T>
+__global__ void k_fold(Geo g, const T* __restrict__ patch, const int* __restrict__ cov_off,
+                       const int2* __restrict__ cov_ent, int nmax1, T scale, T* __restrict__ rho) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    if (idx >= total) return;
+    const int z = (int)(idx % g.N[2]);
+    const int y = (int)((idx / g.N[2]) % g.N[1]);
+    const int x = (int)(idx / ((int64_t)g.N[1] * g.N[2]));
+    const int* ox = cov_off;
+    const int* oy = cov_off + nmax1;
+    const int* oz = cov_off + 2 * nmax1;
+    const int psz = g.E[0] * g.E[1] * g.E[2];
+    T sum = T(0);
+    for (int a = ox[x]; a < ox[x + 1]; ++a) {
+        const int2 ex = cov_ent[a];
+        for (int b = oy[y]; b < oy[y + 1]; ++b) {
+            const int2 ey = cov_ent[b];
+            for (int c = oz[z]; c < oz[z + 1]; ++c) {
+                const int2 ez = cov_ent[c];
+                const int tile = (ex.x * g.nt[1] + ey.x) * g.nt[2] + ez.x;
+                sum += patch[(size_t)tile * psz + (ex.y * g.E[1] + ey.y) * g.E[2] + ez.y];
+            }
+        }
+    }
+    rho[idx] = sum * scale;
+}
+
+template <typename T>
+cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
+                        T scale, T* rho) {
+    int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    int nmax1 = 1 + (g.N[0] > g.N[1] ? (g.N[0] > g.N[2] ? g.N[0] : g.N[2]) : (g.N[1] > g.N[2] ? g.N[1] : g.N[2]));
+    k_fold<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, patch, cov_off, cov_ent, nmax1, scale, rho);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ gather
+//
+// One block per tile.  The three field meshes over the tile plus its stencil
+// halo are staged in shared memory (periodic wrap applied while loading);
+// then each thread interpolates one site: F = prefactor * q * sum W W W E.
+constexpr int kGatherThreads = 64;
+
+template <typename T, int P, typename Out>
+__global__ void __launch_bounds__(kGatherThreads)
+k_gather(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
+         const int* __restrict__ scell, const int* __restrict__ sorig, const T* __restrict__ fields,
+         double prefactor, Out* __restrict__ forces) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tile = blockIdx.x;
+    const int s0 = tile_start[tile], s1 = tile_start[tile + 1];
+    if (s0 == s1) return;  // uniform across the block
+    const int Ex = g.E[0], Ey = g.E[1], Ez = g.E[2];
+    const int psz = Ex * Ey * Ez;
+    T* fx = reinterpret_cast<T*>(smem_raw);
+    T* fy = fx + psz;
+    T* fz = fy + psz;
+    const int tx = tile / (g.nt[1] * g.nt[2]);
+    const int ty = (tile / g.nt[2]) % g.nt[1];
+    const int tz = tile % g.nt[2];
+    const int ox = tx * g.T + g.kmin, oy = ty * g.T + g.kmin, oz = tz * g.T + g.kmin;
+    const int64_t N3 = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    const int eyz = Ey * Ez;
+    for (int i = threadIdx.x; i < psz; i += blockDim.x) {
+        int cx = i / eyz, rem = i - cx * eyz, cy = rem / Ez, cz = rem - cy * Ez;
+        int mx = (ox + cx) % g.N[0]; mx += mx < 0 ? g.N[0] : 0;
+        int my = (oy + cy) % g.N[1]; my += my < 0 ? g.N[1] : 0;
+        int mz = (oz + cz) % g.N[2]; mz += mz < 0 ? g.N[2] : 0;
+        const int64_t f = ((int64_t)mx * g.N[1] + my) * g.N[2] + mz;
+        fx[i] = fields[f];
+        fy[i] = fields[N3 + f];
+        fz[i] = fields[2 * N3 + f];
+    }
+    __syncthreads();
+    BspCoef<T, P> co;
+    co.load();
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const Rec<T> r = srec[s];
+        const int cl = scell[s];
+        const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+        T wx[P], wy[P], wz[P];
+        co.all(r.x0[0], wx);
+        co.all(r.x0[1], wy);
+        co.all(r.x0[2], wz);
+        T ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const T wab = wx[a] * wy[b];
+                const int base = ((lx + a) * Ey + (ly + b)) * Ez + lz;
+#pragma unroll
+                for (int c = 0; c < P; ++c) {
+                    const T w = wab * wz[c];
+                    ax += w * fx[base + c];
+                    ay += w * fy[base + c];
+                    az += w * fz[base + c];
+                }
+            }
+        }
+        const T sc = (T)prefactor * r.q;
+        const int o = sorig[s];
+        forces[3 * (int64_t)o] = (Out)(sc * ax);
+        forces[3 * (int64_t)o + 1] = (Out)(sc * ay);
+        forces[3 * (int64_t)o + 2] = (Out)(sc * az);
+    }
+}
+
+template <typename T, int P, typename Out>
+static cudaError_t gather_p(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+                            const int* scell, const int* sorig, const T* fields, double prefactor, Out* forces) {
+    size_t smem = 3ull * g.E[0] * g.E[1] * g.E[2] * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_gather<T, P, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gather<T, P, Out><<<g.ntiles, kGatherThreads, smem, s>>>(g, tile_start, srec, scell, sorig, fields, prefactor,
+                                                               forces);
+    return cudaGetLastError();
+}
+
+template <typename T, typename Out>
+cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+                          const int* scell, const int* sorig, const T* fields, double prefactor, Out* forces) {
+    switch (g.order) {
+        case 2: return gather_p<T, 2, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
+        case 3: return gather_p<T, 3, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
+        case 4: return gather_p<T, 4, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
+        case 5: return gather_p<T, 5, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
+        case 6: return gather_p<T, 6, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
+        case 7: return gather_p<T, 7, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ instantiations
+#define PPPM_INST_T(T)                                                                                          \
+    template cudaError_t launch_scatter<T>(cudaStream_t, int, const int*, const int*, const int*, const Rec<T>*, \
+                                           const int*, Rec<T>*, int*, int*);                                     \
+    template cudaError_t launch_spread<T>(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*,       \
+                                          const int*, T*);                                                       \
+    template cudaError_t launch_fold<T>(cudaStream_t, const Geo&, const T*, const int*, const int2*, T, T*);
+PPPM_INST_T(float)
+PPPM_INST_T(double)
+#define PPPM_INST_TI(T, I)                                                                                       \
+    template cudaError_t launch_bin<T, I>(cudaStream_t, const Geo&, const I*, const I*, int, int*, int*, int*,   \
+                                          Rec<T>*, int*, int*);                                                   \
+    template cudaError_t launch_gather<T, I>(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*,     \
+                                             const int*, const T*, double, I*);
+PPPM_INST_TI(float, float)
+PPPM_INST_TI(float, double)
+PPPM_INST_TI(double, float)
+PPPM_INST_TI(double, double)
+
+}  // namespace pppm

@@ -1,0 +1,177 @@
+"""Python API over the C ABI: a PPPM plan operating on torch device tensors.
+
+PyTorch provides device memory and streams only; the arithmetic runs in the
+CUDA library (``libpppm.so``).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """PPPM (Poisson-ik) for the Gaussian-charge energy E_Gt of DPLR in one
+    orthorhombic box.
+
+    box: 3 edge lengths (Angstrom); mesh: 3 mesh sizes (2^a 3^b 5^c);
+    order: B-spline order p; beta: splitting parameter (1/Angstrom);
+    precision: "fp32" or "fp64".
+    """
+
+    def __init__(self, box, mesh, order: int = 5, beta: float = 0.4, precision: str = "fp32",
+                 prefactor: float = 1.0, alias: int = 2, tile: int = 0):
+        L = N.lib()
+        self._lib = L
+        self.box = tuple(float(b) for b in np.broadcast_to(np.asarray(box, float), (3,)))
+        self.mesh = tuple(int(m) for m in np.broadcast_to(np.asarray(mesh), (3,)))
+        self.order = int(order)
+        self.beta = float(beta)
+        self.precision = precision
+        prec = {"fp32": N.PPPM_FP32, "fp64": N.PPPM_FP64}[precision]
+        self.real_dtype = torch.float32 if prec == N.PPPM_FP32 else torch.float64
+        b = (ctypes.c_double * 3)(*self.box)
+        m = (ctypes.c_int * 3)(*self.mesh)
+        h = ctypes.c_void_p()
+        N.check(L.pppm_create(b, m, self.order, self.beta, prec, ctypes.byref(h)), "pppm_create")
+        self._h = h
+        opt = N.Options()
+        N.check(L.pppm_default_options(ctypes.byref(opt)))
+        opt.prefactor, opt.alias, opt.tile = float(prefactor), int(alias), int(tile)
+        N.check(L.pppm_set_options(self._h, ctypes.byref(opt)), "pppm_set_options")
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pppm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_options(self, prefactor=None, alias=None, tile=None):
+        opt = N.Options()
+        N.check(self._lib.pppm_get_options(self._h, ctypes.byref(opt)))
+        if prefactor is not None:
+            opt.prefactor = float(prefactor)
+        if alias is not None:
+            opt.alias = int(alias)
+        if tile is not None:
+            opt.tile = int(tile)
+        N.check(self._lib.pppm_set_options(self._h, ctypes.byref(opt)), "pppm_set_options")
+
+    def reserve(self, n: int):
+        N.check(self._lib.pppm_reserve(self._h, int(n)), "pppm_reserve")
+
+    def profile(self, on: bool = True):
+        N.check(self._lib.pppm_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last read (synchronizes)."""
+        ms = (ctypes.c_double * 32)()
+        calls = (ctypes.c_int64 * 32)()
+        k = self._lib.pppm_profile_read(self._h, ms, calls, 32)
+        if k < 0:
+            N.check(k, "pppm_profile_read")
+        return {self._lib.pppm_profile_name(i).decode(): (ms[i], calls[i]) for i in range(k)}
+
+    def status(self) -> int:
+        return self._lib.pppm_status(self._h)
+
+    # ------------------------------------------------------------ compute
+    @staticmethod
+    def _check_sites(pos, q):
+        if pos.dim() != 2 or pos.shape[1] != 3 or q.dim() != 1 or q.shape[0] != pos.shape[0]:
+            raise ValueError("pos must be (n, 3) and q (n,)")
+        if not (pos.is_cuda and q.is_cuda and pos.is_contiguous() and q.is_contiguous()):
+            raise ValueError("pos and q must be contiguous CUDA tensors")
+        if pos.dtype != q.dtype or pos.dtype not in (torch.float32, torch.float64):
+            raise ValueError("pos and q must both be float32 or both float64")
+
+    def compute(self, pos: torch.Tensor, q: torch.Tensor, out=None, stream=None):
+        """Energy (1,), forces (n, 3) and virial (6,) as device tensors.
+        float32 inputs use pppm_compute_f32, float64 pppm_compute."""
+        self._check_sites(pos, q)
+        n = pos.shape[0]
+        if out is None:
+            energy = torch.empty(1, dtype=torch.float64, device=pos.device)
+            forces = torch.empty((n, 3), dtype=pos.dtype, device=pos.device)
+            virial = torch.empty(6, dtype=torch.float64, device=pos.device)
+        else:
+            energy, forces, virial = out
+        fn = self._lib.pppm_compute_f32 if pos.dtype == torch.float32 else self._lib.pppm_compute
+        N.check(fn(self._h, _stream(stream), _ptr(pos), _ptr(q), n, _ptr(energy), _ptr(forces), _ptr(virial)),
+                "pppm_compute")
+        return energy, forces, virial
+
+    def compute_host(self, pos: np.ndarray, q: np.ndarray):
+        """The same evaluation from host numpy arrays (copies inside the call)."""
+        pos = np.ascontiguousarray(pos)
+        q = np.ascontiguousarray(q, dtype=pos.dtype)
+        n = pos.shape[0]
+        energy = np.zeros(1)
+        virial = np.zeros(6)
+        forces = np.zeros((n, 3), dtype=pos.dtype)
+        fn = self._lib.pppm_compute_host_f32 if pos.dtype == np.float32 else self._lib.pppm_compute_host
+        rc = fn(self._h, pos.ctypes.data, q.ctypes.data, n, energy.ctypes.data, forces.ctypes.data,
+                virial.ctypes.data)
+        N.check(rc, "pppm_compute_host")
+        return float(energy[0]), forces, virial
+
+    # ------------------------------------------------------------ stages
+    def spread(self, pos: torch.Tensor, q: torch.Tensor, stream=None) -> torch.Tensor:
+        """Charge density on the mesh (plan precision), from float64 sites."""
+        pos = pos.to(torch.float64).contiguous()
+        q = q.to(torch.float64).contiguous()
+        rho = torch.empty(self.mesh, dtype=self.real_dtype, device=pos.device)
+        N.check(self._lib.pppm_spread(self._h, _stream(stream), _ptr(pos), _ptr(q), pos.shape[0], _ptr(rho)),
+                "pppm_spread")
+        return rho
+
+    def fft_r2c(self, real: torch.Tensor, stream=None) -> torch.Tensor:
+        assert real.dtype == self.real_dtype and tuple(real.shape) == self.mesh and real.is_contiguous()
+        hz = self.mesh[2] // 2 + 1
+        out = torch.empty((self.mesh[0], self.mesh[1], hz, 2), dtype=self.real_dtype, device=real.device)
+        N.check(self._lib.pppm_fft_r2c(self._h, _stream(stream), _ptr(real), _ptr(out)), "pppm_fft_r2c")
+        return torch.view_as_complex(out)
+
+    def fft_c2r(self, spec: torch.Tensor, stream=None) -> torch.Tensor:
+        spec = torch.view_as_real(spec.contiguous()).contiguous()
+        assert spec.dtype == self.real_dtype
+        out = torch.empty(self.mesh, dtype=self.real_dtype, device=spec.device)
+        N.check(self._lib.pppm_fft_c2r(self._h, _stream(stream), _ptr(spec), _ptr(out)), "pppm_fft_c2r")
+        return out
+
+    def influence(self, device="cuda") -> torch.Tensor:
+        hz = self.mesh[2] // 2 + 1
+        G = torch.empty((self.mesh[0], self.mesh[1], hz), dtype=torch.float64, device=device)
+        N.check(self._lib.pppm_influence(self._h, _ptr(G)), "pppm_influence")
+        return G
+
+    def fields(self, pos: torch.Tensor, q: torch.Tensor, stream=None) -> torch.Tensor:
+        pos = pos.to(torch.float64).contiguous()
+        q = q.to(torch.float64).contiguous()
+        f = torch.empty((3,) + self.mesh, dtype=self.real_dtype, device=pos.device)
+        N.check(self._lib.pppm_fields(self._h, _stream(stream), _ptr(pos), _ptr(q), pos.shape[0], _ptr(f)),
+                "pppm_fields")
+        return f

@@ -19,3 +19,12 @@ def cuda_device():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="session")
+def pppm_lib():
+    """Build (if stale) and load the CUDA library."""
+    from paper_2504_15508_gb300.build import build
+    build()
+    from paper_2504_15508_gb300 import _native
+    return _native.lib()
