@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--profile-steps", type=int, default=200)
+    ap.add_argument("--frames", type=int, default=N_FRAMES, help="random-walk frames held on the device")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -242,9 +243,10 @@ def run_ours(args):
     gen = torch.Generator(device=dev)
     gen.manual_seed(NOISE_SEED_1000_STEPS)
     base = torch.tensor(wb.pos, dtype=torch.float64, device=dev)
-    frames = torch.empty((N_FRAMES, n, 3), dtype=torch.float32, device=dev)
+    nf = max(1, min(args.frames, N_FRAMES))
+    frames = torch.empty((nf, n, 3), dtype=torch.float32, device=dev)
     cur = base.clone()
-    for k in range(N_FRAMES):
+    for k in range(nf):
         if k > 0:
             cur += NOISE_SIGMA_1000_STEPS * torch.randn(cur.shape, generator=gen, dtype=torch.float64, device=dev)
         frames[k] = cur.float()
@@ -261,7 +263,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(k):
-        plan.compute(frames[k % N_FRAMES], q, out=out, stream=stream)
+        plan.compute(frames[k % nf], q, out=out, stream=stream)
 
     for k in range(args.warmup):
         flush.fill_(float(k))
@@ -321,7 +323,7 @@ def run_ours(args):
     ms_per_step = total_ms / K
 
     # end to end through the host-pointer C ABI call (copies inside the timed region)
-    E = min(args.e2e_steps, N_FRAMES)
+    E = min(args.e2e_steps, nf)
     host_frames = frames[:E].cpu().pin_memory()
     host_q = q.cpu().pin_memory()
     hq = host_q.numpy()

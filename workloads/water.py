@@ -138,7 +138,7 @@ def smooth_at_least(x: float) -> int:
 # ----------------------------------------------------------------- workloads
 # Sizes of the paper's water systems: 64 waters in a ~12.4 A box (a small
 # variant of the 128-water Table 1 box), 4,096 waters, and 72,192 waters =
-# the 216,576-atom system of the 4,608-node weak-scaling point (Section 5.4).
+# the 216,576-atom system of the 4,608-node weak-scaling point (Section 4.4).
 
 WORKLOADS = {
     "water64": dict(n_mol=64, L=12.42, mesh=(32, 32, 32), order=5, beta=0.4, seed=1),
