@@ -148,6 +148,31 @@ int pppm_influence(pppm_plan *plan, double *G);
 int pppm_fields(pppm_plan *plan, void *stream, const double *pos, const double *q, int64_t n, void *fields);
 
 /*
+ * pppm_spread_noalloc -- the charge spread of pppm_spread (FP32 arithmetic,
+ * float density rho, same layout and scaling) for callers that cannot
+ * allocate device memory: code running inside a host callback or an allocator
+ * hook, in a process whose device memory is owned by another framework's
+ * pool, or in a plugin that must not grow its footprint at run time.  The
+ * paper has no counterpart; this is a deployment convenience.
+ *   box, mesh, order  as in pppm_create (host arrays); no plan is needed
+ *   stream            cudaStream_t as void*
+ *   pos, q            n x 3 positions and n charges, double, device
+ *   rho               Nx x Ny x Nz floats, device, written
+ * It calls no cudaMalloc/cudaFree: its scratch is one file-scope device array
+ * of 32 MiB that every GPU loading this library holds until the process exits.
+ * Inputs needing more scratch than that (about 52 B per site plus
+ * 4 B x (T+p-1)^3 per tile of T^3 mesh cells, T = 8 or 4) return
+ * PPPM_ERR_TOO_LARGE.  All calls share the array and it keeps the last call's
+ * contents (the per-tile counters are cleared by each call); calls whose work
+ * overlaps on the GPU (other streams or threads) race on it and must be
+ * serialized.  The first call on a device looks up the array's device address
+ * and uploads the B-spline coefficients, so make it before any stream
+ * capture.  Non-finite positions are placed at the origin without a status.
+ */
+int pppm_spread_noalloc(const double box[3], const int mesh[3], int order, void *stream,
+                        const double *pos, const double *q, int64_t n, float *rho);
+
+/*
  * Per-kernel timing (for benchmarks).  While enabled, every kernel launch of a
  * compute call is bracketed by CUDA events on the compute stream.
  * pppm_profile_read synchronizes, writes for each kernel slot i < cap the

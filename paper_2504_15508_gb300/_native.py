@@ -64,6 +64,7 @@ SIGNATURES = {
     "pppm_fft_c2r": (cint, [vp, vp, vp, vp]),
     "pppm_influence": (cint, [vp, vp]),
     "pppm_fields": (cint, [vp, vp, vp, vp, i64, vp]),
+    "pppm_spread_noalloc": (cint, [ctypes.POINTER(dbl), ctypes.POINTER(cint), cint, vp, vp, vp, i64, vp]),
     "pppm_profile_enable": (cint, [vp, cint]),
     "pppm_profile_read": (cint, [vp, vp, vp, cint]),
     "pppm_profile_name": (ctypes.c_char_p, [cint]),
