@@ -95,6 +95,9 @@ int pppm_get_options(const pppm_plan *plan, pppm_options *opt);
 int pppm_reserve(pppm_plan *plan, int64_t n);
 void pppm_destroy(pppm_plan *plan);
 const char *pppm_strerror(int code);
+/* Text of the last CUDA failure behind a PPPM_ERR_CUDA on the calling thread
+ * (static thread-local buffer, "" if none). */
+const char *pppm_last_error(void);
 /* Read and clear the device status word (synchronizes the plan's last stream). */
 int pppm_status(pppm_plan *plan);
 

@@ -30,6 +30,8 @@ class PPPMError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
         msg = strerror(code) if _lib is not None else str(code)
+        if code == PPPM_ERR_CUDA and _lib is not None:
+            msg += ": " + _lib.pppm_last_error().decode()
         super().__init__(f"{what}: {msg} (code {code})" if what else f"{msg} (code {code})")
 
 
@@ -54,6 +56,7 @@ SIGNATURES = {
     "pppm_reserve": (cint, [vp, i64]),
     "pppm_destroy": (None, [vp]),
     "pppm_strerror": (ctypes.c_char_p, [cint]),
+    "pppm_last_error": (ctypes.c_char_p, []),
     "pppm_status": (cint, [vp]),
     "pppm_compute": (cint, [vp, vp, vp, vp, i64, vp, vp, vp]),
     "pppm_compute_f32": (cint, [vp, vp, vp, vp, i64, vp, vp, vp]),

@@ -134,10 +134,19 @@ Radix make_radix(int L) {
     return r;
 }
 
-#define CK(x)                                         \
-    do {                                              \
-        cudaError_t e_ = (x);                         \
-        if (e_ != cudaSuccess) return PPPM_ERR_CUDA;  \
+// Text of the last CUDA failure seen by this library on the calling thread.
+thread_local char g_last_error[256] = "";
+
+int record_cuda_error(cudaError_t e, const char* what, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at api.cu:%d in %s", cudaGetErrorString(e),
+             cudaGetErrorName(e), line, what);
+    return PPPM_ERR_CUDA;
+}
+
+#define CK(x)                                                               \
+    do {                                                                    \
+        cudaError_t e_ = (x);                                               \
+        if (e_ != cudaSuccess) return record_cuda_error(e_, #x, __LINE__);  \
     } while (0)
 
 template <typename P>
@@ -371,6 +380,8 @@ int pppm_default_options(pppm_options* opt) {
     opt->tile = 0;
     return PPPM_OK;
 }
+
+const char* pppm_last_error(void) { return g_last_error; }
 
 const char* pppm_strerror(int code) {
     switch (code) {

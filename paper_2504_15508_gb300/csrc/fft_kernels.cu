@@ -16,6 +16,13 @@
 //   z inverse   Hermitian half rows of two rows (or two fields) packed as a + i b.
 // Twiddles come from a table of e^{-2 pi i t / L} built on the device in FP64
 // with sincospi and rounded to the mesh precision.
+//
+// Two FFT engines drive the same kernels: CtEngine<L> for the FP32 mesh sizes
+// the workloads use (every index and radix is a compile-time constant), and
+// GenEngine for any other 2^a 3^b 5^c length and for FP64 (radix plan read at
+// run time).
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace pppm {
@@ -130,32 +137,157 @@ __device__ typename CT<R>::C* stockham(typename CT<R>::C* a, typename CT<R>::C* 
     return src;
 }
 
+
 constexpr int kFftThreads = 256;
 
-// ------------------------------------------------------------------ z forward (R2C)
+// ------------------------------------------------------------------ compile-time radix plan
+constexpr int fft_radix(int L, int s) {
+    int m = L, i = 0;
+    const int fs[4] = {4, 2, 3, 5};
+    for (int q = 0; q < 4; ++q)
+        while (m % fs[q] == 0) {
+            if (i == s) return fs[q];
+            m /= fs[q];
+            ++i;
+        }
+    return 1;
+}
+constexpr int fft_nstages(int L) {
+    int n = 0;
+    while (fft_radix(L, n) != 1) ++n;
+    return n;
+}
+constexpr int fft_ns(int L, int s) {
+    int ns = 1;
+    for (int i = 0; i < s; ++i) ns *= fft_radix(L, i);
+    return ns;
+}
+
+// One Stockham stage with every size a constant.  Thread mapping: line-fast
+// (bundles, lines adjacent in shared memory) uses 16 lanes per line index and
+// blockDim/16 along the butterflies; otherwise 32 lanes walk the butterflies
+// of one line.
+template <typename R, int L, int S, int SIGN, bool LF>
+__device__ __forceinline__ void ct_stage(const typename CT<R>::C* __restrict__ src, typename CT<R>::C* __restrict__ dst,
+                                         int nl, int ls, int ps, const typename CT<R>::C* __restrict__ tw) {
+    typedef typename CT<R>::C C;
+    constexpr int RDX = fft_radix(L, S);
+    constexpr int NS = fft_ns(L, S);
+    constexpr int NBF = L / RDX;
+    constexpr int TSTEP = L / (NS * RDX);
+    int tl, nlt, tj, njt;
+    if (LF) { tl = threadIdx.x & 15; nlt = 16; tj = threadIdx.x >> 4; njt = blockDim.x >> 4; }
+    else { tj = threadIdx.x & 31; njt = 32; tl = threadIdx.x >> 5; nlt = blockDim.x >> 5; }
+    for (int line = tl; line < nl; line += nlt) {
+        const C* sp = src + line * ls;
+        C* dp = dst + line * ls;
+        for (int j = tj; j < NBF; j += njt) {
+            const int k = j % NS;
+            C v[5];
+#pragma unroll
+            for (int r = 0; r < RDX; ++r) v[r] = sp[(j + r * NBF) * ps];
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < RDX; ++r) {
+                    C w = __ldg(&tw[k * r * TSTEP]);
+                    if (SIGN > 0) w.y = -w.y;
+                    v[r] = cmul(v[r], w);
+                }
+            }
+            butterfly<C, R>(v, RDX, R(SIGN));
+            const int d0 = (j / NS) * NS * RDX + k;
+#pragma unroll
+            for (int r = 0; r < RDX; ++r) dp[(d0 + r * NS) * ps] = v[r];
+        }
+    }
+}
+
+template <typename R, int L, int SIGN, bool LF, int S>
+__device__ __forceinline__ typename CT<R>::C* ct_fft(typename CT<R>::C* a, typename CT<R>::C* b, int nl, int ls,
+                                                     int ps, const typename CT<R>::C* __restrict__ tw) {
+    if constexpr (S == fft_nstages(L)) {
+        return a;
+    } else {
+        ct_stage<R, L, S, SIGN, LF>(a, b, nl, ls, ps, tw);
+        __syncthreads();
+        return ct_fft<R, L, SIGN, LF, S + 1>(b, a, nl, ls, ps, tw);
+    }
+}
+
+template <typename R, int L>
+struct CtEngine {
+    typedef typename CT<R>::C C;
+    const C* tw;
+    __device__ __forceinline__ static constexpr int len() { return L; }
+    template <int SIGN, bool LF>
+    __device__ __forceinline__ C* run(C* a, C* b, int nl, int ls, int ps) const {
+        return ct_fft<R, L, SIGN, LF, 0>(a, b, nl, ls, ps, tw);
+    }
+};
+
 template <typename R>
+struct GenEngine {
+    typedef typename CT<R>::C C;
+    Radix rp;
+    const C* tw;
+    __device__ __forceinline__ int len() const { return rp.L; }
+    template <int SIGN, bool LF>
+    __device__ __forceinline__ C* run(C* a, C* b, int nl, int ls, int ps) const {
+        return stockham<R>(a, b, nl, ls, ps, rp, tw, R(SIGN), LF);
+    }
+};
+
+// Runs f(engine) with the compile-time engine when one exists for (T, L).
+template <typename T, typename F>
+cudaError_t with_engine(const Radix& r, const typename Cx<T>::t* tw, F&& f) {
+    if constexpr (std::is_same<T, float>::value) {
+        switch (r.L) {
+            case 32: return f(CtEngine<float, 32>{tw});
+            case 64: return f(CtEngine<float, 64>{tw});
+            case 128: return f(CtEngine<float, 128>{tw});
+            case 160: return f(CtEngine<float, 160>{tw});
+            default: break;
+        }
+    }
+    return f(GenEngine<T>{r, tw});
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t smem) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// 2D loop helpers for the bundle kernels: rows of the line (t) by 16-lane groups,
+// lines (l) by lane within the group.
+#define BUNDLE_LOOP(t, l, L_, nl_)                                              \
+    for (int t = threadIdx.x >> 4; t < (L_); t += blockDim.x >> 4)              \
+        for (int l = threadIdx.x & 15; l < (nl_); l += 16)
+// line-major loops for the z passes: lines by warp, points by lane
+#define LINE_LOOP(line, t, nlines_, len_)                                       \
+    for (int line = threadIdx.x >> 5; line < (nlines_); line += blockDim.x >> 5) \
+        for (int t = threadIdx.x & 31; t < (len_); t += 32)
+
+// ------------------------------------------------------------------ z forward (R2C)
+template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_z_r2c(Geo g, Radix rz, const typename CT<R>::C* __restrict__ tw, const R* __restrict__ in,
-            typename CT<R>::C* __restrict__ out, int rows, int pairs) {
+k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restrict__ out, int rows, int pairs) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Nz = g.N[2], Hz = g.Hz;
+    const int Nz = eng.len(), Hz = g.Hz;
     C* a = reinterpret_cast<C*>(smem_raw);
     C* b = a + pairs * Nz;
     const int pair0 = blockIdx.x * pairs;
     const int npairs_total = (rows + 1) / 2;
     const int np = min(pairs, npairs_total - pair0);
-    for (int i = threadIdx.x; i < np * Nz; i += blockDim.x) {
-        const int p = i / Nz, t = i - p * Nz;
+    LINE_LOOP(p, t, np, Nz) {
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
         const R va = in[(int64_t)r0 * Nz + t];
         const R vb = r1 < rows ? in[(int64_t)r1 * Nz + t] : R(0);
         a[p * Nz + t] = CT<R>::mk(va, vb);
     }
     __syncthreads();
-    C* res = stockham<R>(a, b, np, Nz, 1, rz, tw, R(-1), false);
-    for (int i = threadIdx.x; i < np * Hz; i += blockDim.x) {
-        const int p = i / Hz, k = i - p * Hz;
+    C* res = eng.template run<-1, false>(a, b, np, Nz, 1);
+    LINE_LOOP(p, k, np, Hz) {
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
         const C z = res[p * Nz + k];
         const C zc = cconj(res[p * Nz + (k == 0 ? 0 : Nz - k)]);
@@ -173,23 +305,25 @@ cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, cons
     int pairs = (int)((32 * 1024) / (2 * g.N[2] * sizeof(typename Cx<T>::t)));
     pairs = pairs < 1 ? 1 : (pairs > 16 ? 16 : pairs);
     const int npairs = (rows + 1) / 2;
-    size_t smem = 2ull * pairs * g.N[2] * sizeof(typename Cx<T>::t);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_z_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_fft_z_r2c<T><<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, rz, tw, in, out, rows, pairs);
-    return cudaGetLastError();
+    const size_t smem = 2ull * pairs * g.N[2] * sizeof(typename Cx<T>::t);
+    return with_engine<T>(rz, tw, [&](auto eng) {
+        auto kern = k_fft_z_r2c<T, decltype(eng)>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, eng, in, out, rows, pairs);
+        return cudaGetLastError();
+    });
 }
 
 // ------------------------------------------------------------------ strided-line C2C
 // axis 1: lines along y (outer index x); axis 0: lines along x (outer index y).
-template <typename R>
+template <typename R, typename Eng, int SIGN>
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_bundle(Geo g, int axis, R sgn, Radix rp, Bundle bd, const typename CT<R>::C* __restrict__ tw,
-             typename CT<R>::C* __restrict__ data) {
+k_fft_bundle(Geo g, int axis, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ data) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Hz = g.Hz, L = rp.L, B = bd.B;
-    const int outer = blockIdx.x / bd.nb, bi = blockIdx.x % bd.nb;
+    const int Hz = g.Hz, L = eng.len(), B = bd.B;
+    const int outer = blockIdx.x / bd.nb, bi = blockIdx.x - outer * bd.nb;
     const int kz0 = bi * B;
     const int nl = min(B, Hz - kz0);
     const int64_t es = axis == 1 ? (int64_t)Hz : (int64_t)g.N[1] * Hz;
@@ -197,27 +331,24 @@ k_fft_bundle(Geo g, int axis, R sgn, Radix rp, Bundle bd, const typename CT<R>::
     C* a = reinterpret_cast<C*>(smem_raw);
     C* b = a + L * B;
     C* base = data + outer * os + kz0;
-    for (int i = threadIdx.x; i < L * nl; i += blockDim.x) {
-        const int t = i / nl, l = i - t * nl;
-        a[t * B + l] = base[t * es + l];
-    }
+    BUNDLE_LOOP(t, l, L, nl) a[t * B + l] = base[t * es + l];
     __syncthreads();
-    C* res = stockham<R>(a, b, nl, 1, B, rp, tw, sgn, true);
-    for (int i = threadIdx.x; i < L * nl; i += blockDim.x) {
-        const int t = i / nl, l = i - t * nl;
-        base[t * es + l] = res[t * B + l];
-    }
+    C* res = eng.template run<SIGN, true>(a, b, nl, 1, B);
+    BUNDLE_LOOP(t, l, L, nl) base[t * es + l] = res[t * B + l];
 }
 
 template <typename T>
 cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, const Radix& r, const Bundle& bd,
                               const typename Cx<T>::t* tw, typename Cx<T>::t* data) {
     const int outer = axis == 1 ? g.N[0] : g.N[1];
-    size_t smem = 2ull * r.L * bd.B * sizeof(typename Cx<T>::t);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_bundle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_fft_bundle<T><<<outer * bd.nb, kFftThreads, smem, s>>>(g, axis, (T)sign, r, bd, tw, data);
-    return cudaGetLastError();
+    const size_t smem = 2ull * r.L * bd.B * sizeof(typename Cx<T>::t);
+    return with_engine<T>(r, tw, [&](auto eng) {
+        auto kern = sign < 0 ? k_fft_bundle<T, decltype(eng), -1> : k_fft_bundle<T, decltype(eng), 1>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<outer * bd.nb, kFftThreads, smem, s>>>(g, axis, bd, eng, data);
+        return cudaGetLastError();
+    });
 }
 
 // ------------------------------------------------------------------ x + influence
@@ -229,7 +360,8 @@ cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, 
 //      thread with compensated (TwoSum) sums, reduced per block;
 //   3. P = G rho_hat / (N h^3) and -i kx' P (kx' = 0 on the Nyquist index);
 //   4. inverse FFT along x of both; P -> S (in place), -i kx' P -> Bx.
-// The last block to finish sums the per-block partials in FP64 in block order.
+// The last block to finish sums the per-block partials (TwoSum in the mesh
+// precision, hi + lo in FP64 at the end) in a fixed order.
 //
 // Half-spectrum weights: w = 1 on the kz = 0 plane (and kz = Nz/2 for even Nz),
 // 2 elsewhere, standing for the mirror mode -k.  For the off-diagonal virial a
@@ -255,19 +387,18 @@ __device__ __forceinline__ void two_sum_pair(R& h, R& l, R h2, R l2) {
     l = l + l2 + err;
 }
 
-template <typename R>
+template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_x_influence(Geo g, Radix rx, Bundle bd, const typename CT<R>::C* __restrict__ tw, const R* __restrict__ G,
-                  R beta, R e_scale, R c_field, typename CT<R>::C* __restrict__ S,
-                  typename CT<R>::C* __restrict__ Bx, R* __restrict__ partial,
+k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R e_scale, R c_field,
+                  typename CT<R>::C* __restrict__ S, typename CT<R>::C* __restrict__ Bx, R* __restrict__ partial,
                   unsigned int* __restrict__ counter, double prefactor, double* __restrict__ energy,
                   double* __restrict__ virial) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ R red[kFftThreads / 32][14];
     __shared__ bool is_last;
-    const int Nx = g.N[0], Ny = g.N[1], Nz = g.N[2], Hz = g.Hz, B = bd.B;
-    const int y = blockIdx.x / bd.nb, bi = blockIdx.x % bd.nb;
+    const int Nx = eng.len(), Ny = g.N[1], Nz = g.N[2], Hz = g.Hz, B = bd.B;
+    const int y = blockIdx.x / bd.nb, bi = blockIdx.x - y * bd.nb;
     const int kz0 = bi * B;
     const int nl = min(B, Hz - kz0);
     const int64_t es = (int64_t)Ny * Hz;
@@ -276,12 +407,9 @@ k_fft_x_influence(Geo g, Radix rx, Bundle bd, const typename CT<R>::C* __restric
     C* b0 = a1 + Nx * B;
     C* b1 = b0 + Nx * B;
     C* base = S + (int64_t)y * Hz + kz0;
-    for (int i = threadIdx.x; i < Nx * nl; i += blockDim.x) {
-        const int t = i / nl, l = i - t * nl;
-        a0[t * B + l] = base[t * es + l];
-    }
+    BUNDLE_LOOP(t, l, Nx, nl) a0[t * B + l] = base[t * es + l];
     __syncthreads();
-    C* rh = stockham<R>(a0, a1, nl, 1, B, rx, tw, R(-1), true);
+    C* rh = eng.template run<-1, true>(a0, a1, nl, 1, B);
     C* pbuf = (rh == a0) ? a1 : a0;  // free partner of the result buffer
 
     const int my = y <= Ny / 2 ? y : y - Ny;
@@ -291,8 +419,7 @@ k_fft_x_influence(Geo g, Radix rx, Bundle bd, const typename CT<R>::C* __restric
     R acc_hi[7], acc_lo[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) { acc_hi[q] = R(0); acc_lo[q] = R(0); }
-    for (int i = threadIdx.x; i < Nx * nl; i += blockDim.x) {
-        const int t = i / nl, l = i - t * nl;
+    BUNDLE_LOOP(t, l, Nx, nl) {
         const int kz = kz0 + l;
         const int mx = t <= Nx / 2 ? t : t - Nx;
         const R kx = kfac<R>(g, 0) * mx;
@@ -323,11 +450,10 @@ k_fft_x_influence(Geo g, Radix rx, Bundle bd, const typename CT<R>::C* __restric
         b0[t * B + l] = CT<R>::mk(kxd * P.y, -kxd * P.x);  // -i kx' P
     }
     __syncthreads();
-    C* rA = stockham<R>(pbuf, rh, nl, 1, B, rx, tw, R(1), true);
-    C* rB = stockham<R>(b0, b1, nl, 1, B, rx, tw, R(1), true);
+    C* rA = eng.template run<1, true>(pbuf, rh, nl, 1, B);
+    C* rB = eng.template run<1, true>(b0, b1, nl, 1, B);
     C* obx = Bx + (int64_t)y * Hz + kz0;
-    for (int i = threadIdx.x; i < Nx * nl; i += blockDim.x) {
-        const int t = i / nl, l = i - t * nl;
+    BUNDLE_LOOP(t, l, Nx, nl) {
         base[t * es + l] = rA[t * B + l];
         obx[t * es + l] = rB[t * B + l];
     }
@@ -365,7 +491,8 @@ k_fft_x_influence(Geo g, Radix rx, Bundle bd, const typename CT<R>::C* __restric
             const int q = warp;
             R h = R(0), lo = R(0);
             for (unsigned int b = lane; b < gridDim.x; b += 32) {
-                two_sum_pair(h, lo, __ldcg(&partial[(int64_t)b * 14 + 2 * q]), __ldcg(&partial[(int64_t)b * 14 + 2 * q + 1]));
+                two_sum_pair(h, lo, __ldcg(&partial[(int64_t)b * 14 + 2 * q]),
+                             __ldcg(&partial[(int64_t)b * 14 + 2 * q + 1]));
             }
             for (int off = 16; off > 0; off >>= 1) {
                 const R h2 = __shfl_down_sync(0xffffffffu, h, off);
@@ -389,33 +516,33 @@ cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx
                                    const typename Cx<T>::t* tw, const T* G, double beta, double e_scale,
                                    double c_field, typename Cx<T>::t* S, typename Cx<T>::t* Bx, T* partial,
                                    unsigned int* counter, double prefactor, double* energy, double* virial) {
-    size_t smem = 4ull * g.N[0] * bd.B * sizeof(typename Cx<T>::t);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_fft_x_influence<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_fft_x_influence<T><<<x_influence_blocks(g, bd), kFftThreads, smem, s>>>(
-        g, rx, bd, tw, G, (T)beta, (T)e_scale, (T)c_field, S, Bx, partial, counter, prefactor, energy, virial);
-    return cudaGetLastError();
+    const size_t smem = 4ull * g.N[0] * bd.B * sizeof(typename Cx<T>::t);
+    return with_engine<T>(rx, tw, [&](auto eng) {
+        auto kern = k_fft_x_influence<T, decltype(eng)>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<x_influence_blocks(g, bd), kFftThreads, smem, s>>>(g, bd, eng, G, (T)beta, (T)e_scale, (T)c_field, S,
+                                                                 Bx, partial, counter, prefactor, energy, virial);
+        return cudaGetLastError();
+    });
 }
 
 // ------------------------------------------------------------------ y inverse, three outputs
 // C = IFFT_y(A), D = IFFT_y(-i ky' A), Ex' = IFFT_y(Bx); C overwrites A, Ex' overwrites Bx.
-template <typename R>
+template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_y_inverse3(Geo g, Radix ry, Bundle bd, const typename CT<R>::C* __restrict__ tw,
-                 typename CT<R>::C* __restrict__ A, typename CT<R>::C* __restrict__ Bx,
+k_fft_y_inverse3(Geo g, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ A, typename CT<R>::C* __restrict__ Bx,
                  typename CT<R>::C* __restrict__ D) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Ny = g.N[1], Hz = g.Hz, B = bd.B;
-    const int x = blockIdx.x / bd.nb, bi = blockIdx.x % bd.nb;
+    const int Ny = eng.len(), Hz = g.Hz, B = bd.B;
+    const int x = blockIdx.x / bd.nb, bi = blockIdx.x - x * bd.nb;
     const int kz0 = bi * B;
     const int nl = min(B, Hz - kz0);
     const int64_t off = (int64_t)x * Ny * Hz + kz0;
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int sz = Ny * B;
-    for (int i = threadIdx.x; i < Ny * nl; i += blockDim.x) {
-        const int t = i / nl, l = i - t * nl;
+    BUNDLE_LOOP(t, l, Ny, nl) {
         const C va = A[off + (int64_t)t * Hz + l];
         const int my = t <= Ny / 2 ? t : t - Ny;
         const R kyd = ((Ny % 2 == 0) && (t == Ny / 2)) ? R(0) : kfac<R>(g, 1) * my;
@@ -424,11 +551,10 @@ k_fft_y_inverse3(Geo g, Radix ry, Bundle bd, const typename CT<R>::C* __restrict
         buf[4 * sz + t * B + l] = Bx[off + (int64_t)t * Hz + l];
     }
     __syncthreads();
-    C* rC = stockham<R>(buf, buf + sz, nl, 1, B, ry, tw, R(1), true);
-    C* rD = stockham<R>(buf + 2 * sz, buf + 3 * sz, nl, 1, B, ry, tw, R(1), true);
-    C* rE = stockham<R>(buf + 4 * sz, buf + 5 * sz, nl, 1, B, ry, tw, R(1), true);
-    for (int i = threadIdx.x; i < Ny * nl; i += blockDim.x) {
-        const int t = i / nl, l = i - t * nl;
+    C* rC = eng.template run<1, true>(buf, buf + sz, nl, 1, B);
+    C* rD = eng.template run<1, true>(buf + 2 * sz, buf + 3 * sz, nl, 1, B);
+    C* rE = eng.template run<1, true>(buf + 4 * sz, buf + 5 * sz, nl, 1, B);
+    BUNDLE_LOOP(t, l, Ny, nl) {
         A[off + (int64_t)t * Hz + l] = rC[t * B + l];
         D[off + (int64_t)t * Hz + l] = rD[t * B + l];
         Bx[off + (int64_t)t * Hz + l] = rE[t * B + l];
@@ -439,11 +565,14 @@ template <typename T>
 cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry, const Bundle& bd,
                                   const typename Cx<T>::t* tw, typename Cx<T>::t* A, typename Cx<T>::t* Bx,
                                   typename Cx<T>::t* D) {
-    size_t smem = 6ull * g.N[1] * bd.B * sizeof(typename Cx<T>::t);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_y_inverse3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_fft_y_inverse3<T><<<g.N[0] * bd.nb, kFftThreads, smem, s>>>(g, ry, bd, tw, A, Bx, D);
-    return cudaGetLastError();
+    const size_t smem = 6ull * g.N[1] * bd.B * sizeof(typename Cx<T>::t);
+    return with_engine<T>(ry, tw, [&](auto eng) {
+        auto kern = k_fft_y_inverse3<T, decltype(eng)>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<g.N[0] * bd.nb, kFftThreads, smem, s>>>(g, bd, eng, A, Bx, D);
+        return cudaGetLastError();
+    });
 }
 
 // ------------------------------------------------------------------ z inverse (C2R)
@@ -454,12 +583,12 @@ struct ZOut {
     int nf;
 };
 
-template <typename R>
+template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_z_c2r(Geo g, Radix rz, const typename CT<R>::C* __restrict__ tw, ZOut zo, int rows, int pairs) {
+k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Nz = g.N[2], Hz = g.Hz;
+    const int Nz = eng.len(), Hz = g.Hz;
     const int nf = zo.nf;
     C* a = reinterpret_cast<C*>(smem_raw);
     C* b = a + nf * pairs * Nz;
@@ -468,8 +597,7 @@ k_fft_z_c2r(Geo g, Radix rz, const typename CT<R>::C* __restrict__ tw, ZOut zo, 
     const int np = min(pairs, npairs_total - pair0);
     const int nlines = nf * np;
     const bool even = (Nz % 2) == 0;
-    for (int i = threadIdx.x; i < nlines * Nz; i += blockDim.x) {
-        const int line = i / Nz, t = i - line * Nz;
+    LINE_LOOP(line, t, nlines, Nz) {
         const int f = line / np, p = line - f * np;
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
         const C* src = reinterpret_cast<const C*>(zo.src[f]);
@@ -490,9 +618,8 @@ k_fft_z_c2r(Geo g, Radix rz, const typename CT<R>::C* __restrict__ tw, ZOut zo, 
         a[line * Nz + t] = CT<R>::mk(h0.x - h1.y, h0.y + h1.x);  // h0 + i h1
     }
     __syncthreads();
-    C* res = stockham<R>(a, b, nlines, Nz, 1, rz, tw, R(1), false);
-    for (int i = threadIdx.x; i < nlines * Nz; i += blockDim.x) {
-        const int line = i / Nz, t = i - line * Nz;
+    C* res = eng.template run<1, false>(a, b, nlines, Nz, 1);
+    LINE_LOOP(line, t, nlines, Nz) {
         const int f = line / np, p = line - f * np;
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
         R* out = reinterpret_cast<R*>(zo.out[f]);
@@ -516,11 +643,14 @@ cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, cons
     int pairs = (int)((48 * 1024) / (2 * nf * g.N[2] * sizeof(typename Cx<T>::t)));
     pairs = pairs < 1 ? 1 : (pairs > 8 ? 8 : pairs);
     const int npairs = (rows + 1) / 2;
-    size_t smem = 2ull * nf * pairs * g.N[2] * sizeof(typename Cx<T>::t);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_z_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_fft_z_c2r<T><<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, rz, tw, zo, rows, pairs);
-    return cudaGetLastError();
+    const size_t smem = 2ull * nf * pairs * g.N[2] * sizeof(typename Cx<T>::t);
+    return with_engine<T>(rz, tw, [&](auto eng) {
+        auto kern = k_fft_z_c2r<T, decltype(eng)>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, eng, zo, rows, pairs);
+        return cudaGetLastError();
+    });
 }
 
 #define PPPM_INST_FFT(T)                                                                                           \

@@ -94,35 +94,50 @@ template <typename T, typename In>
 __global__ void k_bin(Geo g, const In* __restrict__ pos, const In* __restrict__ q, int n,
                       int* __restrict__ tile_count, int* __restrict__ tile_of, int* __restrict__ slot_of,
                       Rec<T>* __restrict__ rec, int* __restrict__ cell, int* __restrict__ status) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const bool odd = (g.order & 1) != 0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    const int lane = threadIdx.x & 31;
+    int t = -1 - lane, lx = 0, ly = 0, lz = 0;
     Rec<T> r;
-    int gc[3];
-    bool ok = true;
+    if (valid) {
+        const bool odd = (g.order & 1) != 0;
+        int gc[3];
+        bool ok = true;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        T x0;
-        if constexpr (sizeof(T) == 4 && sizeof(In) == 4) {
-            float xf;
-            ok &= locate((float)pos[3 * i + d], g.s_hi[d], g.s_lo[d], g.s[d], g.N[d], odd, gc[d], xf);
-            x0 = xf;
-        } else {
-            ok &= locate<T>((double)pos[3 * i + d], 0.f, 0.f, g.s[d], g.N[d], odd, gc[d], x0);
+        for (int d = 0; d < 3; ++d) {
+            T x0;
+            if constexpr (sizeof(T) == 4 && sizeof(In) == 4) {
+                float xf;
+                ok &= locate((float)pos[3 * i + d], g.s_hi[d], g.s_lo[d], g.s[d], g.N[d], odd, gc[d], xf);
+                x0 = xf;
+            } else {
+                ok &= locate<T>((double)pos[3 * i + d], 0.f, 0.f, g.s[d], g.N[d], odd, gc[d], x0);
+            }
+            r.x0[d] = x0;
         }
-        r.x0[d] = x0;
+        T qi = (T)q[i];
+        if (!isfinite((double)qi)) { ok = false; qi = (T)0; }
+        r.q = qi;
+        if (!ok) atomicOr(status, 1);
+        const int tx = gc[0] / g.T, ty = gc[1] / g.T, tz = gc[2] / g.T;
+        t = (tx * g.nt[1] + ty) * g.nt[2] + tz;
+        lx = gc[0] - tx * g.T;
+        ly = gc[1] - ty * g.T;
+        lz = gc[2] - tz * g.T;
     }
-    T qi = (T)q[i];
-    if (!isfinite((double)qi)) { ok = false; qi = (T)0; }
-    r.q = qi;
-    if (!ok) atomicOr(status, 1);
-    int tx = gc[0] / g.T, ty = gc[1] / g.T, tz = gc[2] / g.T;
-    int t = (tx * g.nt[1] + ty) * g.nt[2] + tz;
-    int lx = gc[0] - tx * g.T, ly = gc[1] - ty * g.T, lz = gc[2] - tz * g.T;
-    tile_of[i] = t;
-    slot_of[i] = atomicAdd(&tile_count[t], 1);
-    rec[i] = r;
-    cell[i] = lx | (ly << 8) | (lz << 16);
+    // one atomic per distinct tile in the warp; lanes of a tile get consecutive slots
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (valid && lane == leader) base = atomicAdd(&tile_count[t], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) {
+        tile_of[i] = t;
+        slot_of[i] = base + rank;
+        rec[i] = r;
+        cell[i] = lx | (ly << 8) | (lz << 16);
+    }
 }
 
 template <typename T, typename In>
@@ -290,9 +305,39 @@ static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int* tile_start,
     return cudaGetLastError();
 }
 
+template <typename T, int P, int TILE>
+static cudaError_t spread_fast(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*, const int*, T*);
+template <typename T, int P, int TILE, typename Out>
+static cudaError_t gather_fast(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*, const int*, const T*,
+                               double, Out*);
+
+// The fast kernels need full tiles on every axis and a tile edge of 4 or 8.
+static bool fast_tiles(const Geo& g) {
+    return (g.T == 4 || g.T == 8) && g.Tt[0] == g.T && g.Tt[1] == g.T && g.Tt[2] == g.T;
+}
+
+#define PPPM_FAST_SWITCH(FN, T_, ...)                                                             \
+    switch (g.order * 16 + g.T) {                                                                 \
+        case 2 * 16 + 4: return FN<T_, 2, 4>(__VA_ARGS__);                                        \
+        case 2 * 16 + 8: return FN<T_, 2, 8>(__VA_ARGS__);                                        \
+        case 3 * 16 + 4: return FN<T_, 3, 4>(__VA_ARGS__);                                        \
+        case 3 * 16 + 8: return FN<T_, 3, 8>(__VA_ARGS__);                                        \
+        case 4 * 16 + 4: return FN<T_, 4, 4>(__VA_ARGS__);                                        \
+        case 4 * 16 + 8: return FN<T_, 4, 8>(__VA_ARGS__);                                        \
+        case 5 * 16 + 4: return FN<T_, 5, 4>(__VA_ARGS__);                                        \
+        case 5 * 16 + 8: return FN<T_, 5, 8>(__VA_ARGS__);                                        \
+        case 6 * 16 + 4: return FN<T_, 6, 4>(__VA_ARGS__);                                        \
+        case 6 * 16 + 8: return FN<T_, 6, 8>(__VA_ARGS__);                                        \
+        case 7 * 16 + 4: return FN<T_, 7, 4>(__VA_ARGS__);                                        \
+        case 7 * 16 + 8: return FN<T_, 7, 8>(__VA_ARGS__);                                        \
+    }
+
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
                           const int* scell, const int* sorig, T* patch) {
+    if (fast_tiles(g)) {
+        PPPM_FAST_SWITCH(spread_fast, T, s, g, tile_start, srec, scell, sorig, patch)
+    }
     switch (g.order) {
         case 2: return spread_p<T, 2>(s, g, tile_start, srec, scell, sorig, patch);
         case 3: return spread_p<T, 3>(s, g, tile_start, srec, scell, sorig, patch);
@@ -337,15 +382,6 @@ __global__ void k_fold(Geo g, const T* __restrict__ patch, const int* __restrict
         }
     }
     rho[idx] = sum * scale;
-}
-
-template <typename T>
-cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
-                        T scale, T* rho) {
-    int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2];
-    int nmax1 = 1 + (g.N[0] > g.N[1] ? (g.N[0] > g.N[2] ? g.N[0] : g.N[2]) : (g.N[1] > g.N[2] ? g.N[1] : g.N[2]));
-    k_fold<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, patch, cov_off, cov_ent, nmax1, scale, rho);
-    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ gather
@@ -431,9 +467,28 @@ static cudaError_t gather_p(cudaStream_t s, const Geo& g, const int* tile_start,
     return cudaGetLastError();
 }
 
+#define PPPM_FAST_SWITCH_G(T_, O_, ...)                                                           \
+    switch (g.order * 16 + g.T) {                                                                 \
+        case 2 * 16 + 4: return gather_fast<T_, 2, 4, O_>(__VA_ARGS__);                           \
+        case 2 * 16 + 8: return gather_fast<T_, 2, 8, O_>(__VA_ARGS__);                           \
+        case 3 * 16 + 4: return gather_fast<T_, 3, 4, O_>(__VA_ARGS__);                           \
+        case 3 * 16 + 8: return gather_fast<T_, 3, 8, O_>(__VA_ARGS__);                           \
+        case 4 * 16 + 4: return gather_fast<T_, 4, 4, O_>(__VA_ARGS__);                           \
+        case 4 * 16 + 8: return gather_fast<T_, 4, 8, O_>(__VA_ARGS__);                           \
+        case 5 * 16 + 4: return gather_fast<T_, 5, 4, O_>(__VA_ARGS__);                           \
+        case 5 * 16 + 8: return gather_fast<T_, 5, 8, O_>(__VA_ARGS__);                           \
+        case 6 * 16 + 4: return gather_fast<T_, 6, 4, O_>(__VA_ARGS__);                           \
+        case 6 * 16 + 8: return gather_fast<T_, 6, 8, O_>(__VA_ARGS__);                           \
+        case 7 * 16 + 4: return gather_fast<T_, 7, 4, O_>(__VA_ARGS__);                           \
+        case 7 * 16 + 8: return gather_fast<T_, 7, 8, O_>(__VA_ARGS__);                           \
+    }
+
 template <typename T, typename Out>
 cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
                           const int* scell, const int* sorig, const T* fields, double prefactor, Out* forces) {
+    if (fast_tiles(g)) {
+        PPPM_FAST_SWITCH_G(T, Out, s, g, tile_start, srec, scell, sorig, fields, prefactor, forces)
+    }
     switch (g.order) {
         case 2: return gather_p<T, 2, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
         case 3: return gather_p<T, 3, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
@@ -443,6 +498,309 @@ cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, c
         case 7: return gather_p<T, 7, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
     }
     return cudaErrorInvalidValue;
+}
+
+
+// ------------------------------------------------------------------ fast paths
+//
+// The kernels below are the ones the workloads run: tile edge and order are
+// compile-time constants (so every index is constant arithmetic) and every
+// axis has at least one full tile (N >= T).  The kernels above stay as the
+// general path for meshes smaller than a tile.
+
+constexpr int kFastCap = 256;  // sites per tile ordered by index in the fast spread
+
+// Spread: as k_spread, with the tile's records staged through shared memory in
+// batches of 32 (one coalesced load per lane instead of one dependent load per
+// site) and a padded patch pitch (PZ odd) that keeps the p^2 stencil rows of a
+// site in distinct banks.
+template <typename T, int P, int TILE>
+struct SpreadWarpSmem {
+    static constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
+    Rec<T> st_rec[32];
+    T pt[PSIZE];
+    int st_cell[32];
+    int2 keys[kFastCap];
+};
+
+template <typename T, int P, int TILE>
+__global__ void __launch_bounds__(kSpreadWarps * 32)
+k_spread_fast(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
+              const int* __restrict__ scell, const int* __restrict__ sorig, T* __restrict__ patch) {
+    typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
+    constexpr int E = WarpSmem::E, PZ = WarpSmem::PZ, PLANE = WarpSmem::PLANE, PSIZE = WarpSmem::PSIZE;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * kSpreadWarps + warp;
+    WarpSmem& W = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
+    if (tile >= g.ntiles) return;  // whole warp; no block-level barrier below
+    for (int i = lane; i < PSIZE; i += 32) W.pt[i] = T(0);
+    const int s0 = tile_start[tile];
+    const int c = tile_start[tile + 1] - s0;
+    const bool sorted = c > 1 && c <= kFastCap;
+    if (sorted) {
+        int cp = 2;
+        while (cp < c) cp <<= 1;
+        for (int i = lane; i < cp; i += 32)
+            W.keys[i] = i < c ? make_int2(sorig[s0 + i], s0 + i) : make_int2(INT_MAX, -1);
+        __syncwarp();
+        for (int k = 2; k <= cp; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < cp; i += 32) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const int2 a = W.keys[i], b = W.keys[ixj];
+                        if ((a.x > b.x) == ((i & k) == 0)) { W.keys[i] = b; W.keys[ixj] = a; }
+                    }
+                }
+                __syncwarp();
+            }
+    }
+    __syncwarp();
+    constexpr int NR = (P * P + 31) / 32;
+    BspCoef<T, P> cx;
+    cx.load();
+    BspPiece<T, P> py[NR], pz[NR];
+    int roff[NR];
+    bool ract[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const int row = lane + 32 * j;
+        ract[j] = row < P * P;
+        const int iy = ract[j] ? row / P : 0, iz = ract[j] ? row % P : 0;
+        py[j].load(iy);
+        pz[j].load(iz);
+        roff[j] = iy * PZ + iz;
+    }
+    for (int t0 = 0; t0 < c; t0 += 32) {
+        const int nb = min(32, c - t0);
+        if (lane < nb) {
+            const int s = sorted ? W.keys[t0 + lane].y : s0 + t0 + lane;
+            W.st_rec[lane] = srec[s];
+            W.st_cell[lane] = scell[s];
+        }
+        __syncwarp();
+        for (int j = 0; j < nb; ++j) {
+            const Rec<T> r = W.st_rec[j];
+            const int cl = W.st_cell[j];
+            const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+            T wx[P];
+            cx.all(r.x0[0], wx);
+            T* base0 = W.pt + lx * PLANE + ly * PZ + lz;
+#pragma unroll
+            for (int jr = 0; jr < NR; ++jr) {
+                const T wyz = py[jr].eval(r.x0[1]) * pz[jr].eval(r.x0[2]) * r.q;
+                if (ract[jr]) {
+                    T* b = base0 + roff[jr];
+#pragma unroll
+                    for (int a = 0; a < P; ++a) b[a * PLANE] += wx[a] * wyz;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    T* dst = patch + (size_t)tile * (E * E * E);
+    for (int i = lane; i < E * E * E; i += 32) {
+        const int x = i / (E * E), y = (i / E) % E, z = i % E;
+        dst[i] = W.pt[x * PLANE + y * PZ + z];
+    }
+}
+
+template <typename T, int P, int TILE>
+static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+                               const int* scell, const int* sorig, T* patch) {
+    const size_t smem = kSpreadWarps * sizeof(SpreadWarpSmem<T, P, TILE>);
+    cudaError_t e = cudaFuncSetAttribute(k_spread_fast<T, P, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
+    k_spread_fast<T, P, TILE><<<blocks, kSpreadWarps * 32, smem, s>>>(g, tile_start, srec, scell, sorig, patch);
+    return cudaGetLastError();
+}
+
+// Gather: one block (4 warps) per tile; the three field meshes over the tile
+// and its halo are staged in shared memory with the padded pitch.  A warp
+// takes the tile's sites eight at a time: lane (iy, iz) forms its row's share
+// W_y W_z sum_x W_x E of each of the eight forces, then a transposing butterfly
+// (31 shuffles for 8 sites x 4 components) leaves lane L holding the total of
+// site L/4, component L%4, which it scales and stores.
+constexpr int kGatherWarps = 4;
+
+template <typename T, int P, int TILE, typename Out>
+__global__ void __launch_bounds__(kGatherWarps * 32)
+k_gather_fast(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
+              const int* __restrict__ scell, const int* __restrict__ sorig, const T* __restrict__ fields,
+              double prefactor, Out* __restrict__ forces) {
+    constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
+    constexpr size_t FIELD_BYTES = (3 * PSIZE * sizeof(T) + 31) / 32 * 32;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    Rec<T>* st_rec = reinterpret_cast<Rec<T>*>(smem_raw);  // [warps][8]
+    T* fx = reinterpret_cast<T*>(smem_raw + kGatherWarps * 8 * sizeof(Rec<T>));
+    T* fy = fx + PSIZE;
+    T* fz = fy + PSIZE;
+    int* st_cell = reinterpret_cast<int*>(smem_raw + kGatherWarps * 8 * sizeof(Rec<T>) + FIELD_BYTES);
+    int* st_orig = st_cell + kGatherWarps * 8;
+    int* map = st_orig + kGatherWarps * 8;  // 3 * E mesh indices of the patch coordinates
+    const int tile = blockIdx.x;
+    const int s0 = tile_start[tile], s1 = tile_start[tile + 1];
+    if (s0 == s1) return;  // uniform across the block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tx = tile / (g.nt[1] * g.nt[2]);
+    const int ty = (tile / g.nt[2]) % g.nt[1];
+    const int tz = tile % g.nt[2];
+    if (threadIdx.x < 3 * E) {
+        const int d = threadIdx.x / E, c = threadIdx.x - d * E;
+        const int t = d == 0 ? tx : (d == 1 ? ty : tz);
+        int m = (t * TILE + g.kmin + c) % g.N[d];
+        map[threadIdx.x] = m < 0 ? m + g.N[d] : m;
+    }
+    __syncthreads();
+    const int64_t N3 = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    for (int i = threadIdx.x; i < E * E * E; i += blockDim.x) {
+        const int x = i / (E * E), y = (i / E) % E, z = i % E;
+        const int64_t f = ((int64_t)map[x] * g.N[1] + map[E + y]) * g.N[2] + map[2 * E + z];
+        const int o = x * PLANE + y * PZ + z;
+        fx[o] = fields[f];
+        fy[o] = fields[N3 + f];
+        fz[o] = fields[2 * N3 + f];
+    }
+    __syncthreads();
+    constexpr int NR = (P * P + 31) / 32;
+    BspCoef<T, P> cx;
+    cx.load();
+    BspPiece<T, P> py[NR], pz[NR];
+    int roff[NR];
+    bool ract[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const int row = lane + 32 * j;
+        ract[j] = row < P * P;
+        const int iy = ract[j] ? row / P : 0, iz = ract[j] ? row % P : 0;
+        py[j].load(iy);
+        pz[j].load(iz);
+        roff[j] = iy * PZ + iz;
+    }
+    Rec<T>* wrec = st_rec + warp * 8;
+    int* wcell = st_cell + warp * 8;
+    int* worig = st_orig + warp * 8;
+    const int nsites = s1 - s0;
+    for (int b = warp * 8; b < nsites; b += kGatherWarps * 8) {
+        const int nb = min(8, nsites - b);
+        if (lane < nb) {
+            wrec[lane] = srec[s0 + b + lane];
+            wcell[lane] = scell[s0 + b + lane];
+            worig[lane] = sorig[s0 + b + lane];
+        }
+        __syncwarp();
+        T v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j < nb) {
+                const Rec<T> r = wrec[j];
+                const int cl = wcell[j];
+                const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+                T wx[P];
+                cx.all(r.x0[0], wx);
+                const int base0 = lx * PLANE + ly * PZ + lz;
+#pragma unroll
+                for (int jr = 0; jr < NR; ++jr) {
+                    if (ract[jr]) {
+                        const T wyz = py[jr].eval(r.x0[1]) * pz[jr].eval(r.x0[2]);
+                        const int o0 = base0 + roff[jr];
+#pragma unroll
+                        for (int a = 0; a < P; ++a) {
+                            const T w = wx[a] * wyz;
+                            const int o = o0 + a * PLANE;
+                            v[4 * j] += w * fx[o];
+                            v[4 * j + 1] += w * fy[o];
+                            v[4 * j + 2] += w * fz[o];
+                        }
+                    }
+                }
+            }
+        }
+        // transposing butterfly: after step h, lane keeps the half of its values
+        // selected by its bit h and adds the partner's copy of the same half
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+            const bool up = (lane & h) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const T send = up ? v[i] : v[i + h];
+                const T keep = up ? v[i + h] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+            }
+        }
+        const int site = lane >> 2, comp = lane & 3;
+        if (site < nb && comp < 3) {
+            const T sc = (T)prefactor * wrec[site].q;
+            forces[3 * (int64_t)worig[site] + comp] = (Out)(sc * v[0]);
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T, int P, int TILE, typename Out>
+static cudaError_t gather_fast(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+                               const int* scell, const int* sorig, const T* fields, double prefactor, Out* forces) {
+    constexpr int E = TILE + P - 1, PZ = E | 1;
+    const size_t smem = kGatherWarps * 8 * sizeof(Rec<T>) + (3 * (size_t)E * E * PZ * sizeof(T) + 31) / 32 * 32 +
+                        kGatherWarps * 8 * 2 * sizeof(int) + 3 * E * sizeof(int);
+    cudaError_t e = cudaFuncSetAttribute(k_gather_fast<T, P, TILE, Out>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gather_fast<T, P, TILE, Out><<<g.ntiles, kGatherWarps * 32, smem, s>>>(g, tile_start, srec, scell, sorig,
+                                                                             fields, prefactor, forces);
+    return cudaGetLastError();
+}
+
+// Fold with one block per mesh row (x, y): the x and y cover lists are the
+// same for the whole block, the z list is read per point.
+template <typename T>
+__global__ void k_fold_rows(Geo g, const T* __restrict__ patch, const int* __restrict__ cov_off,
+                            const int2* __restrict__ cov_ent, int nmax1, T scale, T* __restrict__ rho) {
+    const int row = blockIdx.x;
+    const int x = row / g.N[1], y = row - x * g.N[1];
+    const int* ox = cov_off;
+    const int* oy = cov_off + nmax1;
+    const int* oz = cov_off + 2 * nmax1;
+    const int psz = g.E[0] * g.E[1] * g.E[2];
+    const int ax0 = __ldg(&ox[x]), ax1 = __ldg(&ox[x + 1]);
+    const int ay0 = __ldg(&oy[y]), ay1 = __ldg(&oy[y + 1]);
+    T* out = rho + (int64_t)row * g.N[2];
+    for (int z = threadIdx.x; z < g.N[2]; z += blockDim.x) {
+        const int az0 = __ldg(&oz[z]), az1 = __ldg(&oz[z + 1]);
+        T sum = T(0);
+        for (int a = ax0; a < ax1; ++a) {
+            const int2 ex = __ldg(&cov_ent[a]);
+            for (int b = ay0; b < ay1; ++b) {
+                const int2 ey = __ldg(&cov_ent[b]);
+                const int tb = (ex.x * g.nt[1] + ey.x) * g.nt[2];
+                const int ob = (ex.y * g.E[1] + ey.y) * g.E[2];
+                for (int c = az0; c < az1; ++c) {
+                    const int2 ez = __ldg(&cov_ent[c]);
+                    sum += patch[(size_t)(tb + ez.x) * psz + ob + ez.y];
+                }
+            }
+        }
+        out[z] = sum * scale;
+    }
+}
+
+template <typename T>
+cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
+                        T scale, T* rho) {
+    int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    int nmax1 = 1 + (g.N[0] > g.N[1] ? (g.N[0] > g.N[2] ? g.N[0] : g.N[2]) : (g.N[1] > g.N[2] ? g.N[1] : g.N[2]));
+    if (g.N[2] >= 32) {
+        const int threads = g.N[2] >= 128 ? 128 : (g.N[2] >= 64 ? 64 : 32);
+        k_fold_rows<T><<<g.N[0] * g.N[1], threads, 0, s>>>(g, patch, cov_off, cov_ent, nmax1, scale, rho);
+        return cudaGetLastError();
+    }
+    k_fold<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, patch, cov_off, cov_ent, nmax1, scale, rho);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ instantiations
