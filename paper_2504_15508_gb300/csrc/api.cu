@@ -17,6 +17,9 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "internal.cuh"
 
 using namespace pppm;
@@ -39,7 +42,10 @@ struct pppm_plan {
     void* tw[3] = {nullptr, nullptr, nullptr};
     void* rho = nullptr;
     void* cx[3] = {nullptr, nullptr, nullptr};
-    void* fields = nullptr;
+    void* fields = nullptr;  // padded (ghosted) field meshes, see FieldLayout
+    FieldLayout flayout{};
+    CUtensorMap fmap;        // 4D TMA descriptor of the padded fields
+    bool fmap_ok = false;
     void* partial = nullptr;
     unsigned int* counter = nullptr;
     int* status = nullptr;
@@ -48,6 +54,7 @@ struct pppm_plan {
     void* patch = nullptr;
     int* cov_off = nullptr;
     int2* cov_ent = nullptr;
+    int4* cov2 = nullptr;  // two-slot cover table (null when some index has more covers)
     int* tile_count = nullptr;
     int* tile_start = nullptr;
     // sites
@@ -59,6 +66,7 @@ struct pppm_plan {
     void* srec = nullptr;
     int* scell = nullptr;
     int* sorig = nullptr;
+    void* swt = nullptr;  // per-site B-spline weights in tile order
     // host-API staging
     cudaStream_t own = nullptr;
     void* h_stage = nullptr;
@@ -175,6 +183,8 @@ int choose_tile(const pppm_plan* P, int64_t n) {
     return density * 512.0 <= 160.0 ? 8 : 4;
 }
 
+int build_field_map(pppm_plan* P);
+
 // (Re)build the tile geometry, the patch scratch and the fold cover lists.
 int setup_tiles(pppm_plan* P, int T) {
     if (T == P->tileT && P->patch) return PPPM_OK;
@@ -192,9 +202,10 @@ int setup_tiles(pppm_plan* P, int T) {
     dfree(P->patch);
     dfree(P->cov_off);
     dfree(P->cov_ent);
+    dfree(P->cov2);
     dfree(P->tile_count);
     dfree(P->tile_start);
-    const size_t psz = (size_t)g.E[0] * g.E[1] * g.E[2];
+    const size_t psz = (size_t)g.E[0] * g.E[1] * g.Pz;
     int rc;
     if ((rc = dalloc(&P->patch, (size_t)g.ntiles * psz * P->esz)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->tile_count, sizeof(int) * (size_t)g.ntiles)) != PPPM_OK) return rc;
@@ -228,7 +239,26 @@ int setup_tiles(pppm_plan* P, int T) {
     if ((rc = dalloc(&P->cov_ent, sizeof(int2) * ent.size())) != PPPM_OK) return rc;
     CK(cudaMemcpy(P->cov_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->cov_ent, ent.data(), sizeof(int2) * ent.size(), cudaMemcpyHostToDevice));
+    // the same lists in two-slot form, if no index has more than two covers
+    {
+        std::vector<int4> c2(3 * (size_t)nmax, make_int4(-1, 0, -1, 0));
+        bool ok = true;
+        for (int d = 0; d < 3 && ok; ++d)
+            for (int m = 0; m < g.N[d]; ++m) {
+                const int b = off[(size_t)d * nmax1 + m], e = off[(size_t)d * nmax1 + m + 1];
+                if (e - b > 2) { ok = false; break; }
+                int4& v = c2[(size_t)d * nmax + m];
+                if (e - b >= 1) { v.x = ent[b].x; v.y = ent[b].y; }
+                if (e - b == 2) { v.z = ent[b + 1].x; v.w = ent[b + 1].y; }
+            }
+        if (ok) {
+            if ((rc = dalloc(&P->cov2, sizeof(int4) * c2.size())) != PPPM_OK) return rc;
+            CK(cudaMemcpy(P->cov2, c2.data(), sizeof(int4) * c2.size(), cudaMemcpyHostToDevice));
+        }
+    }
     P->tileT = T;
+    P->fmap_ok = false;
+    if (P->fields) build_field_map(P);
     return PPPM_OK;
 }
 
@@ -242,6 +272,7 @@ int reserve_sites(pppm_plan* P, int64_t n) {
     dfree(P->srec);
     dfree(P->scell);
     dfree(P->sorig);
+    dfree(P->swt);
     P->cap = 0;
     const size_t rs = 4 * P->esz;
     int rc;
@@ -252,6 +283,7 @@ int reserve_sites(pppm_plan* P, int64_t n) {
     if ((rc = dalloc(&P->srec, rs * n)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->scell, sizeof(int) * n)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->sorig, sizeof(int) * n)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->swt, P->esz * wstride(P->order) * n)) != PPPM_OK) return rc;
     P->cap = n;
     return PPPM_OK;
 }
@@ -264,9 +296,42 @@ int build_influence(pppm_plan* P) {
     return PPPM_OK;
 }
 
+// TMA descriptor of the padded field meshes as one 4D tensor (z, y, x, field)
+// whose box is a tile's stencil patch.  Built on the first call with each
+// tile edge (the box depends on it); a failure leaves the plain-load gather.
+int build_field_map(pppm_plan* P) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return PPPM_ERR_CUDA;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const FieldLayout& fl = P->flayout;
+    const int E = P->g.T + P->order - 1, EZ = (E + 3) & ~3;
+    const cuuint64_t dims[4] = {(cuuint64_t)fl.Zp, (cuuint64_t)fl.Yp, (cuuint64_t)fl.Xp, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)fl.Zp * P->esz, (cuuint64_t)fl.Zp * fl.Yp * P->esz,
+                                   (cuuint64_t)fl.fstride * P->esz};
+    const cuuint32_t box[4] = {(cuuint32_t)EZ, (cuuint32_t)E, (cuuint32_t)E, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode(&P->fmap, P->precision == PPPM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                        4, P->fields, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    P->fmap_ok = (r == CUDA_SUCCESS);
+    return PPPM_OK;
+}
+
 // ---------------------------------------------------------------- the path
+// Sites to tile patches (bin, scan, scatter, spread).  With rho_out the
+// patches are also folded into that mesh (scaled); without it the fold is left
+// to the forward z FFT, which reads the patches directly.
 template <typename T, typename In>
-int run_sites_to_mesh(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_t n, T* rho_out, T scale) {
+int run_sites_to_patches(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_t n, T* rho_out, T scale) {
     Geo& g = P->g;
     CK(cudaMemsetAsync(P->tile_count, 0, sizeof(int) * (size_t)g.ntiles, s));
     { PROF(K_BIN);
@@ -274,12 +339,30 @@ int run_sites_to_mesh(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, 
                             P->status))); }
     { PROF(K_SCAN); CK(launch_scan(s, P->tile_count, g.ntiles, P->tile_start)); }
     { PROF(K_SCATTER);
-      CK(launch_scatter<T>(s, (int)n, P->tile_of, P->slot_of, P->tile_start, (const Rec<T>*)P->rec, P->cell,
-                           (Rec<T>*)P->srec, P->scell, P->sorig)); }
+      CK(launch_scatter<T>(s, g, (int)n, P->tile_of, P->slot_of, P->tile_start, (const Rec<T>*)P->rec, P->cell,
+                           (Rec<T>*)P->srec, P->scell, P->sorig, (T*)P->swt)); }
     { PROF(K_SPREAD);
-      CK(launch_spread<T>(s, g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig, (T*)P->patch)); }
-    { PROF(K_FOLD); CK(launch_fold<T>(s, g, (const T*)P->patch, P->cov_off, P->cov_ent, scale, rho_out)); }
+      CK(launch_spread<T>(s, g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig, (const T*)P->swt,
+                          (T*)P->patch)); }
+    if (rho_out) {
+        PROF(K_FOLD);
+        CK(launch_fold<T>(s, g, (const T*)P->patch, P->cov_off, P->cov_ent, scale, rho_out));
+    }
     return PPPM_OK;
+}
+
+template <typename T>
+PatchSrc<T> patch_source(const pppm_plan* P) {
+    const Geo& g = P->g;
+    PatchSrc<T> ps{};
+    ps.patch = (const T*)P->patch;
+    ps.cov2 = P->cov2;
+    int nmax = g.N[0];
+    if (g.N[1] > nmax) nmax = g.N[1];
+    if (g.N[2] > nmax) nmax = g.N[2];
+    ps.nmax = nmax;
+    ps.psz = g.E[0] * g.E[1] * g.Pz;
+    return ps;
 }
 
 template <typename T>
@@ -293,7 +376,11 @@ int run_solve(pppm_plan* P, cudaStream_t s, double* energy, double* virial, T* f
     C* c0 = (C*)P->cx[0];
     C* c1 = (C*)P->cx[1];
     C* c2 = (C*)P->cx[2];
-    { PROF(K_FFT_Z_R2C); CK(launch_fft_z_r2c<T>(s, g, P->rad[2], (const C*)P->tw[2], (const T*)P->rho, c0)); }
+    { PROF(K_FFT_Z_R2C);
+      if (P->cov2)
+          CK(launch_fft_z_r2c<T>(s, g, P->rad[2], (const C*)P->tw[2], nullptr, c0, patch_source<T>(P)));
+      else
+          CK(launch_fft_z_r2c<T>(s, g, P->rad[2], (const C*)P->tw[2], (const T*)P->rho, c0, PatchSrc<T>{})); }
     { PROF(K_FFT_Y); CK(launch_fft_bundle<T>(s, g, 1, -1, P->rad[1], P->bd, (const C*)P->tw[1], c0)); }
     { PROF(K_FFT_X_INFLUENCE);
       CK(launch_fft_x_influence<T>(s, g, P->rad[0], P->bd, (const C*)P->tw[0], (const T*)P->G, P->beta, e_scale,
@@ -302,8 +389,15 @@ int run_solve(pppm_plan* P, cudaStream_t s, double* energy, double* virial, T* f
     const int64_t N3 = mesh_points(P);
     const C* src[3] = {c1, c2, c0};
     const int mk[3] = {0, 0, 1};
-    T* out[3] = {fields_out, fields_out + N3, fields_out + 2 * N3};
-    { PROF(K_FFT_Z_C2R); CK(launch_fft_z_c2r<T>(s, g, P->rad[2], (const C*)P->tw[2], 3, src, mk, out)); }
+    FieldLayout fl{};
+    if (fields_out == (T*)P->fields) {
+        fl = P->flayout;
+    } else {
+        fl.padded = 0;
+        fl.fstride = N3;
+    }
+    T* out[3] = {fields_out, fields_out + fl.fstride, fields_out + 2 * fl.fstride};
+    { PROF(K_FFT_Z_C2R); CK(launch_fft_z_c2r<T>(s, g, P->rad[2], (const C*)P->tw[2], 3, src, mk, out, fl)); }
     return PPPM_OK;
 }
 
@@ -314,13 +408,16 @@ int run_compute(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_
     if ((rc = setup_tiles(P, choose_tile(P, n))) != PPPM_OK) return rc;
     if ((rc = reserve_sites(P, n)) != PPPM_OK) return rc;
     P->last = s;
-    if ((rc = run_sites_to_mesh<T, In>(P, s, pos, q, n, (T*)P->rho, T(1))) != PPPM_OK) return rc;
+    // with a two-slot cover table the forward z FFT folds the patches itself
+    T* rho = P->cov2 ? (T*)nullptr : (T*)P->rho;
+    if ((rc = run_sites_to_patches<T, In>(P, s, pos, q, n, rho, T(1))) != PPPM_OK) return rc;
     T* fl = fields_out ? fields_out : (T*)P->fields;
     if ((rc = run_solve<T>(P, s, energy, virial, fl)) != PPPM_OK) return rc;
     if (forces && n > 0) {
         PROF(K_GATHER);
-        CK((launch_gather<T, In>(s, P->g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig, fl,
-                                 P->opt.prefactor, forces)));
+        CK((launch_gather<T, In>(s, P->g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig,
+                                 (const T*)P->swt, fl, P->flayout, P->fmap_ok ? (const void*)&P->fmap : nullptr,
+                                 P->opt.prefactor, forces, P->status)));
     }
     return PPPM_OK;
 }
@@ -464,7 +561,15 @@ int pppm_create(const double box[3], const int mesh[3], int order, double beta, 
     if ((rc = dalloc(&P->rho, P->esz * N3)) != PPPM_OK) return fail(rc);
     for (int c = 0; c < 3; ++c)
         if ((rc = dalloc(&P->cx[c], csz(P) * NH)) != PPPM_OK) return fail(rc);
-    if ((rc = dalloc(&P->fields, 3 * P->esz * N3)) != PPPM_OK) return fail(rc);
+    {
+        FieldLayout& fl = P->flayout;
+        fl.padded = 1;
+        fl.Xp = mesh[0] + order - 1;
+        fl.Yp = mesh[1] + order - 1;
+        fl.Zp = (mesh[2] + order - 1 + 3) & ~3;
+        fl.fstride = (int64_t)fl.Xp * fl.Yp * fl.Zp;
+        if ((rc = dalloc(&P->fields, 3 * P->esz * fl.fstride)) != PPPM_OK) return fail(rc);
+    }
     const int nblk = x_influence_blocks(g, P->bd);
     if ((rc = dalloc(&P->partial, 14 * P->esz * (size_t)nblk)) != PPPM_OK) return fail(rc);
     if ((rc = dalloc(&P->counter, sizeof(unsigned int))) != PPPM_OK) return fail(rc);
@@ -527,6 +632,7 @@ void pppm_destroy(pppm_plan* P) {
     dfree(P->patch);
     dfree(P->cov_off);
     dfree(P->cov_ent);
+    dfree(P->cov2);
     dfree(P->tile_count);
     dfree(P->tile_start);
     dfree(P->tile_of);
@@ -536,6 +642,7 @@ void pppm_destroy(pppm_plan* P) {
     dfree(P->srec);
     dfree(P->scell);
     dfree(P->sorig);
+    dfree(P->swt);
     dfree(P->h_stage);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : P->pend_a) cudaEventDestroy(e);
@@ -616,8 +723,9 @@ int pppm_spread(pppm_plan* P, void* stream, const double* pos, const double* q, 
     P->last = s;
     const Geo& g = P->g;
     const double h3 = (g.L[0] / g.N[0]) * (g.L[1] / g.N[1]) * (g.L[2] / g.N[2]);
-    if (P->precision == PPPM_FP32) return run_sites_to_mesh<float, double>(P, s, pos, q, n, (float*)rho, (float)(1.0 / h3));
-    return run_sites_to_mesh<double, double>(P, s, pos, q, n, (double*)rho, 1.0 / h3);
+    if (P->precision == PPPM_FP32)
+        return run_sites_to_patches<float, double>(P, s, pos, q, n, (float*)rho, (float)(1.0 / h3));
+    return run_sites_to_patches<double, double>(P, s, pos, q, n, (double*)rho, 1.0 / h3);
 }
 
 int pppm_fft_r2c(pppm_plan* P, void* stream, const void* in, void* out) {
@@ -626,11 +734,13 @@ int pppm_fft_r2c(pppm_plan* P, void* stream, const void* in, void* out) {
     cudaStream_t s = (cudaStream_t)stream;
     P->last = s;
     if (P->precision == PPPM_FP32) {
-        CK(launch_fft_z_r2c<float>(s, P->g, P->rad[2], (const float2*)P->tw[2], (const float*)in, (float2*)out));
+        CK(launch_fft_z_r2c<float>(s, P->g, P->rad[2], (const float2*)P->tw[2], (const float*)in, (float2*)out,
+                                   PatchSrc<float>{}));
         CK(launch_fft_bundle<float>(s, P->g, 1, -1, P->rad[1], P->bd, (const float2*)P->tw[1], (float2*)out));
         CK(launch_fft_bundle<float>(s, P->g, 0, -1, P->rad[0], P->bd, (const float2*)P->tw[0], (float2*)out));
     } else {
-        CK(launch_fft_z_r2c<double>(s, P->g, P->rad[2], (const double2*)P->tw[2], (const double*)in, (double2*)out));
+        CK(launch_fft_z_r2c<double>(s, P->g, P->rad[2], (const double2*)P->tw[2], (const double*)in,
+                                    (double2*)out, PatchSrc<double>{}));
         CK(launch_fft_bundle<double>(s, P->g, 1, -1, P->rad[1], P->bd, (const double2*)P->tw[1], (double2*)out));
         CK(launch_fft_bundle<double>(s, P->g, 0, -1, P->rad[0], P->bd, (const double2*)P->tw[0], (double2*)out));
     }
@@ -650,14 +760,18 @@ int pppm_fft_c2r(pppm_plan* P, void* stream, const void* in, void* out) {
         CK(launch_fft_bundle<float>(s, P->g, 1, 1, P->rad[1], P->bd, (const float2*)P->tw[1], c0));
         const float2* src[1] = {c0};
         float* o[1] = {(float*)out};
-        CK(launch_fft_z_c2r<float>(s, P->g, P->rad[2], (const float2*)P->tw[2], 1, src, mk, o));
+        FieldLayout fl{};
+        fl.fstride = mesh_points(P);
+        CK(launch_fft_z_c2r<float>(s, P->g, P->rad[2], (const float2*)P->tw[2], 1, src, mk, o, fl));
     } else {
         double2* c0 = (double2*)P->cx[0];
         CK(launch_fft_bundle<double>(s, P->g, 0, 1, P->rad[0], P->bd, (const double2*)P->tw[0], c0));
         CK(launch_fft_bundle<double>(s, P->g, 1, 1, P->rad[1], P->bd, (const double2*)P->tw[1], c0));
         const double2* src[1] = {c0};
         double* o[1] = {(double*)out};
-        CK(launch_fft_z_c2r<double>(s, P->g, P->rad[2], (const double2*)P->tw[2], 1, src, mk, o));
+        FieldLayout fl{};
+        fl.fstride = mesh_points(P);
+        CK(launch_fft_z_c2r<double>(s, P->g, P->rad[2], (const double2*)P->tw[2], 1, src, mk, o, fl));
     }
     return PPPM_OK;
 }

@@ -268,9 +268,34 @@ cudaError_t set_smem(K kernel, size_t smem) {
         for (int t = threadIdx.x & 31; t < (len_); t += 32)
 
 // ------------------------------------------------------------------ z forward (R2C)
+// Sum of the tile patches covering mesh point (x, y, z) (the fold of the
+// atomics-free spread) in a fixed order: the two x slots, two y slots and two
+// z slots give at most eight independent loads, empty slots contributing 0.
+template <typename R>
+__device__ __forceinline__ R fold_point(const Geo& g, const PatchSrc<R>& ps, int4 cx, int4 cy, int z) {
+    const int4 cz = __ldg(&ps.cov2[2 * ps.nmax + z]);
+    const int tx[2] = {cx.x, cx.z}, ox[2] = {cx.y, cx.w};
+    const int ty[2] = {cy.x, cy.z}, oy[2] = {cy.y, cy.w};
+    const int tz[2] = {cz.x, cz.z}, oz[2] = {cz.y, cz.w};
+    R sum = R(0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (tx[a] >= 0 && ty[b] >= 0 && tz[c] >= 0) {
+                    const int tile = (tx[a] * g.nt[1] + ty[b]) * g.nt[2] + tz[c];
+                    sum += ps.patch[(size_t)tile * ps.psz + (ox[a] * g.E[1] + oy[b]) * g.Pz + oz[c]];
+                }
+            }
+    return sum;
+}
+
 template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restrict__ out, int rows, int pairs) {
+k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restrict__ out, int rows, int pairs,
+            PatchSrc<R> ps) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Nz = eng.len(), Hz = g.Hz;
@@ -279,11 +304,32 @@ k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restr
     const int pair0 = blockIdx.x * pairs;
     const int npairs_total = (rows + 1) / 2;
     const int np = min(pairs, npairs_total - pair0);
-    LINE_LOOP(p, t, np, Nz) {
-        const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
-        const R va = in[(int64_t)r0 * Nz + t];
-        const R vb = r1 < rows ? in[(int64_t)r1 * Nz + t] : R(0);
-        a[p * Nz + t] = CT<R>::mk(va, vb);
+    if (ps.patch) {
+        const int4 empty = make_int4(-1, 0, -1, 0);
+        for (int p = threadIdx.x >> 5; p < np; p += blockDim.x >> 5) {
+            const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
+            const int x0 = r0 / g.N[1], y0 = r0 - x0 * g.N[1];
+            const int4 cx0 = __ldg(&ps.cov2[x0]), cy0 = __ldg(&ps.cov2[ps.nmax + y0]);
+            int4 cx1 = empty, cy1 = empty;
+            if (r1 < rows) {
+                const int x1 = r1 / g.N[1], y1 = r1 - x1 * g.N[1];
+                cx1 = __ldg(&ps.cov2[x1]);
+                cy1 = __ldg(&ps.cov2[ps.nmax + y1]);
+            }
+#pragma unroll 2
+            for (int t = threadIdx.x & 31; t < Nz; t += 32) {
+                const R va = fold_point(g, ps, cx0, cy0, t);
+                const R vb = fold_point(g, ps, cx1, cy1, t);  // empty slots give 0
+                a[p * Nz + t] = CT<R>::mk(va, vb);
+            }
+        }
+    } else {
+        LINE_LOOP(p, t, np, Nz) {
+            const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
+            const R va = in[(int64_t)r0 * Nz + t];
+            const R vb = r1 < rows ? in[(int64_t)r1 * Nz + t] : R(0);
+            a[p * Nz + t] = CT<R>::mk(va, vb);
+        }
     }
     __syncthreads();
     C* res = eng.template run<-1, false>(a, b, np, Nz, 1);
@@ -300,7 +346,7 @@ k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restr
 
 template <typename T>
 cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw,
-                             const T* in, typename Cx<T>::t* out) {
+                             const T* in, typename Cx<T>::t* out, const PatchSrc<T>& ps) {
     const int rows = g.N[0] * g.N[1];
     int pairs = (int)((32 * 1024) / (2 * g.N[2] * sizeof(typename Cx<T>::t)));
     pairs = pairs < 1 ? 1 : (pairs > 16 ? 16 : pairs);
@@ -310,7 +356,7 @@ cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, cons
         auto kern = k_fft_z_r2c<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        kern<<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, eng, in, out, rows, pairs);
+        kern<<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, eng, in, out, rows, pairs, ps);
         return cudaGetLastError();
     });
 }
@@ -581,6 +627,7 @@ struct ZOut {
     void* out[3];
     int mulkz[3];
     int nf;
+    FieldLayout fl;
 };
 
 template <typename R, typename Eng>
@@ -619,21 +666,60 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
     }
     __syncthreads();
     C* res = eng.template run<1, false>(a, b, nlines, Nz, 1);
-    LINE_LOOP(line, t, nlines, Nz) {
+    if (!zo.fl.padded) {
+        LINE_LOOP(line, t, nlines, Nz) {
+            const int f = line / np, p = line - f * np;
+            const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
+            R* out = reinterpret_cast<R*>(zo.out[f]);
+            const C z = res[line * Nz + t];
+            out[(int64_t)r0 * Nz + t] = z.x;
+            if (r1 < rows) out[(int64_t)r1 * Nz + t] = z.y;
+        }
+        return;
+    }
+    // padded: every output row also lands on its periodic ghost images, and
+    // each row is extended by p - 1 ghost points along z
+    const FieldLayout& fl = zo.fl;
+    const int Ny = g.N[1], Nx = g.N[0], kmin = g.kmin;
+    const int zlen = Nz + g.order - 1;
+    for (int line = threadIdx.x >> 5; line < nlines; line += blockDim.x >> 5) {
         const int f = line / np, p = line - f * np;
-        const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
         R* out = reinterpret_cast<R*>(zo.out[f]);
-        const C z = res[line * Nz + t];
-        out[(int64_t)r0 * Nz + t] = z.x;
-        if (r1 < rows) out[(int64_t)r1 * Nz + t] = z.y;
+        const C* rrow = res + line * Nz;
+        for (int half = 0; half < 2; ++half) {
+            const int r = 2 * (pair0 + p) + half;
+            if (r >= rows) break;
+            const int x = r / Ny, y = r - x * Ny;
+            const int px0 = x - kmin, py0 = y - kmin;
+            // at most one ghost image per axis (Xp < 2 Nx)
+            const int pxg = px0 + Nx < fl.Xp ? px0 + Nx : (px0 - Nx >= 0 ? px0 - Nx : -1);
+            const int pyg = py0 + Ny < fl.Yp ? py0 + Ny : (py0 - Ny >= 0 ? py0 - Ny : -1);
+            R* o00 = out + ((int64_t)px0 * fl.Yp + py0) * fl.Zp;
+            R* o10 = pxg >= 0 ? out + ((int64_t)pxg * fl.Yp + py0) * fl.Zp : nullptr;
+            R* o01 = pyg >= 0 ? out + ((int64_t)px0 * fl.Yp + pyg) * fl.Zp : nullptr;
+            R* o11 = (pxg >= 0 && pyg >= 0) ? out + ((int64_t)pxg * fl.Yp + pyg) * fl.Zp : nullptr;
+            for (int pz = threadIdx.x & 31; pz < zlen; pz += 32) {
+                int zz = pz + kmin;
+                zz += zz < 0 ? Nz : 0;
+                zz -= zz >= Nz ? Nz : 0;
+                const C zv = rrow[zz];
+                const R v = half ? zv.y : zv.x;
+                o00[pz] = v;
+                if (o10) o10[pz] = v;
+                if (o01) o01[pz] = v;
+                if (o11) o11[pz] = v;
+            }
+        }
     }
 }
 
 template <typename T>
 cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw, int nf,
-                             const typename Cx<T>::t* const* src, const int* mulkz, T* const* out) {
+                             const typename Cx<T>::t* const* src, const int* mulkz, T* const* out,
+                             const FieldLayout& fl) {
     ZOut zo;
     zo.nf = nf;
+    zo.fl = fl;
     for (int f = 0; f < 3; ++f) {
         zo.src[f] = f < nf ? src[f] : nullptr;
         zo.out[f] = f < nf ? out[f] : nullptr;
@@ -655,7 +741,7 @@ cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, cons
 
 #define PPPM_INST_FFT(T)                                                                                           \
     template cudaError_t launch_fft_z_r2c<T>(cudaStream_t, const Geo&, const Radix&, const Cx<T>::t*, const T*,    \
-                                             Cx<T>::t*);                                                           \
+                                             Cx<T>::t*, const PatchSrc<T>&);                                       \
     template cudaError_t launch_fft_bundle<T>(cudaStream_t, const Geo&, int, int, const Radix&, const Bundle&,     \
                                               const Cx<T>::t*, Cx<T>::t*);                                         \
     template cudaError_t launch_fft_x_influence<T>(cudaStream_t, const Geo&, const Radix&, const Bundle&,          \
@@ -664,7 +750,7 @@ cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, cons
     template cudaError_t launch_fft_y_inverse3<T>(cudaStream_t, const Geo&, const Radix&, const Bundle&,           \
                                                   const Cx<T>::t*, Cx<T>::t*, Cx<T>::t*, Cx<T>::t*);               \
     template cudaError_t launch_fft_z_c2r<T>(cudaStream_t, const Geo&, const Radix&, const Cx<T>::t*, int,         \
-                                             const Cx<T>::t* const*, const int*, T* const*);
+                                             const Cx<T>::t* const*, const int*, T* const*, const FieldLayout&);
 PPPM_INST_FFT(float)
 PPPM_INST_FFT(double)
 

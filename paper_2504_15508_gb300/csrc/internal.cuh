@@ -23,6 +23,10 @@ constexpr int kMaxRadixStages = 16;
 constexpr int kSortCap = 1024;       // sites per tile sorted by index in the spread
 constexpr int kMaxMesh = 2048;
 
+// Values stored per site for the precomputed B-spline weights of order p:
+// 3p weights padded to a multiple of 4.
+__host__ __device__ constexpr int wstride(int p) { return (3 * p + 3) & ~3; }
+
 // Radix plan of one FFT length: L = prod(r[0..n-1]), each r in {2, 3, 4, 5, 8}.
 struct Radix {
     int L;
@@ -47,12 +51,37 @@ struct Geo {
     int nt[3];       // tiles per axis
     int ntiles;
     int E[3];        // patch extent per axis = Tt + p - 1
-    int Pz;          // padded z pitch of the spread patch in shared memory
+    int Pz;          // z pitch of a spread patch, in shared memory and in the patch scratch
+};
+
+// Where the forward z FFT reads its real input: a mesh, or the spread's tile
+// patches summed on the fly (the fold), through the per-axis cover lists.
+// Each mesh index is covered by at most two tile patches per axis when every
+// axis holds at least T + p - 1 points; cov2[d * nmax + m] lists them as
+// {tile, coordinate, tile, coordinate}, tile -1 for an empty slot.
+template <typename R>
+struct PatchSrc {
+    const R* patch;       // nullptr: read the mesh
+    const int4* cov2;     // two-slot cover table, 3 axes of nmax entries each
+    int nmax;
+    int psz;              // elements per tile patch = E0 * E1 * Pz
 };
 
 template <typename R> __host__ __device__ __forceinline__ R kfac(const Geo& g, int d);
 template <> __host__ __device__ __forceinline__ float kfac<float>(const Geo& g, int d) { return g.kfac_f[d]; }
 template <> __host__ __device__ __forceinline__ double kfac<double>(const Geo& g, int d) { return g.kfac_d[d]; }
+
+// Layout of the three field meshes E_x, E_y, E_z.  Unpadded: three
+// consecutive Nx x Ny x Nz meshes.  Padded ("ghosted"): each mesh extended by
+// p - 1 periodic ghost points per axis, so that a tile's stencil patch is one
+// contiguous box: padded index = mesh index - kmin, extents Xp = Nx + p - 1,
+// Yp = Ny + p - 1, Zp = Nz + p - 1 rounded up to a multiple of 4 (TMA needs
+// 16-byte row strides).
+struct FieldLayout {
+    int padded;
+    int Xp, Yp, Zp;
+    int64_t fstride;  // elements between consecutive fields
+};
 
 // Bundle shape of a strided-line FFT pass (lines along y or x, B adjacent kz
 // columns per block).
@@ -68,23 +97,25 @@ cudaError_t launch_bin(cudaStream_t s, const Geo& g, const In* pos, const In* q,
                        int* tile_of, int* slot_of, Rec<T>* rec, int* cell, int* status);
 cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int* start);
 template <typename T>
-cudaError_t launch_scatter(cudaStream_t s, int n, const int* tile_of, const int* slot_of, const int* tile_start,
-                           const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell, int* sorig);
+cudaError_t launch_scatter(cudaStream_t s, const Geo& g, int n, const int* tile_of, const int* slot_of,
+                           const int* tile_start, const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell,
+                           int* sorig, T* swt);
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                          const int* scell, const int* sorig, T* patch);
+                          const int* scell, const int* sorig, const T* swt, T* patch);
 template <typename T>
 cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
                         T scale, T* rho);
 template <typename T, typename Out>
 cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* fields, double prefactor, Out* forces);
+                          const int* scell, const int* sorig, const T* swt, const T* fields, const FieldLayout& fl,
+                          const void* tmap, double prefactor, Out* forces, int* status);
 void upload_bspline_coefficients();
 
 // fft_kernels.cu
 template <typename T>
 cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw,
-                             const T* in, typename Cx<T>::t* out);
+                             const T* in, typename Cx<T>::t* out, const PatchSrc<T>& ps);
 template <typename T>
 cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, const Radix& r, const Bundle& bd,
                               const typename Cx<T>::t* tw, typename Cx<T>::t* data);
@@ -100,7 +131,8 @@ cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry,
 // nf fields: out[f] = C2R_z(src[f] * (mulkz[f] ? -i kz' : 1)); src/out arrays of nf pointers
 template <typename T>
 cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw, int nf,
-                             const typename Cx<T>::t* const* src, const int* mulkz, T* const* out);
+                             const typename Cx<T>::t* const* src, const int* mulkz, T* const* out,
+                             const FieldLayout& fl);
 int x_influence_blocks(const Geo& g, const Bundle& bd);
 
 // influence.cu

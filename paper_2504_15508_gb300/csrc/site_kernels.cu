@@ -6,6 +6,8 @@
 // stencil (bspline.cuh); the spread is the transpose of the gather.
 #include <climits>
 
+#include <cuda.h>
+
 #include "bspline.cuh"
 #include "internal.cuh"
 
@@ -177,24 +179,71 @@ cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int* start
     return cudaGetLastError();
 }
 
-template <typename T>
+// Scatter to tile order.  Each site's B-spline weights are evaluated here,
+// once, one thread per site: swt holds per site {q W_x[0..p-1], W_y[0..p-1],
+// W_z[0..p-1]} padded to wstride(p) values; the fast spread and gather read
+// them instead of re-evaluating the splines in every lane.
+template <typename T, int P>
 __global__ void k_scatter(int n, const int* __restrict__ tile_of, const int* __restrict__ slot_of,
                           const int* __restrict__ tile_start, const Rec<T>* __restrict__ rec,
                           const int* __restrict__ cell, Rec<T>* __restrict__ srec, int* __restrict__ scell,
-                          int* __restrict__ sorig) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+                          int* __restrict__ sorig, T* __restrict__ swt) {
+    constexpr int WS = wstride(P);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int dst = tile_start[tile_of[i]] + slot_of[i];
-    srec[dst] = rec[i];
+    const int dst = tile_start[tile_of[i]] + slot_of[i];
+    const Rec<T> r = rec[i];
+    srec[dst] = r;
     scell[dst] = cell[i];
     sorig[dst] = i;
+    BspCoef<T, P> co;
+    co.load();
+    T w[WS];
+    T t[P];
+    co.all(r.x0[0], t);
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[a] = t[a] * r.q;
+    co.all(r.x0[1], t);
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[P + a] = t[a];
+    co.all(r.x0[2], t);
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[2 * P + a] = t[a];
+#pragma unroll
+    for (int a = 3 * P; a < WS; ++a) w[a] = T(0);
+    T* o = swt + (size_t)dst * WS;
+#pragma unroll
+    for (int a = 0; a < WS; a += 4) {
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4*>(o + a) = make_float4(w[a], w[a + 1], w[a + 2], w[a + 3]);
+        } else {
+            *reinterpret_cast<double2*>(o + a) = make_double2(w[a], w[a + 1]);
+            *reinterpret_cast<double2*>(o + a + 2) = make_double2(w[a + 2], w[a + 3]);
+        }
+    }
 }
 
 template <typename T>
-cudaError_t launch_scatter(cudaStream_t s, int n, const int* tile_of, const int* slot_of, const int* tile_start,
-                           const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell, int* sorig) {
+cudaError_t launch_scatter(cudaStream_t s, const Geo& g, int n, const int* tile_of, const int* slot_of,
+                           const int* tile_start, const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell,
+                           int* sorig, T* swt) {
     if (n == 0) return cudaSuccess;
-    k_scatter<T><<<(n + 255) / 256, 256, 0, s>>>(n, tile_of, slot_of, tile_start, rec, cell, srec, scell, sorig);
+    const int blocks = (n + 255) / 256;
+#define PPPM_SCATTER_P(PP)                                                                                  \
+    case PP:                                                                                                \
+        k_scatter<T, PP><<<blocks, 256, 0, s>>>(n, tile_of, slot_of, tile_start, rec, cell, srec, scell, sorig, \
+                                                swt);                                                       \
+        break;
+    switch (g.order) {
+        PPPM_SCATTER_P(2)
+        PPPM_SCATTER_P(3)
+        PPPM_SCATTER_P(4)
+        PPPM_SCATTER_P(5)
+        PPPM_SCATTER_P(6)
+        PPPM_SCATTER_P(7)
+        default: return cudaErrorInvalidValue;
+    }
+#undef PPPM_SCATTER_P
     return cudaGetLastError();
 }
 
@@ -285,12 +334,8 @@ k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
         }
         __syncwarp();
     }
-    T* dst = patch + (size_t)tile * (Ex * Ey * Ez);
-    const int eyz = Ey * Ez;
-    for (int i = lane; i < Ex * eyz; i += 32) {
-        int x = i / eyz, rem = i - x * eyz, y = rem / Ez, z = rem - y * Ez;
-        dst[i] = pt[x * plane + y * Pz + z];
-    }
+    T* dst = patch + (size_t)tile * psize;  // same padded layout as the shared patch
+    for (int i = lane; i < psize; i += 32) dst[i] = pt[i];
 }
 
 template <typename T, int P>
@@ -306,10 +351,13 @@ static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int* tile_start,
 }
 
 template <typename T, int P, int TILE>
-static cudaError_t spread_fast(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*, const int*, T*);
+static cudaError_t spread_fast(cudaStream_t, const Geo&, const int*, const int*, const int*, const T*, T*);
 template <typename T, int P, int TILE, typename Out>
-static cudaError_t gather_fast(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*, const int*, const T*,
+static cudaError_t gather_fast(cudaStream_t, const Geo&, const int*, const int*, const int*, const T*, const T*,
                                double, Out*);
+template <typename T, int P, int TILE, typename Out>
+static cudaError_t gather_tma(cudaStream_t, const Geo&, const int*, const int*, const int*, const T*, const void*,
+                              double, Out*, int*);
 
 // The fast kernels need full tiles on every axis and a tile edge of 4 or 8.
 static bool fast_tiles(const Geo& g) {
@@ -334,9 +382,9 @@ static bool fast_tiles(const Geo& g) {
 
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                          const int* scell, const int* sorig, T* patch) {
+                          const int* scell, const int* sorig, const T* swt, T* patch) {
     if (fast_tiles(g)) {
-        PPPM_FAST_SWITCH(spread_fast, T, s, g, tile_start, srec, scell, sorig, patch)
+        PPPM_FAST_SWITCH(spread_fast, T, s, g, tile_start, scell, sorig, swt, patch)
     }
     switch (g.order) {
         case 2: return spread_p<T, 2>(s, g, tile_start, srec, scell, sorig, patch);
@@ -368,7 +416,7 @@ __global__ void k_fold(Geo g, const T* __restrict__ patch, const int* __restrict
     const int* ox = cov_off;
     const int* oy = cov_off + nmax1;
     const int* oz = cov_off + 2 * nmax1;
-    const int psz = g.E[0] * g.E[1] * g.E[2];
+    const int psz = g.E[0] * g.E[1] * g.Pz;
     T sum = T(0);
     for (int a = ox[x]; a < ox[x + 1]; ++a) {
         const int2 ex = cov_ent[a];
@@ -377,7 +425,7 @@ __global__ void k_fold(Geo g, const T* __restrict__ patch, const int* __restrict
             for (int c = oz[z]; c < oz[z + 1]; ++c) {
                 const int2 ez = cov_ent[c];
                 const int tile = (ex.x * g.nt[1] + ey.x) * g.nt[2] + ez.x;
-                sum += patch[(size_t)tile * psz + (ex.y * g.E[1] + ey.y) * g.E[2] + ez.y];
+                sum += patch[(size_t)tile * psz + (ex.y * g.E[1] + ey.y) * g.Pz + ez.y];
             }
         }
     }
@@ -394,7 +442,7 @@ constexpr int kGatherThreads = 64;
 template <typename T, int P, typename Out>
 __global__ void __launch_bounds__(kGatherThreads)
 k_gather(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
-         const int* __restrict__ scell, const int* __restrict__ sorig, const T* __restrict__ fields,
+         const int* __restrict__ scell, const int* __restrict__ sorig, const T* __restrict__ fields, FieldLayout fl,
          double prefactor, Out* __restrict__ forces) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = blockIdx.x;
@@ -409,17 +457,17 @@ k_gather(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
     const int ty = (tile / g.nt[2]) % g.nt[1];
     const int tz = tile % g.nt[2];
     const int ox = tx * g.T + g.kmin, oy = ty * g.T + g.kmin, oz = tz * g.T + g.kmin;
-    const int64_t N3 = (int64_t)g.N[0] * g.N[1] * g.N[2];
     const int eyz = Ey * Ez;
     for (int i = threadIdx.x; i < psz; i += blockDim.x) {
         int cx = i / eyz, rem = i - cx * eyz, cy = rem / Ez, cz = rem - cy * Ez;
         int mx = (ox + cx) % g.N[0]; mx += mx < 0 ? g.N[0] : 0;
         int my = (oy + cy) % g.N[1]; my += my < 0 ? g.N[1] : 0;
         int mz = (oz + cz) % g.N[2]; mz += mz < 0 ? g.N[2] : 0;
-        const int64_t f = ((int64_t)mx * g.N[1] + my) * g.N[2] + mz;
+        const int64_t f = fl.padded ? ((int64_t)(mx - g.kmin) * fl.Yp + (my - g.kmin)) * fl.Zp + (mz - g.kmin)
+                                    : ((int64_t)mx * g.N[1] + my) * g.N[2] + mz;
         fx[i] = fields[f];
-        fy[i] = fields[N3 + f];
-        fz[i] = fields[2 * N3 + f];
+        fy[i] = fields[fl.fstride + f];
+        fz[i] = fields[2 * fl.fstride + f];
     }
     __syncthreads();
     BspCoef<T, P> co;
@@ -458,44 +506,52 @@ k_gather(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
 
 template <typename T, int P, typename Out>
 static cudaError_t gather_p(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                            const int* scell, const int* sorig, const T* fields, double prefactor, Out* forces) {
+                            const int* scell, const int* sorig, const T* fields, const FieldLayout& fl,
+                            double prefactor, Out* forces) {
     size_t smem = 3ull * g.E[0] * g.E[1] * g.E[2] * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_gather<T, P, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gather<T, P, Out><<<g.ntiles, kGatherThreads, smem, s>>>(g, tile_start, srec, scell, sorig, fields, prefactor,
-                                                               forces);
+    k_gather<T, P, Out><<<g.ntiles, kGatherThreads, smem, s>>>(g, tile_start, srec, scell, sorig, fields, fl,
+                                                               prefactor, forces);
     return cudaGetLastError();
 }
 
-#define PPPM_FAST_SWITCH_G(T_, O_, ...)                                                           \
+#define PPPM_FAST_SWITCH_G(FN, T_, O_, ...)                                                       \
     switch (g.order * 16 + g.T) {                                                                 \
-        case 2 * 16 + 4: return gather_fast<T_, 2, 4, O_>(__VA_ARGS__);                           \
-        case 2 * 16 + 8: return gather_fast<T_, 2, 8, O_>(__VA_ARGS__);                           \
-        case 3 * 16 + 4: return gather_fast<T_, 3, 4, O_>(__VA_ARGS__);                           \
-        case 3 * 16 + 8: return gather_fast<T_, 3, 8, O_>(__VA_ARGS__);                           \
-        case 4 * 16 + 4: return gather_fast<T_, 4, 4, O_>(__VA_ARGS__);                           \
-        case 4 * 16 + 8: return gather_fast<T_, 4, 8, O_>(__VA_ARGS__);                           \
-        case 5 * 16 + 4: return gather_fast<T_, 5, 4, O_>(__VA_ARGS__);                           \
-        case 5 * 16 + 8: return gather_fast<T_, 5, 8, O_>(__VA_ARGS__);                           \
-        case 6 * 16 + 4: return gather_fast<T_, 6, 4, O_>(__VA_ARGS__);                           \
-        case 6 * 16 + 8: return gather_fast<T_, 6, 8, O_>(__VA_ARGS__);                           \
-        case 7 * 16 + 4: return gather_fast<T_, 7, 4, O_>(__VA_ARGS__);                           \
-        case 7 * 16 + 8: return gather_fast<T_, 7, 8, O_>(__VA_ARGS__);                           \
+        case 2 * 16 + 4: return FN<T_, 2, 4, O_>(__VA_ARGS__);                                    \
+        case 2 * 16 + 8: return FN<T_, 2, 8, O_>(__VA_ARGS__);                                    \
+        case 3 * 16 + 4: return FN<T_, 3, 4, O_>(__VA_ARGS__);                                    \
+        case 3 * 16 + 8: return FN<T_, 3, 8, O_>(__VA_ARGS__);                                    \
+        case 4 * 16 + 4: return FN<T_, 4, 4, O_>(__VA_ARGS__);                                    \
+        case 4 * 16 + 8: return FN<T_, 4, 8, O_>(__VA_ARGS__);                                    \
+        case 5 * 16 + 4: return FN<T_, 5, 4, O_>(__VA_ARGS__);                                    \
+        case 5 * 16 + 8: return FN<T_, 5, 8, O_>(__VA_ARGS__);                                    \
+        case 6 * 16 + 4: return FN<T_, 6, 4, O_>(__VA_ARGS__);                                    \
+        case 6 * 16 + 8: return FN<T_, 6, 8, O_>(__VA_ARGS__);                                    \
+        case 7 * 16 + 4: return FN<T_, 7, 4, O_>(__VA_ARGS__);                                    \
+        case 7 * 16 + 8: return FN<T_, 7, 8, O_>(__VA_ARGS__);                                    \
     }
 
 template <typename T, typename Out>
 cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* fields, double prefactor, Out* forces) {
+                          const int* scell, const int* sorig, const T* swt, const T* fields, const FieldLayout& fl,
+                          const void* tmap, double prefactor, Out* forces, int* status) {
     if (fast_tiles(g)) {
-        PPPM_FAST_SWITCH_G(T, Out, s, g, tile_start, srec, scell, sorig, fields, prefactor, forces)
+        if (fl.padded && tmap) {
+            PPPM_FAST_SWITCH_G(gather_tma, T, Out, s, g, tile_start, scell, sorig, swt, tmap, prefactor, forces,
+                               status)
+        }
+        if (!fl.padded) {
+            PPPM_FAST_SWITCH_G(gather_fast, T, Out, s, g, tile_start, scell, sorig, swt, fields, prefactor, forces)
+        }
     }
     switch (g.order) {
-        case 2: return gather_p<T, 2, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
-        case 3: return gather_p<T, 3, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
-        case 4: return gather_p<T, 4, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
-        case 5: return gather_p<T, 5, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
-        case 6: return gather_p<T, 6, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
-        case 7: return gather_p<T, 7, Out>(s, g, tile_start, srec, scell, sorig, fields, prefactor, forces);
+        case 2: return gather_p<T, 2, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 3: return gather_p<T, 3, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 4: return gather_p<T, 4, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 5: return gather_p<T, 5, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 6: return gather_p<T, 6, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 7: return gather_p<T, 7, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
     }
     return cudaErrorInvalidValue;
 }
@@ -517,7 +573,8 @@ constexpr int kFastCap = 256;  // sites per tile ordered by index in the fast sp
 template <typename T, int P, int TILE>
 struct SpreadWarpSmem {
     static constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
-    Rec<T> st_rec[32];
+    static constexpr int WSP = wstride(P) + 4;  // staging row pitch (keeps vector stores conflict-light)
+    T st_w[32][WSP];
     T pt[PSIZE];
     int st_cell[32];
     int2 keys[kFastCap];
@@ -525,10 +582,11 @@ struct SpreadWarpSmem {
 
 template <typename T, int P, int TILE>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
-k_spread_fast(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
-              const int* __restrict__ scell, const int* __restrict__ sorig, T* __restrict__ patch) {
+k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
+              const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch) {
     typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
     constexpr int E = WarpSmem::E, PZ = WarpSmem::PZ, PLANE = WarpSmem::PLANE, PSIZE = WarpSmem::PSIZE;
+    constexpr int WS = wstride(P);
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x * kSpreadWarps + warp;
@@ -557,64 +615,61 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restric
             }
     }
     __syncwarp();
+    // lane -> stencil rows (iy, iz); orders above 5 have more rows than lanes
     constexpr int NR = (P * P + 31) / 32;
-    BspCoef<T, P> cx;
-    cx.load();
-    BspPiece<T, P> py[NR], pz[NR];
-    int roff[NR];
+    int roff[NR], riy[NR], riz[NR];
     bool ract[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
         const int row = lane + 32 * j;
         ract[j] = row < P * P;
-        const int iy = ract[j] ? row / P : 0, iz = ract[j] ? row % P : 0;
-        py[j].load(iy);
-        pz[j].load(iz);
-        roff[j] = iy * PZ + iz;
+        riy[j] = ract[j] ? row / P : 0;
+        riz[j] = ract[j] ? row % P : 0;
+        roff[j] = riy[j] * PZ + riz[j];
     }
     for (int t0 = 0; t0 < c; t0 += 32) {
         const int nb = min(32, c - t0);
         if (lane < nb) {
             const int s = sorted ? W.keys[t0 + lane].y : s0 + t0 + lane;
-            W.st_rec[lane] = srec[s];
+            const T* src = swt + (size_t)s * WS;
+#pragma unroll
+            for (int a = 0; a < WS; ++a) W.st_w[lane][a] = src[a];
             W.st_cell[lane] = scell[s];
         }
         __syncwarp();
         for (int j = 0; j < nb; ++j) {
-            const Rec<T> r = W.st_rec[j];
             const int cl = W.st_cell[j];
             const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
-            T wx[P];
-            cx.all(r.x0[0], wx);
+            T wxq[P];
+#pragma unroll
+            for (int a = 0; a < P; ++a) wxq[a] = W.st_w[j][a];
             T* base0 = W.pt + lx * PLANE + ly * PZ + lz;
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr) {
-                const T wyz = py[jr].eval(r.x0[1]) * pz[jr].eval(r.x0[2]) * r.q;
                 if (ract[jr]) {
+                    const T wyz = W.st_w[j][P + riy[jr]] * W.st_w[j][2 * P + riz[jr]];
                     T* b = base0 + roff[jr];
 #pragma unroll
-                    for (int a = 0; a < P; ++a) b[a * PLANE] += wx[a] * wyz;
+                    for (int a = 0; a < P; ++a) b[a * PLANE] += wxq[a] * wyz;
                 }
             }
             __syncwarp();
         }
+        __syncwarp();
     }
-    T* dst = patch + (size_t)tile * (E * E * E);
-    for (int i = lane; i < E * E * E; i += 32) {
-        const int x = i / (E * E), y = (i / E) % E, z = i % E;
-        dst[i] = W.pt[x * PLANE + y * PZ + z];
-    }
+    T* dst = patch + (size_t)tile * PSIZE;  // same padded layout as the shared patch
+    for (int i = lane; i < PSIZE; i += 32) dst[i] = W.pt[i];
 }
 
 template <typename T, int P, int TILE>
-static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                               const int* scell, const int* sorig, T* patch) {
+static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+                               const int* sorig, const T* swt, T* patch) {
     const size_t smem = kSpreadWarps * sizeof(SpreadWarpSmem<T, P, TILE>);
     cudaError_t e = cudaFuncSetAttribute(k_spread_fast<T, P, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
-    k_spread_fast<T, P, TILE><<<blocks, kSpreadWarps * 32, smem, s>>>(g, tile_start, srec, scell, sorig, patch);
+    k_spread_fast<T, P, TILE><<<blocks, kSpreadWarps * 32, smem, s>>>(g, tile_start, scell, sorig, swt, patch);
     return cudaGetLastError();
 }
 
@@ -628,17 +683,19 @@ constexpr int kGatherWarps = 4;
 
 template <typename T, int P, int TILE, typename Out>
 __global__ void __launch_bounds__(kGatherWarps * 32)
-k_gather_fast(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
-              const int* __restrict__ scell, const int* __restrict__ sorig, const T* __restrict__ fields,
+k_gather_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
+              const int* __restrict__ sorig, const T* __restrict__ swt, const T* __restrict__ fields,
               double prefactor, Out* __restrict__ forces) {
     constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
+    constexpr int WS = wstride(P), WSP = WS + 4;
+    constexpr size_t STAGE_BYTES = (kGatherWarps * 8 * WSP * sizeof(T) + 31) / 32 * 32;
     constexpr size_t FIELD_BYTES = (3 * PSIZE * sizeof(T) + 31) / 32 * 32;
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    Rec<T>* st_rec = reinterpret_cast<Rec<T>*>(smem_raw);  // [warps][8]
-    T* fx = reinterpret_cast<T*>(smem_raw + kGatherWarps * 8 * sizeof(Rec<T>));
+    T* st_w = reinterpret_cast<T*>(smem_raw);  // [warps][8][WSP]
+    T* fx = reinterpret_cast<T*>(smem_raw + STAGE_BYTES);
     T* fy = fx + PSIZE;
     T* fz = fy + PSIZE;
-    int* st_cell = reinterpret_cast<int*>(smem_raw + kGatherWarps * 8 * sizeof(Rec<T>) + FIELD_BYTES);
+    int* st_cell = reinterpret_cast<int*>(smem_raw + STAGE_BYTES + FIELD_BYTES);
     int* st_orig = st_cell + kGatherWarps * 8;
     int* map = st_orig + kGatherWarps * 8;  // 3 * E mesh indices of the patch coordinates
     const int tile = blockIdx.x;
@@ -666,28 +723,27 @@ k_gather_fast(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restric
     }
     __syncthreads();
     constexpr int NR = (P * P + 31) / 32;
-    BspCoef<T, P> cx;
-    cx.load();
-    BspPiece<T, P> py[NR], pz[NR];
-    int roff[NR];
+    int roff[NR], riy[NR], riz[NR];
     bool ract[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
         const int row = lane + 32 * j;
         ract[j] = row < P * P;
-        const int iy = ract[j] ? row / P : 0, iz = ract[j] ? row % P : 0;
-        py[j].load(iy);
-        pz[j].load(iz);
-        roff[j] = iy * PZ + iz;
+        riy[j] = ract[j] ? row / P : 0;
+        riz[j] = ract[j] ? row % P : 0;
+        roff[j] = riy[j] * PZ + riz[j];
     }
-    Rec<T>* wrec = st_rec + warp * 8;
+    T* ww = st_w + warp * 8 * WSP;
     int* wcell = st_cell + warp * 8;
     int* worig = st_orig + warp * 8;
     const int nsites = s1 - s0;
     for (int b = warp * 8; b < nsites; b += kGatherWarps * 8) {
         const int nb = min(8, nsites - b);
+        for (int k = lane; k < nb * WS; k += 32) {
+            const int j = k / WS, a = k - j * WS;
+            ww[j * WSP + a] = swt[(size_t)(s0 + b + j) * WS + a];
+        }
         if (lane < nb) {
-            wrec[lane] = srec[s0 + b + lane];
             wcell[lane] = scell[s0 + b + lane];
             worig[lane] = sorig[s0 + b + lane];
         }
@@ -698,20 +754,18 @@ k_gather_fast(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restric
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             if (j < nb) {
-                const Rec<T> r = wrec[j];
                 const int cl = wcell[j];
                 const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
-                T wx[P];
-                cx.all(r.x0[0], wx);
+                const T* wj = ww + j * WSP;
                 const int base0 = lx * PLANE + ly * PZ + lz;
 #pragma unroll
                 for (int jr = 0; jr < NR; ++jr) {
                     if (ract[jr]) {
-                        const T wyz = py[jr].eval(r.x0[1]) * pz[jr].eval(r.x0[2]);
+                        const T wyz = wj[P + riy[jr]] * wj[2 * P + riz[jr]];
                         const int o0 = base0 + roff[jr];
 #pragma unroll
                         for (int a = 0; a < P; ++a) {
-                            const T w = wx[a] * wyz;
+                            const T w = wj[a] * wyz;
                             const int o = o0 + a * PLANE;
                             v[4 * j] += w * fx[o];
                             v[4 * j + 1] += w * fy[o];
@@ -734,25 +788,179 @@ k_gather_fast(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restric
             }
         }
         const int site = lane >> 2, comp = lane & 3;
-        if (site < nb && comp < 3) {
-            const T sc = (T)prefactor * wrec[site].q;
-            forces[3 * (int64_t)worig[site] + comp] = (Out)(sc * v[0]);
-        }
+        if (site < nb && comp < 3) forces[3 * (int64_t)worig[site] + comp] = (Out)((T)prefactor * v[0]);
         __syncwarp();
     }
 }
 
 template <typename T, int P, int TILE, typename Out>
-static cudaError_t gather_fast(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                               const int* scell, const int* sorig, const T* fields, double prefactor, Out* forces) {
-    constexpr int E = TILE + P - 1, PZ = E | 1;
-    const size_t smem = kGatherWarps * 8 * sizeof(Rec<T>) + (3 * (size_t)E * E * PZ * sizeof(T) + 31) / 32 * 32 +
-                        kGatherWarps * 8 * 2 * sizeof(int) + 3 * E * sizeof(int);
+static cudaError_t gather_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+                               const int* sorig, const T* swt, const T* fields, double prefactor, Out* forces) {
+    constexpr int E = TILE + P - 1, PZ = E | 1, WSP = wstride(P) + 4;
+    const size_t smem = (kGatherWarps * 8 * WSP * sizeof(T) + 31) / 32 * 32 +
+                        (3 * (size_t)E * E * PZ * sizeof(T) + 31) / 32 * 32 + kGatherWarps * 8 * 2 * sizeof(int) +
+                        3 * E * sizeof(int);
     cudaError_t e = cudaFuncSetAttribute(k_gather_fast<T, P, TILE, Out>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gather_fast<T, P, TILE, Out><<<g.ntiles, kGatherWarps * 32, smem, s>>>(g, tile_start, srec, scell, sorig,
+    k_gather_fast<T, P, TILE, Out><<<g.ntiles, kGatherWarps * 32, smem, s>>>(g, tile_start, scell, sorig, swt,
                                                                              fields, prefactor, forces);
+    return cudaGetLastError();
+}
+
+// Gather with TMA staging: the three padded field meshes form one 4D tensor
+// (z, y, x, field); the tile's stencil patch is the box starting at padded
+// coordinates (tz T, ty T, tx T, 0), fetched by a single cp.async.bulk.tensor
+// issued by one thread and waited on through an mbarrier.  The wait is
+// bounded: if it runs out the block records PPPM_ERR_TIMEOUT in the status
+// word (bit 2) and returns without touching the patch.
+constexpr long long kTmaSpinLimit = 1ll << 26;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+    for (long long it = 0; it < kTmaSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <typename T, int P, int TILE, typename Out>
+__global__ void __launch_bounds__(kGatherWarps * 32)
+k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
+             const int* __restrict__ sorig, const T* __restrict__ swt, const __grid_constant__ CUtensorMap tmap,
+             double prefactor, Out* __restrict__ forces, int* __restrict__ status) {
+    constexpr int E = TILE + P - 1, EZ = (E + 3) & ~3, PLANE = E * EZ, PSIZE = E * PLANE;
+    constexpr int WS = wstride(P), WSP = WS + 4;
+    constexpr uint32_t TX_BYTES = 3u * PSIZE * sizeof(T);
+    constexpr size_t FIELD_BYTES = (3 * PSIZE * sizeof(T) + 127) / 128 * 128;
+    constexpr size_t STAGE_BYTES = (kGatherWarps * 8 * WSP * sizeof(T) + 31) / 32 * 32;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* fx = reinterpret_cast<T*>(smem_raw);  // TMA box: [field][x][y][z]
+    T* fy = fx + PSIZE;
+    T* fz = fy + PSIZE;
+    T* st_w = reinterpret_cast<T*>(smem_raw + FIELD_BYTES);  // [warps][8][WSP]
+    int* st_cell = reinterpret_cast<int*>(smem_raw + FIELD_BYTES + STAGE_BYTES);
+    int* st_orig = st_cell + kGatherWarps * 8;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(st_orig + kGatherWarps * 8);
+    const int tile = blockIdx.x;
+    const int s0 = tile_start[tile], s1 = tile_start[tile + 1];
+    if (s0 == s1) return;  // uniform across the block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int tx = tile / (g.nt[1] * g.nt[2]);
+        const int ty = (tile / g.nt[2]) % g.nt[1];
+        const int tz = tile % g.nt[2];
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(fx);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_s), "r"(TX_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(tz * TILE), "r"(ty * TILE), "r"(tx * TILE), "r"(0),
+            "r"(mbar_s)
+            : "memory");
+    }
+    constexpr int NR = (P * P + 31) / 32;
+    int roff[NR], riy[NR], riz[NR];
+    bool ract[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const int row = lane + 32 * j;
+        ract[j] = row < P * P;
+        riy[j] = ract[j] ? row / P : 0;
+        riz[j] = ract[j] ? row % P : 0;
+        roff[j] = riy[j] * EZ + riz[j];
+    }
+    if (!mbar_wait_bounded(mbar_s, 0)) {
+        if (threadIdx.x == 0) atomicOr(status, 2);
+        mbar_wait_bounded(mbar_s, 0);  // give the copy in flight a second bounded chance to land
+        return;
+    }
+    T* ww = st_w + warp * 8 * WSP;
+    int* wcell = st_cell + warp * 8;
+    int* worig = st_orig + warp * 8;
+    const int nsites = s1 - s0;
+    for (int b = warp * 8; b < nsites; b += kGatherWarps * 8) {
+        const int nb = min(8, nsites - b);
+        for (int k = lane; k < nb * WS; k += 32) {
+            const int j = k / WS, a = k - j * WS;
+            ww[j * WSP + a] = swt[(size_t)(s0 + b + j) * WS + a];
+        }
+        if (lane < nb) {
+            wcell[lane] = scell[s0 + b + lane];
+            worig[lane] = sorig[s0 + b + lane];
+        }
+        __syncwarp();
+        T v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j < nb) {
+                const int cl = wcell[j];
+                const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+                const T* wj = ww + j * WSP;
+                const int base0 = lx * PLANE + ly * EZ + lz;
+#pragma unroll
+                for (int jr = 0; jr < NR; ++jr) {
+                    if (ract[jr]) {
+                        const T wyz = wj[P + riy[jr]] * wj[2 * P + riz[jr]];
+                        const int o0 = base0 + roff[jr];
+#pragma unroll
+                        for (int a = 0; a < P; ++a) {
+                            const T w = wj[a] * wyz;
+                            const int o = o0 + a * PLANE;
+                            v[4 * j] += w * fx[o];
+                            v[4 * j + 1] += w * fy[o];
+                            v[4 * j + 2] += w * fz[o];
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+            const bool up = (lane & h) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const T send = up ? v[i] : v[i + h];
+                const T keep = up ? v[i + h] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+            }
+        }
+        const int site = lane >> 2, comp = lane & 3;
+        if (site < nb && comp < 3) forces[3 * (int64_t)worig[site] + comp] = (Out)((T)prefactor * v[0]);
+        __syncwarp();
+    }
+}
+
+template <typename T, int P, int TILE, typename Out>
+static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+                              const int* sorig, const T* swt, const void* tmap, double prefactor, Out* forces,
+                              int* status) {
+    constexpr int E = TILE + P - 1, EZ = (E + 3) & ~3, WSP = wstride(P) + 4;
+    const size_t smem = (3 * (size_t)E * E * EZ * sizeof(T) + 127) / 128 * 128 +
+                        (kGatherWarps * 8 * WSP * sizeof(T) + 31) / 32 * 32 + kGatherWarps * 8 * 2 * sizeof(int) +
+                        16;
+    cudaError_t e = cudaFuncSetAttribute(k_gather_tma<T, P, TILE, Out>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gather_tma<T, P, TILE, Out><<<g.ntiles, kGatherWarps * 32, smem, s>>>(
+        g, tile_start, scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), prefactor, forces, status);
     return cudaGetLastError();
 }
 
@@ -766,7 +974,7 @@ __global__ void k_fold_rows(Geo g, const T* __restrict__ patch, const int* __res
     const int* ox = cov_off;
     const int* oy = cov_off + nmax1;
     const int* oz = cov_off + 2 * nmax1;
-    const int psz = g.E[0] * g.E[1] * g.E[2];
+    const int psz = g.E[0] * g.E[1] * g.Pz;
     const int ax0 = __ldg(&ox[x]), ax1 = __ldg(&ox[x + 1]);
     const int ay0 = __ldg(&oy[y]), ay1 = __ldg(&oy[y + 1]);
     T* out = rho + (int64_t)row * g.N[2];
@@ -778,7 +986,7 @@ __global__ void k_fold_rows(Geo g, const T* __restrict__ patch, const int* __res
             for (int b = ay0; b < ay1; ++b) {
                 const int2 ey = __ldg(&cov_ent[b]);
                 const int tb = (ex.x * g.nt[1] + ey.x) * g.nt[2];
-                const int ob = (ex.y * g.E[1] + ey.y) * g.E[2];
+                const int ob = (ex.y * g.E[1] + ey.y) * g.Pz;
                 for (int c = az0; c < az1; ++c) {
                     const int2 ez = __ldg(&cov_ent[c]);
                     sum += patch[(size_t)(tb + ez.x) * psz + ob + ez.y];
@@ -805,10 +1013,10 @@ cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int*
 
 // ------------------------------------------------------------------ instantiations
 #define PPPM_INST_T(T)                                                                                          \
-    template cudaError_t launch_scatter<T>(cudaStream_t, int, const int*, const int*, const int*, const Rec<T>*, \
-                                           const int*, Rec<T>*, int*, int*);                                     \
+    template cudaError_t launch_scatter<T>(cudaStream_t, const Geo&, int, const int*, const int*, const int*,     \
+                                           const Rec<T>*, const int*, Rec<T>*, int*, int*, T*);                  \
     template cudaError_t launch_spread<T>(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*,       \
-                                          const int*, T*);                                                       \
+                                          const int*, const T*, T*);                                             \
     template cudaError_t launch_fold<T>(cudaStream_t, const Geo&, const T*, const int*, const int2*, T, T*);
 PPPM_INST_T(float)
 PPPM_INST_T(double)
@@ -816,7 +1024,8 @@ PPPM_INST_T(double)
     template cudaError_t launch_bin<T, I>(cudaStream_t, const Geo&, const I*, const I*, int, int*, int*, int*,   \
                                           Rec<T>*, int*, int*);                                                   \
     template cudaError_t launch_gather<T, I>(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*,     \
-                                             const int*, const T*, double, I*);
+                                             const int*, const T*, const T*, const FieldLayout&, const void*,    \
+                                             double, I*, int*);
 PPPM_INST_TI(float, float)
 PPPM_INST_TI(float, double)
 PPPM_INST_TI(double, float)
