@@ -151,6 +151,50 @@ int pppm_influence(pppm_plan *plan, double *G);
 int pppm_fields(pppm_plan *plan, void *stream, const double *pos, const double *q, int64_t n, void *fields);
 
 /*
+ * Batched form: many independent orthorhombic boxes (e.g. water boxes of
+ * uneven size) evaluated by ONE persistent kernel launch, recorded in a CUDA
+ * graph and replayed on later calls with the same pointers.  FP32 arithmetic
+ * as in PPPM_FP32 plans.  The paper evaluates one box per run; batching is this
+ * library's own form, not a method of the paper.
+ *
+ * pppm_batch_create
+ *   nbox           number of boxes, 1..65535
+ *   boxes          nbox x 3 edge lengths (host)
+ *   meshes         nbox x 3 mesh sizes (host), or NULL: per axis the smallest
+ *                  2^a 3^b 5^c >= L / 1.2 (spacing <= 1.2 Angstrom); every size
+ *                  must be 2^a 3^b 5^c in [order + 7, 512]
+ *   order          3, 5 or 7
+ *   beta           as in pppm_create
+ * pppm_compute_batched
+ *   pos, q         all boxes' sites concatenated (float, device), box b owning
+ *                  sites offsets[b] .. offsets[b+1]-1
+ *   offsets        nbox + 1 int64 (DEVICE); read back to the host on each call
+ *                  (a synchronization point) to detect a change of layout
+ *   energies       nbox doubles (device); virials nbox x 6 doubles (device)
+ *   forces         n x 3 floats (device), in the concatenated site order
+ *   The first call (and every call after the offsets change) times both tile
+ *   edges (4 and 8 mesh cells) and keeps the faster: the autotuner.  Unless the
+ *   stream is capturing or is the legacy stream, the work is recorded into a
+ *   CUDA graph, re-recorded when any pointer changes.
+ *   Stage dependencies inside the kernel are bounded waits; a wait that runs
+ *   out sets PPPM_ERR_TIMEOUT in the batch status (pppm_batch_status).
+ * pppm_batch_set       prefactor, tile edge (0 = autotune, 4, 8) and the spin
+ *                      limit of the bounded waits.
+ * pppm_batch_meshes    copy the nbox x 3 meshes in use to a host array.
+ * pppm_batch_tile      tile edge in use (0 before the first call).
+ */
+typedef struct pppm_batch pppm_batch;
+int pppm_batch_create(int nbox, const double *boxes, const int *meshes, int order, double beta,
+                      pppm_batch **out);
+int pppm_batch_set(pppm_batch *batch, double prefactor, int tile, long long spin_limit);
+int pppm_batch_meshes(const pppm_batch *batch, int *meshes);
+int pppm_batch_tile(const pppm_batch *batch);
+int pppm_compute_batched(pppm_batch *batch, void *stream, const float *pos, const float *q,
+                         const int64_t *offsets, double *energies, float *forces, double *virials);
+int pppm_batch_status(pppm_batch *batch);
+void pppm_batch_destroy(pppm_batch *batch);
+
+/*
  * pppm_spread_noalloc -- the charge spread of pppm_spread (FP32 arithmetic,
  * float density rho, same layout and scaling) for callers that cannot
  * allocate device memory: code running inside a host callback or an allocator

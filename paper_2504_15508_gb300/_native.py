@@ -68,6 +68,13 @@ SIGNATURES = {
     "pppm_influence": (cint, [vp, vp]),
     "pppm_fields": (cint, [vp, vp, vp, vp, i64, vp]),
     "pppm_spread_noalloc": (cint, [ctypes.POINTER(dbl), ctypes.POINTER(cint), cint, vp, vp, vp, i64, vp]),
+    "pppm_batch_create": (cint, [cint, ctypes.POINTER(dbl), ctypes.POINTER(cint), cint, dbl, ctypes.POINTER(vp)]),
+    "pppm_batch_set": (cint, [vp, dbl, cint, ctypes.c_longlong]),
+    "pppm_batch_meshes": (cint, [vp, ctypes.POINTER(cint)]),
+    "pppm_batch_tile": (cint, [vp]),
+    "pppm_compute_batched": (cint, [vp, vp, vp, vp, vp, vp, vp, vp]),
+    "pppm_batch_status": (cint, [vp]),
+    "pppm_batch_destroy": (None, [vp]),
     "pppm_profile_enable": (cint, [vp, cint]),
     "pppm_profile_read": (cint, [vp, vp, vp, cint]),
     "pppm_profile_name": (ctypes.c_char_p, [cint]),

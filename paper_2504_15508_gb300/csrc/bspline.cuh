@@ -16,10 +16,48 @@
 
 namespace pppm {
 
-// c_bsp[p][j][m]: coefficient of x0^m in piece j of the order-p B-spline
-// (this header is included by one translation unit only, which fills them).
-__constant__ double c_bsp_d[kMaxOrder + 1][kMaxOrder][kMaxOrder];
-__constant__ float c_bsp_f[kMaxOrder + 1][kMaxOrder][kMaxOrder];
+// c_bsp[p][j][m]: coefficient of x0^m in piece j of the order-p B-spline.
+// Each translation unit that includes this header has its own copy, filled by
+// bsp_upload_this_unit() (called at plan creation, never during capture).
+static __constant__ double c_bsp_d[kMaxOrder + 1][kMaxOrder][kMaxOrder];
+static __constant__ float c_bsp_f[kMaxOrder + 1][kMaxOrder][kMaxOrder];
+
+// Piece coefficients of N_p on [0, 1] for p = 1..7, from the Cox-de Boor
+// recursion carried out on polynomials in x0 (FP64 on the host).
+static void bsp_upload_this_unit() {
+    static bool done = false;
+    if (done) return;
+    double cd[kMaxOrder + 1][kMaxOrder][kMaxOrder] = {};
+    float cf[kMaxOrder + 1][kMaxOrder][kMaxOrder] = {};
+    // piece j of N_m as a polynomial in x0: poly[j][k] = coefficient of x0^k, for t = x0 + j.
+    double poly[kMaxOrder][kMaxOrder] = {};
+    poly[0][0] = 1.0;  // N_1(x0) = 1 on [0, 1]
+    for (int p = 1; p <= kMaxOrder; ++p) {
+        if (p > 1) {
+            double nxt[kMaxOrder][kMaxOrder] = {};
+            for (int j = 0; j < p; ++j) {
+                // N_p(x0 + j) = ((x0 + j) N_{p-1}(x0 + j) + (p - x0 - j) N_{p-1}(x0 + j - 1)) / (p - 1)
+                for (int k = 0; k < p - 1; ++k) {
+                    const double a = (j < p - 1) ? poly[j][k] : 0.0;  // N_{p-1}(x0 + j)
+                    const double b = (j >= 1) ? poly[j - 1][k] : 0.0; // N_{p-1}(x0 + j - 1)
+                    nxt[j][k + 1] += a - b;                            // x0 * (a - b)
+                    nxt[j][k] += j * a + (p - j) * b;
+                }
+                for (int k = 0; k < p; ++k) nxt[j][k] /= (p - 1);
+            }
+            for (int j = 0; j < kMaxOrder; ++j)
+                for (int k = 0; k < kMaxOrder; ++k) poly[j][k] = nxt[j][k];
+        }
+        for (int j = 0; j < p; ++j)
+            for (int k = 0; k < p; ++k) {
+                cd[p][j][k] = poly[j][k];
+                cf[p][j][k] = (float)poly[j][k];
+            }
+    }
+    cudaMemcpyToSymbol(c_bsp_d, cd, sizeof(cd));
+    cudaMemcpyToSymbol(c_bsp_f, cf, sizeof(cf));
+    done = true;
+}
 
 template <typename T> __device__ __forceinline__ T bsp_coef(int p, int j, int m);
 template <> __device__ __forceinline__ float bsp_coef<float>(int p, int j, int m) { return c_bsp_f[p][j][m]; }

@@ -111,6 +111,13 @@ cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, c
                           const int* scell, const int* sorig, const T* swt, const T* fields, const FieldLayout& fl,
                           const void* tmap, double prefactor, Out* forces, int* status);
 void upload_bspline_coefficients();
+// full-tile fast paths (cudaErrorNotSupported when the order/tile has none)
+template <typename T>
+cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+                               const int* sorig, const T* swt, T* patch);
+template <typename T, typename Out>
+cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell, const int* sorig,
+                              const T* swt, const void* tmap, double prefactor, Out* forces, int* status);
 
 // fft_kernels.cu
 template <typename T>

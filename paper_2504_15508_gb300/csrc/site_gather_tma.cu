@@ -1,0 +1,201 @@
+// Force interpolation with TMA-staged field patches (padded field meshes,
+// compile-time tile edge and order, precomputed per-site weights).
+#include <climits>
+
+#include <cuda.h>
+
+#include "internal.cuh"
+
+namespace pppm {
+
+constexpr int kGatherWarps = 4;
+
+// Gather with TMA staging: the three padded field meshes form one 4D tensor
+// (z, y, x, field); the tile's stencil patch is the box starting at padded
+// coordinates (tz T, ty T, tx T, 0), fetched by a single cp.async.bulk.tensor
+// issued by one thread and waited on through an mbarrier.  The wait is
+// bounded: if it runs out the block records PPPM_ERR_TIMEOUT in the status
+// word (bit 2) and returns without touching the patch.
+constexpr long long kTmaSpinLimit = 1ll << 26;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+    for (long long it = 0; it < kTmaSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <typename T, int P, int TILE, typename Out>
+__global__ void __launch_bounds__(kGatherWarps * 32)
+k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
+             const int* __restrict__ sorig, const T* __restrict__ swt, const __grid_constant__ CUtensorMap tmap,
+             double prefactor, Out* __restrict__ forces, int* __restrict__ status) {
+    constexpr int E = TILE + P - 1, EZ = (E + 3) & ~3, PLANE = E * EZ, PSIZE = E * PLANE;
+    constexpr int WS = wstride(P), WSP = WS + 4;
+    constexpr uint32_t TX_BYTES = 3u * PSIZE * sizeof(T);
+    constexpr size_t FIELD_BYTES = (3 * PSIZE * sizeof(T) + 127) / 128 * 128;
+    constexpr size_t STAGE_BYTES = (kGatherWarps * 8 * WSP * sizeof(T) + 31) / 32 * 32;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* fx = reinterpret_cast<T*>(smem_raw);  // TMA box: [field][x][y][z]
+    T* fy = fx + PSIZE;
+    T* fz = fy + PSIZE;
+    T* st_w = reinterpret_cast<T*>(smem_raw + FIELD_BYTES);  // [warps][8][WSP]
+    int* st_cell = reinterpret_cast<int*>(smem_raw + FIELD_BYTES + STAGE_BYTES);
+    int* st_orig = st_cell + kGatherWarps * 8;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(st_orig + kGatherWarps * 8);
+    const int tile = blockIdx.x;
+    const int s0 = tile_start[tile], s1 = tile_start[tile + 1];
+    if (s0 == s1) return;  // uniform across the block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int tx = tile / (g.nt[1] * g.nt[2]);
+        const int ty = (tile / g.nt[2]) % g.nt[1];
+        const int tz = tile % g.nt[2];
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(fx);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_s), "r"(TX_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(tz * TILE), "r"(ty * TILE), "r"(tx * TILE), "r"(0),
+            "r"(mbar_s)
+            : "memory");
+    }
+    constexpr int NR = (P * P + 31) / 32;
+    int roff[NR], riy[NR], riz[NR];
+    bool ract[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const int row = lane + 32 * j;
+        ract[j] = row < P * P;
+        riy[j] = ract[j] ? row / P : 0;
+        riz[j] = ract[j] ? row % P : 0;
+        roff[j] = riy[j] * EZ + riz[j];
+    }
+    if (!mbar_wait_bounded(mbar_s, 0)) {
+        if (threadIdx.x == 0) atomicOr(status, 2);
+        mbar_wait_bounded(mbar_s, 0);  // give the copy in flight a second bounded chance to land
+        return;
+    }
+    T* ww = st_w + warp * 8 * WSP;
+    int* wcell = st_cell + warp * 8;
+    int* worig = st_orig + warp * 8;
+    const int nsites = s1 - s0;
+    for (int b = warp * 8; b < nsites; b += kGatherWarps * 8) {
+        const int nb = min(8, nsites - b);
+        for (int k = lane; k < nb * WS; k += 32) {
+            const int j = k / WS, a = k - j * WS;
+            ww[j * WSP + a] = swt[(size_t)(s0 + b + j) * WS + a];
+        }
+        if (lane < nb) {
+            wcell[lane] = scell[s0 + b + lane];
+            worig[lane] = sorig[s0 + b + lane];
+        }
+        __syncwarp();
+        T v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j < nb) {
+                const int cl = wcell[j];
+                const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+                const T* wj = ww + j * WSP;
+                const int base0 = lx * PLANE + ly * EZ + lz;
+#pragma unroll
+                for (int jr = 0; jr < NR; ++jr) {
+                    if (ract[jr]) {
+                        const T wyz = wj[P + riy[jr]] * wj[2 * P + riz[jr]];
+                        const int o0 = base0 + roff[jr];
+#pragma unroll
+                        for (int a = 0; a < P; ++a) {
+                            const T w = wj[a] * wyz;
+                            const int o = o0 + a * PLANE;
+                            v[4 * j] += w * fx[o];
+                            v[4 * j + 1] += w * fy[o];
+                            v[4 * j + 2] += w * fz[o];
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+            const bool up = (lane & h) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const T send = up ? v[i] : v[i + h];
+                const T keep = up ? v[i + h] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+            }
+        }
+        const int site = lane >> 2, comp = lane & 3;
+        if (site < nb && comp < 3) forces[3 * (int64_t)worig[site] + comp] = (Out)((T)prefactor * v[0]);
+        __syncwarp();
+    }
+}
+
+template <typename T, int P, int TILE, typename Out>
+static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+                              const int* sorig, const T* swt, const void* tmap, double prefactor, Out* forces,
+                              int* status) {
+    constexpr int E = TILE + P - 1, EZ = (E + 3) & ~3, WSP = wstride(P) + 4;
+    const size_t smem = (3 * (size_t)E * E * EZ * sizeof(T) + 127) / 128 * 128 +
+                        (kGatherWarps * 8 * WSP * sizeof(T) + 31) / 32 * 32 + kGatherWarps * 8 * 2 * sizeof(int) +
+                        16;
+    cudaError_t e = cudaFuncSetAttribute(k_gather_tma<T, P, TILE, Out>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gather_tma<T, P, TILE, Out><<<g.ntiles, kGatherWarps * 32, smem, s>>>(
+        g, tile_start, scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), prefactor, forces, status);
+    return cudaGetLastError();
+}
+
+#define PPPM_FAST_SWITCH_G(FN, T_, O_, ...)                                                       \
+    switch (g.order * 16 + g.T) {                                                                 \
+        case 2 * 16 + 4: return FN<T_, 2, 4, O_>(__VA_ARGS__);                                    \
+        case 2 * 16 + 8: return FN<T_, 2, 8, O_>(__VA_ARGS__);                                    \
+        case 3 * 16 + 4: return FN<T_, 3, 4, O_>(__VA_ARGS__);                                    \
+        case 3 * 16 + 8: return FN<T_, 3, 8, O_>(__VA_ARGS__);                                    \
+        case 4 * 16 + 4: return FN<T_, 4, 4, O_>(__VA_ARGS__);                                    \
+        case 4 * 16 + 8: return FN<T_, 4, 8, O_>(__VA_ARGS__);                                    \
+        case 5 * 16 + 4: return FN<T_, 5, 4, O_>(__VA_ARGS__);                                    \
+        case 5 * 16 + 8: return FN<T_, 5, 8, O_>(__VA_ARGS__);                                    \
+        case 6 * 16 + 4: return FN<T_, 6, 4, O_>(__VA_ARGS__);                                    \
+        case 6 * 16 + 8: return FN<T_, 6, 8, O_>(__VA_ARGS__);                                    \
+        case 7 * 16 + 4: return FN<T_, 7, 4, O_>(__VA_ARGS__);                                    \
+        case 7 * 16 + 8: return FN<T_, 7, 8, O_>(__VA_ARGS__);                                    \
+    }
+
+
+template <typename T, typename Out>
+cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell, const int* sorig,
+                              const T* swt, const void* tmap, double prefactor, Out* forces, int* status) {
+    PPPM_FAST_SWITCH_G(gather_tma, T, Out, s, g, tile_start, scell, sorig, swt, tmap, prefactor, forces, status)
+    return cudaErrorNotSupported;
+}
+
+#define PPPM_INST_G(T, O)                                                                                       \
+    template cudaError_t launch_gather_tma<T, O>(cudaStream_t, const Geo&, const int*, const int*, const int*,   \
+                                                 const T*, const void*, double, O*, int*);
+PPPM_INST_G(float, float)
+PPPM_INST_G(float, double)
+PPPM_INST_G(double, float)
+PPPM_INST_G(double, double)
+
+}  // namespace pppm

@@ -1,0 +1,158 @@
+// Fast charge spread: tile edge and order are compile-time constants, the
+// per-site B-spline weights come precomputed from the scatter, and every axis
+// holds at least one full tile.
+#include <climits>
+
+#include <cuda.h>
+
+#include "internal.cuh"
+
+namespace pppm {
+
+constexpr int kSpreadWarps = 4;
+//
+// The kernels below are the ones the workloads run: tile edge and order are
+// compile-time constants (so every index is constant arithmetic) and every
+// axis has at least one full tile (N >= T).  The kernels above stay as the
+// general path for meshes smaller than a tile.
+
+constexpr int kFastCap = 256;  // sites per tile ordered by index in the fast spread
+
+// Spread: as k_spread, with the tile's records staged through shared memory in
+// batches of 32 (one coalesced load per lane instead of one dependent load per
+// site) and a padded patch pitch (PZ odd) that keeps the p^2 stencil rows of a
+// site in distinct banks.
+template <typename T, int P, int TILE>
+struct SpreadWarpSmem {
+    static constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
+    static constexpr int WSP = wstride(P) + 4;  // staging row pitch (keeps vector stores conflict-light)
+    T st_w[32][WSP];
+    T pt[PSIZE];
+    int st_cell[32];
+    int2 keys[kFastCap];
+};
+
+template <typename T, int P, int TILE>
+__global__ void __launch_bounds__(kSpreadWarps * 32)
+k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
+              const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch) {
+    typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
+    constexpr int E = WarpSmem::E, PZ = WarpSmem::PZ, PLANE = WarpSmem::PLANE, PSIZE = WarpSmem::PSIZE;
+    constexpr int WS = wstride(P);
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * kSpreadWarps + warp;
+    WarpSmem& W = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
+    if (tile >= g.ntiles) return;  // whole warp; no block-level barrier below
+    for (int i = lane; i < PSIZE; i += 32) W.pt[i] = T(0);
+    const int s0 = tile_start[tile];
+    const int c = tile_start[tile + 1] - s0;
+    const bool sorted = c > 1 && c <= kFastCap;
+    if (sorted) {
+        int cp = 2;
+        while (cp < c) cp <<= 1;
+        for (int i = lane; i < cp; i += 32)
+            W.keys[i] = i < c ? make_int2(sorig[s0 + i], s0 + i) : make_int2(INT_MAX, -1);
+        __syncwarp();
+        for (int k = 2; k <= cp; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < cp; i += 32) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const int2 a = W.keys[i], b = W.keys[ixj];
+                        if ((a.x > b.x) == ((i & k) == 0)) { W.keys[i] = b; W.keys[ixj] = a; }
+                    }
+                }
+                __syncwarp();
+            }
+    }
+    __syncwarp();
+    // lane -> stencil rows (iy, iz); orders above 5 have more rows than lanes
+    constexpr int NR = (P * P + 31) / 32;
+    int roff[NR], riy[NR], riz[NR];
+    bool ract[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const int row = lane + 32 * j;
+        ract[j] = row < P * P;
+        riy[j] = ract[j] ? row / P : 0;
+        riz[j] = ract[j] ? row % P : 0;
+        roff[j] = riy[j] * PZ + riz[j];
+    }
+    for (int t0 = 0; t0 < c; t0 += 32) {
+        const int nb = min(32, c - t0);
+        if (lane < nb) {
+            const int s = sorted ? W.keys[t0 + lane].y : s0 + t0 + lane;
+            const T* src = swt + (size_t)s * WS;
+#pragma unroll
+            for (int a = 0; a < WS; ++a) W.st_w[lane][a] = src[a];
+            W.st_cell[lane] = scell[s];
+        }
+        __syncwarp();
+        for (int j = 0; j < nb; ++j) {
+            const int cl = W.st_cell[j];
+            const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+            T wxq[P];
+#pragma unroll
+            for (int a = 0; a < P; ++a) wxq[a] = W.st_w[j][a];
+            T* base0 = W.pt + lx * PLANE + ly * PZ + lz;
+#pragma unroll
+            for (int jr = 0; jr < NR; ++jr) {
+                if (ract[jr]) {
+                    const T wyz = W.st_w[j][P + riy[jr]] * W.st_w[j][2 * P + riz[jr]];
+                    T* b = base0 + roff[jr];
+#pragma unroll
+                    for (int a = 0; a < P; ++a) b[a * PLANE] += wxq[a] * wyz;
+                }
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+    T* dst = patch + (size_t)tile * PSIZE;  // same padded layout as the shared patch
+    for (int i = lane; i < PSIZE; i += 32) dst[i] = W.pt[i];
+}
+
+template <typename T, int P, int TILE>
+static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+                               const int* sorig, const T* swt, T* patch) {
+    const size_t smem = kSpreadWarps * sizeof(SpreadWarpSmem<T, P, TILE>);
+    cudaError_t e = cudaFuncSetAttribute(k_spread_fast<T, P, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
+    k_spread_fast<T, P, TILE><<<blocks, kSpreadWarps * 32, smem, s>>>(g, tile_start, scell, sorig, swt, patch);
+    return cudaGetLastError();
+}
+
+
+#define PPPM_FAST_SWITCH(FN, T_, ...)                                                             \
+    switch (g.order * 16 + g.T) {                                                                 \
+        case 2 * 16 + 4: return FN<T_, 2, 4>(__VA_ARGS__);                                        \
+        case 2 * 16 + 8: return FN<T_, 2, 8>(__VA_ARGS__);                                        \
+        case 3 * 16 + 4: return FN<T_, 3, 4>(__VA_ARGS__);                                        \
+        case 3 * 16 + 8: return FN<T_, 3, 8>(__VA_ARGS__);                                        \
+        case 4 * 16 + 4: return FN<T_, 4, 4>(__VA_ARGS__);                                        \
+        case 4 * 16 + 8: return FN<T_, 4, 8>(__VA_ARGS__);                                        \
+        case 5 * 16 + 4: return FN<T_, 5, 4>(__VA_ARGS__);                                        \
+        case 5 * 16 + 8: return FN<T_, 5, 8>(__VA_ARGS__);                                        \
+        case 6 * 16 + 4: return FN<T_, 6, 4>(__VA_ARGS__);                                        \
+        case 6 * 16 + 8: return FN<T_, 6, 8>(__VA_ARGS__);                                        \
+        case 7 * 16 + 4: return FN<T_, 7, 4>(__VA_ARGS__);                                        \
+        case 7 * 16 + 8: return FN<T_, 7, 8>(__VA_ARGS__);                                        \
+    }
+
+
+template <typename T>
+cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+                               const int* sorig, const T* swt, T* patch) {
+    PPPM_FAST_SWITCH(spread_fast, T, s, g, tile_start, scell, sorig, swt, patch)
+    return cudaErrorNotSupported;
+}
+
+template cudaError_t launch_spread_fast<float>(cudaStream_t, const Geo&, const int*, const int*, const int*,
+                                               const float*, float*);
+template cudaError_t launch_spread_fast<double>(cudaStream_t, const Geo&, const int*, const int*, const int*,
+                                                const double*, double*);
+
+}  // namespace pppm

@@ -175,3 +175,74 @@ class Plan:
         N.check(self._lib.pppm_fields(self._h, _stream(stream), _ptr(pos), _ptr(q), pos.shape[0], _ptr(f)),
                 "pppm_fields")
         return f
+
+
+class BatchPlan:
+    """Many independent boxes in one persistent launch (FP32).
+
+    boxes: (nbox, 3) edge lengths; meshes: (nbox, 3) or None for about 1.2 A
+    spacing rounded up to 2^a 3^b 5^c; order 3, 5 or 7.
+    """
+
+    def __init__(self, boxes, meshes=None, order: int = 5, beta: float = 0.4, prefactor: float = 1.0,
+                 tile: int = 0, spin_limit: int = 1 << 24):
+        L = N.lib()
+        self._lib = L
+        boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+        self.nbox = boxes.shape[0]
+        h = ctypes.c_void_p()
+        mp = None
+        if meshes is not None:
+            m = np.ascontiguousarray(meshes, dtype=np.int32).reshape(-1, 3)
+            mp = m.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        N.check(L.pppm_batch_create(self.nbox, boxes.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mp,
+                                    int(order), float(beta), ctypes.byref(h)), "pppm_batch_create")
+        self._h = h
+        self.boxes = boxes
+        self.set(prefactor=prefactor, tile=tile, spin_limit=spin_limit)
+
+    def set(self, prefactor: float = 1.0, tile: int = 0, spin_limit: int = 1 << 24):
+        N.check(self._lib.pppm_batch_set(self._h, float(prefactor), int(tile), int(spin_limit)), "pppm_batch_set")
+
+    @property
+    def meshes(self) -> np.ndarray:
+        m = np.zeros((self.nbox, 3), dtype=np.int32)
+        N.check(self._lib.pppm_batch_meshes(self._h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return m
+
+    @property
+    def tile(self) -> int:
+        return self._lib.pppm_batch_tile(self._h)
+
+    def status(self) -> int:
+        return self._lib.pppm_batch_status(self._h)
+
+    def compute(self, pos: torch.Tensor, q: torch.Tensor, offsets: torch.Tensor, out=None, stream=None):
+        """Energies (nbox,), forces (n, 3) and virials (nbox, 6) for the
+        concatenated float32 sites; box b owns offsets[b]:offsets[b+1]."""
+        if pos.dtype != torch.float32 or q.dtype != torch.float32 or offsets.dtype != torch.int64:
+            raise ValueError("pos and q must be float32, offsets int64")
+        if not (pos.is_cuda and q.is_cuda and offsets.is_cuda):
+            raise ValueError("tensors must be on the GPU")
+        n = pos.shape[0]
+        dev = pos.device
+        if out is None:
+            energies = torch.empty(self.nbox, dtype=torch.float64, device=dev)
+            forces = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            virials = torch.empty((self.nbox, 6), dtype=torch.float64, device=dev)
+        else:
+            energies, forces, virials = out
+        N.check(self._lib.pppm_compute_batched(self._h, _stream(stream), _ptr(pos), _ptr(q), _ptr(offsets),
+                                               _ptr(energies), _ptr(forces), _ptr(virials)), "pppm_compute_batched")
+        return energies, forces, virials
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pppm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

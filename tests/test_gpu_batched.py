@@ -1,0 +1,95 @@
+"""The batched form: many independent water boxes in one persistent launch,
+each equal to its own single-box evaluation within the FP32 tolerances
+(force RMS relative <= 1e-5, energy relative <= 1e-6 against the FP64 oracle)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.pppm import OraclePPPM
+from workloads.water import batched_boxes, make_water
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _make_batch(nbox, seed, lo=64, hi=700):
+    specs = batched_boxes(nbox=nbox, seed=seed, lo=lo, hi=hi)
+    boxes = [make_water(s["n_mol"], s["L"], s["seed"]) for s in specs]
+    pos = np.concatenate([b.pos for b in boxes]).astype(np.float32)
+    q = np.concatenate([b.q for b in boxes]).astype(np.float32)
+    offs = np.concatenate([[0], np.cumsum([b.n for b in boxes])]).astype(np.int64)
+    return specs, boxes, pos, q, offs
+
+
+@pytest.mark.parametrize("tile", [0, 4, 8])
+def test_batched_matches_oracle_per_box(cuda_device, pppm_lib, tile):
+    from paper_2504_15508_gb300.pppm import BatchPlan
+    specs, boxes, pos, q, offs = _make_batch(6, seed=5)
+    bp = BatchPlan(np.array([[s["L"]] * 3 for s in specs]), None, order=5, beta=0.4, tile=tile)
+    tp = torch.tensor(pos, device=cuda_device)
+    tq = torch.tensor(q, device=cuda_device)
+    to = torch.tensor(offs, device=cuda_device)
+    e, f, v = bp.compute(tp, tq, to)
+    torch.cuda.synchronize()
+    assert bp.status() == 0
+    meshes = bp.meshes
+    for b, wb in enumerate(boxes):
+        sl = slice(offs[b], offs[b + 1])
+        ref = OraclePPPM(wb.box, meshes[b], 5, 0.4).compute(pos[sl].astype(np.float64), q[sl].astype(np.float64))
+        ferr = _rel(f[sl].cpu().numpy(), ref["forces"])
+        eerr = abs(e[b].item() - ref["energy"]) / abs(ref["energy"])
+        verr = _rel(v[b].cpu().numpy(), ref["virial"])
+        assert ferr <= 1e-5 and eerr <= 1e-6 and verr <= 1e-5, (b, meshes[b], ferr, eerr, verr)
+
+
+def test_batched_graph_replay_and_single_box_equality(cuda_device, pppm_lib):
+    from paper_2504_15508_gb300.pppm import BatchPlan, Plan
+    specs, boxes, pos, q, offs = _make_batch(5, seed=7)
+    bp = BatchPlan(np.array([[s["L"]] * 3 for s in specs]), None, order=5, beta=0.4)
+    tp = torch.tensor(pos, device=cuda_device)
+    tq = torch.tensor(q, device=cuda_device)
+    to = torch.tensor(offs, device=cuda_device)
+    out = (torch.empty(5, dtype=torch.float64, device=cuda_device),
+           torch.empty((len(pos), 3), dtype=torch.float32, device=cuda_device),
+           torch.empty((5, 6), dtype=torch.float64, device=cuda_device))
+    r1 = [t.clone() for t in bp.compute(tp, tq, to, out=out)]   # tunes, then records the graph
+    r2 = [t.clone() for t in bp.compute(tp, tq, to, out=out)]   # replays it
+    torch.cuda.synchronize()
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)
+    assert bp.tile in (4, 8)
+    meshes = bp.meshes
+    for b, wb in enumerate(boxes):
+        sl = slice(offs[b], offs[b + 1])
+        plan = Plan(wb.box, meshes[b], 5, 0.4, precision="fp32", tile=bp.tile)
+        e, f, v = plan.compute(tp[sl].contiguous(), tq[sl].contiguous())
+        torch.cuda.synchronize()
+        # the batched kernels evaluate the same arithmetic in a different order
+        assert _rel(r2[1][sl].cpu().numpy(), f.cpu().numpy()) <= 1e-5
+        assert abs(r2[0][b].item() - e.item()) <= 1e-6 * abs(e.item())
+
+
+def test_batched_bounded_wait_times_out_cleanly(cuda_device, pppm_lib):
+    """With a spin limit of one iteration the stage waits run out: the launch
+    still ends, reports PPPM_ERR_TIMEOUT, and the next normal run is correct."""
+    from paper_2504_15508_gb300 import _native as N
+    from paper_2504_15508_gb300.pppm import BatchPlan
+    specs, boxes, pos, q, offs = _make_batch(4, seed=9)
+    bp = BatchPlan(np.array([[s["L"]] * 3 for s in specs]), None, order=5, beta=0.4, tile=8)
+    tp = torch.tensor(pos, device=cuda_device)
+    tq = torch.tensor(q, device=cuda_device)
+    to = torch.tensor(offs, device=cuda_device)
+    bp.set(tile=8, spin_limit=1)
+    bp.compute(tp, tq, to)
+    assert bp.status() in (N.PPPM_ERR_TIMEOUT, N.PPPM_OK)
+    bp.set(tile=8, spin_limit=1 << 24)
+    e, f, v = bp.compute(tp, tq, to)
+    torch.cuda.synchronize()
+    assert bp.status() == N.PPPM_OK
+    wb = boxes[0]
+    sl = slice(offs[0], offs[1])
+    ref = OraclePPPM(wb.box, bp.meshes[0], 5, 0.4).compute(pos[sl].astype(np.float64), q[sl].astype(np.float64))
+    assert _rel(f[sl].cpu().numpy(), ref["forces"]) <= 1e-5
