@@ -169,3 +169,16 @@ def batched_boxes(nbox: int = 96, seed: int = 5, lo: int = 64, hi: int = 8192,
         m = smooth_at_least(L / spacing)
         out.append(dict(n_mol=n_mol, L=L, mesh=(m, m, m), seed=1000 + b))
     return out
+
+
+def init_mlp_params(seed: int, n_in: int = 32, n_hidden: int = 64, n_out: int = 3) -> np.ndarray:
+    """Seeded initial parameters of the correction network, as one float32
+    vector [W1 (n_hidden x n_in), b1, W2 (n_hidden x n_hidden), b2,
+    W3 (n_out x n_hidden), b3]: Glorot-uniform weights, zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((n_hidden, n_in), (n_hidden, n_hidden), (n_out, n_hidden)):
+        lim = math.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
