@@ -221,6 +221,111 @@ int pppm_spread_noalloc(const double box[3], const int mesh[3], int order, void 
                         const double *pos, const double *q, int64_t n, float *rho);
 
 /*
+ * pppm_set_potential -- when on (nonzero), every later compute call of an FP32
+ * plan also writes the mesh potential phi (the inverse FFT of G(k) rho_hat(k),
+ * Eq. DPLR:EGt's reciprocal-space potential, same scaling as the field meshes)
+ * into the plan's own workspace as a fourth padded mesh; it costs one more
+ * inverse z pass.  Used by the correction network below.  Off by default.
+ */
+int pppm_set_potential(pppm_plan *plan, int on);
+
+/*
+ * Learned coarse-mesh correction.  A coarse-mesh FP32 PPPM is corrected per
+ * site by a small network over local features of the coarse mesh potential;
+ * the network is trained on forces of a fine-mesh PPPM of the same
+ * configurations.  The paper's accuracy table (Section "Evaluation",
+ * Table "Error of the energy and force") shows coarse FFT meshes keeping the
+ * force error of the fine one, which motivates a cheaper coarse solve; the
+ * network itself has no counterpart in the paper.
+ *
+ *   features x_i (48 BF16 values per site, row-major n x 48):
+ *     x_i[9 a + 3 b + c] = s_in * phi(r_i + h * (a-1, b-1, c-1)), a, b, c in
+ *     {0, 1, 2}, phi interpolated from the coarse potential mesh with the
+ *     plan's order-p B-spline weights (h = box / mesh per axis);
+ *     x_i[27 + t] = 1 for the site type t in {0, 1, 2}, 0 otherwise;
+ *     x_i[30 + 2 d] = sin(2 pi u_d), x_i[31 + 2 d] = cos(2 pi u_d), d = x, y,
+ *     z, with u_d = x_d N_d / L_d (the site's offset inside its mesh cell);
+ *     x_i[36..47] = 0.
+ *   network  h1 = tanh(W1 x + b1) (64), h2 = tanh(W2 h1 + b2) (64),
+ *            y = W3 h2 + b3 (3).  Parameters: one FP32 vector of
+ *            pppm_corr_nparams() = 7491 values [W1 64x48 row-major, b1, W2
+ *            64x64, b2, W3 3x64, b3].  Inference and training use them rounded
+ *            to BF16; accumulation is FP32.
+ *   forces   F_i = F_coarse,i + q_i * s_out * y_i.
+ *   training target t_i = (F_fine,i - F_coarse,i) / (q_i * s_out) (n x 3
+ *            FP32); loss = (1/nb) sum over the nb sites of |y_i - t_i|^2;
+ *            Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master weights.
+ *
+ * pppm_corr_create      borrow an FP32 coarse plan (it must outlive the
+ *                       corrector; its potential output is switched on);
+ *                       parameters start at zero, s_in = s_out = 1.
+ * pppm_corr_nparams     7491.
+ * pppm_corr_set_weights host FP32 parameters and the scales s_in, s_out (> 0);
+ *                       resets the Adam moments and step count.
+ * pppm_corr_get_weights host copy of the FP32 master parameters and scales
+ *                       (s_in, s_out may be NULL).
+ * pppm_corr_features    run the coarse PPPM on (pos, q) (device, FP32, n x 3
+ *                       and n), write its forces to forces (device n x 3) and
+ *                       the features to feat (device, n x 48 BF16, 96 B per
+ *                       row, 16-byte aligned); types is a device array of n
+ *                       signed chars.
+ * pppm_corr_calibrate   choose the scales from one configuration: runs the
+ *                       coarse PPPM and the features with s_in = 1, then sets
+ *                       s_in = 1 / rms of the 27 potential samples and
+ *                       s_out = rms over sites and axes of
+ *                       (F_fine - F_coarse) / q (f_fine: device n x 3, the
+ *                       fine-mesh forces of the same sites).  Synchronizes
+ *                       the stream; PPPM_ERR_NONFINITE if a scale is 0 or
+ *                       not finite.  Does not touch the parameters.
+ * pppm_corr_get_scales  current s_in, s_out.
+ * pppm_corr_targets     training targets t_i = (f_fine,i - f_coarse,i) /
+ *                       (q_i s_out), 0 where q_i = 0 (device n x 3 FP32).
+ * pppm_corr_forward     y = network(feat) for n feature rows -> out (device
+ *                       n x 3 FP32).
+ * pppm_corr_apply       corrected PPPM: coarse compute (energy, virial:
+ *                       device doubles, uncorrected) and forces + q s_out y.
+ * pppm_corr_grad        loss and its gradient w.r.t. the parameters over the
+ *                       nb rows idx[0..nb) of the nrows-row tables feat /
+ *                       target (idx device int32, NULL = rows 0..nb, then
+ *                       nb <= nrows; an index outside [0, nrows) counts as a
+ *                       row that contributes nothing); grad: device, 7491
+ *                       floats; loss: device float (may be NULL).
+ *                       Deterministic: fixed-order sums, no atomics.
+ * pppm_corr_train_step  the same gradient, then one Adam step with learning
+ *                       rate lr (> 0); the BF16 copies are refreshed.
+ * pppm_corr_save/load   binary checkpoint: "PPPMCORR", version 1, parameter
+ *                       count, s_in, s_out, Adam step, master parameters and
+ *                       both Adam moments.  Resuming from it continues
+ *                       training bit for bit.
+ * All calls are asynchronous on the given stream except set/get/save/load,
+ * which synchronize the device.  Errors: PPPM_ERR_INVALID_ARG for null or
+ * inconsistent arguments or an unreadable checkpoint, PPPM_ERR_CUDA.
+ */
+typedef struct pppm_corr pppm_corr;
+int pppm_corr_create(pppm_plan *coarse, pppm_corr **out);
+int pppm_corr_nparams(void);
+int pppm_corr_set_weights(pppm_corr *corr, const float *params, double s_in, double s_out);
+int pppm_corr_get_weights(const pppm_corr *corr, float *params, double *s_in, double *s_out);
+int pppm_corr_features(pppm_corr *corr, void *stream, const float *pos, const float *q,
+                       const signed char *types, int64_t n, void *feat, float *forces);
+int pppm_corr_calibrate(pppm_corr *corr, void *stream, const float *pos, const float *q,
+                        const signed char *types, int64_t n, const float *f_fine);
+int pppm_corr_get_scales(const pppm_corr *corr, double *s_in, double *s_out);
+int pppm_corr_targets(pppm_corr *corr, void *stream, const float *f_fine, const float *f_coarse,
+                      const float *q, int64_t n, float *target);
+int pppm_corr_forward(pppm_corr *corr, void *stream, const void *feat, int64_t n, float *out);
+int pppm_corr_apply(pppm_corr *corr, void *stream, const float *pos, const float *q,
+                    const signed char *types, int64_t n, double *energy, float *forces,
+                    double *virial);
+int pppm_corr_grad(pppm_corr *corr, void *stream, const void *feat, const float *target,
+                   int64_t nrows, const int *idx, int64_t nb, float *grad, float *loss);
+int pppm_corr_train_step(pppm_corr *corr, void *stream, const void *feat, const float *target,
+                         int64_t nrows, const int *idx, int64_t nb, float lr, float *loss);
+int pppm_corr_save(const pppm_corr *corr, const char *path);
+int pppm_corr_load(pppm_corr *corr, const char *path);
+void pppm_corr_destroy(pppm_corr *corr);
+
+/*
  * Per-kernel timing (for benchmarks).  While enabled, every kernel launch of a
  * compute call is bracketed by CUDA events on the compute stream.
  * pppm_profile_read synchronizes, writes for each kernel slot i < cap the

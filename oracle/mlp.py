@@ -1,15 +1,30 @@
 """FP64 CPU reference of the coarse-mesh correction network (test infrastructure only).
 
-The network maps per-site features (27 mesh-potential samples around the site
-and a one-hot site type, padded to 32 inputs) to 3 outputs through two tanh
-hidden layers of 64 units:
+The network maps per-site features (27 mesh-potential samples around the site,
+a one-hot site type and the site's position inside its mesh cell, padded to 48
+inputs) to 3 outputs through two tanh hidden layers of 64 units:
 
     h1 = tanh(W1 x + b1),  h2 = tanh(W2 h1 + b2),  y = W3 h2 + b3,
     loss = mean over sites of sum_c (y_c - t_c)^2.
 
 Weights are rounded to BF16 before use (the GPU stores BF16 copies of FP32
 master weights); everything else here is FP64.  The parameter vector is laid
-out as [W1 (64x32, row-major), b1 (64), W2 (64x64), b2 (64), W3 (3x64), b3 (3)].
+out as [W1 (64x48, row-major), b1 (64), W2 (64x64), b2 (64), W3 (3x64), b3 (3)].
+With ``act_bf16`` the hidden activations are rounded to BF16 as well before
+they enter the next layer: that is how tensor-core inference consumes them
+(BF16 operands, FP32 accumulation); training keeps them unrounded.
+
+Features (``features``): for each site, the coarse mesh potential phi
+B-spline-interpolated at the 27 points r_i + h (a, b, c), a, b, c in
+{-1, 0, 1} (h = box / mesh per axis), in the order 9 (a+1) + 3 (b+1) + (c+1),
+times a scale s_in; then the one-hot site type (O, H, WC); then
+sin(2 pi u_d), cos(2 pi u_d) for d = x, y, z with u_d = x_d N_d / L_d the
+site's coordinate in mesh units (its offset inside the mesh cell); then
+twelve zeros.  The interpolation is the oracle PPPM's own (the same order-p
+stencil as its charge assignment), evaluated at the shifted points: the
+definition itself.
+
+``adam_step`` is the Adam update (Kingma and Ba, 2015) with bias correction.
 
 Only tests/, the smoke check and the benchmark's CPU-baseline leg may use this
 module.
@@ -18,7 +33,8 @@ from __future__ import annotations
 
 import numpy as np
 
-N_IN, N_H, N_OUT = 32, 64, 3
+N_IN, N_H, N_OUT = 48, 64, 3
+N_PHI, N_TYPE, N_CELL = 27, 3, 6
 SHAPES = [("W1", (N_H, N_IN)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)),
           ("W3", (N_OUT, N_H)), ("b3", (N_OUT,))]
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
@@ -46,15 +62,19 @@ def pack(p: dict) -> np.ndarray:
     return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in SHAPES])
 
 
-def forward(theta: np.ndarray, X: np.ndarray, bf16: bool = True):
+def forward(theta: np.ndarray, X: np.ndarray, bf16: bool = True, act_bf16: bool = False):
     """Outputs (n, 3) and the activations needed by backward."""
     t = bf16_round(theta) if bf16 else np.asarray(theta, dtype=np.float64)
     p = unpack(t)
     X = np.asarray(X, dtype=np.float64)
     z1 = X @ p["W1"].T + p["b1"]
     h1 = np.tanh(z1)
+    if act_bf16:
+        h1 = bf16_round(h1)
     z2 = h1 @ p["W2"].T + p["b2"]
     h2 = np.tanh(z2)
+    if act_bf16:
+        h2 = bf16_round(h2)
     y = h2 @ p["W3"].T + p["b3"]
     return y, (X, h1, h2, p)
 
@@ -77,3 +97,37 @@ def loss_and_grad(theta: np.ndarray, X: np.ndarray, T: np.ndarray, bf16: bool = 
     g["W1"] = dz1.T @ X
     g["b1"] = dz1.sum(axis=0)
     return loss, pack(g)
+
+
+def adam_step(theta, m, v, g, step: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    """One Adam update at step number ``step`` (1-based); returns the new
+    (theta, m, v).  m and v are the running first and second moments."""
+    m = b1 * np.asarray(m, np.float64) + (1.0 - b1) * g
+    v = b2 * np.asarray(v, np.float64) + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** step)
+    vhat = v / (1.0 - b2 ** step)
+    return np.asarray(theta, np.float64) - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def features(phi: np.ndarray, pos: np.ndarray, types: np.ndarray, box, mesh, p: int, s_in: float = 1.0):
+    """Per-site network inputs (n, 48), FP64, from the mesh potential phi."""
+    from .pppm import interpolate
+    pos = np.asarray(pos, dtype=np.float64)
+    h = np.asarray(box, np.float64) / np.asarray(mesh, np.float64)
+    n = pos.shape[0]
+    X = np.zeros((n, N_IN))
+    k = 0
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            for c in (-1, 0, 1):
+                shifted = pos + h * np.array([a, b, c], np.float64)
+                X[:, k] = s_in * interpolate([phi], shifted, box, mesh, p)[:, 0]
+                k += 1
+    t = np.asarray(types).astype(np.int64)
+    for j in range(3):
+        X[:, 27 + j] = (t == j).astype(np.float64)
+    for d in range(3):
+        u = pos[:, d] / h[d]
+        X[:, 30 + 2 * d] = np.sin(2.0 * np.pi * u)
+        X[:, 31 + 2 * d] = np.cos(2.0 * np.pi * u)
+    return X

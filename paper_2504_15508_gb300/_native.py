@@ -75,6 +75,22 @@ SIGNATURES = {
     "pppm_compute_batched": (cint, [vp, vp, vp, vp, vp, vp, vp, vp]),
     "pppm_batch_status": (cint, [vp]),
     "pppm_batch_destroy": (None, [vp]),
+    "pppm_set_potential": (cint, [vp, cint]),
+    "pppm_corr_create": (cint, [vp, ctypes.POINTER(vp)]),
+    "pppm_corr_nparams": (cint, []),
+    "pppm_corr_set_weights": (cint, [vp, vp, dbl, dbl]),
+    "pppm_corr_get_weights": (cint, [vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+    "pppm_corr_features": (cint, [vp, vp, vp, vp, vp, i64, vp, vp]),
+    "pppm_corr_calibrate": (cint, [vp, vp, vp, vp, vp, i64, vp]),
+    "pppm_corr_get_scales": (cint, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+    "pppm_corr_targets": (cint, [vp, vp, vp, vp, vp, i64, vp]),
+    "pppm_corr_forward": (cint, [vp, vp, vp, i64, vp]),
+    "pppm_corr_apply": (cint, [vp, vp, vp, vp, vp, i64, vp, vp, vp]),
+    "pppm_corr_grad": (cint, [vp, vp, vp, vp, i64, vp, i64, vp, vp]),
+    "pppm_corr_train_step": (cint, [vp, vp, vp, vp, i64, vp, i64, ctypes.c_float, vp]),
+    "pppm_corr_save": (cint, [vp, ctypes.c_char_p]),
+    "pppm_corr_load": (cint, [vp, ctypes.c_char_p]),
+    "pppm_corr_destroy": (None, [vp]),
     "pppm_profile_enable": (cint, [vp, cint]),
     "pppm_profile_read": (cint, [vp, vp, vp, cint]),
     "pppm_profile_name": (ctypes.c_char_p, [cint]),

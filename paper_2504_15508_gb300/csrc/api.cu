@@ -21,65 +21,9 @@
 #include <cudaTypedefs.h>
 
 #include "internal.cuh"
+#include "plan.cuh"
 
 using namespace pppm;
-
-struct pppm_plan {
-    int precision = PPPM_FP32;
-    int device = 0;
-    double box[3] = {0, 0, 0};
-    int mesh[3] = {0, 0, 0};
-    int order = 5;
-    double beta = 0.0;
-    pppm_options opt{};
-    Geo g{};
-    Radix rad[3]{};
-    Bundle bd{};
-    size_t esz = 4;  // sizeof(real)
-    // mesh workspace
-    double* G64 = nullptr;
-    void* G = nullptr;
-    void* tw[3] = {nullptr, nullptr, nullptr};
-    void* rho = nullptr;
-    void* cx[3] = {nullptr, nullptr, nullptr};
-    void* fields = nullptr;  // padded (ghosted) field meshes, see FieldLayout
-    FieldLayout flayout{};
-    CUtensorMap fmap;        // 4D TMA descriptor of the padded fields
-    bool fmap_ok = false;
-    void* partial = nullptr;
-    unsigned int* counter = nullptr;
-    int* status = nullptr;
-    // tiles
-    int tileT = 0;
-    void* patch = nullptr;
-    int* cov_off = nullptr;
-    int2* cov_ent = nullptr;
-    int4* cov2 = nullptr;  // two-slot cover table (null when some index has more covers)
-    int* tile_count = nullptr;
-    int* tile_start = nullptr;
-    // sites
-    int64_t cap = 0;
-    int* tile_of = nullptr;
-    int* slot_of = nullptr;
-    void* rec = nullptr;
-    int* cell = nullptr;
-    void* srec = nullptr;
-    int* scell = nullptr;
-    int* sorig = nullptr;
-    void* swt = nullptr;  // per-site B-spline weights in tile order
-    // host-API staging
-    cudaStream_t own = nullptr;
-    void* h_stage = nullptr;
-    size_t h_stage_bytes = 0;
-    cudaStream_t last = nullptr;
-    // optional per-kernel timing with CUDA events (pppm_profile_enable)
-    bool prof_on = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<int> pend_slot;
-    std::vector<cudaEvent_t> pend_a, pend_b;
-    double prof_ms[16] = {};
-    int64_t prof_calls[16] = {};
-};
 
 namespace {
 
@@ -387,8 +331,8 @@ int run_solve(pppm_plan* P, cudaStream_t s, double* energy, double* virial, T* f
                                    c_field, c0, c1, (T*)P->partial, P->counter, P->opt.prefactor, energy, virial)); }
     { PROF(K_FFT_Y_INV3); CK(launch_fft_y_inverse3<T>(s, g, P->rad[1], P->bd, (const C*)P->tw[1], c0, c1, c2)); }
     const int64_t N3 = mesh_points(P);
-    const C* src[3] = {c1, c2, c0};
-    const int mk[3] = {0, 0, 1};
+    const C* src[4] = {c1, c2, c0, c0};
+    const int mk[4] = {0, 0, 1, 0};
     FieldLayout fl{};
     if (fields_out == (T*)P->fields) {
         fl = P->flayout;
@@ -396,8 +340,9 @@ int run_solve(pppm_plan* P, cudaStream_t s, double* energy, double* virial, T* f
         fl.padded = 0;
         fl.fstride = N3;
     }
-    T* out[3] = {fields_out, fields_out + fl.fstride, fields_out + 2 * fl.fstride};
-    { PROF(K_FFT_Z_C2R); CK(launch_fft_z_c2r<T>(s, g, P->rad[2], (const C*)P->tw[2], 3, src, mk, out, fl)); }
+    T* out[4] = {fields_out, fields_out + fl.fstride, fields_out + 2 * fl.fstride, fields_out + 3 * fl.fstride};
+    const int nf = (P->potential && fields_out == (T*)P->fields) ? 4 : 3;
+    { PROF(K_FFT_Z_C2R); CK(launch_fft_z_c2r<T>(s, g, P->rad[2], (const C*)P->tw[2], nf, src, mk, out, fl)); }
     return PPPM_OK;
 }
 
@@ -568,7 +513,7 @@ int pppm_create(const double box[3], const int mesh[3], int order, double beta, 
         fl.Yp = mesh[1] + order - 1;
         fl.Zp = (mesh[2] + order - 1 + 3) & ~3;
         fl.fstride = (int64_t)fl.Xp * fl.Yp * fl.Zp;
-        if ((rc = dalloc(&P->fields, 3 * P->esz * fl.fstride)) != PPPM_OK) return fail(rc);
+        if ((rc = dalloc(&P->fields, 4 * P->esz * fl.fstride)) != PPPM_OK) return fail(rc);
     }
     const int nblk = x_influence_blocks(g, P->bd);
     if ((rc = dalloc(&P->partial, 14 * P->esz * (size_t)nblk)) != PPPM_OK) return fail(rc);
@@ -649,6 +594,12 @@ void pppm_destroy(pppm_plan* P) {
     for (cudaEvent_t e : P->pend_b) cudaEventDestroy(e);
     if (P->own) cudaStreamDestroy(P->own);
     delete P;
+}
+
+int pppm_set_potential(pppm_plan* P, int on) {
+    if (!P) return PPPM_ERR_INVALID_ARG;
+    P->potential = on != 0;
+    return PPPM_OK;
 }
 
 int pppm_profile_enable(pppm_plan* P, int on) {

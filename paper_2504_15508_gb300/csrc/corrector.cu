@@ -1,0 +1,846 @@
+// Learned correction of a coarse-mesh PPPM: a small per-site network maps
+// local features of the coarse mesh potential to a correction of the field,
+// trained on forces of a fine-mesh PPPM of the same positions.
+//
+//   features  x_i = [27 samples of the coarse mesh potential phi, interpolated
+//             with the site's order-p B-spline weights at r_i + h (dx, dy, dz),
+//             d in {-1, 0, 1}^3, times s_in; one-hot site type (3);
+//             sin, cos of 2 pi u_d per axis, u = position in mesh units (6);
+//             12 zeros] (BF16, 48 per site)
+//   network   h1 = tanh(W1 x + b1) (48 -> 64), h2 = tanh(W2 h1 + b2) (64 -> 64),
+//             y = W3 h2 + b3 (64 -> 3); BF16 weights, FP32 accumulation
+//   forces    F_i = F_coarse,i + q_i s_out y_i
+//   training  target t_i = (F_fine,i - F_coarse,i) / (q_i s_out); loss mean |y - t|^2;
+//             Adam on FP32 master weights, BF16 copies for inference
+//
+// Inference runs on the tensor cores (mma.sync m16n8k16 BF16 -> FP32; the
+// accumulator fragments of one layer are exactly the A fragments of the next,
+// so a warp chains all three layers in registers).  Training is FP32 on the
+// CUDA cores, one block of 128 threads per 128 sites, with the per-block weight
+// gradients reduced in a fixed order before the Adam step.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "plan.cuh"
+
+namespace pppm {
+namespace corr {
+
+constexpr int NIN = 48, NH = 64, NOUT = 3, NOUT_PAD = 8;
+constexpr int KC1 = NIN / 16;  // k-chunks of the first layer
+constexpr int O_W1 = 0, O_B1 = O_W1 + NH * NIN, O_W2 = O_B1 + NH, O_B2 = O_W2 + NH * NH, O_W3 = O_B2 + NH,
+              O_B3 = O_W3 + NOUT * NH, NPARAM = O_B3 + NOUT;
+// BF16 weight layout for the tensor-core forward: rows padded so that the
+// per-lane B-fragment loads hit distinct banks
+constexpr int K1P = NIN + 8, K2P = NH + 8;
+constexpr int BW1 = 0, BW2 = BW1 + NH * K1P, BW3 = BW2 + NH * K2P, NBF = BW3 + NOUT_PAD * K2P;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// ------------------------------------------------------------------ features
+__device__ __forceinline__ void locate_site(float x, float s_hi, float s_lo, int N, bool odd, int& g, float& x0) {
+    float u = x * s_hi;
+    const float e = fmaf(x, s_hi, -u);
+    float ul = fmaf(x, s_lo, e);
+    if (!(fabsf(u) < 4.0e6f)) { u = 0.f; ul = 0.f; }
+    float gf = odd ? floorf(u + 0.5f) : floorf(u);
+    float d = (u - gf) + ul;
+    if (odd) {
+        if (d >= 0.5f) { gf += 1.f; d -= 1.f; } else if (d < -0.5f) { gf -= 1.f; d += 1.f; }
+        x0 = 0.5f - d;
+    } else {
+        if (d >= 1.f) { gf += 1.f; d -= 1.f; } else if (d < 0.f) { gf -= 1.f; d += 1.f; }
+        x0 = 1.f - d;
+    }
+    const int gi = (int)gf % N;
+    g = gi < 0 ? gi + N : gi;
+}
+
+// all p weights N_p(x0 + j) by the Cox-de Boor recursion
+template <int P>
+__device__ __forceinline__ void bspline_all(float x0, float w[P]) {
+    w[0] = 1.f;
+#pragma unroll
+    for (int m = 2; m <= P; ++m) {
+        const float inv = 1.f / (m - 1);
+        w[m - 1] = (1.f - x0) * w[m - 2] * inv;
+#pragma unroll
+        for (int j = m - 2; j >= 1; --j) w[j] = ((x0 + j) * w[j] + (m - x0 - j) * w[j - 1]) * inv;
+        w[0] = x0 * w[0] * inv;
+    }
+}
+
+// One thread per site.  The 27 samples share the site's weights; with the
+// (p+2)^3 mesh values around the site they are three separable contractions.
+template <int P>
+__global__ void k_features(Geo g, FieldLayout fl, const float* __restrict__ phi, const float* __restrict__ pos,
+                           const signed char* __restrict__ types, int n, float s_in,
+                           __nv_bfloat16* __restrict__ feat) {
+    constexpr int W = P + 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool odd = (g.order & 1) != 0;
+    int gc[3];
+    float w[3][P];
+    float dfrac[3];  // u - g, the offset of the site from its base mesh point
+    int idx[3][W];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float x0;
+        locate_site(pos[3 * i + d], g.s_hi[d], g.s_lo[d], g.N[d], odd, gc[d], x0);
+        dfrac[d] = odd ? 0.5f - x0 : 1.f - x0;
+        bspline_all<P>(x0, w[d]);
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            int m = (gc[d] + g.kmin - 1 + a) % g.N[d];
+            m += m < 0 ? g.N[d] : 0;
+            idx[d][a] = m - g.kmin;  // padded coordinate
+        }
+    }
+    float F[27];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) F[k] = 0.f;
+#pragma unroll
+    for (int a = 0; a < W; ++a) {  // x offset of the mesh row
+        float Sy[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Sy[k] = 0.f;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {  // y offset
+            const float* row = phi + ((int64_t)idx[0][a] * fl.Yp + idx[1][b]) * fl.Zp;
+            float v[W];
+#pragma unroll
+            for (int c = 0; c < W; ++c) v[c] = __ldg(&row[idx[2][c]]);
+            float Sz[3];
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz) {
+                float s = 0.f;
+#pragma unroll
+                for (int kz = 0; kz < P; ++kz) s += w[2][kz] * v[dz + kz];
+                Sz[dz] = s;
+            }
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) {
+                const int ky = b - dy;
+                if (ky >= 0 && ky < P) {
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz) Sy[dy * 3 + dz] += w[1][ky] * Sz[dz];
+                }
+            }
+        }
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+            const int kx = a - dx;
+            if (kx >= 0 && kx < P) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) F[dx * 9 + k] += w[0][kx] * Sy[k];
+            }
+        }
+    }
+    // the row as 24 packed pairs, written with 16-byte stores
+    float v[NIN];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) v[k] = F[k] * s_in;
+    const int t = types[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[27 + k] = t == k ? 1.f : 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sincospif(2.f * dfrac[d], &v[30 + 2 * d], &v[31 + 2 * d]);
+#pragma unroll
+    for (int k = 36; k < NIN; ++k) v[k] = 0.f;
+    uint4* o = reinterpret_cast<uint4*>(feat + (int64_t)i * NIN);
+#pragma unroll
+    for (int k = 0; k < NIN / 8; ++k) {
+        uint4 w;
+        w.x = pack_bf16(v[8 * k + 0], v[8 * k + 1]);
+        w.y = pack_bf16(v[8 * k + 2], v[8 * k + 3]);
+        w.z = pack_bf16(v[8 * k + 4], v[8 * k + 5]);
+        w.w = pack_bf16(v[8 * k + 6], v[8 * k + 7]);
+        o[k] = w;
+    }
+}
+
+// ------------------------------------------------------------------ tensor-core forward
+__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+
+// accumulators of eight n-tiles (64 columns) -> tanh -> A fragments of four k-chunks
+__device__ __forceinline__ void act_to_a(const float acc[8][4], const float* __restrict__ bias, int tig,
+                                         uint32_t a[4][4]) {
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int nt = 2 * kc + h;
+            const int col = nt * 8 + 2 * tig;
+            const float b0 = bias[col], b1 = bias[col + 1];
+            a[kc][2 * h] = pack_bf16(tanhf(acc[nt][0] + b0), tanhf(acc[nt][1] + b1));
+            a[kc][2 * h + 1] = pack_bf16(tanhf(acc[nt][2] + b0), tanhf(acc[nt][3] + b1));
+        }
+}
+
+// One warp per 16 sites (grid-stride).  With forces/q given, adds
+// q_i s_out y_i to forces (the corrected PPPM); else writes y to out.
+__global__ void __launch_bounds__(128)
+k_mlp_forward(const __nv_bfloat16* __restrict__ feat, int n, const __nv_bfloat16* __restrict__ wbf,
+              const float* __restrict__ master, float s_out, const float* __restrict__ q, float* __restrict__ forces,
+              float* __restrict__ out) {
+    __shared__ __align__(16) __nv_bfloat16 sw[NBF];
+    __shared__ float sb[NH + NH + NOUT_PAD];
+    for (int k = threadIdx.x; k < NBF; k += blockDim.x) sw[k] = wbf[k];
+    for (int k = threadIdx.x; k < NH; k += blockDim.x) {  // biases are BF16 parameters too
+        sb[k] = __bfloat162float(__float2bfloat16_rn(master[O_B1 + k]));
+        sb[NH + k] = __bfloat162float(__float2bfloat16_rn(master[O_B2 + k]));
+    }
+    if (threadIdx.x < NOUT_PAD)
+        sb[2 * NH + threadIdx.x] =
+            threadIdx.x < NOUT ? __bfloat162float(__float2bfloat16_rn(master[O_B3 + threadIdx.x])) : 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t* w32 = reinterpret_cast<const uint32_t*>(sw);
+    for (int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile * 16 < n; tile += warps) {
+        const int r0 = tile * 16 + gid, r1 = r0 + 8;
+        // layer 1: A from the features (16 x 48), three k-chunks
+        uint32_t a1[KC1][4];
+        const uint32_t* f0 = reinterpret_cast<const uint32_t*>(feat + (int64_t)min(r0, n - 1) * NIN);
+        const uint32_t* f1 = reinterpret_cast<const uint32_t*>(feat + (int64_t)min(r1, n - 1) * NIN);
+#pragma unroll
+        for (int kc = 0; kc < KC1; ++kc) {
+            a1[kc][0] = f0[kc * 8 + tig];
+            a1[kc][1] = f1[kc * 8 + tig];
+            a1[kc][2] = f0[kc * 8 + 4 + tig];
+            a1[kc][3] = f1[kc * 8 + 4 + tig];
+        }
+        float acc[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+            const int nrow = nt * 8 + gid;  // output unit handled by this lane's B fragment
+#pragma unroll
+            for (int kc = 0; kc < KC1; ++kc) {
+                const uint32_t b0 = w32[(BW1 + nrow * K1P + kc * 16) / 2 + tig];
+                const uint32_t b1 = w32[(BW1 + nrow * K1P + kc * 16 + 8) / 2 + tig];
+                mma_bf16(acc[nt], a1[kc], b0, b1);
+            }
+        }
+        uint32_t a2[4][4];
+        act_to_a(acc, sb, tig, a2);
+        // layer 2
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+            const int nrow = nt * 8 + gid;
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                const uint32_t b0 = w32[(BW2 + nrow * K2P + kc * 16) / 2 + tig];
+                const uint32_t b1 = w32[(BW2 + nrow * K2P + kc * 16 + 8) / 2 + tig];
+                mma_bf16(acc[nt], a2[kc], b0, b1);
+            }
+        }
+        uint32_t a3[4][4];
+        act_to_a(acc, sb + NH, tig, a3);
+        // layer 3 (three outputs padded to an n-tile of 8)
+        float y[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc) {
+            const uint32_t b0 = w32[(BW3 + gid * K2P + kc * 16) / 2 + tig];
+            const uint32_t b1 = w32[(BW3 + gid * K2P + kc * 16 + 8) / 2 + tig];
+            mma_bf16(y, a3[kc], b0, b1);
+        }
+        // lane holds rows r0 (y[0], y[1]) and r1 (y[2], y[3]) at columns 2 tig, 2 tig + 1
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = h ? r1 : r0;
+            if (r >= n) continue;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int c = 2 * tig + e;
+                if (c >= NOUT) continue;
+                const float v = y[2 * h + e] + sb[2 * NH + c];
+                if (forces) forces[3 * (int64_t)r + c] += q[r] * s_out * v;
+                else out[3 * (int64_t)r + c] = v;
+            }
+        }
+    }
+}
+
+// FP32 master -> padded BF16 copy for the forward
+__global__ void k_to_bf16(const float* __restrict__ master, __nv_bfloat16* __restrict__ wbf) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < NBF; k += gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (k < BW2) {
+            const int r = k / K1P, c = k - r * K1P;
+            if (c < NIN) v = master[O_W1 + r * NIN + c];
+        } else if (k < BW3) {
+            const int r = (k - BW2) / K2P, c = (k - BW2) - r * K2P;
+            if (c < NH) v = master[O_W2 + r * NH + c];
+        } else {
+            const int r = (k - BW3) / K2P, c = (k - BW3) - r * K2P;
+            if (r < NOUT && c < NH) v = master[O_W3 + r * NH + c];
+        }
+        wbf[k] = __float2bfloat16_rn(v);
+    }
+}
+
+// ------------------------------------------------------------------ training
+constexpr int TB = 128;  // sites per training block
+constexpr int XP = NIN + 1, HP = NH + 1;
+
+__device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Per block: forward and backward of 128 sites (FP32, weights rounded to BF16
+// as used by inference), per-block gradient sums to partial[block][NPARAM],
+// and the block's share of the loss to lossp[block].
+__global__ void __launch_bounds__(TB)
+k_mlp_grad(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ target, int64_t nrows,
+           const int* __restrict__ idx, int nb, float inv_total, const float* __restrict__ master, float* __restrict__ partial,
+           float* __restrict__ lossp) {
+    extern __shared__ __align__(16) float sm[];
+    float* W1 = sm;                  // 64 x 48
+    float* W2 = W1 + NH * NIN;       // 64 x 64
+    float* W3 = W2 + NH * NH;        // 3 x 64
+    float* bb = W3 + NOUT * NH;      // b1 64, b2 64, b3 3 (+1)
+    float* X = bb + 2 * NH + 4;      // TB x XP
+    float* H1 = X + TB * XP;         // TB x HP
+    float* H2 = H1 + TB * HP;        // TB x HP
+    float* DY = H2 + TB * HP;        // TB x 4
+    float* red = DY + TB * 4;        // 32
+    const int t = threadIdx.x;
+    for (int k = t; k < NH * NIN; k += TB) W1[k] = bfr(master[O_W1 + k]);
+    for (int k = t; k < NH * NH; k += TB) W2[k] = bfr(master[O_W2 + k]);
+    for (int k = t; k < NOUT * NH; k += TB) W3[k] = bfr(master[O_W3 + k]);
+    for (int k = t; k < NH; k += TB) {
+        bb[k] = bfr(master[O_B1 + k]);
+        bb[NH + k] = bfr(master[O_B2 + k]);
+    }
+    if (t < NOUT) bb[2 * NH + t] = bfr(master[O_B3 + t]);
+    const int s = blockIdx.x * TB + t;
+    int site = s < nb ? (idx ? idx[s] : s) : -1;
+    const bool valid = site >= 0 && site < nrows;  // rows outside the table contribute nothing
+    if (!valid) site = 0;
+    for (int k = 0; k < NIN; ++k) X[t * XP + k] = valid ? __bfloat162float(feat[(int64_t)site * NIN + k]) : 0.f;
+    __syncthreads();
+    // forward of this thread's site
+    for (int j = 0; j < NH; ++j) {
+        float z = bb[j];
+        for (int k = 0; k < NIN; ++k) z += W1[j * NIN + k] * X[t * XP + k];
+        H1[t * HP + j] = tanhf(z);
+    }
+    for (int j = 0; j < NH; ++j) {
+        float z = bb[NH + j];
+        for (int k = 0; k < NH; ++k) z += W2[j * NH + k] * H1[t * HP + k];
+        H2[t * HP + j] = tanhf(z);
+    }
+    float l = 0.f;
+    for (int c = 0; c < NOUT; ++c) {
+        float y = bb[2 * NH + c];
+        for (int k = 0; k < NH; ++k) y += W3[c * NH + k] * H2[t * HP + k];
+        const float r = valid ? y - target[3 * (int64_t)site + c] : 0.f;
+        l += r * r;
+        DY[t * 4 + c] = 2.f * r * inv_total;
+    }
+    // block loss (fixed-order tree)
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
+    if ((t & 31) == 0) red[t >> 5] = l;
+    __syncthreads();
+    float* g = partial + (size_t)blockIdx.x * NPARAM;
+    if (t == 0) lossp[blockIdx.x] = (red[0] + red[1] + red[2] + red[3]) * inv_total;
+    // dW3, db3
+    for (int o = t; o < NOUT * NH + NOUT; o += TB) {
+        float acc = 0.f;
+        if (o < NOUT * NH) {
+            const int c = o / NH, j = o - c * NH;
+            for (int r = 0; r < TB; ++r) acc += DY[r * 4 + c] * H2[r * HP + j];
+            g[O_W3 + o] = acc;
+        } else {
+            const int c = o - NOUT * NH;
+            for (int r = 0; r < TB; ++r) acc += DY[r * 4 + c];
+            g[O_B3 + c] = acc;
+        }
+    }
+    __syncthreads();
+    // dZ2 over H2 (own row)
+    for (int j = 0; j < NH; ++j) {
+        float dh = 0.f;
+        for (int c = 0; c < NOUT; ++c) dh += DY[t * 4 + c] * W3[c * NH + j];
+        const float h = H2[t * HP + j];
+        H2[t * HP + j] = dh * (1.f - h * h);
+    }
+    __syncthreads();
+    // dW2 (thread: column k, rows j = t/64 + 2m), db2
+    {
+        const int k = t & (NH - 1), j0 = t >> 6;
+        float acc[NH / 2];
+        for (int m = 0; m < NH / 2; ++m) acc[m] = 0.f;
+        for (int r = 0; r < TB; ++r) {
+            const float hk = H1[r * HP + k];
+#pragma unroll
+            for (int m = 0; m < NH / 2; ++m) acc[m] += H2[r * HP + j0 + 2 * m] * hk;
+        }
+        for (int m = 0; m < NH / 2; ++m) g[O_W2 + (j0 + 2 * m) * NH + k] = acc[m];
+    }
+    if (t < NH) {
+        float acc = 0.f;
+        for (int r = 0; r < TB; ++r) acc += H2[r * HP + t];
+        g[O_B2 + t] = acc;
+    }
+    __syncthreads();
+    // dZ1 over H1 (own row)
+    for (int k = 0; k < NH; ++k) {
+        float dh = 0.f;
+        for (int j = 0; j < NH; ++j) dh += H2[t * HP + j] * W2[j * NH + k];
+        const float h = H1[t * HP + k];
+        H1[t * HP + k] = dh * (1.f - h * h);
+    }
+    __syncthreads();
+    // dW1 (thread: columns k0 + 16 c, c < 3, k0 = t % 16; rows j0 + 8 m, m < 8, j0 = t / 16), db1
+    {
+        static_assert(NIN == 48 && NH == 64 && TB == 128, "dW1 thread map");
+        const int k0 = t & 15, j0 = t >> 4;
+        float acc[3][8];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[c][m] = 0.f;
+        for (int r = 0; r < TB; ++r) {
+            float xk[3], hj[8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) xk[c] = X[r * XP + k0 + 16 * c];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) hj[m] = H1[r * HP + j0 + 8 * m];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int m = 0; m < 8; ++m) acc[c][m] += hj[m] * xk[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) g[O_W1 + (j0 + 8 * m) * NIN + k0 + 16 * c] = acc[c][m];
+    }
+    if (t < NH) {
+        float acc = 0.f;
+        for (int r = 0; r < TB; ++r) acc += H1[r * HP + t];
+        g[O_B1 + t] = acc;
+    }
+}
+
+// Sum the per-block gradients in block order; then either return them or take
+// one Adam step (FP32 master, moments m, v) and refresh nothing else (the BF16
+// copy is rebuilt by k_to_bf16).
+__global__ void k_reduce_adam(const float* __restrict__ partial, const float* __restrict__ lossp, int nblk,
+                              float* __restrict__ grad_out, float* __restrict__ loss_out, float* __restrict__ master,
+                              float* __restrict__ m1, float* __restrict__ m2, float lr, float b1, float b2, float eps,
+                              float bc1, float bc2) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0 && loss_out) {
+        float l = 0.f;
+        for (int b = 0; b < nblk; ++b) l += lossp[b];
+        *loss_out = l;
+    }
+    if (p >= NPARAM) return;
+    float gsum = 0.f;
+    for (int b = 0; b < nblk; ++b) gsum += partial[(size_t)b * NPARAM + p];
+    if (grad_out) grad_out[p] = gsum;
+    if (master) {
+        const float mm = b1 * m1[p] + (1.f - b1) * gsum;
+        const float vv = b2 * m2[p] + (1.f - b2) * gsum * gsum;
+        m1[p] = mm;
+        m2[p] = vv;
+        master[p] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+    }
+}
+
+// training targets t_i = (F_fine,i - F_coarse,i) / (q_i s_out); 0 where q_i = 0
+__global__ void k_targets(const float* __restrict__ ff, const float* __restrict__ fc, const float* __restrict__ q,
+                          int64_t n, float s_out, float* __restrict__ t) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    const float qi = q[k / 3];
+    t[k] = qi != 0.f ? (ff[k] - fc[k]) / (qi * s_out) : 0.f;
+}
+
+// Calibration sums, one partial per block (summed on the host in block order):
+// [0] sum of squares of the 27 potential samples, [1] sum over sites with
+// q != 0 of |F_fine - F_coarse|^2 / q^2, [2] number of such sites.
+constexpr int kCalBlocks = 256;
+__global__ void __launch_bounds__(256)
+k_calibrate(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ ff, const float* __restrict__ fc,
+            const float* __restrict__ q, int n, double* __restrict__ part) {
+    __shared__ double red[3][8];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int k = 0; k < 27; ++k) {
+            const double v = __bfloat162float(feat[(int64_t)i * NIN + k]);
+            a += v * v;
+        }
+        const float qi = q[i];
+        if (qi != 0.f) {
+            for (int d = 0; d < 3; ++d) {
+                const double e = ((double)ff[3 * (int64_t)i + d] - (double)fc[3 * (int64_t)i + d]) / qi;
+                b += e * e;
+            }
+            c += 1.0;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+        c += __shfl_down_sync(0xffffffffu, c, off);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = a; red[1][w] = b; red[2][w] = c; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int k = 0; k < 8; ++k) s += red[threadIdx.x][k];
+        part[3 * blockIdx.x + threadIdx.x] = s;
+    }
+}
+
+}  // namespace corr
+}  // namespace pppm
+
+// ====================================================================== host side
+using namespace pppm;
+using namespace pppm::corr;
+
+struct pppm_corr {
+    pppm_plan* plan = nullptr;  // coarse plan (borrowed)
+    float* master = nullptr;
+    float* m1 = nullptr;
+    float* m2 = nullptr;
+    __nv_bfloat16* wbf = nullptr;
+    float* partial = nullptr;
+    float* lossp = nullptr;
+    int partial_blocks = 0;
+    __nv_bfloat16* feat = nullptr;
+    int64_t feat_cap = 0;
+    float s_in = 1.f, s_out = 1.f;
+    long long step = 0;
+    double* ev = nullptr;  // scratch energy/virial of internal coarse evaluations
+};
+
+namespace {
+
+#define CC(x)                                          \
+    do {                                               \
+        if ((x) != cudaSuccess) return PPPM_ERR_CUDA;  \
+    } while (0)
+
+int ensure_feat(pppm_corr* C, int64_t n) {
+    if (n <= C->feat_cap) return PPPM_OK;
+    if (C->feat) cudaFree(C->feat);
+    C->feat = nullptr;
+    C->feat_cap = 0;
+    CC(cudaMalloc((void**)&C->feat, sizeof(__nv_bfloat16) * NIN * (n > 0 ? n : 1)));
+    C->feat_cap = n;
+    return PPPM_OK;
+}
+
+int ensure_partial(pppm_corr* C, int nblk) {
+    if (nblk <= C->partial_blocks) return PPPM_OK;
+    if (C->partial) cudaFree(C->partial);
+    if (C->lossp) cudaFree(C->lossp);
+    C->partial = nullptr;
+    C->lossp = nullptr;
+    C->partial_blocks = 0;
+    CC(cudaMalloc((void**)&C->partial, sizeof(float) * NPARAM * (size_t)nblk));
+    CC(cudaMalloc((void**)&C->lossp, sizeof(float) * nblk));
+    C->partial_blocks = nblk;
+    return PPPM_OK;
+}
+
+int refresh_bf16(pppm_corr* C, cudaStream_t s) {
+    k_to_bf16<<<(NBF + 255) / 256, 256, 0, s>>>(C->master, C->wbf);
+    CC(cudaGetLastError());
+    return PPPM_OK;
+}
+
+cudaError_t launch_features(pppm_corr* C, cudaStream_t s, const float* pos, const signed char* types, int64_t n,
+                            __nv_bfloat16* feat) {
+    pppm_plan* P = C->plan;
+    const float* phi = (const float*)P->fields + 3 * P->flayout.fstride;
+    const int blocks = (int)((n + 127) / 128);
+    switch (P->order) {
+        case 3: k_features<3><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
+        case 4: k_features<4><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
+        case 5: k_features<5><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
+        case 6: k_features<6><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
+        case 7: k_features<7><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int mlp_forward(pppm_corr* C, cudaStream_t s, const __nv_bfloat16* feat, int64_t n, const float* q, float* forces,
+                float* out) {
+    if (n == 0) return PPPM_OK;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = (int)((n + 15) / 16);
+    int blocks = (tiles + 3) / 4;
+    if (blocks > 8 * nsm) blocks = 8 * nsm;
+    k_mlp_forward<<<blocks, 128, 0, s>>>(feat, (int)n, C->wbf, C->master, C->s_out, q, forces, out);
+    CC(cudaGetLastError());
+    return PPPM_OK;
+}
+
+constexpr size_t kGradSmem =
+    sizeof(float) * (NH * NIN + NH * NH + NOUT * NH + 2 * NH + 4 + TB * XP + 2 * TB * HP + TB * 4 + 32);
+
+int grad_step(pppm_corr* C, cudaStream_t s, const __nv_bfloat16* feat, const float* target, int64_t nrows,
+              const int* idx, int64_t nb, float* grad_out, float* loss_out, bool adam, float lr) {
+    if (nb <= 0 || nrows <= 0 || nb > (int64_t(1) << 30) || (!idx && nb > nrows)) return PPPM_ERR_INVALID_ARG;
+    const int nblk = (int)((nb + TB - 1) / TB);
+    int rc = ensure_partial(C, nblk);
+    if (rc != PPPM_OK) return rc;
+    CC(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem));
+    k_mlp_grad<<<nblk, TB, kGradSmem, s>>>(feat, target, nrows, idx, (int)nb, 1.f / (float)nb, C->master, C->partial,
+                                          C->lossp);
+    CC(cudaGetLastError());
+    float bc1 = 1.f, bc2 = 1.f;
+    if (adam) {
+        C->step += 1;
+        bc1 = 1.f - powf(0.9f, (float)C->step);
+        bc2 = 1.f - powf(0.999f, (float)C->step);
+    }
+    k_reduce_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(C->partial, C->lossp, nblk, grad_out, loss_out,
+                                                       adam ? C->master : nullptr, C->m1, C->m2, lr, 0.9f, 0.999f,
+                                                       1e-8f, bc1, bc2);
+    CC(cudaGetLastError());
+    if (adam) return refresh_bf16(C, s);
+    return PPPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pppm_corr_create(pppm_plan* coarse, pppm_corr** out) {
+    if (!out) return PPPM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!coarse || coarse->precision != PPPM_FP32) return PPPM_ERR_INVALID_ARG;
+    pppm_corr* C = new (std::nothrow) pppm_corr();
+    if (!C) return PPPM_ERR_CUDA;
+    C->plan = coarse;
+    coarse->potential = true;
+    auto fail = [&](int code) {
+        pppm_corr_destroy(C);
+        return code;
+    };
+    if (cudaMalloc((void**)&C->master, sizeof(float) * NPARAM) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    if (cudaMalloc((void**)&C->m1, sizeof(float) * NPARAM) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    if (cudaMalloc((void**)&C->m2, sizeof(float) * NPARAM) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    if (cudaMalloc((void**)&C->wbf, sizeof(__nv_bfloat16) * NBF) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    if (cudaMalloc((void**)&C->ev, sizeof(double) * 8) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    if (cudaMemset(C->master, 0, sizeof(float) * NPARAM) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    if (cudaMemset(C->m1, 0, sizeof(float) * NPARAM) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    if (cudaMemset(C->m2, 0, sizeof(float) * NPARAM) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    if (refresh_bf16(C, nullptr) != PPPM_OK || cudaDeviceSynchronize() != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    *out = C;
+    return PPPM_OK;
+}
+
+void pppm_corr_destroy(pppm_corr* C) {
+    if (!C) return;
+    cudaDeviceSynchronize();
+    for (void* p : {(void*)C->master, (void*)C->m1, (void*)C->m2, (void*)C->wbf, (void*)C->partial, (void*)C->lossp,
+                    (void*)C->feat, (void*)C->ev})
+        if (p) cudaFree(p);
+    delete C;
+}
+
+int pppm_corr_nparams(void) { return NPARAM; }
+
+int pppm_corr_set_weights(pppm_corr* C, const float* params, double s_in, double s_out) {
+    if (!C || !params || !(s_in > 0.0) || !(s_out > 0.0)) return PPPM_ERR_INVALID_ARG;
+    CC(cudaMemcpy(C->master, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+    CC(cudaMemset(C->m1, 0, sizeof(float) * NPARAM));
+    CC(cudaMemset(C->m2, 0, sizeof(float) * NPARAM));
+    C->step = 0;
+    C->s_in = (float)s_in;
+    C->s_out = (float)s_out;
+    int rc = refresh_bf16(C, nullptr);
+    if (rc != PPPM_OK) return rc;
+    CC(cudaDeviceSynchronize());
+    return PPPM_OK;
+}
+
+int pppm_corr_get_weights(const pppm_corr* C, float* params, double* s_in, double* s_out) {
+    if (!C || !params) return PPPM_ERR_INVALID_ARG;
+    CC(cudaDeviceSynchronize());
+    CC(cudaMemcpy(params, C->master, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    if (s_in) *s_in = C->s_in;
+    if (s_out) *s_out = C->s_out;
+    return PPPM_OK;
+}
+
+int pppm_corr_features(pppm_corr* C, void* stream, const float* pos, const float* q, const signed char* types,
+                       int64_t n, void* feat, float* forces) {
+    if (!C || n < 0 || !feat || (n > 0 && (!pos || !q || !types || !forces))) return PPPM_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(feat) & 15) return PPPM_ERR_INVALID_ARG;  // rows are written as 16-byte vectors
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = pppm_compute_f32(C->plan, stream, pos, q, n, C->ev, forces, C->ev + 1);
+    if (rc != PPPM_OK) return rc;
+    if (n == 0) return PPPM_OK;
+    CC(launch_features(C, s, pos, types, n, (__nv_bfloat16*)feat));
+    return PPPM_OK;
+}
+
+int pppm_corr_targets(pppm_corr* C, void* stream, const float* f_fine, const float* f_coarse, const float* q,
+                      int64_t n, float* target) {
+    if (!C || n < 0 || (n > 0 && (!f_fine || !f_coarse || !q || !target))) return PPPM_ERR_INVALID_ARG;
+    if (n == 0) return PPPM_OK;
+    const int64_t m = 3 * n;
+    k_targets<<<(unsigned)((m + 255) / 256), 256, 0, (cudaStream_t)stream>>>(f_fine, f_coarse, q, n, C->s_out,
+                                                                             target);
+    CC(cudaGetLastError());
+    return PPPM_OK;
+}
+
+int pppm_corr_calibrate(pppm_corr* C, void* stream, const float* pos, const float* q, const signed char* types,
+                        int64_t n, const float* f_fine) {
+    if (!C || n <= 0 || !pos || !q || !types || !f_fine) return PPPM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_feat(C, n);
+    if (rc != PPPM_OK) return rc;
+    float* fc = nullptr;
+    double* part = nullptr;
+    auto done = [&](int code) {
+        if (fc) cudaFree(fc);
+        if (part) cudaFree(part);
+        return code;
+    };
+    if (cudaMalloc((void**)&fc, sizeof(float) * 3 * (size_t)n) != cudaSuccess) return done(PPPM_ERR_CUDA);
+    if (cudaMalloc((void**)&part, sizeof(double) * 3 * kCalBlocks) != cudaSuccess) return done(PPPM_ERR_CUDA);
+    const float keep_in = C->s_in;
+    C->s_in = 1.f;
+    rc = pppm_corr_features(C, stream, pos, q, types, n, C->feat, fc);
+    C->s_in = keep_in;
+    if (rc != PPPM_OK) return done(rc);
+    k_calibrate<<<kCalBlocks, 256, 0, s>>>(C->feat, f_fine, fc, q, (int)n, part);
+    if (cudaGetLastError() != cudaSuccess) return done(PPPM_ERR_CUDA);
+    std::vector<double> h(3 * kCalBlocks);
+    if (cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return done(PPPM_ERR_CUDA);
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < kCalBlocks; ++k) {
+        a += h[3 * k];
+        b += h[3 * k + 1];
+        c += h[3 * k + 2];
+    }
+    const double rms_in = std::sqrt(a / (27.0 * (double)n));
+    const double rms_out = c > 0 ? std::sqrt(b / (3.0 * c)) : 0.0;
+    if (!(rms_in > 0.0) || !(rms_out > 0.0) || !std::isfinite(rms_in) || !std::isfinite(rms_out))
+        return done(PPPM_ERR_NONFINITE);
+    C->s_in = (float)(1.0 / rms_in);
+    C->s_out = (float)rms_out;
+    return done(PPPM_OK);
+}
+
+int pppm_corr_get_scales(const pppm_corr* C, double* s_in, double* s_out) {
+    if (!C || !s_in || !s_out) return PPPM_ERR_INVALID_ARG;
+    *s_in = C->s_in;
+    *s_out = C->s_out;
+    return PPPM_OK;
+}
+
+int pppm_corr_forward(pppm_corr* C, void* stream, const void* feat, int64_t n, float* out) {
+    if (!C || n < 0 || (n > 0 && (!feat || !out))) return PPPM_ERR_INVALID_ARG;
+    return mlp_forward(C, (cudaStream_t)stream, (const __nv_bfloat16*)feat, n, nullptr, nullptr, out);
+}
+
+int pppm_corr_apply(pppm_corr* C, void* stream, const float* pos, const float* q, const signed char* types,
+                    int64_t n, double* energy, float* forces, double* virial) {
+    if (!C || n < 0 || !energy || !virial || (n > 0 && (!pos || !q || !types || !forces)))
+        return PPPM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = pppm_compute_f32(C->plan, stream, pos, q, n, energy, forces, virial);
+    if (rc != PPPM_OK) return rc;
+    if (n == 0) return PPPM_OK;
+    if ((rc = ensure_feat(C, n)) != PPPM_OK) return rc;
+    CC(launch_features(C, s, pos, types, n, C->feat));
+    return mlp_forward(C, s, C->feat, n, q, forces, nullptr);
+}
+
+int pppm_corr_grad(pppm_corr* C, void* stream, const void* feat, const float* target, int64_t nrows,
+                   const int* idx, int64_t nb, float* grad, float* loss) {
+    if (!C || !feat || !target || !grad) return PPPM_ERR_INVALID_ARG;
+    return grad_step(C, (cudaStream_t)stream, (const __nv_bfloat16*)feat, target, nrows, idx, nb, grad, loss, false,
+                     0.f);
+}
+
+int pppm_corr_train_step(pppm_corr* C, void* stream, const void* feat, const float* target, int64_t nrows,
+                         const int* idx, int64_t nb, float lr, float* loss) {
+    if (!C || !feat || !target || !(lr > 0.f)) return PPPM_ERR_INVALID_ARG;
+    return grad_step(C, (cudaStream_t)stream, (const __nv_bfloat16*)feat, target, nrows, idx, nb, nullptr, loss, true,
+                     lr);
+}
+
+// file: magic "PPPMCORR", version 1, nparams, s_in, s_out, step, master, m1, m2
+int pppm_corr_save(const pppm_corr* C, const char* path) {
+    if (!C || !path) return PPPM_ERR_INVALID_ARG;
+    std::vector<float> buf(3 * (size_t)NPARAM);
+    CC(cudaDeviceSynchronize());
+    CC(cudaMemcpy(buf.data(), C->master, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    CC(cudaMemcpy(buf.data() + NPARAM, C->m1, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    CC(cudaMemcpy(buf.data() + 2 * NPARAM, C->m2, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    FILE* f = fopen(path, "wb");
+    if (!f) return PPPM_ERR_INVALID_ARG;
+    const int32_t hdr[2] = {1, NPARAM};
+    const double sc[2] = {C->s_in, C->s_out};
+    const int64_t st = C->step;
+    bool ok = fwrite("PPPMCORR", 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              fwrite(sc, sizeof(sc), 1, f) == 1 && fwrite(&st, sizeof(st), 1, f) == 1 &&
+              fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? PPPM_OK : PPPM_ERR_INVALID_ARG;
+}
+
+int pppm_corr_load(pppm_corr* C, const char* path) {
+    if (!C || !path) return PPPM_ERR_INVALID_ARG;
+    FILE* f = fopen(path, "rb");
+    if (!f) return PPPM_ERR_INVALID_ARG;
+    char magic[8];
+    int32_t hdr[2];
+    double sc[2];
+    int64_t st;
+    std::vector<float> buf(3 * (size_t)NPARAM);
+    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "PPPMCORR", 8) == 0 &&
+              fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == 1 && hdr[1] == NPARAM &&
+              fread(sc, sizeof(sc), 1, f) == 1 && fread(&st, sizeof(st), 1, f) == 1 &&
+              fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return PPPM_ERR_INVALID_ARG;
+    CC(cudaMemcpy(C->master, buf.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+    CC(cudaMemcpy(C->m1, buf.data() + NPARAM, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+    CC(cudaMemcpy(C->m2, buf.data() + 2 * NPARAM, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+    C->s_in = (float)sc[0];
+    C->s_out = (float)sc[1];
+    C->step = st;
+    int rc = refresh_bf16(C, nullptr);
+    if (rc != PPPM_OK) return rc;
+    CC(cudaDeviceSynchronize());
+    return PPPM_OK;
+}
+
+}  // extern "C"

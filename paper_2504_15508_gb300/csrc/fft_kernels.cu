@@ -513,9 +513,9 @@ cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry,
 
 // ------------------------------------------------------------------ z inverse (C2R)
 struct ZOut {
-    const void* src[3];
-    void* out[3];
-    int mulkz[3];
+    const void* src[4];
+    void* out[4];
+    int mulkz[4];
     int nf;
     FieldLayout fl;
 };
@@ -610,7 +610,7 @@ cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, cons
     ZOut zo;
     zo.nf = nf;
     zo.fl = fl;
-    for (int f = 0; f < 3; ++f) {
+    for (int f = 0; f < 4; ++f) {
         zo.src[f] = f < nf ? src[f] : nullptr;
         zo.out[f] = f < nf ? out[f] : nullptr;
         zo.mulkz[f] = f < nf ? mulkz[f] : 0;

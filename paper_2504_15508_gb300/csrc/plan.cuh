@@ -1,0 +1,68 @@
+// The plan object behind the opaque pppm_plan handle (shared by the C ABI
+// implementation and the correction-network code).
+#pragma once
+
+#include <cuda.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+struct pppm_plan {
+    int precision = PPPM_FP32;
+    int device = 0;
+    double box[3] = {0, 0, 0};
+    int mesh[3] = {0, 0, 0};
+    int order = 5;
+    double beta = 0.0;
+    pppm_options opt{};
+    pppm::Geo g{};
+    pppm::Radix rad[3]{};
+    pppm::Bundle bd{};
+    size_t esz = 4;  // sizeof(real)
+    // mesh workspace
+    double* G64 = nullptr;
+    void* G = nullptr;
+    void* tw[3] = {nullptr, nullptr, nullptr};
+    void* rho = nullptr;
+    void* cx[3] = {nullptr, nullptr, nullptr};
+    void* fields = nullptr;  // padded (ghosted) field meshes, see FieldLayout
+    pppm::FieldLayout flayout{};
+    bool potential = false;  // also produce the mesh potential as a 4th padded field
+    CUtensorMap fmap;        // 4D TMA descriptor of the padded fields
+    bool fmap_ok = false;
+    void* partial = nullptr;
+    unsigned int* counter = nullptr;
+    int* status = nullptr;
+    // tiles
+    int tileT = 0;
+    void* patch = nullptr;
+    int* cov_off = nullptr;
+    int2* cov_ent = nullptr;
+    int4* cov2 = nullptr;  // two-slot cover table (null when some index has more covers)
+    int* tile_count = nullptr;
+    int* tile_start = nullptr;
+    // sites
+    int64_t cap = 0;
+    int* tile_of = nullptr;
+    int* slot_of = nullptr;
+    void* rec = nullptr;
+    int* cell = nullptr;
+    void* srec = nullptr;
+    int* scell = nullptr;
+    int* sorig = nullptr;
+    void* swt = nullptr;  // per-site B-spline weights in tile order
+    // host-API staging
+    cudaStream_t own = nullptr;
+    void* h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    cudaStream_t last = nullptr;
+    // optional per-kernel timing with CUDA events (pppm_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> pend_slot;
+    std::vector<cudaEvent_t> pend_a, pend_b;
+    double prof_ms[16] = {};
+    int64_t prof_calls[16] = {};
+};
+

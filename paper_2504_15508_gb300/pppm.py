@@ -246,3 +246,153 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+class Corrector:
+    """Learned correction of a coarse-mesh FP32 PPPM (see include/pppm.h,
+    pppm_corr_*): per-site features of the coarse mesh potential go through a
+    32-64-64-3 tanh network with BF16 weights; its output, times q_i s_out, is
+    added to the coarse forces.  Training runs on the GPU (forward, backward and
+    Adam in the library's own kernels) against fine-mesh forces.
+    """
+
+    N_IN = 48
+
+    def __init__(self, coarse: Plan, params=None, s_in: float = 1.0, s_out: float = 1.0):
+        if coarse.precision != "fp32":
+            raise ValueError("the correction runs on an FP32 coarse plan")
+        L = N.lib()
+        self._lib = L
+        self.coarse = coarse  # keeps the borrowed plan alive
+        h = ctypes.c_void_p()
+        N.check(L.pppm_corr_create(coarse.handle, ctypes.byref(h)), "pppm_corr_create")
+        self._h = h
+        self.nparams = int(L.pppm_corr_nparams())
+        if params is not None:
+            self.set_weights(params, s_in, s_out)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pppm_corr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ parameters
+    def set_weights(self, params, s_in: float, s_out: float):
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        if p.size != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters, got {p.size}")
+        N.check(self._lib.pppm_corr_set_weights(self._h, p.ctypes.data, float(s_in), float(s_out)),
+                "pppm_corr_set_weights")
+
+    def get_weights(self):
+        p = np.empty(self.nparams, dtype=np.float32)
+        si, so = ctypes.c_double(), ctypes.c_double()
+        N.check(self._lib.pppm_corr_get_weights(self._h, p.ctypes.data, ctypes.byref(si), ctypes.byref(so)),
+                "pppm_corr_get_weights")
+        return p, si.value, so.value
+
+    @property
+    def scales(self):
+        si, so = ctypes.c_double(), ctypes.c_double()
+        N.check(self._lib.pppm_corr_get_scales(self._h, ctypes.byref(si), ctypes.byref(so)))
+        return si.value, so.value
+
+    def save(self, path: str):
+        N.check(self._lib.pppm_corr_save(self._h, str(path).encode()), "pppm_corr_save")
+
+    def load(self, path: str):
+        N.check(self._lib.pppm_corr_load(self._h, str(path).encode()), "pppm_corr_load")
+
+    # ------------------------------------------------------------ checks
+    @staticmethod
+    def _sites(pos, q, types):
+        Plan._check_sites(pos, q)
+        if pos.dtype != torch.float32:
+            raise ValueError("the correction takes float32 sites")
+        if types.dtype != torch.int8 or types.shape != q.shape or not (types.is_cuda and types.is_contiguous()):
+            raise ValueError("types must be a contiguous int8 CUDA tensor of shape (n,)")
+
+    def _check_table(self, feat, target, idx):
+        if feat.dtype != torch.bfloat16 or feat.dim() != 2 or feat.shape[1] != self.N_IN or not feat.is_contiguous():
+            raise ValueError("feat must be a contiguous (n, 32) bfloat16 tensor")
+        if target.dtype != torch.float32 or tuple(target.shape) != (feat.shape[0], 3) or not target.is_contiguous():
+            raise ValueError("target must be a contiguous (n, 3) float32 tensor")
+        if idx is not None and (idx.dtype != torch.int32 or idx.dim() != 1 or not idx.is_contiguous()):
+            raise ValueError("idx must be a contiguous 1-D int32 tensor")
+
+    # ------------------------------------------------------------ evaluation
+    def features(self, pos, q, types, feat=None, forces=None, stream=None):
+        """Coarse forces (n, 3) and features (n, 32) bf16."""
+        self._sites(pos, q, types)
+        n = pos.shape[0]
+        if feat is None:
+            feat = torch.empty((n, self.N_IN), dtype=torch.bfloat16, device=pos.device)
+        if forces is None:
+            forces = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        N.check(self._lib.pppm_corr_features(self._h, _stream(stream), _ptr(pos), _ptr(q), _ptr(types), n,
+                                             _ptr(feat), _ptr(forces)), "pppm_corr_features")
+        return feat, forces
+
+    def forward(self, feat, out=None, stream=None):
+        n = feat.shape[0]
+        assert feat.dtype == torch.bfloat16 and feat.is_contiguous() and feat.shape[1] == self.N_IN
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=feat.device)
+        N.check(self._lib.pppm_corr_forward(self._h, _stream(stream), _ptr(feat), n, _ptr(out)),
+                "pppm_corr_forward")
+        return out
+
+    def apply(self, pos, q, types, out=None, stream=None):
+        """Corrected PPPM: energy (1,), forces (n, 3), virial (6,) (energy and
+        virial are the coarse mesh's)."""
+        self._sites(pos, q, types)
+        n = pos.shape[0]
+        if out is None:
+            energy = torch.empty(1, dtype=torch.float64, device=pos.device)
+            forces = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+            virial = torch.empty(6, dtype=torch.float64, device=pos.device)
+        else:
+            energy, forces, virial = out
+        N.check(self._lib.pppm_corr_apply(self._h, _stream(stream), _ptr(pos), _ptr(q), _ptr(types), n,
+                                          _ptr(energy), _ptr(forces), _ptr(virial)), "pppm_corr_apply")
+        return energy, forces, virial
+
+    # ------------------------------------------------------------ training
+    def calibrate(self, pos, q, types, f_fine, stream=None):
+        self._sites(pos, q, types)
+        N.check(self._lib.pppm_corr_calibrate(self._h, _stream(stream), _ptr(pos), _ptr(q), _ptr(types),
+                                              pos.shape[0], _ptr(f_fine.contiguous())), "pppm_corr_calibrate")
+        return self.scales
+
+    def targets(self, f_fine, f_coarse, q, out=None, stream=None):
+        n = q.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=q.device)
+        N.check(self._lib.pppm_corr_targets(self._h, _stream(stream), _ptr(f_fine), _ptr(f_coarse), _ptr(q), n,
+                                            _ptr(out)), "pppm_corr_targets")
+        return out
+
+    def grad(self, feat, target, idx=None, nb=None, stream=None):
+        """Loss (device scalar) and gradient (device, nparams) over rows idx
+        (int32 device tensor) or the first nb rows."""
+        self._check_table(feat, target, idx)
+        nb = int(idx.shape[0]) if idx is not None else int(nb if nb is not None else feat.shape[0])
+        g = torch.empty(self.nparams, dtype=torch.float32, device=feat.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        N.check(self._lib.pppm_corr_grad(self._h, _stream(stream), _ptr(feat), _ptr(target), feat.shape[0],
+                                         _ptr(idx), nb, _ptr(g), _ptr(loss)), "pppm_corr_grad")
+        return loss, g
+
+    def train_step(self, feat, target, idx, lr: float, loss=None, stream=None):
+        self._check_table(feat, target, idx)
+        nb = int(idx.shape[0]) if idx is not None else int(feat.shape[0])
+        N.check(self._lib.pppm_corr_train_step(self._h, _stream(stream), _ptr(feat), _ptr(target), feat.shape[0],
+                                               _ptr(idx), nb, ctypes.c_float(lr), _ptr(loss)),
+                "pppm_corr_train_step")
+        return loss

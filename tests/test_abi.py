@@ -65,3 +65,26 @@ def test_null_plan_calls_are_rejected(pppm_lib):
     L.pppm_destroy(None)
     for code in range(-8, 1):
         assert N.strerror(code) != "unknown error"
+
+
+def test_corrector_calls_validate_arguments(pppm_lib):
+    from oracle import mlp
+    L = pppm_lib
+    assert L.pppm_corr_nparams() == mlp.N_PARAMS == 7491
+    h = ctypes.c_void_p()
+    assert L.pppm_corr_create(None, ctypes.byref(h)) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_create(None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_set_potential(None, 1) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_set_weights(None, None, 1.0, 1.0) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_get_weights(None, None, None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_features(None, None, None, None, None, 0, None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_forward(None, None, None, 0, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_apply(None, None, None, None, None, 0, None, None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_grad(None, None, None, None, 1, None, 1, None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_train_step(None, None, None, None, 1, None, 1, 1e-3, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_calibrate(None, None, None, None, None, 1, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_targets(None, None, None, None, None, 0, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_get_scales(None, None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_save(None, b"x") == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_corr_load(None, b"x") == N.PPPM_ERR_INVALID_ARG
+    L.pppm_corr_destroy(None)

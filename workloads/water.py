@@ -171,7 +171,7 @@ def batched_boxes(nbox: int = 96, seed: int = 5, lo: int = 64, hi: int = 8192,
     return out
 
 
-def init_mlp_params(seed: int, n_in: int = 32, n_hidden: int = 64, n_out: int = 3) -> np.ndarray:
+def init_mlp_params(seed: int, n_in: int = 48, n_hidden: int = 64, n_out: int = 3) -> np.ndarray:
     """Seeded initial parameters of the correction network, as one float32
     vector [W1 (n_hidden x n_in), b1, W2 (n_hidden x n_hidden), b2,
     W3 (n_out x n_hidden), b3]: Glorot-uniform weights, zero biases."""
