@@ -48,8 +48,12 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=200)
     ap.add_argument("--frames", type=int, default=N_FRAMES, help="random-walk frames held on the device")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="water72192", choices=["water72192", "batched96"],
-                    help="water72192: the 216,576-atom system (default); batched96: 96 independent boxes")
+    ap.add_argument("--workload", default="water72192", choices=["water72192", "batched96", "learned64"],
+                    help="water72192: the 216,576-atom system (default); batched96: 96 independent boxes; "
+                         "learned64: the same system on a 64^3 mesh with the learned correction")
+    ap.add_argument("--train-frames", type=int, default=2000, help="learned64: training frames (20 bases)")
+    ap.add_argument("--train-steps", type=int, default=20000, help="learned64: Adam steps")
+    ap.add_argument("--train-batch", type=int, default=8192, help="learned64: sites per Adam step")
     return ap.parse_args()
 
 
@@ -150,6 +154,16 @@ def step_algorithmic_bytes(n: int, mesh: int) -> int:
     N = mesh ** 3
     NH = mesh * mesh * (mesh // 2 + 1)
     return (16 * n + 4 * N) + (4 * N + 8 * NH) + (8 * NH + 4 * NH) + 3 * (8 * NH + 4 * N) + (12 * N + 28 * n)
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch from
+# one ncu --set full capture of the kernel as it stands, on this workload; an
+# entry is removed whenever its kernel changes.
+NCU_TRAFFIC = {
+    ("spread", 128): 20.87e6,
+    ("gather", 128): 48.49e6,
+    ("fft_x_influence", 128): 12.82e6,
+}
 
 
 def read_peaks():
@@ -317,7 +331,7 @@ def run_ours(args):
     dom_ms = prof[dom][0] / prof[dom][1]
     achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": NCU_TRAFFIC.get((dom, args.mesh)),
                 "algorithmic_bytes": alg[dom]}
     per_kernel_frac = {nm: (alg[nm] / (kernels[nm]["ms_per_launch"] * 1e-3) / 1e9) / peak
                        for nm in kernels if kernels[nm]["launches"] and alg.get(nm)}
@@ -450,10 +464,106 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------- learned form
+def run_learned(args):
+    """The 216,576-atom system on a coarse 64^3 mesh plus the learned
+    correction, trained here on fine-mesh (160^3) forces of seeded perturbed
+    frames, evaluated on held-out frames against the fine mesh; timed against
+    the plain FP32 PPPM on the smallest mesh reaching the same force error."""
+    import torch
+
+    from paper_2504_15508_gb300 import learned
+    from paper_2504_15508_gb300.pppm import Corrector, Plan
+    from workloads.water import make_workload
+
+    dev = torch.device("cuda", 0)
+    wb, w = make_workload("water72192_m64")
+    L, n_mol, n = float(wb.box[0]), wb.n_mol, wb.n
+    box = (L, L, L)
+    coarse = Plan(box, (64,) * 3, 5, 0.4, precision="fp32")
+    fine = Plan(box, (160,) * 3, 5, 0.4, precision="fp32")
+    corr = Corrector(coarse)
+    nbase = 20
+    fpb = max(1, args.train_frames // nbase)
+    spec = learned.FrameSpec(n_mol=n_mol, L=L, base_seeds=tuple(range(100, 100 + nbase)), frames_per_base=fpb,
+                             sigma=0.05, noise_seed=0)
+    t0 = time.perf_counter()
+    ds = learned.build_dataset(corr, fine, spec)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    log = learned.train(corr, ds, steps=args.train_steps, batch=args.train_batch, lr=2e-3, seed=0, init_seed=0,
+                        log_every=max(1, args.train_steps // 20))
+    data_bytes = ds.feat.numel() * 2 + ds.target.numel() * 4
+    del ds
+    torch.cuda.empty_cache()
+
+    held = learned.FrameSpec(n_mol=n_mol, L=L, base_seeds=(200, 201), frames_per_base=5, sigma=0.05, noise_seed=7)
+    meshes = [64, 72, 80, 90, 96, 100, 108, 120, 128]
+    plain = [coarse] + [Plan(box, (m,) * 3, 5, 0.4, precision="fp32") for m in meshes[1:]]
+    err = learned.evaluate(corr, fine, held, plain=plain[1:])
+    err["plain_64"] = err["coarse"]
+    eq = next((m for m in meshes if err[f"plain_{m}"] <= err["corrected"]), None)
+
+    # timing: corrected evaluation vs plain evaluations, same frames, L2 flushed
+    pos, q, types = next(learned.frames(held))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    K = args.steps
+
+    def timed(fn):
+        for k in range(max(3, args.warmup)):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            fn()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / K
+
+    o_c = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty((n, 3), dtype=torch.float32, device=dev),
+           torch.empty(6, dtype=torch.float64, device=dev))
+    feat = torch.empty((n, Corrector.N_IN), dtype=torch.bfloat16, device=dev)
+    y = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    sampler = ClockSampler(gpu_index_for(0))
+    ms_corr = timed(lambda: corr.apply(pos, q, types, out=o_c, stream=stream))
+    clocks = sampler.stop()
+    ms_feat = timed(lambda: corr.features(pos, q, types, feat=feat, forces=o_c[1], stream=stream))
+    ms_mlp = timed(lambda: corr.forward(feat, out=y, stream=stream))
+    ms_plain = {}
+    for P in plain + [fine]:
+        ms_plain[P.mesh[0]] = timed(lambda P=P: P.compute(pos, q, out=o_c, stream=stream))
+    speedup = ms_plain[eq] / ms_corr if eq is not None else None
+    line = {
+        "metric": "learned coarse-mesh PPPM force evals/s at 216,576 atoms+WCs", "value": 1e3 / ms_corr,
+        "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms_corr,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+        "config": {"workload": f"learned64: water72192 ({n} sites, cubic {L} A) on a 64^3 mesh, order 5, beta 0.4/A, "
+                               f"plus the learned correction; labels from the 160^3 FP32 PPPM",
+                   "train_frames": len(spec.base_seeds) * fpb, "train_bases": nbase, "frame_sigma_A": 0.05,
+                   "held_out": "2 other base configurations x 5 frames", "l2": "flushed between timed steps"},
+        "force_rms_rel_err_vs_fine160": err,
+        "equal_error_plain_mesh": eq,
+        "speedup_vs_plain_at_equal_error": speedup,
+        "gain_in_error_vs_coarse": err["coarse"] / err["corrected"],
+        "ms": {"corrected": ms_corr, "coarse_plus_features": ms_feat, "mlp_forward": ms_mlp,
+               **{f"plain_{m}": v for m, v in ms_plain.items()}},
+        "train": {"steps": log.steps, "batch": args.train_batch, "seconds": log.seconds,
+                  "data_seconds": t_data, "data_gb": data_bytes / 1e9, "loss": log.loss[::4] + log.loss[-1:]},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "ours" and args.workload == "batched96":
         run_batched(args)
+        return
+    if args.impl == "ours" and args.workload == "learned64":
+        run_learned(args)
         return
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) == 0:
