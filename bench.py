@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--train-frames", type=int, default=2000, help="learned64: training frames (20 bases)")
     ap.add_argument("--train-steps", type=int, default=20000, help="learned64: Adam steps")
     ap.add_argument("--train-batch", type=int, default=8192, help="learned64: sites per Adam step")
+    ap.add_argument("--held-frames", type=int, default=100, help="learned64: held-out frames per base (2 bases)")
     return ap.parse_args()
 
 
@@ -497,7 +498,8 @@ def run_learned(args):
     del ds
     torch.cuda.empty_cache()
 
-    held = learned.FrameSpec(n_mol=n_mol, L=L, base_seeds=(200, 201), frames_per_base=5, sigma=0.05, noise_seed=7)
+    held = learned.FrameSpec(n_mol=n_mol, L=L, base_seeds=(200, 201), frames_per_base=args.held_frames, sigma=0.05,
+                             noise_seed=7)
     meshes = [64, 72, 80, 90, 96, 100, 108, 120, 128]
     plain = [coarse] + [Plan(box, (m,) * 3, 5, 0.4, precision="fp32") for m in meshes[1:]]
     err = learned.evaluate(corr, fine, held, plain=plain[1:])
@@ -536,6 +538,16 @@ def run_learned(args):
     for P in plain + [fine]:
         ms_plain[P.mesh[0]] = timed(lambda P=P: P.compute(pos, q, out=o_c, stream=stream))
     speedup = ms_plain[eq] / ms_corr if eq is not None else None
+    # the plain mesh of exactly the corrected error, by interpolating log(error)
+    # and time linearly between the two neighbouring meshes
+    interp = None
+    for m0, m1 in zip(meshes, meshes[1:]):
+        e0, e1 = err[f"plain_{m0}"], err[f"plain_{m1}"]
+        if e1 <= err["corrected"] <= e0:
+            f = math.log(e0 / err["corrected"]) / math.log(e0 / e1)
+            t = ms_plain[m0] + f * (ms_plain[m1] - ms_plain[m0])
+            interp = {"mesh": m0 + f * (m1 - m0), "ms": t, "speedup": t / ms_corr}
+            break
     line = {
         "metric": "learned coarse-mesh PPPM force evals/s at 216,576 atoms+WCs", "value": 1e3 / ms_corr,
         "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms_corr,
@@ -543,10 +555,12 @@ def run_learned(args):
         "config": {"workload": f"learned64: water72192 ({n} sites, cubic {L} A) on a 64^3 mesh, order 5, beta 0.4/A, "
                                f"plus the learned correction; labels from the 160^3 FP32 PPPM",
                    "train_frames": len(spec.base_seeds) * fpb, "train_bases": nbase, "frame_sigma_A": 0.05,
-                   "held_out": "2 other base configurations x 5 frames", "l2": "flushed between timed steps"},
+                   "held_out": f"2 other base configurations (seeds 200, 201) x {args.held_frames} frames",
+                   "l2": "flushed between timed steps"},
         "force_rms_rel_err_vs_fine160": err,
         "equal_error_plain_mesh": eq,
         "speedup_vs_plain_at_equal_error": speedup,
+        "equal_error_interpolated": interp,
         "gain_in_error_vs_coarse": err["coarse"] / err["corrected"],
         "ms": {"corrected": ms_corr, "coarse_plus_features": ms_feat, "mlp_forward": ms_mlp,
                **{f"plain_{m}": v for m, v in ms_plain.items()}},
