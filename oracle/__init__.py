@@ -14,5 +14,7 @@ Contents:
   influence.c        the optimal ik influence function as plain loops.
   native.py          ctypes wrapper that compiles and loads the two C files.
   pppm.py             plain FP64 PPPM (Poisson-ik) with numpy.
-  mlp.py              FP64 forward/backward of the coarse-mesh correction MLP.
+  mlp.py              FP64 features, forward/backward and Adam of the
+                      coarse-mesh correction network.
+  wc_fold.py          FP64 fold of WC forces onto atoms (Eq. DPLR:F_final).
 """
