@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=200)
     ap.add_argument("--frames", type=int, default=N_FRAMES, help="random-walk frames held on the device")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-wc-fold", action="store_true", help="skip the WC force fold measurement")
     ap.add_argument("--workload", default="water72192", choices=["water72192", "batched96", "learned64"],
                     help="water72192: the 216,576-atom system (default); batched96: 96 independent boxes; "
                          "learned64: the same system on a 64^3 mesh with the learned correction")
@@ -238,6 +239,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------- WC fold
+def run_wc_fold(args, wb, forces, flush, stream, peak):
+    """Time the fold of the WC forces onto the atoms with a synthetic
+    Deep-Wannier Jacobian of local sparsity (each WC depends on the 81 atoms of
+    the 27 molecules around it): one launch streams the Jacobian once."""
+    import torch
+
+    from paper_2504_15508_gb300.pppm import wc_fold
+    from workloads.water import dw_jacobian
+
+    dev = forces.device
+    hp, hw, jp, jw, _ = dw_jacobian(wb, seed=11, values=False)
+    n_atoms, n_wc = 3 * wb.n_mol, wb.n_mol
+    nnz = int(jp[-1])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    jac = 0.02 * torch.randn((nnz, 3, 3), generator=gen, dtype=torch.float32, device=dev)
+    maps = (torch.tensor(hp, device=dev), torch.tensor(hw, device=dev), torch.tensor(jp, device=dev),
+            torch.tensor(jw, device=dev), jac)
+    out = torch.empty((n_atoms, 3), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        wc_fold(forces, n_atoms, *maps, out=out, stream=stream)
+    K = min(args.steps, 200)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        wc_fold(forces, n_atoms, *maps, out=out, stream=stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / K
+    # Jacobian blocks + WC indices, row offsets, host map, site forces in, atom forces out
+    alg = nnz * (36 + 4) + (n_atoms + 1) * (8 + 4) + n_wc * 4 + (n_atoms + n_wc) * 12 + n_atoms * 12
+    achieved = alg / (ms * 1e-3) / 1e9
+    return {"kernel": "wc_fold", "n_atoms": n_atoms, "n_wc": n_wc, "jacobian_blocks": nnz,
+            "us_per_launch": ms * 1e3, "launches": K,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "algorithmic_bytes": alg, "traffic": None}}
+
+
 # --------------------------------------------------------------------- ours
 def run_ours(args):
     import torch
@@ -354,6 +396,9 @@ def run_ours(args):
     e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 12 * n + 56,
            "steps": E, "host_memory": "pinned"}
 
+    # the WC force fold (Eq. DPLR:F_final) on this step's forces, timed on its own
+    wc_fold_line = run_wc_fold(args, wb, forces, flush, stream, peak) if not args.no_wc_fold else None
+
     # parity of frame 0 and the CPU baseline (rank 0, N = 1 only)
     parity, cpu = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -382,6 +427,7 @@ def run_ours(args):
                           "achieved_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
                           "frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
         "parity": parity, "wall_s_timed_loop": wall,
+        "wc_fold": wc_fold_line,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -326,6 +326,38 @@ int pppm_corr_load(pppm_corr *corr, const char *path);
 void pppm_corr_destroy(pppm_corr *corr);
 
 /*
+ * pppm_wc_fold -- long-range force on atoms from the site forces, the fold of
+ * Eq. DPLR:F_final.  A Wannier centroid sits at W_n = R_host(n) + Delta_n(R)
+ * (Eq. DPLR:Wn); by the chain rule of Eq. DPLR:F_inter the force on atom j is
+ *   F_j = F_site[j] + sum over the WCs n hosted by j of F_site[n_atoms + n]
+ *         + sum over the blocks (n, J) of row j of J^T F_site[n_atoms + n],
+ * with J = dDelta_n/dR_j (3 x 3, row-major: J[a][b] = dDelta_{n,a}/dR_{j,b}),
+ * supplied by the caller (in DPLR, by the Deep Wannier model).
+ *   f_sites        (n_atoms + n_wc) x 3, device: the PPPM forces of the atoms
+ *                  (sites 0..n_atoms-1) then of the WCs, e.g. pppm_compute's
+ *                  output when the sites are ordered that way
+ *   host_ptr/wc    compressed rows (n_atoms + 1 offsets, device int32): the
+ *                  WCs each atom hosts; NULL for none
+ *   jac_ptr/wc/jac compressed rows (n_atoms + 1 offsets, device int64; WC
+ *                  index per block, device int32; 9 values per block, device):
+ *                  the blocks of the WCs whose displacement depends on each
+ *                  atom; NULL for none
+ *   f_atoms        n_atoms x 3, device, written
+ *   status         device int or NULL: bit 0 is set (atomically) if a WC
+ *                  index was outside [0, n_wc); that entry is skipped
+ * Row offsets must be non-decreasing and inside the arrays (not checked).
+ * Asynchronous on the stream; each atom's sum has a fixed order, so the
+ * result is bitwise reproducible.  The paper computes this in its MD code;
+ * here it is one warp per atom streaming the Jacobian once.
+ */
+int pppm_wc_fold(void *stream, int64_t n_atoms, int64_t n_wc, const double *f_sites,
+                 const int *host_ptr, const int *host_wc, const int64_t *jac_ptr,
+                 const int *jac_wc, const double *jac, double *f_atoms, int *status);
+int pppm_wc_fold_f32(void *stream, int64_t n_atoms, int64_t n_wc, const float *f_sites,
+                     const int *host_ptr, const int *host_wc, const int64_t *jac_ptr,
+                     const int *jac_wc, const float *jac, float *f_atoms, int *status);
+
+/*
  * Per-kernel timing (for benchmarks).  While enabled, every kernel launch of a
  * compute call is bracketed by CUDA events on the compute stream.
  * pppm_profile_read synchronizes, writes for each kernel slot i < cap the

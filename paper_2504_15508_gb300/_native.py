@@ -91,6 +91,8 @@ SIGNATURES = {
     "pppm_corr_save": (cint, [vp, ctypes.c_char_p]),
     "pppm_corr_load": (cint, [vp, ctypes.c_char_p]),
     "pppm_corr_destroy": (None, [vp]),
+    "pppm_wc_fold": (cint, [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "pppm_wc_fold_f32": (cint, [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
     "pppm_profile_enable": (cint, [vp, cint]),
     "pppm_profile_read": (cint, [vp, vp, vp, cint]),
     "pppm_profile_name": (ctypes.c_char_p, [cint]),

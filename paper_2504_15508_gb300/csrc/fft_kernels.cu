@@ -29,12 +29,17 @@
 namespace pppm {
 
 constexpr int kFftThreads = 256;
+// z passes keep their lines at a pitch of Nz + 8 complex in shared memory, so
+// that neighbouring lines start half a bank cycle apart
+constexpr int kZPad = 8;
 
 // ------------------------------------------------------------------ compile-time radix plan
+// Radices 16, 10 and 8 are DFTs in registers (below), so the workload lengths
+// take two Stockham stages: 128 = 16 x 8, 160 = 16 x 10, 64 = 16 x 4, 32 = 16 x 2.
 constexpr int fft_radix(int L, int s) {
     int m = L, i = 0;
-    const int fs[4] = {4, 2, 3, 5};
-    for (int q = 0; q < 4; ++q)
+    const int fs[7] = {16, 10, 8, 4, 2, 3, 5};
+    for (int q = 0; q < 7; ++q)
         while (m % fs[q] == 0) {
             if (i == s) return fs[q];
             m /= fs[q];
@@ -53,10 +58,81 @@ constexpr int fft_ns(int L, int s) {
     return ns;
 }
 
+// cos and sin of 2 pi m / N for the twiddles inside the register DFTs
+// (N = 8, 10, 16; closed forms of the regular 8-, 10- and 16-gon)
+template <int N>
+__device__ __forceinline__ constexpr double unit_cos(int m) {
+    constexpr double r = 0.70710678118654752440, c8 = 0.92387953251128675613, s8 = 0.38268343236508977173;
+    constexpr double c5 = 0.80901699437494742410, c25 = 0.30901699437494742410;
+    if (N == 16) {
+        const double t[16] = {1, c8, r, s8, 0, -s8, -r, -c8, -1, -c8, -r, -s8, 0, s8, r, c8};
+        return t[m & 15];
+    } else if (N == 8) {
+        const double t[8] = {1, r, 0, -r, -1, -r, 0, r};
+        return t[m & 7];
+    } else {
+        const double t[10] = {1, c5, c25, -c25, -c5, -1, -c5, -c25, c25, c5};
+        return t[m % 10];
+    }
+}
+template <int N>
+__device__ __forceinline__ constexpr double unit_sin(int m) {
+    constexpr double r = 0.70710678118654752440, c8 = 0.92387953251128675613, s8 = 0.38268343236508977173;
+    constexpr double s5 = 0.58778525229247312917, s25 = 0.95105651629515357212;
+    if (N == 16) {
+        const double t[16] = {0, s8, r, c8, 1, c8, r, s8, 0, -s8, -r, -c8, -1, -c8, -r, -s8};
+        return t[m & 15];
+    } else if (N == 8) {
+        const double t[8] = {0, r, 1, r, 0, -r, -1, -r};
+        return t[m & 7];
+    } else {
+        const double t[10] = {0, s5, s25, s25, s5, 0, -s5, -s25, -s25, -s5};
+        return t[m % 10];
+    }
+}
+
+// DFT of N = A B points in registers, X[k] = sum_n x[n] e^{SIGN 2 pi i n k / N}:
+// with n = B n1 + n2 and k = k1 + A k2, a size-A DFT over n1 for each n2, the
+// twiddle e^{SIGN 2 pi i n2 k1 / N}, then a size-B DFT over n2 for each k1.
+template <typename C, typename R, int A, int B, int SIGN>
+__device__ __forceinline__ void dft_ab(C* v) {
+    constexpr int N = A * B;
+    C t[B][A];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+        for (int n1 = 0; n1 < A; ++n1) t[n2][n1] = v[B * n1 + n2];
+        butterfly<C, R>(t[n2], A, R(SIGN));
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1)
+            if (n2 > 0) {
+                const C w = CT<R>::mk(R(unit_cos<N>(n2 * k1)), R(SIGN) * R(unit_sin<N>(n2 * k1)));
+                t[n2][k1] = cmul(t[n2][k1], w);
+            }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+        C u[B];
+#pragma unroll
+        for (int n2 = 0; n2 < B; ++n2) u[n2] = t[n2][k1];
+        butterfly<C, R>(u, B, R(SIGN));
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = u[k2];
+    }
+}
+
+template <typename C, typename R, int RDX, int SIGN>
+__device__ __forceinline__ void bfly(C* v) {
+    if constexpr (RDX == 16) dft_ab<C, R, 4, 4, SIGN>(v);
+    else if constexpr (RDX == 10) dft_ab<C, R, 5, 2, SIGN>(v);
+    else if constexpr (RDX == 8) dft_ab<C, R, 4, 2, SIGN>(v);
+    else butterfly<C, R>(v, RDX, R(SIGN));
+}
+
 // One Stockham stage with every size a constant.  Thread mapping: line-fast
 // (bundles, lines adjacent in shared memory) uses 16 lanes per line index and
-// blockDim/16 along the butterflies; otherwise 32 lanes walk the butterflies
-// of one line.
+// the other threads along the butterflies; otherwise consecutive threads walk
+// the butterflies of a line and then the lines.
 template <typename R, int L, int S, int SIGN, bool LF>
 __device__ __forceinline__ void ct_stage(const typename CT<R>::C* __restrict__ src, typename CT<R>::C* __restrict__ dst,
                                          int nl, int ls, int ps, const typename CT<R>::C* __restrict__ tw) {
@@ -65,30 +141,32 @@ __device__ __forceinline__ void ct_stage(const typename CT<R>::C* __restrict__ s
     constexpr int NS = fft_ns(L, S);
     constexpr int NBF = L / RDX;
     constexpr int TSTEP = L / (NS * RDX);
-    int tl, nlt, tj, njt;
-    if (LF) { tl = threadIdx.x & 15; nlt = 16; tj = threadIdx.x >> 4; njt = blockDim.x >> 4; }
-    else { tj = threadIdx.x & 31; njt = 32; tl = threadIdx.x >> 5; nlt = blockDim.x >> 5; }
-    for (int line = tl; line < nl; line += nlt) {
+    auto one = [&](int line, int j) {
+        const int k = j % NS;
         const C* sp = src + line * ls;
         C* dp = dst + line * ls;
-        for (int j = tj; j < NBF; j += njt) {
-            const int k = j % NS;
-            C v[5];
+        C v[RDX];
 #pragma unroll
-            for (int r = 0; r < RDX; ++r) v[r] = sp[(j + r * NBF) * ps];
-            if (NS > 1) {
+        for (int r = 0; r < RDX; ++r) v[r] = sp[(j + r * NBF) * ps];
+        if (NS > 1) {
 #pragma unroll
-                for (int r = 1; r < RDX; ++r) {
-                    C w = __ldg(&tw[k * r * TSTEP]);
-                    if (SIGN > 0) w.y = -w.y;
-                    v[r] = cmul(v[r], w);
-                }
+            for (int r = 1; r < RDX; ++r) {
+                C w = __ldg(&tw[k * r * TSTEP]);
+                if (SIGN > 0) w.y = -w.y;
+                v[r] = cmul(v[r], w);
             }
-            butterfly<C, R>(v, RDX, R(SIGN));
-            const int d0 = (j / NS) * NS * RDX + k;
-#pragma unroll
-            for (int r = 0; r < RDX; ++r) dp[(d0 + r * NS) * ps] = v[r];
         }
+        bfly<C, R, RDX, SIGN>(v);
+        const int d0 = (j / NS) * NS * RDX + k;
+#pragma unroll
+        for (int r = 0; r < RDX; ++r) dp[(d0 + r * NS) * ps] = v[r];
+    };
+    if (LF) {
+        const int tl = threadIdx.x & 15, tj = threadIdx.x >> 4;
+        for (int line = tl; line < nl; line += 16)
+            for (int j = tj; j < NBF; j += kFftThreads >> 4) one(line, j);
+    } else {
+        for (int it = threadIdx.x; it < nl * NBF; it += kFftThreads) one(it / NBF, it % NBF);
     }
 }
 
@@ -107,6 +185,7 @@ __device__ __forceinline__ typename CT<R>::C* ct_fft(typename CT<R>::C* a, typen
 template <typename R, int L>
 struct CtEngine {
     typedef typename CT<R>::C C;
+    static constexpr int kLen = L;  // compile-time length (0: known at run time)
     const C* tw;
     __device__ __forceinline__ static constexpr int len() { return L; }
     template <int SIGN, bool LF>
@@ -118,6 +197,7 @@ struct CtEngine {
 template <typename R>
 struct GenEngine {
     typedef typename CT<R>::C C;
+    static constexpr int kLen = 0;
     Radix rp;
     const C* tw;
     __device__ __forceinline__ int len() const { return rp.L; }
@@ -150,12 +230,16 @@ cudaError_t set_smem(K kernel, size_t smem) {
 // 2D loop helpers for the bundle kernels: rows of the line (t) by 16-lane groups,
 // lines (l) by lane within the group.
 #define BUNDLE_LOOP(t, l, L_, nl_)                                              \
-    for (int t = threadIdx.x >> 4; t < (L_); t += blockDim.x >> 4)              \
+    _Pragma("unroll") for (int t = threadIdx.x >> 4; t < (L_); t += kFftThreads >> 4) \
+        for (int l = threadIdx.x & 15; l < (nl_); l += 16)
+// the same without unrolling, for loop bodies too heavy to replicate
+#define BUNDLE_LOOP_ROLLED(t, l, L_, nl_)                                       \
+    _Pragma("unroll 1") for (int t = threadIdx.x >> 4; t < (L_); t += kFftThreads >> 4) \
         for (int l = threadIdx.x & 15; l < (nl_); l += 16)
 // line-major loops for the z passes: lines by warp, points by lane
 #define LINE_LOOP(line, t, nlines_, len_)                                       \
-    for (int line = threadIdx.x >> 5; line < (nlines_); line += blockDim.x >> 5) \
-        for (int t = threadIdx.x & 31; t < (len_); t += 32)
+    for (int line = threadIdx.x >> 5; line < (nlines_); line += kFftThreads >> 5) \
+        _Pragma("unroll") for (int t = threadIdx.x & 31; t < (len_); t += 32)
 
 // ------------------------------------------------------------------ z forward (R2C)
 // Sum of the tile patches covering mesh point (x, y, z) (the fold of the
@@ -188,15 +272,15 @@ k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restr
             PatchSrc<R> ps) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Nz = eng.len(), Hz = g.Hz;
+    const int Nz = eng.len(), Hz = g.Hz, ZP = Nz + kZPad;  // padded line pitch
     C* a = reinterpret_cast<C*>(smem_raw);
-    C* b = a + pairs * Nz;
+    C* b = a + pairs * ZP;
     const int pair0 = blockIdx.x * pairs;
     const int npairs_total = (rows + 1) / 2;
     const int np = min(pairs, npairs_total - pair0);
     if (ps.patch) {
         const int4 empty = make_int4(-1, 0, -1, 0);
-        for (int p = threadIdx.x >> 5; p < np; p += blockDim.x >> 5) {
+        for (int p = threadIdx.x >> 5; p < np; p += kFftThreads >> 5) {
             const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
             const int x0 = r0 / g.N[1], y0 = r0 - x0 * g.N[1];
             const int4 cx0 = __ldg(&ps.cov2[x0]), cy0 = __ldg(&ps.cov2[ps.nmax + y0]);
@@ -210,7 +294,7 @@ k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restr
             for (int t = threadIdx.x & 31; t < Nz; t += 32) {
                 const R va = fold_point(g, ps, cx0, cy0, t);
                 const R vb = fold_point(g, ps, cx1, cy1, t);  // empty slots give 0
-                a[p * Nz + t] = CT<R>::mk(va, vb);
+                a[p * ZP + t] = CT<R>::mk(va, vb);
             }
         }
     } else {
@@ -218,15 +302,15 @@ k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restr
             const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
             const R va = in[(int64_t)r0 * Nz + t];
             const R vb = r1 < rows ? in[(int64_t)r1 * Nz + t] : R(0);
-            a[p * Nz + t] = CT<R>::mk(va, vb);
+            a[p * ZP + t] = CT<R>::mk(va, vb);
         }
     }
     __syncthreads();
-    C* res = eng.template run<-1, false>(a, b, np, Nz, 1);
+    C* res = eng.template run<-1, false>(a, b, np, ZP, 1);
     LINE_LOOP(p, k, np, Hz) {
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
-        const C z = res[p * Nz + k];
-        const C zc = cconj(res[p * Nz + (k == 0 ? 0 : Nz - k)]);
+        const C z = res[p * ZP + k];
+        const C zc = cconj(res[p * ZP + (k == 0 ? 0 : Nz - k)]);
         const C x0 = cscale(cadd(z, zc), R(0.5));
         const C d = csub(z, zc);  // = 2 i X1
         out[(int64_t)r0 * Hz + k] = x0;
@@ -238,10 +322,10 @@ template <typename T>
 cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw,
                              const T* in, typename Cx<T>::t* out, const PatchSrc<T>& ps) {
     const int rows = g.N[0] * g.N[1];
-    int pairs = (int)((32 * 1024) / (2 * g.N[2] * sizeof(typename Cx<T>::t)));
+    int pairs = (int)((32 * 1024) / (2 * (g.N[2] + kZPad) * sizeof(typename Cx<T>::t)));
     pairs = pairs < 1 ? 1 : (pairs > 16 ? 16 : pairs);
     const int npairs = (rows + 1) / 2;
-    const size_t smem = 2ull * pairs * g.N[2] * sizeof(typename Cx<T>::t);
+    const size_t smem = 2ull * pairs * (g.N[2] + kZPad) * sizeof(typename Cx<T>::t);
     return with_engine<T>(rz, tw, [&](auto eng) {
         auto kern = k_fft_z_r2c<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
@@ -324,7 +408,7 @@ __device__ __forceinline__ void two_sum_pair(R& h, R& l, R h2, R l2) {
 }
 
 template <typename R, typename Eng>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, 4)
 k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R e_scale, R c_field,
                   typename CT<R>::C* __restrict__ S, typename CT<R>::C* __restrict__ Bx, R* __restrict__ partial,
                   unsigned int* __restrict__ counter, double prefactor, double* __restrict__ energy,
@@ -338,12 +422,25 @@ k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R 
     const int kz0 = bi * B;
     const int nl = min(B, Hz - kz0);
     const int64_t es = (int64_t)Ny * Hz;
+    // three line buffers; each transform returns the one holding its result
+    // and the others are reused as they free up
     C* a0 = reinterpret_cast<C*>(smem_raw);
     C* a1 = a0 + Nx * B;
     C* b0 = a1 + Nx * B;
-    C* b1 = b0 + Nx * B;
     C* base = S + (int64_t)y * Hz + kz0;
     BUNDLE_LOOP(t, l, Nx, nl) a0[t * B + l] = base[t * es + l];
+    // with a compile-time length, each thread's G values are fetched now so
+    // that their latency hides behind the forward FFT
+    constexpr int NG = Eng::kLen > 0 ? Eng::kLen / (kFftThreads / 16) : 1;
+    R gpre[NG];
+    if constexpr (Eng::kLen > 0) {
+        const int l = threadIdx.x & 15;
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+            const int t = (threadIdx.x >> 4) + i * (kFftThreads / 16);
+            gpre[i] = l < nl ? __ldg(&G[((int64_t)t * Ny + y) * Hz + kz0 + l]) : R(0);
+        }
+    }
     __syncthreads();
     C* rh = eng.template run<-1, true>(a0, a1, nl, 1, B);
     C* pbuf = (rh == a0) ? a1 : a0;  // free partner of the result buffer
@@ -355,13 +452,22 @@ k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R 
     R acc_hi[7], acc_lo[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) { acc_hi[q] = R(0); acc_lo[q] = R(0); }
-    BUNDLE_LOOP(t, l, Nx, nl) {
+    BUNDLE_LOOP_ROLLED(t, l, Nx, nl) {
         const int kz = kz0 + l;
         const int mx = t <= Nx / 2 ? t : t - Nx;
         const R kx = kfac<R>(g, 0) * mx;
         const R kzv = kfac<R>(g, 2) * kz;
         const bool nyq_x = (Nx % 2 == 0) && (t == Nx / 2);
-        const R gk = G[((int64_t)t * Ny + y) * Hz + kz];
+        R gk;
+        if constexpr (Eng::kLen > 0) {
+            // t = (threadIdx.x >> 4) + i (kFftThreads / 16): pick gpre[i] by selects
+            const int i = (t - (threadIdx.x >> 4)) / (kFftThreads / 16);
+            gk = gpre[0];
+#pragma unroll
+            for (int q = 1; q < NG; ++q) gk = (i == q) ? gpre[q] : gk;
+        } else {
+            gk = G[((int64_t)t * Ny + y) * Hz + kz];
+        }
         const C v = rh[t * B + l];
         const bool plane1 = (kz == 0) || ((Nz % 2 == 0) && (kz == Nz / 2));
         const R w = plane1 ? R(1) : R(2);
@@ -386,8 +492,9 @@ k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R 
         b0[t * B + l] = CT<R>::mk(kxd * P.y, -kxd * P.x);  // -i kx' P
     }
     __syncthreads();
-    C* rA = eng.template run<1, true>(pbuf, rh, nl, 1, B);
-    C* rB = eng.template run<1, true>(b0, b1, nl, 1, B);
+    C* rA = eng.template run<1, true>(pbuf, rh, nl, 1, B);  // rho_hat is no longer needed: scratch
+    C* fr = (rA == pbuf) ? rh : pbuf;
+    C* rB = eng.template run<1, true>(b0, fr, nl, 1, B);
     C* obx = Bx + (int64_t)y * Hz + kz0;
     BUNDLE_LOOP(t, l, Nx, nl) {
         base[t * es + l] = rA[t * B + l];
@@ -452,7 +559,7 @@ cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx
                                    const typename Cx<T>::t* tw, const T* G, double beta, double e_scale,
                                    double c_field, typename Cx<T>::t* S, typename Cx<T>::t* Bx, T* partial,
                                    unsigned int* counter, double prefactor, double* energy, double* virial) {
-    const size_t smem = 4ull * g.N[0] * bd.B * sizeof(typename Cx<T>::t);
+    const size_t smem = 3ull * g.N[0] * bd.B * sizeof(typename Cx<T>::t);
     return with_engine<T>(rx, tw, [&](auto eng) {
         auto kern = k_fft_x_influence<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
@@ -520,15 +627,22 @@ struct ZOut {
     FieldLayout fl;
 };
 
+// element f of a 4-entry kernel-parameter array, by selects (a dynamic index
+// would copy the whole parameter struct to local memory)
+template <typename X>
+__device__ __forceinline__ X pick4(const X (&a)[4], int f) {
+    return f == 0 ? a[0] : f == 1 ? a[1] : f == 2 ? a[2] : a[3];
+}
+
 template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads)
 k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Nz = eng.len(), Hz = g.Hz;
+    const int Nz = eng.len(), Hz = g.Hz, ZP = Nz + kZPad;  // padded line pitch
     const int nf = zo.nf;
     C* a = reinterpret_cast<C*>(smem_raw);
-    C* b = a + nf * pairs * Nz;
+    C* b = a + nf * pairs * ZP;
     const int pair0 = blockIdx.x * pairs;
     const int npairs_total = (rows + 1) / 2;
     const int np = min(pairs, npairs_total - pair0);
@@ -537,31 +651,32 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
     LINE_LOOP(line, t, nlines, Nz) {
         const int f = line / np, p = line - f * np;
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
-        const C* src = reinterpret_cast<const C*>(zo.src[f]);
+        const C* src = reinterpret_cast<const C*>(pick4(zo.src, f));
+        const int mulkz = pick4(zo.mulkz, f);
         // Hermitian extension: t < Hz reads the half row, t >= Hz the conjugate of Nz - t
         const int kk = t < Hz ? t : Nz - t;
         const bool cj = t >= Hz;
         const bool realonly = (kk == 0) || (even && kk == Nz / 2);
         R kzd = R(0);
-        if (zo.mulkz[f] && !(even && kk == Nz / 2)) kzd = kfac<R>(g, 2) * kk;
+        if (mulkz && !(even && kk == Nz / 2)) kzd = kfac<R>(g, 2) * kk;
         C h0 = src[(int64_t)r0 * Hz + kk];
         C h1 = r1 < rows ? src[(int64_t)r1 * Hz + kk] : CT<R>::mk(R(0), R(0));
-        if (zo.mulkz[f]) {  // -i kz' h
+        if (mulkz) {  // -i kz' h
             h0 = CT<R>::mk(kzd * h0.y, -kzd * h0.x);
             h1 = CT<R>::mk(kzd * h1.y, -kzd * h1.x);
         }
         if (realonly) { h0.y = R(0); h1.y = R(0); }
         if (cj) { h0.y = -h0.y; h1.y = -h1.y; }
-        a[line * Nz + t] = CT<R>::mk(h0.x - h1.y, h0.y + h1.x);  // h0 + i h1
+        a[line * ZP + t] = CT<R>::mk(h0.x - h1.y, h0.y + h1.x);  // h0 + i h1
     }
     __syncthreads();
-    C* res = eng.template run<1, false>(a, b, nlines, Nz, 1);
+    C* res = eng.template run<1, false>(a, b, nlines, ZP, 1);
     if (!zo.fl.padded) {
         LINE_LOOP(line, t, nlines, Nz) {
             const int f = line / np, p = line - f * np;
             const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
-            R* out = reinterpret_cast<R*>(zo.out[f]);
-            const C z = res[line * Nz + t];
+            R* out = reinterpret_cast<R*>(pick4(zo.out, f));
+            const C z = res[line * ZP + t];
             out[(int64_t)r0 * Nz + t] = z.x;
             if (r1 < rows) out[(int64_t)r1 * Nz + t] = z.y;
         }
@@ -572,10 +687,10 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
     const FieldLayout& fl = zo.fl;
     const int Ny = g.N[1], Nx = g.N[0], kmin = g.kmin;
     const int zlen = Nz + g.order - 1;
-    for (int line = threadIdx.x >> 5; line < nlines; line += blockDim.x >> 5) {
+    for (int line = threadIdx.x >> 5; line < nlines; line += kFftThreads >> 5) {
         const int f = line / np, p = line - f * np;
-        R* out = reinterpret_cast<R*>(zo.out[f]);
-        const C* rrow = res + line * Nz;
+        R* out = reinterpret_cast<R*>(pick4(zo.out, f));
+        const C* rrow = res + line * ZP;
         for (int half = 0; half < 2; ++half) {
             const int r = 2 * (pair0 + p) + half;
             if (r >= rows) break;
@@ -616,10 +731,10 @@ cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, cons
         zo.mulkz[f] = f < nf ? mulkz[f] : 0;
     }
     const int rows = g.N[0] * g.N[1];
-    int pairs = (int)((48 * 1024) / (2 * nf * g.N[2] * sizeof(typename Cx<T>::t)));
+    int pairs = (int)((48 * 1024) / (2 * nf * (g.N[2] + kZPad) * sizeof(typename Cx<T>::t)));
     pairs = pairs < 1 ? 1 : (pairs > 8 ? 8 : pairs);
     const int npairs = (rows + 1) / 2;
-    const size_t smem = 2ull * nf * pairs * g.N[2] * sizeof(typename Cx<T>::t);
+    const size_t smem = 2ull * nf * pairs * (g.N[2] + kZPad) * sizeof(typename Cx<T>::t);
     return with_engine<T>(rz, tw, [&](auto eng) {
         auto kern = k_fft_z_c2r<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);

@@ -396,3 +396,28 @@ class Corrector:
                                                _ptr(idx), nb, ctypes.c_float(lr), _ptr(loss)),
                 "pppm_corr_train_step")
         return loss
+
+
+def wc_fold(f_sites: torch.Tensor, n_atoms: int, host_ptr=None, host_wc=None, jac_ptr=None, jac_wc=None,
+            jac=None, out=None, status=None, stream=None) -> torch.Tensor:
+    """Atom forces (n_atoms, 3) from site forces (atoms then WCs), Eq.
+    DPLR:F_final: see pppm_wc_fold in include/pppm.h.  Index arrays: host_ptr
+    int32 (n_atoms + 1), host_wc int32, jac_ptr int64 (n_atoms + 1), jac_wc
+    int32, jac (nnz, 3, 3) in the dtype of f_sites; all CUDA tensors."""
+    L = N.lib()
+    f_sites = f_sites.contiguous()
+    if f_sites.dtype not in (torch.float32, torch.float64) or not f_sites.is_cuda:
+        raise ValueError("f_sites must be a float32 or float64 CUDA tensor")
+    n_wc = f_sites.shape[0] - int(n_atoms)
+    if n_wc < 0:
+        raise ValueError("f_sites has fewer rows than n_atoms")
+    for t, dt in ((host_ptr, torch.int32), (host_wc, torch.int32), (jac_ptr, torch.int64), (jac_wc, torch.int32),
+                  (jac, f_sites.dtype)):
+        if t is not None and (t.dtype != dt or not t.is_cuda or not t.is_contiguous()):
+            raise ValueError(f"index/Jacobian arrays: expected contiguous CUDA {dt}")
+    if out is None:
+        out = torch.empty((int(n_atoms), 3), dtype=f_sites.dtype, device=f_sites.device)
+    fn = L.pppm_wc_fold_f32 if f_sites.dtype == torch.float32 else L.pppm_wc_fold
+    N.check(fn(_stream(stream), int(n_atoms), int(n_wc), _ptr(f_sites), _ptr(host_ptr), _ptr(host_wc),
+               _ptr(jac_ptr), _ptr(jac_wc), _ptr(jac), _ptr(out), _ptr(status)), "pppm_wc_fold")
+    return out

@@ -88,3 +88,10 @@ def test_corrector_calls_validate_arguments(pppm_lib):
     assert L.pppm_corr_save(None, b"x") == N.PPPM_ERR_INVALID_ARG
     assert L.pppm_corr_load(None, b"x") == N.PPPM_ERR_INVALID_ARG
     L.pppm_corr_destroy(None)
+
+
+def test_wc_fold_validates_arguments(pppm_lib):
+    L = pppm_lib
+    assert L.pppm_wc_fold(None, 5, 0, None, None, None, None, None, None, None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_wc_fold_f32(None, -1, 0, None, None, None, None, None, None, None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_wc_fold(None, 0, 0, None, None, None, None, None, None, None, None) == N.PPPM_OK

@@ -182,3 +182,50 @@ def init_mlp_params(seed: int, n_in: int = 48, n_hidden: int = 64, n_out: int = 
         parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
         parts.append(np.zeros(fan_out))
     return np.concatenate(parts).astype(np.float32)
+
+
+def dw_jacobian(wb: WaterBox, seed: int, scale: float = 0.02, dtype=np.float64, values: bool = True):
+    """A synthetic Deep-Wannier Jacobian for the fold of Eq. DPLR:F_final, with
+    the sparsity of a local model: the displacement Delta_n of the WC of
+    molecule n depends on the three atoms of every molecule whose lattice
+    point lies within one lattice step of n's (periodic; 27 molecules, 81
+    atoms when all points are occupied).  Blocks are N(0, scale) 3 x 3.
+
+    Atoms are the first 3 n_mol sites (O then H), WC n is hosted by O n.
+    Returns compressed rows per atom: host_ptr (int32), host_wc (int32),
+    jac_ptr (int64), jac_wc (int32), jac (nnz x 3 x 3, ``dtype``; None without
+    ``values``, for callers that draw the blocks themselves)."""
+    n_mol = wb.n_mol
+    L = float(wb.box[0])
+    ns = int(math.ceil(round(n_mol ** (1.0 / 3.0), 9)))
+    while ns ** 3 < n_mol:
+        ns += 1
+    spacing = L / ns
+    o = wb.pos[:n_mol]
+    lat = np.floor(o / spacing).astype(np.int64) % ns
+    grid = np.full((ns, ns, ns), -1, np.int64)
+    grid[lat[:, 0], lat[:, 1], lat[:, 2]] = np.arange(n_mol)
+    offs = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)])
+    cx = (lat[:, None, 0] + offs[None, :, 0]) % ns
+    cy = (lat[:, None, 1] + offs[None, :, 1]) % ns
+    cz = (lat[:, None, 2] + offs[None, :, 2]) % ns
+    nb = grid.ravel()[(cx * ns + cy) * ns + cz]                      # (n_mol, 27) molecule or -1
+    # the relation is symmetric: atom j of molecule m feeds the WCs of m's neighbours
+    nbs = np.sort(nb, axis=1)
+    valid = nbs >= 0
+    cnt = valid.sum(axis=1)
+    o_rows = nbs[valid]                                              # O atoms, molecule order
+    h_rows = np.repeat(nbs, 2, axis=0)[np.repeat(valid, 2, axis=0)]  # H1, H2 of each molecule
+    wcs = np.concatenate([o_rows, h_rows])
+    n_atoms = 3 * n_mol
+    jac_ptr = np.zeros(n_atoms + 1, np.int64)
+    jac_ptr[1:] = np.cumsum(np.concatenate([cnt, np.repeat(cnt, 2)]))
+    jac = None
+    if values:
+        rng = np.random.default_rng(seed)
+        jac = (rng.standard_normal(size=(wcs.size, 3, 3), dtype=np.float32) * np.float32(scale)).astype(dtype)
+    host_ptr = np.zeros(n_atoms + 1, np.int32)
+    host_ptr[1:n_mol + 1] = np.arange(1, n_mol + 1)
+    host_ptr[n_mol + 1:] = n_mol
+    host_wc = np.arange(n_mol, dtype=np.int32)
+    return host_ptr, host_wc, jac_ptr, wcs.astype(np.int32), jac
