@@ -87,26 +87,51 @@ k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ 
         riz[j] = ract[j] ? row % P : 0;
         roff[j] = riy[j] * EZ + riz[j];
     }
+    T* ww = st_w + warp * 8 * WSP;
+    int* wcell = st_cell + warp * 8;
+    int* worig = st_orig + warp * 8;
+    const int nsites = s1 - s0;
+    // registers holding the next batch of 8 sites (weights, cell, original
+    // index): the first batch is fetched while the TMA copy is in flight, each
+    // later one while the previous batch is being interpolated
+    constexpr int NQ = (8 * WS + 31) / 32;
+    T nw[NQ];
+    int ncell = 0, norig = 0;
+    auto fetch = [&](int b) {
+        const int nb = min(8, nsites - b);
+        if (nb <= 0) return;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int k = lane + 32 * q;
+            if (k < nb * WS) nw[q] = __ldg(&swt[(size_t)(s0 + b) * WS + k]);
+        }
+        if (lane < nb) {
+            ncell = __ldg(&scell[s0 + b + lane]);
+            norig = __ldg(&sorig[s0 + b + lane]);
+        }
+    };
+    fetch(warp * 8);
     if (!mbar_wait_bounded(mbar_s, 0)) {
         if (threadIdx.x == 0) atomicOr(status, 2);
         mbar_wait_bounded(mbar_s, 0);  // give the copy in flight a second bounded chance to land
         return;
     }
-    T* ww = st_w + warp * 8 * WSP;
-    int* wcell = st_cell + warp * 8;
-    int* worig = st_orig + warp * 8;
-    const int nsites = s1 - s0;
     for (int b = warp * 8; b < nsites; b += kGatherWarps * 8) {
         const int nb = min(8, nsites - b);
-        for (int k = lane; k < nb * WS; k += 32) {
-            const int j = k / WS, a = k - j * WS;
-            ww[j * WSP + a] = swt[(size_t)(s0 + b + j) * WS + a];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int k = lane + 32 * q;
+            if (k < nb * WS) {
+                const int j = k / WS, a = k - j * WS;
+                ww[j * WSP + a] = nw[q];
+            }
         }
         if (lane < nb) {
-            wcell[lane] = scell[s0 + b + lane];
-            worig[lane] = sorig[s0 + b + lane];
+            wcell[lane] = ncell;
+            worig[lane] = norig;
         }
         __syncwarp();
+        fetch(b + kGatherWarps * 8);
         T v[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = T(0);

@@ -19,17 +19,33 @@ constexpr int kSpreadWarps = 4;
 constexpr int kFastCap = 256;  // sites per tile ordered by index in the fast spread
 
 // Spread: as k_spread, with the tile's records staged through shared memory in
-// batches of 32 (one coalesced load per lane instead of one dependent load per
-// site) and a padded patch pitch (PZ odd) that keeps the p^2 stencil rows of a
-// site in distinct banks.
+// batches of 32 (the next batch's weights are loaded into registers, as
+// 16-byte vectors, while the current one is spread) and a padded patch pitch
+// (PZ odd) that keeps the p^2 stencil rows of a site in distinct banks.  The
+// canonical order (by original index) comes from ranking the tile's sites by
+// counting: one pass of broadcast compares, no sorting network.
+template <typename T>
+struct Vec16T;
+template <>
+struct Vec16T<float> {
+    typedef float4 t;
+};
+template <>
+struct Vec16T<double> {
+    typedef double2 t;
+};
+
 template <typename T, int P, int TILE>
-struct SpreadWarpSmem {
+struct __align__(16) SpreadWarpSmem {  // 16-byte aligned: staged rows take vector stores
     static constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
-    static constexpr int WSP = wstride(P) + 4;  // staging row pitch (keeps vector stores conflict-light)
-    T st_w[32][WSP];
+    static constexpr int WSP = wstride(P) + 4;  // staging row pitch (conflict-free 16-byte stores)
+    union {
+        int keys[kFastCap];  // original indices, while ranking
+        T st_w[32][WSP];     // staged weights, while spreading
+    } u;
     T pt[PSIZE];
     int st_cell[32];
-    int2 keys[kFastCap];
+    short perm[kFastCap];  // canonical position -> slot in the tile
 };
 
 template <typename T, int P, int TILE>
@@ -37,34 +53,39 @@ __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
               const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch) {
     typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
+    typedef typename Vec16T<T>::t V;
     constexpr int E = WarpSmem::E, PZ = WarpSmem::PZ, PLANE = WarpSmem::PLANE, PSIZE = WarpSmem::PSIZE;
-    constexpr int WS = wstride(P);
+    constexpr int WS = wstride(P), NV = WS * (int)sizeof(T) / 16;  // 16-byte vectors per weight row
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x * kSpreadWarps + warp;
     WarpSmem& W = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
     if (tile >= g.ntiles) return;  // whole warp; no block-level barrier below
-    for (int i = lane; i < PSIZE; i += 32) W.pt[i] = T(0);
     const int s0 = tile_start[tile];
     const int c = tile_start[tile + 1] - s0;
-    const bool sorted = c > 1 && c <= kFastCap;
-    if (sorted) {
-        int cp = 2;
-        while (cp < c) cp <<= 1;
-        for (int i = lane; i < cp; i += 32)
-            W.keys[i] = i < c ? make_int2(sorig[s0 + i], s0 + i) : make_int2(INT_MAX, -1);
-        __syncwarp();
-        for (int k = 2; k <= cp; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = lane; i < cp; i += 32) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const int2 a = W.keys[i], b = W.keys[ixj];
-                        if ((a.x > b.x) == ((i & k) == 0)) { W.keys[i] = b; W.keys[ixj] = a; }
-                    }
-                }
-                __syncwarp();
-            }
+    const bool ranked = c > 1 && c <= kFastCap;
+    if (ranked) {
+        for (int i = lane; i < c; i += 32) W.u.keys[i] = __ldg(&sorig[s0 + i]);
+    }
+    for (int i = lane; i < PSIZE; i += 32) W.pt[i] = T(0);
+    __syncwarp();
+    if (ranked) {
+        // rank of item i = number of items with a smaller original index
+        constexpr int MI = kFastCap / 32;
+        int key[MI], rank[MI];
+#pragma unroll
+        for (int m = 0; m < MI; ++m) {
+            key[m] = lane + 32 * m < c ? W.u.keys[lane + 32 * m] : INT_MAX;
+            rank[m] = 0;
+        }
+        for (int j = 0; j < c; ++j) {
+            const int kj = W.u.keys[j];
+#pragma unroll
+            for (int m = 0; m < MI; ++m) rank[m] += kj < key[m];
+        }
+#pragma unroll
+        for (int m = 0; m < MI; ++m)
+            if (lane + 32 * m < c) W.perm[rank[m]] = (short)(lane + 32 * m);
     }
     __syncwarp();
     // lane -> stencil rows (iy, iz); orders above 5 have more rows than lanes
@@ -79,27 +100,40 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
         riz[j] = ract[j] ? row % P : 0;
         roff[j] = riy[j] * PZ + riz[j];
     }
+    // registers holding the next batch's weights and cell
+    V nw[NV];
+    int ncell = 0;
+    auto fetch = [&](int t0) {
+        if (t0 + lane < c) {
+            const int s = s0 + (ranked ? (int)W.perm[t0 + lane] : t0 + lane);
+            const V* src = reinterpret_cast<const V*>(swt + (size_t)s * WS);
+#pragma unroll
+            for (int a = 0; a < NV; ++a) nw[a] = __ldg(&src[a]);
+            ncell = __ldg(&scell[s]);
+        }
+    };
+    fetch(0);
     for (int t0 = 0; t0 < c; t0 += 32) {
         const int nb = min(32, c - t0);
         if (lane < nb) {
-            const int s = sorted ? W.keys[t0 + lane].y : s0 + t0 + lane;
-            const T* src = swt + (size_t)s * WS;
+            V* dst = reinterpret_cast<V*>(&W.u.st_w[lane][0]);
 #pragma unroll
-            for (int a = 0; a < WS; ++a) W.st_w[lane][a] = src[a];
-            W.st_cell[lane] = scell[s];
+            for (int a = 0; a < NV; ++a) dst[a] = nw[a];
+            W.st_cell[lane] = ncell;
         }
         __syncwarp();
+        fetch(t0 + 32);  // in flight while this batch is spread
         for (int j = 0; j < nb; ++j) {
             const int cl = W.st_cell[j];
             const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
             T wxq[P];
 #pragma unroll
-            for (int a = 0; a < P; ++a) wxq[a] = W.st_w[j][a];
+            for (int a = 0; a < P; ++a) wxq[a] = W.u.st_w[j][a];
             T* base0 = W.pt + lx * PLANE + ly * PZ + lz;
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr) {
                 if (ract[jr]) {
-                    const T wyz = W.st_w[j][P + riy[jr]] * W.st_w[j][2 * P + riz[jr]];
+                    const T wyz = W.u.st_w[j][P + riy[jr]] * W.u.st_w[j][2 * P + riz[jr]];
                     T* b = base0 + roff[jr];
 #pragma unroll
                     for (int a = 0; a < P; ++a) b[a * PLANE] += wxq[a] * wyz;
