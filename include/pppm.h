@@ -358,6 +358,30 @@ int pppm_wc_fold_f32(void *stream, int64_t n_atoms, int64_t n_wc, const float *f
                      const int *jac_wc, const float *jac, float *f_atoms, int *status);
 
 /*
+ * Captured steps.  pppm_graph_create runs one ordinary compute call on the
+ * stream (so that every buffer is allocated), then captures a second one as a
+ * CUDA graph.  pppm_graph_launch replays it on a stream; pos and q may be new
+ * device pointers (NULL: keep the previous ones), which are patched into the
+ * one kernel that reads them, so a run can hand a different resident frame to
+ * every step without a copy.  The site count, the outputs (energy, forces,
+ * virial) and the plan's options are those of the capture: to change them,
+ * destroy the graph and create a new one.  The stream must not be the legacy
+ * default stream, and per-kernel timing (pppm_profile_enable) must be off.
+ * Replays of one graph must not overlap each other or other calls on the same
+ * plan (they share its workspace).  Destroy the graph before the plan.
+ * Errors: PPPM_ERR_INVALID_ARG (null or empty arguments, profiling on, input
+ * precision differing from the capture's), PPPM_ERR_CUDA.
+ */
+typedef struct pppm_graph pppm_graph;
+int pppm_graph_create(pppm_plan *plan, void *stream, const double *pos, const double *q, int64_t n,
+                      double *energy, double *forces, double *virial, pppm_graph **out);
+int pppm_graph_create_f32(pppm_plan *plan, void *stream, const float *pos, const float *q, int64_t n,
+                          double *energy, float *forces, double *virial, pppm_graph **out);
+int pppm_graph_launch(pppm_graph *graph, void *stream, const double *pos, const double *q);
+int pppm_graph_launch_f32(pppm_graph *graph, void *stream, const float *pos, const float *q);
+void pppm_graph_destroy(pppm_graph *graph);
+
+/*
  * Per-kernel timing (for benchmarks).  While enabled, every kernel launch of a
  * compute call is bracketed by CUDA events on the compute stream.
  * pppm_profile_read synchronizes, writes for each kernel slot i < cap the

@@ -93,6 +93,11 @@ SIGNATURES = {
     "pppm_corr_destroy": (None, [vp]),
     "pppm_wc_fold": (cint, [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
     "pppm_wc_fold_f32": (cint, [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "pppm_graph_create": (cint, [vp, vp, vp, vp, i64, vp, vp, vp, ctypes.POINTER(vp)]),
+    "pppm_graph_create_f32": (cint, [vp, vp, vp, vp, i64, vp, vp, vp, ctypes.POINTER(vp)]),
+    "pppm_graph_launch": (cint, [vp, vp, vp, vp]),
+    "pppm_graph_launch_f32": (cint, [vp, vp, vp, vp]),
+    "pppm_graph_destroy": (None, [vp]),
     "pppm_profile_enable": (cint, [vp, cint]),
     "pppm_profile_read": (cint, [vp, vp, vp, cint]),
     "pppm_profile_name": (ctypes.c_char_p, [cint]),

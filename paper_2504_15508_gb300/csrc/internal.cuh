@@ -96,6 +96,7 @@ template <typename T, typename In>
 cudaError_t launch_bin(cudaStream_t s, const Geo& g, const In* pos, const In* q, int n, int* tile_count,
                        int* tile_of, int* slot_of, Rec<T>* rec, int* cell, int* status);
 cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int* start);
+bool is_bin_kernel(const void* func);
 template <typename T>
 cudaError_t launch_scatter(cudaStream_t s, const Geo& g, int n, const int* tile_of, const int* slot_of,
                            const int* tile_start, const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell,

@@ -229,4 +229,10 @@ PPPM_INST_TI(float, double)
 PPPM_INST_TI(double, float)
 PPPM_INST_TI(double, double)
 
+// the bin kernel's entry (the one node of a captured step that reads the sites)
+bool is_bin_kernel(const void* func) {
+    return func == (const void*)k_bin<float, float> || func == (const void*)k_bin<float, double> ||
+           func == (const void*)k_bin<double, float> || func == (const void*)k_bin<double, double>;
+}
+
 }  // namespace pppm

@@ -138,6 +138,10 @@ class Plan:
         N.check(rc, "pppm_compute_host")
         return float(energy[0]), forces, virial
 
+    def graph(self, pos: torch.Tensor, q: torch.Tensor, out=None, stream=None) -> "StepGraph":
+        """Capture one force evaluation as a CUDA graph (see StepGraph)."""
+        return StepGraph(self, pos, q, out=out, stream=stream)
+
     # ------------------------------------------------------------ stages
     def spread(self, pos: torch.Tensor, q: torch.Tensor, stream=None) -> torch.Tensor:
         """Charge density on the mesh (plan precision), from float64 sites."""
@@ -175,6 +179,64 @@ class Plan:
         N.check(self._lib.pppm_fields(self._h, _stream(stream), _ptr(pos), _ptr(q), pos.shape[0], _ptr(f)),
                 "pppm_fields")
         return f
+
+
+class StepGraph:
+    """One captured force evaluation of a plan, replayed with launch().
+
+    The outputs (energy, forces, virial: ``self.out``), the site count and the
+    plan's options are fixed at capture; launch() may pass new position and
+    charge tensors of the same shape and dtype.  The capture stream must not be
+    the legacy default stream; by default a dedicated stream is used."""
+
+    def __init__(self, plan: Plan, pos, q, out=None, stream=None):
+        Plan._check_sites(pos, q)
+        L = N.lib()
+        self._lib = L
+        self.plan = plan
+        n = pos.shape[0]
+        if out is None:
+            out = (torch.empty(1, dtype=torch.float64, device=pos.device),
+                   torch.empty((n, 3), dtype=pos.dtype, device=pos.device),
+                   torch.empty(6, dtype=torch.float64, device=pos.device))
+        self.out = out
+        self.dtype = pos.dtype
+        self.shape = tuple(pos.shape)
+        if stream is None:
+            stream = torch.cuda.Stream(device=pos.device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        fn = L.pppm_graph_create_f32 if pos.dtype == torch.float32 else L.pppm_graph_create
+        N.check(fn(plan.handle, _stream(stream), _ptr(pos), _ptr(q), n, _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
+                   ctypes.byref(h)), "pppm_graph_create")
+        self._h = h
+        stream.synchronize()  # the capture's warm-up call shares the plan's workspace with later launches
+        self._refs = (pos, q)
+
+    def launch(self, pos=None, q=None, stream=None):
+        """Replay on `stream` (default: the capture stream) with new sites (or
+        the previous ones); returns the output tensors."""
+        for t in (pos, q):
+            if t is not None and (t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous()):
+                raise ValueError("sites must be contiguous CUDA tensors of the captured dtype")
+        if pos is not None and tuple(pos.shape) != self.shape:
+            raise ValueError("the site count is fixed at capture")
+        fn = self._lib.pppm_graph_launch_f32 if self.dtype == torch.float32 else self._lib.pppm_graph_launch
+        N.check(fn(self._h, _stream(stream if stream is not None else self.stream), _ptr(pos), _ptr(q)),
+                "pppm_graph_launch")
+        self._refs = (pos if pos is not None else self._refs[0], q if q is not None else self._refs[1])
+        return self.out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pppm_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BatchPlan:

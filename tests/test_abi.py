@@ -95,3 +95,13 @@ def test_wc_fold_validates_arguments(pppm_lib):
     assert L.pppm_wc_fold(None, 5, 0, None, None, None, None, None, None, None, None) == N.PPPM_ERR_INVALID_ARG
     assert L.pppm_wc_fold_f32(None, -1, 0, None, None, None, None, None, None, None, None) == N.PPPM_ERR_INVALID_ARG
     assert L.pppm_wc_fold(None, 0, 0, None, None, None, None, None, None, None, None) == N.PPPM_OK
+
+
+def test_graph_calls_validate_arguments(pppm_lib):
+    L = pppm_lib
+    h = ctypes.c_void_p()
+    assert L.pppm_graph_create(None, None, None, None, 1, None, None, None, ctypes.byref(h)) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_graph_create_f32(None, None, None, None, 1, None, None, None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_graph_launch(None, None, None, None) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_graph_launch_f32(None, None, None, None) == N.PPPM_ERR_INVALID_ARG
+    L.pppm_graph_destroy(None)

@@ -1,0 +1,55 @@
+"""Captured steps: a replayed CUDA graph gives bitwise the results of the
+ordinary call, for the captured sites and for new site pointers."""
+import numpy as np
+import pytest
+import torch
+
+from workloads.water import make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(name, prec):
+    from paper_2504_15508_gb300.pppm import Plan
+    wb, w = make_workload(name)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    plan = Plan(wb.box, w["mesh"], w["order"], w["beta"], precision=prec)
+    pos = torch.tensor(wb.pos, dtype=dt, device="cuda")
+    q = torch.tensor(wb.q, dtype=dt, device="cuda")
+    return plan, pos, q
+
+
+@pytest.mark.parametrize("name,prec", [("water4096", "fp32"), ("water64", "fp64"), ("water72192_m128", "fp32")])
+def test_replay_matches_eager(cuda_device, name, prec):
+    plan, pos, q = _setup(name, prec)
+    g = plan.graph(pos, q)
+    # a second frame at another address
+    rng = np.random.default_rng(1)
+    pos2 = (pos + torch.tensor(rng.normal(0, 0.05, size=tuple(pos.shape)), dtype=pos.dtype, device="cuda")).contiguous()
+    for p in (pos, pos2, pos, pos2):
+        e, f, v = (t.clone() for t in g.launch(p, q, stream=torch.cuda.current_stream()))
+        e0, f0, v0 = plan.compute(p, q)
+        torch.cuda.synchronize()
+        assert torch.equal(f, f0) and torch.equal(e, e0) and torch.equal(v, v0)
+    # no new pointers: the previous sites again
+    e, f, v = (t.clone() for t in g.launch(stream=torch.cuda.current_stream()))
+    torch.cuda.synchronize()
+    assert torch.equal(f, f0)
+    g.close()
+
+
+def test_graph_rejects_bad_use(cuda_device):
+    from paper_2504_15508_gb300 import _native as N
+    plan, pos, q = _setup("water64", "fp32")
+    with pytest.raises(N.PPPMError):
+        plan.graph(pos, q, stream=torch.cuda.default_stream())   # legacy stream cannot be captured
+    plan.profile(True)
+    with pytest.raises(N.PPPMError):
+        plan.graph(pos, q)
+    plan.profile(False)
+    g = plan.graph(pos, q)
+    with pytest.raises(ValueError):
+        g.launch(pos.double(), q.double())
+    with pytest.raises(ValueError):
+        g.launch(pos[:10].contiguous(), q[:10].contiguous())
+    g.close()
