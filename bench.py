@@ -394,15 +394,19 @@ def run_ours(args):
     host_frames = frames[:E].cpu().pin_memory()
     host_q = q.cpu().pin_memory()
     hq = host_q.numpy()
+    # results land in pinned host buffers owned by the caller
+    h_out = (torch.zeros(1, dtype=torch.float64).pin_memory().numpy(),
+             torch.zeros((n, 3), dtype=torch.float32).pin_memory().numpy(),
+             torch.zeros(6, dtype=torch.float64).pin_memory().numpy())
     for k in range(min(3, E)):
-        plan.compute_host(host_frames[k].numpy(), hq)
+        plan.compute_host(host_frames[k].numpy(), hq, out=h_out)
     t0 = time.perf_counter()
     for k in range(E):
-        e_h, f_h, v_h = plan.compute_host(host_frames[k].numpy(), hq)
+        e_h, f_h, v_h = plan.compute_host(host_frames[k].numpy(), hq, out=h_out)
     e2e_s = time.perf_counter() - t0
     e2e_val = world * E / e2e_s if world == 1 else E / e2e_s * world
     e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 12 * n + 56,
-           "steps": E, "host_memory": "pinned"}
+           "steps": E, "host_memory": "pinned inputs and outputs"}
 
     # the WC force fold (Eq. DPLR:F_final) on this step's forces, timed on its own
     wc_fold_line = run_wc_fold(args, wb, forces, flush, stream, peak) if not args.no_wc_fold else None

@@ -369,8 +369,11 @@ int pppm_wc_fold_f32(void *stream, int64_t n_atoms, int64_t n_wc, const float *f
  * default stream, and per-kernel timing (pppm_profile_enable) must be off.
  * Replays of one graph must not overlap each other or other calls on the same
  * plan (they share its workspace).  Destroy the graph before the plan.
+ * A launch fails with PPPM_ERR_INVALID_ARG once the plan has changed since
+ * the capture (an option, the potential output, or a workspace reallocation
+ * by a compute call with more sites or another tile size); create a new graph.
  * Errors: PPPM_ERR_INVALID_ARG (null or empty arguments, profiling on, input
- * precision differing from the capture's), PPPM_ERR_CUDA.
+ * precision differing from the capture's, plan changed), PPPM_ERR_CUDA.
  */
 typedef struct pppm_graph pppm_graph;
 int pppm_graph_create(pppm_plan *plan, void *stream, const double *pos, const double *q, int64_t n,

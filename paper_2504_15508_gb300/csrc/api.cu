@@ -132,6 +132,7 @@ int build_field_map(pppm_plan* P);
 // (Re)build the tile geometry, the patch scratch and the fold cover lists.
 int setup_tiles(pppm_plan* P, int T) {
     if (T == P->tileT && P->patch) return PPPM_OK;
+    ++P->gen;
     Geo& g = P->g;
     const int p = P->order;
     g.T = T;
@@ -209,6 +210,7 @@ int setup_tiles(pppm_plan* P, int T) {
 int reserve_sites(pppm_plan* P, int64_t n) {
     if (n <= P->cap) return PPPM_OK;
     if (n > (int64_t)1 << 30) return PPPM_ERR_TOO_LARGE;
+    ++P->gen;
     dfree(P->tile_of);
     dfree(P->slot_of);
     dfree(P->rec);
@@ -386,6 +388,8 @@ int compute_host(pppm_plan* P, const In* pos, const In* q, int64_t n, double* en
     const size_t need = sizeof(In) * (size_t)(7 * n) + 8 * sizeof(double) + 256;
     if (need > P->h_stage_bytes) {
         dfree(P->h_stage);
+    if (P->h_status) cudaFreeHost(P->h_status);
+    if (P->host_graph) cudaGraphExecDestroy(P->host_graph);
         P->h_stage_bytes = 0;
         int rc;
         if ((rc = dalloc(&P->h_stage, need)) != PPPM_OK) return rc;
@@ -401,13 +405,49 @@ int compute_host(pppm_plan* P, const In* pos, const In* q, int64_t n, double* en
         CK(cudaMemcpyAsync(d_pos, pos, sizeof(In) * 3 * n, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d_q, q, sizeof(In) * n, cudaMemcpyHostToDevice, s));
     }
-    int rc = compute_dispatch<In>(P, s, d_pos, d_q, n, d_e, d_f, d_v);
-    if (rc != PPPM_OK) return rc;
+    // the device part replays a graph captured on an earlier call with the
+    // same site count and plan state (its buffers are the plan's own)
+    const bool fits = P->host_graph && P->host_graph_n == n && P->host_graph_in == (int)sizeof(In) &&
+                      P->host_graph_gen == P->gen && !P->prof_on;
+    if (fits) {
+        CK(cudaGraphLaunch(P->host_graph, s));
+        P->last = s;
+    } else {
+        int rc = compute_dispatch<In>(P, s, d_pos, d_q, n, d_e, d_f, d_v);
+        if (rc != PPPM_OK) return rc;
+        if (P->host_graph) {
+            cudaGraphExecDestroy(P->host_graph);
+            P->host_graph = nullptr;
+        }
+        if (n > 0 && !P->prof_on) {  // capture the same call for the next ones
+            cudaGraph_t gr = nullptr;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                rc = compute_dispatch<In>(P, s, d_pos, d_q, n, d_e, d_f, d_v);
+                const cudaError_t ce = cudaStreamEndCapture(s, &gr);
+                if (rc == PPPM_OK && ce == cudaSuccess && gr &&
+                    cudaGraphInstantiate(&P->host_graph, gr, 0) == cudaSuccess) {
+                    P->host_graph_n = n;
+                    P->host_graph_in = (int)sizeof(In);
+                    P->host_graph_gen = P->gen;
+                } else {
+                    P->host_graph = nullptr;
+                }
+                if (gr) cudaGraphDestroy(gr);
+                cudaGetLastError();  // a failed capture leaves no sticky error; the eager result stands
+            }
+        }
+    }
+    if (!P->h_status) CK(cudaMallocHost((void**)&P->h_status, sizeof(int)));
     CK(cudaMemcpyAsync(energy, d_e, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(virial, d_v, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (n > 0) CK(cudaMemcpyAsync(forces, d_f, sizeof(In) * 3 * n, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return pppm_status(P);
+    CK(cudaMemcpyAsync(P->h_status, P->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));  // one synchronization for the outputs and the status word
+    if (*P->h_status) {
+        CK(cudaMemset(P->status, 0, sizeof(int)));
+        return PPPM_ERR_NONFINITE;
+    }
+    return PPPM_OK;
 }
 
 }  // namespace
@@ -535,6 +575,7 @@ int pppm_create(const double box[3], const int mesh[3], int order, double beta, 
 
 int pppm_set_options(pppm_plan* P, const pppm_options* opt) {
     if (!P || !opt) return PPPM_ERR_INVALID_ARG;
+    ++P->gen;
     if (!std::isfinite(opt->prefactor) || opt->alias < 0 || opt->alias > 8 || opt->tile < 0 || opt->tile > 16 ||
         (opt->tile != 0 && opt->tile != 4 && opt->tile != 8 && opt->tile != 16))
         return PPPM_ERR_INVALID_ARG;
@@ -589,6 +630,8 @@ void pppm_destroy(pppm_plan* P) {
     dfree(P->sorig);
     dfree(P->swt);
     dfree(P->h_stage);
+    if (P->h_status) cudaFreeHost(P->h_status);
+    if (P->host_graph) cudaGraphExecDestroy(P->host_graph);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : P->pend_a) cudaEventDestroy(e);
     for (cudaEvent_t e : P->pend_b) cudaEventDestroy(e);
@@ -598,6 +641,7 @@ void pppm_destroy(pppm_plan* P) {
 
 int pppm_set_potential(pppm_plan* P, int on) {
     if (!P) return PPPM_ERR_INVALID_ARG;
+    ++P->gen;
     P->potential = on != 0;
     return PPPM_OK;
 }

@@ -28,6 +28,7 @@ struct pppm_graph {
     int n = 0;
     void* ptrs[6] = {};
     int in_size = 4;  // bytes per input value (float or double)
+    uint64_t gen = 0;  // plan state at capture
 };
 
 namespace {
@@ -88,6 +89,7 @@ int graph_create(pppm_plan* P, void* stream, const In* pos, const In* q, int64_t
     }
     if (!G->bin) return fail(PPPM_ERR_CUDA);
     if (cudaGraphInstantiate(&G->exec, g, 0) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    G->gen = P->gen;
     *out = G;
     return PPPM_OK;
 }
@@ -95,6 +97,8 @@ int graph_create(pppm_plan* P, void* stream, const In* pos, const In* q, int64_t
 template <typename In>
 int graph_launch(pppm_graph* G, void* stream, const In* pos, const In* q) {
     if (!G || !G->exec || (int)sizeof(In) != G->in_size) return PPPM_ERR_INVALID_ARG;
+    // the plan reallocated a buffer or changed an option since the capture
+    if (G->plan->gen != G->gen) return PPPM_ERR_INVALID_ARG;
     if (cudaSetDevice(G->plan->device) != cudaSuccess) return PPPM_ERR_CUDA;
     const void* np = pos ? (const void*)pos : G->pos;
     const void* nq = q ? (const void*)q : G->q;

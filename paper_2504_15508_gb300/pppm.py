@@ -124,14 +124,22 @@ class Plan:
                 "pppm_compute")
         return energy, forces, virial
 
-    def compute_host(self, pos: np.ndarray, q: np.ndarray):
-        """The same evaluation from host numpy arrays (copies inside the call)."""
+    def compute_host(self, pos: np.ndarray, q: np.ndarray, out=None):
+        """The same evaluation from host numpy arrays (copies inside the call).
+        out = (energy (1,), forces (n, 3), virial (6,)) host arrays to fill
+        (pinned memory makes the device-to-host copies direct)."""
         pos = np.ascontiguousarray(pos)
         q = np.ascontiguousarray(q, dtype=pos.dtype)
         n = pos.shape[0]
-        energy = np.zeros(1)
-        virial = np.zeros(6)
-        forces = np.zeros((n, 3), dtype=pos.dtype)
+        if out is None:
+            energy = np.zeros(1)
+            virial = np.zeros(6)
+            forces = np.zeros((n, 3), dtype=pos.dtype)
+        else:
+            energy, forces, virial = out
+            if (energy.dtype != np.float64 or virial.dtype != np.float64 or forces.dtype != pos.dtype
+                    or forces.shape != (n, 3) or not forces.flags.c_contiguous):
+                raise ValueError("out must be (float64 (1,), (n, 3) of the site dtype, float64 (6,))")
         fn = self._lib.pppm_compute_host_f32 if pos.dtype == np.float32 else self._lib.pppm_compute_host
         rc = fn(self._h, pos.ctypes.data, q.ctypes.data, n, energy.ctypes.data, forces.ctypes.data,
                 virial.ctypes.data)

@@ -53,3 +53,37 @@ def test_graph_rejects_bad_use(cuda_device):
     with pytest.raises(ValueError):
         g.launch(pos[:10].contiguous(), q[:10].contiguous())
     g.close()
+
+
+def test_launch_refuses_a_changed_plan(cuda_device):
+    from paper_2504_15508_gb300 import _native as N
+    plan, pos, q = _setup("water64", "fp32")
+    g = plan.graph(pos, q)
+    g.launch(pos, q)
+    plan.set_options(prefactor=2.0)          # options are baked into the capture
+    with pytest.raises(N.PPPMError):
+        g.launch(pos, q)
+    g.close()
+    g = plan.graph(pos, q)
+    big = torch.cat([pos, pos + 0.5]).contiguous()
+    plan.compute(big, torch.cat([q, q]).contiguous())   # more sites: the site buffers grow
+    with pytest.raises(N.PPPMError):
+        g.launch(pos, q)
+    g.close()
+
+
+def test_host_call_replays_its_graph_bitwise(cuda_device):
+    """The host-pointer call captures its device part on the first call and
+    replays it afterwards; every call must give the ordinary result."""
+    plan, pos, q = _setup("water4096", "fp32")
+    e0, f0, v0 = plan.compute(pos, q)
+    torch.cuda.synchronize()
+    hp, hq = pos.cpu().numpy(), q.cpu().numpy()
+    out = (np.zeros(1), np.zeros(tuple(pos.shape), np.float32), np.zeros(6))
+    for k in range(3):
+        e, f, v = plan.compute_host(hp, hq, out=out)
+        assert e == e0.item() and np.array_equal(f, f0.cpu().numpy()) and np.array_equal(v, v0.cpu().numpy())
+    # a changed plan is recaptured, not replayed stale
+    plan.set_options(prefactor=2.0)
+    e, f, v = plan.compute_host(hp, hq, out=out)
+    assert np.allclose(f, 2.0 * f0.cpu().numpy(), rtol=1e-6, atol=0)
