@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--frames", type=int, default=N_FRAMES, help="random-walk frames held on the device")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-wc-fold", action="store_true", help="skip the WC force fold measurement")
-    ap.add_argument("--workload", default="water72192", choices=["water72192", "batched96", "learned64"],
+    ap.add_argument("--workload", default="water72192", choices=["water72192", "batched96", "learned64", "overlap"],
                     help="water72192: the 216,576-atom system (default); batched96: 96 independent boxes; "
-                         "learned64: the same system on a 64^3 mesh with the learned correction")
+                         "learned64: the same system on a 64^3 mesh with the learned correction; "
+                         "overlap: the 128^3 step concurrent with a short-range stand-in on a second stream")
     ap.add_argument("--train-frames", type=int, default=2000, help="learned64: training frames (20 bases)")
     ap.add_argument("--train-steps", type=int, default=20000, help="learned64: Adam steps")
     ap.add_argument("--train-batch", type=int, default=8192, help="learned64: sites per Adam step")
@@ -629,8 +630,135 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------- long/short-range overlap
+class ShortRangeStandIn:
+    """A stand-in for the short-range model's per-atom cost: the fitting-net
+    shape of the paper's DP model (three hidden layers of 240, tanh) applied
+    to a synthetic 128-wide descriptor per atom, in BF16 through torch's
+    cuBLAS matmuls.  It is load, not part of the method: its only role is to
+    occupy the GPU the way short-range inference would."""
+
+    def __init__(self, n_atoms, device, seed=17, width=240, d_in=128):
+        import torch
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+        self.x = torch.randn((n_atoms, d_in), generator=g, device=device).to(torch.bfloat16)
+        dims = [d_in, width, width, width, 1]
+        self.w = [(torch.randn((dims[i], dims[i + 1]), generator=g, device=device) / dims[i] ** 0.5)
+                  .to(torch.bfloat16) for i in range(4)]
+        self.flops = 2 * n_atoms * sum(dims[i] * dims[i + 1] for i in range(4))
+        self.out = None
+
+    def __call__(self):
+        import torch
+        h = self.x
+        for w in self.w[:-1]:
+            h = torch.tanh(h @ w)
+        self.out = h @ self.w[-1]
+        return self.out
+
+
+def run_overlap(args):
+    """The 128^3 force evaluation (one captured graph) and the short-range
+    stand-in, alone, back to back on one stream, and concurrently on two
+    streams (the long-range one at high priority), as in the paper's overlap
+    of long- and short-range forces (Section "Long-range and Short-range Force
+    Overlap")."""
+    import torch
+
+    from paper_2504_15508_gb300.pppm import Plan
+    from workloads.water import make_workload
+
+    dev = torch.device("cuda", 0)
+    wb, w = make_workload("water72192_m128")
+    n = wb.n
+    pos = torch.tensor(wb.pos, dtype=torch.float32, device=dev)
+    q = torch.tensor(wb.q, dtype=torch.float32, device=dev)
+    plan = Plan(wb.box, w["mesh"], w["order"], w["beta"], precision="fp32")
+    plan.reserve(n)
+    lo = torch.cuda.Stream(device=dev, priority=0)
+    hi = torch.cuda.Stream(device=dev, priority=-1)
+    g = plan.graph(pos, q)
+    sr = ShortRangeStandIn(3 * wb.n_mol, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    main = torch.cuda.current_stream()
+    K = args.steps
+
+    def timed(body):
+        for k in range(max(3, args.warmup)):
+            body()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
+            flush.fill_(float(k))
+            evs[k][0].record(main)
+            body()
+            evs[k][1].record(main)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / K
+
+    def lr_alone():
+        g.launch(pos, q, stream=main)
+
+    def sr_alone():
+        sr()
+
+    def sequential():
+        g.launch(pos, q, stream=main)
+        sr()
+
+    lo2 = torch.cuda.Stream(device=dev, priority=0)
+
+    def concurrent(lr_stream, sr_stream):
+        def body():
+            start = torch.cuda.Event()
+            start.record(main)
+            lr_stream.wait_event(start)
+            sr_stream.wait_event(start)
+            g.launch(pos, q, stream=lr_stream)
+            with torch.cuda.stream(sr_stream):
+                sr()
+            done_lr, done_sr = torch.cuda.Event(), torch.cuda.Event()
+            done_lr.record(lr_stream)
+            done_sr.record(sr_stream)
+            main.wait_event(done_lr)
+            main.wait_event(done_sr)
+        return body
+
+    t_lr = timed(lr_alone)
+    t_sr = timed(sr_alone)
+    t_seq = timed(sequential)
+    t_par = timed(concurrent(hi, lo))      # long range on the high-priority stream
+    t_par_eq = timed(concurrent(lo2, lo))  # both at the same priority
+    f_ref = g.out[1].clone()
+    # results under overlap are those of the step alone
+    g.launch(pos, q, stream=main)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(g.out[1], f_ref))
+    line = {
+        "metric": "long-range step concurrent with a short-range load", "value": 1e3 / t_par,
+        "unit": "steps/s", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": t_par,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+        "config": {"workload": f"overlap: water72192 ({n} sites) PPPM on 128^3 (captured graph, high-priority "
+                               f"stream) with a {3 * wb.n_mol}-atom 128-240-240-240-1 BF16 MLP stand-in "
+                               f"({sr.flops / 1e9:.1f} GFLOP) on a second stream",
+                   "l2": "flushed between timed steps"},
+        "ms": {"long_range_alone": t_lr, "short_range_alone": t_sr, "sequential": t_seq, "concurrent": t_par,
+               "concurrent_equal_priority": t_par_eq},
+        "speedup_vs_sequential": t_seq / t_par,
+        "hidden_fraction_of_shorter": (t_lr + t_sr - t_par) / min(t_lr, t_sr),
+        "short_range_tflops_alone": sr.flops / (t_sr * 1e-3) / 1e12,
+        "pppm_results_unchanged": same,
+    }
+    g.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.impl == "ours" and args.workload == "overlap":
+        run_overlap(args)
+        return
     if args.impl == "ours" and args.workload == "batched96":
         run_batched(args)
         return
