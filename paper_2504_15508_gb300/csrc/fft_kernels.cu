@@ -29,9 +29,6 @@
 namespace pppm {
 
 constexpr int kFftThreads = 256;
-// z passes keep their lines at a pitch of Nz + 8 complex in shared memory, so
-// that neighbouring lines start half a bank cycle apart
-constexpr int kZPad = 8;
 
 // ------------------------------------------------------------------ compile-time radix plan
 // Radices 16, 10 and 8 are DFTs in registers (below), so the workload lengths
@@ -272,9 +269,12 @@ k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restr
             PatchSrc<R> ps) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Nz = eng.len(), Hz = g.Hz, ZP = Nz + kZPad;  // padded line pitch
+    // lines interleaved in shared memory: point t of line p at a[t * pairs + p]
+    // (pairs odd, so that a run of t is conflict-free; lanes walk the lines
+    // in the FFT stages)
+    const int Nz = eng.len(), Hz = g.Hz, PL = pairs;
     C* a = reinterpret_cast<C*>(smem_raw);
-    C* b = a + pairs * ZP;
+    C* b = a + pairs * Nz;
     const int pair0 = blockIdx.x * pairs;
     const int npairs_total = (rows + 1) / 2;
     const int np = min(pairs, npairs_total - pair0);
@@ -294,7 +294,7 @@ k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restr
             for (int t = threadIdx.x & 31; t < Nz; t += 32) {
                 const R va = fold_point(g, ps, cx0, cy0, t);
                 const R vb = fold_point(g, ps, cx1, cy1, t);  // empty slots give 0
-                a[p * ZP + t] = CT<R>::mk(va, vb);
+                a[t * PL + p] = CT<R>::mk(va, vb);
             }
         }
     } else {
@@ -302,15 +302,15 @@ k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restr
             const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
             const R va = in[(int64_t)r0 * Nz + t];
             const R vb = r1 < rows ? in[(int64_t)r1 * Nz + t] : R(0);
-            a[p * ZP + t] = CT<R>::mk(va, vb);
+            a[t * PL + p] = CT<R>::mk(va, vb);
         }
     }
     __syncthreads();
-    C* res = eng.template run<-1, false>(a, b, np, ZP, 1);
+    C* res = eng.template run<-1, true>(a, b, np, 1, PL);
     LINE_LOOP(p, k, np, Hz) {
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
-        const C z = res[p * ZP + k];
-        const C zc = cconj(res[p * ZP + (k == 0 ? 0 : Nz - k)]);
+        const C z = res[k * PL + p];
+        const C zc = cconj(res[(k == 0 ? 0 : Nz - k) * PL + p]);
         const C x0 = cscale(cadd(z, zc), R(0.5));
         const C d = csub(z, zc);  // = 2 i X1
         out[(int64_t)r0 * Hz + k] = x0;
@@ -322,10 +322,12 @@ template <typename T>
 cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw,
                              const T* in, typename Cx<T>::t* out, const PatchSrc<T>& ps) {
     const int rows = g.N[0] * g.N[1];
-    int pairs = (int)((32 * 1024) / (2 * (g.N[2] + kZPad) * sizeof(typename Cx<T>::t)));
-    pairs = pairs < 1 ? 1 : (pairs > 16 ? 16 : pairs);
+    // up to 15 row pairs (an odd count) per block, within 32 KB of shared memory
+    int pairs = (int)((32 * 1024) / (2 * g.N[2] * sizeof(typename Cx<T>::t)));
+    pairs = pairs < 1 ? 1 : (pairs > 15 ? 15 : pairs);
+    pairs |= 1;
     const int npairs = (rows + 1) / 2;
-    const size_t smem = 2ull * pairs * (g.N[2] + kZPad) * sizeof(typename Cx<T>::t);
+    const size_t smem = 2ull * pairs * g.N[2] * sizeof(typename Cx<T>::t);
     return with_engine<T>(rz, tw, [&](auto eng) {
         auto kern = k_fft_z_r2c<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
@@ -639,10 +641,13 @@ __global__ void __launch_bounds__(kFftThreads)
 k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Nz = eng.len(), Hz = g.Hz, ZP = Nz + kZPad;  // padded line pitch
+    // lines interleaved in shared memory: point t of line L at a[t * PL + L],
+    // PL odd (a run of t is conflict-free); lanes walk the lines in the stages
+    const int Nz = eng.len(), Hz = g.Hz;
     const int nf = zo.nf;
+    const int PL = (nf * pairs) | 1;
     C* a = reinterpret_cast<C*>(smem_raw);
-    C* b = a + nf * pairs * ZP;
+    C* b = a + PL * Nz;
     const int pair0 = blockIdx.x * pairs;
     const int npairs_total = (rows + 1) / 2;
     const int np = min(pairs, npairs_total - pair0);
@@ -667,16 +672,16 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
         }
         if (realonly) { h0.y = R(0); h1.y = R(0); }
         if (cj) { h0.y = -h0.y; h1.y = -h1.y; }
-        a[line * ZP + t] = CT<R>::mk(h0.x - h1.y, h0.y + h1.x);  // h0 + i h1
+        a[t * PL + line] = CT<R>::mk(h0.x - h1.y, h0.y + h1.x);  // h0 + i h1
     }
     __syncthreads();
-    C* res = eng.template run<1, false>(a, b, nlines, ZP, 1);
+    C* res = eng.template run<1, true>(a, b, nlines, 1, PL);
     if (!zo.fl.padded) {
         LINE_LOOP(line, t, nlines, Nz) {
             const int f = line / np, p = line - f * np;
             const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
             R* out = reinterpret_cast<R*>(pick4(zo.out, f));
-            const C z = res[line * ZP + t];
+            const C z = res[t * PL + line];
             out[(int64_t)r0 * Nz + t] = z.x;
             if (r1 < rows) out[(int64_t)r1 * Nz + t] = z.y;
         }
@@ -690,7 +695,7 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
     for (int line = threadIdx.x >> 5; line < nlines; line += kFftThreads >> 5) {
         const int f = line / np, p = line - f * np;
         R* out = reinterpret_cast<R*>(pick4(zo.out, f));
-        const C* rrow = res + line * ZP;
+        const C* rrow = res + line;  // point z of this line at rrow[z * PL]
         for (int half = 0; half < 2; ++half) {
             const int r = 2 * (pair0 + p) + half;
             if (r >= rows) break;
@@ -707,7 +712,7 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
                 int zz = pz + kmin;
                 zz += zz < 0 ? Nz : 0;
                 zz -= zz >= Nz ? Nz : 0;
-                const C zv = rrow[zz];
+                const C zv = rrow[zz * PL];
                 const R v = half ? zv.y : zv.x;
                 o00[pz] = v;
                 if (o10) o10[pz] = v;
@@ -731,10 +736,12 @@ cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, cons
         zo.mulkz[f] = f < nf ? mulkz[f] : 0;
     }
     const int rows = g.N[0] * g.N[1];
-    int pairs = (int)((48 * 1024) / (2 * nf * (g.N[2] + kZPad) * sizeof(typename Cx<T>::t)));
-    pairs = pairs < 1 ? 1 : (pairs > 8 ? 8 : pairs);
+    // at most 16 lines (nf fields x pairs) per block, the 16 lanes of a group
+    // each taking one line in the FFT stages
+    int pairs = 16 / nf;
+    if (pairs < 1) pairs = 1;
     const int npairs = (rows + 1) / 2;
-    const size_t smem = 2ull * nf * pairs * (g.N[2] + kZPad) * sizeof(typename Cx<T>::t);
+    const size_t smem = 2ull * ((nf * pairs) | 1) * g.N[2] * sizeof(typename Cx<T>::t);
     return with_engine<T>(rz, tw, [&](auto eng) {
         auto kern = k_fft_z_c2r<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
