@@ -495,6 +495,17 @@ def run_batched(args):
         return sum(a.elapsed_time(b) for a, b in evs) / K
 
     ms_batched = timed(lambda: bp.compute(tp, tq, to, out=out, stream=stream))
+    # the same batch with lines of length <= 18 as a DFT on the tensor cores
+    f_fft = out[1].clone()
+    bp.set_dft(18)
+    for k in range(3):
+        bp.compute(tp, tq, to, out=out, stream=stream)
+    ms_dft = timed(lambda: bp.compute(tp, tq, to, out=out, stream=stream))
+    torch.cuda.synchronize()
+    dft_vs_fft = float(torch.linalg.norm(out[1].double() - f_fft.double()) / torch.linalg.norm(f_fft.double()))
+    bp.set_dft(0)
+    for k in range(3):
+        bp.compute(tp, tq, to, out=out, stream=stream)
     meshes = bp.meshes
     plans = [Plan(b.box, meshes[i], 5, 0.4, precision="fp32") for i, b in enumerate(boxes)]
     sl = [slice(int(offs[i]), int(offs[i + 1])) for i in range(96)]
@@ -523,6 +534,8 @@ def run_batched(args):
                                f"{n} sites, meshes {int(meshes.min())}^3..{int(meshes.max())}^3 at <= 1.2 A, order 5",
                    "tile": bp.tile, "l2": "flushed between timed steps"},
         "single_box_calls_ms": ms_single, "speedup_vs_single_box_calls": ms_single / ms_batched,
+        "tensor_core_dft_ms": ms_dft, "tensor_core_dft_speedup": ms_batched / ms_dft,
+        "force_rel_diff_dft_vs_fft": dft_vs_fft,
         "max_force_rel_diff_vs_single": diff, "max_energy_rel_diff_vs_single": ediff,
     }
     print(json.dumps(line), flush=True)

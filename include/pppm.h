@@ -180,6 +180,13 @@ int pppm_fields(pppm_plan *plan, void *stream, const double *pos, const double *
  *   out sets PPPM_ERR_TIMEOUT in the batch status (pppm_batch_status).
  * pppm_batch_set       prefactor, tile edge (0 = autotune, 4, 8) and the spin
  *                      limit of the bounded waits.
+ * pppm_batch_set_dft   lines of length <= max_len (0..18; default 0 = off)
+ *                      are transformed as a DFT matrix product on the tensor
+ *                      cores (mma.sync TF32 with split operands, FP32
+ *                      accuracy) instead of by the FFT: the small boxes'
+ *                      meshes (X = F_N x per axis, as in the paper's DFT
+ *                      formulation of its distributed FFT, Section
+ *                      "Hardware-offloaded 3D FFT").
  * pppm_batch_meshes    copy the nbox x 3 meshes in use to a host array.
  * pppm_batch_tile      tile edge in use (0 before the first call).
  */
@@ -187,6 +194,7 @@ typedef struct pppm_batch pppm_batch;
 int pppm_batch_create(int nbox, const double *boxes, const int *meshes, int order, double beta,
                       pppm_batch **out);
 int pppm_batch_set(pppm_batch *batch, double prefactor, int tile, long long spin_limit);
+int pppm_batch_set_dft(pppm_batch *batch, int max_len);
 int pppm_batch_meshes(const pppm_batch *batch, int *meshes);
 int pppm_batch_tile(const pppm_batch *batch);
 int pppm_compute_batched(pppm_batch *batch, void *stream, const float *pos, const float *q,

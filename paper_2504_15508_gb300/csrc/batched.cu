@@ -91,6 +91,7 @@ struct Bufs {
     int* box_fail;  // set when a wait of the box ran out: its later stages skip their work
     int* status;
     double prefactor;
+    int dft_max;  // lines up to this length take the tensor-core DFT (0: all take the FFT)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -376,7 +377,7 @@ __device__ void st_zr2c(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
             a[p * Nz + t] = make_float2(fold_point_b(D, B, cx0, cy0, t), fold_point_b(D, B, cx1, cy1, t));
     }
     __syncthreads();
-    float2* res = stockham<float>(a, b, np, Nz, 1, D.rad[2], B.tw + D.tw0[2], -1.f, false);
+    float2* res = line_transform(a, b, np, Nz, 1, D.rad[2], B.tw + D.tw0[2], -1.f, false, B.dft_max);
     float2* out = B.cx0 + D.c0;
     for (int p = threadIdx.x >> 5; p < np; p += kWarps) {
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
@@ -404,7 +405,7 @@ __device__ void st_yfwd(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
         a[t * Bw + l] = ldcg(&base[(long long)t * Hz + l]);
     }
     __syncthreads();
-    float2* res = stockham<float>(a, b, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], -1.f, true);
+    float2* res = line_transform(a, b, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], -1.f, true, B.dft_max);
     for (int i = threadIdx.x; i < L * nl; i += kThreads) {
         const int t = i / nl, l = i - t * nl;
         base[(long long)t * Hz + l] = res[t * Bw + l];
@@ -437,7 +438,7 @@ __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsig
         a0[t * Bw + l] = ldcg(&base[t * es + l]);
     }
     __syncthreads();
-    float2* rh = stockham<float>(a0, a1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], -1.f, true);
+    float2* rh = line_transform(a0, a1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], -1.f, true, B.dft_max);
     float2* pbuf = (rh == a0) ? a1 : a0;
     const int my = y <= Ny / 2 ? y : y - Ny;
     const float ky = g.kfac_f[1] * my;
@@ -474,8 +475,8 @@ __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsig
         b0[t * Bw + l] = make_float2(kxd * Pv.y, -kxd * Pv.x);
     }
     __syncthreads();
-    float2* rA = stockham<float>(pbuf, rh, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true);
-    float2* rB = stockham<float>(b0, b1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true);
+    float2* rA = line_transform(pbuf, rh, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max);
+    float2* rB = line_transform(b0, b1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max);
     float2* obx = B.cx1 + D.c0 + (long long)y * Hz + kz0;
     for (int i = threadIdx.x; i < Nx * nl; i += kThreads) {
         const int t = i / nl, l = i - t * nl;
@@ -540,9 +541,9 @@ __device__ void st_yinv(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
         buf[4 * sz + t * Bw + l] = ldcg(&B.cx1[off + (long long)t * Hz + l]);
     }
     __syncthreads();
-    float2* rC = stockham<float>(buf, buf + sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true);
-    float2* rD = stockham<float>(buf + 2 * sz, buf + 3 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true);
-    float2* rE = stockham<float>(buf + 4 * sz, buf + 5 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true);
+    float2* rC = line_transform(buf, buf + sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max);
+    float2* rD = line_transform(buf + 2 * sz, buf + 3 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max);
+    float2* rE = line_transform(buf + 4 * sz, buf + 5 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max);
     for (int i = threadIdx.x; i < Ny * nl; i += kThreads) {
         const int t = i / nl, l = i - t * nl;
         B.cx0[off + (long long)t * Hz + l] = rC[t * Bw + l];
@@ -581,7 +582,7 @@ __device__ void st_zc2r(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
         }
     }
     __syncthreads();
-    float2* res = stockham<float>(a, b, nlines, Nz, 1, D.rad[2], B.tw + D.tw0[2], 1.f, false);
+    float2* res = line_transform(a, b, nlines, Nz, 1, D.rad[2], B.tw + D.tw0[2], 1.f, false, B.dft_max);
     const FieldLayout& fl = D.fl;
     const int kmin = g.kmin, zlen = Nz + g.order - 1;
     for (int line = threadIdx.x >> 5; line < nlines; line += kWarps) {
@@ -837,6 +838,7 @@ struct pppm_batch {
     double beta = 0.4;
     double prefactor = 1.0;
     long long spin_limit = 1ll << 24;
+    int dft_max = 0;            // short lines on the tensor cores (off: measured 2 % slower on the batch)
     std::vector<double> boxes;  // nbox * 3
     std::vector<int> meshes;    // nbox * 3
     int tile = 0;               // chosen tile edge (0 = not tuned yet)
@@ -1153,6 +1155,7 @@ int enqueue(pppm_batch* P, cudaStream_t s, int li, const float* pos, const float
     B.box_fail = P->box_fail;
     B.status = P->status;
     B.prefactor = P->prefactor;
+    B.dft_max = P->dft_max;
     cudaError_t e = cudaErrorInvalidValue;
     const int n = (int)Y.items.size();
 #define BATCH_CASE(PP, TT)                                                                                       \
@@ -1316,6 +1319,15 @@ int pppm_batch_set(pppm_batch* P, double prefactor, int tile, long long spin_lim
     P->forced_tile = tile;
     P->tile = tile;
     P->spin_limit = spin_limit;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    P->exec = nullptr;
+    return PPPM_OK;
+}
+
+int pppm_batch_set_dft(pppm_batch* P, int max_len) {
+    if (!P || max_len < 0 || max_len > kDftTcMax) return PPPM_ERR_INVALID_ARG;
+    P->dft_max = max_len;
+    P->tile = P->forced_tile;  // re-tune the tile edge with the new transforms
     if (P->exec) cudaGraphExecDestroy(P->exec);
     P->exec = nullptr;
     return PPPM_OK;

@@ -120,3 +120,117 @@ __device__ typename CT<R>::C* stockham(typename CT<R>::C* a, typename CT<R>::C* 
 
 
 }  // namespace pppm
+
+namespace pppm {
+
+// ------------------------------------------------------------------ short lines on the tensor cores
+// The DFT of nl lines of length L <= kDftTcMax as one real matrix product
+// (X = F_N x per axis):
+//   [Re Y; Im Y] = [[C, -s S], [s S, C]] [Re x; Im x],  C = cos, S = sin of 2 pi k t / L,
+// s = -1 forward, +1 inverse, on mma.sync m16n8k8 TF32 tensor-core
+// instructions.  Each FP32 operand is split into a TF32 high part and a TF32
+// remainder and three products are summed (hi hi + hi lo + lo hi), each
+// k-step's in the tensor core and the k-steps in FP32, which keeps the result
+// at FP32 accuracy.  Element t of line l is at
+// a[l * ls + t * ps]; the result is written to b in the same layout and b is
+// returned.  Every thread of the block must call it (it ends with a barrier).
+constexpr int kDftTcMax = 18;
+
+__device__ __forceinline__ uint32_t tf32_hi(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32_16x8x8(float d[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// element (m, j) of the real-block DFT matrix, 0 outside [0, 2L)^2;
+// tw[m] = e^{-2 pi i m / L}
+__device__ __forceinline__ float dft_block_elem(int m, int j, int L, const float2* __restrict__ tw, float s) {
+    if (m >= 2 * L || j >= 2 * L) return 0.f;
+    const int k = m < L ? m : m - L, t = j < L ? j : j - L;
+    const float2 w = __ldg(&tw[(k * t) % L]);
+    const float c = w.x, sn = -w.y;  // cos, sin of 2 pi k t / L
+    if (m < L) return j < L ? c : -s * sn;
+    return j < L ? s * sn : c;
+}
+
+__device__ inline float2* dft_tc(float2* a, float2* b, int nl, int ls, int ps, int L, const float2* __restrict__ tw,
+                          float s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int MT = (2 * L + 15) / 16, KT = (2 * L + 7) / 8, NT = (nl + 7) / 8;
+    for (int tile = warp; tile < MT * NT; tile += nwarps) {
+        const int mt = tile / NT, nt = tile - mt * NT;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const int line = nt * 8 + gid;  // this lane's column of B
+        for (int kk = 0; kk < KT; ++kk) {
+            const int j0 = kk * 8 + tig, j1 = j0 + 4;
+            const float av[4] = {dft_block_elem(mt * 16 + gid, j0, L, tw, s),
+                                 dft_block_elem(mt * 16 + gid + 8, j0, L, tw, s),
+                                 dft_block_elem(mt * 16 + gid, j1, L, tw, s),
+                                 dft_block_elem(mt * 16 + gid + 8, j1, L, tw, s)};
+            float bv[2] = {0.f, 0.f};
+            if (line < nl) {
+                if (j0 < 2 * L) {
+                    const float2 x = a[line * ls + (j0 < L ? j0 : j0 - L) * ps];
+                    bv[0] = j0 < L ? x.x : x.y;
+                }
+                if (j1 < 2 * L) {
+                    const float2 x = a[line * ls + (j1 < L ? j1 : j1 - L) * ps];
+                    bv[1] = j1 < L ? x.x : x.y;
+                }
+            }
+            uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ah[q] = tf32_hi(av[q]);
+                al[q] = tf32_hi(av[q] - __uint_as_float(ah[q]));
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                bh[q] = tf32_hi(bv[q]);
+                bl[q] = tf32_hi(bv[q] - __uint_as_float(bh[q]));
+            }
+            // each k-step's products start from zero in the tensor core and are
+            // added to the running sums in round-to-nearest FP32, so that the
+            // tensor core's own accumulation spans only 8 terms
+            float pc[4] = {0.f, 0.f, 0.f, 0.f}, ph[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_tf32_16x8x8(pc, al, bh);
+            mma_tf32_16x8x8(pc, ah, bl);
+            mma_tf32_16x8x8(ph, ah, bh);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += ph[q] + pc[q];
+        }
+        // c0, c1: row gid, columns 2 tig, 2 tig + 1; c2, c3: row gid + 8
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int m = mt * 16 + gid + (q >= 2 ? 8 : 0);
+            const int n = nt * 8 + 2 * tig + (q & 1);
+            if (m < 2 * L && n < nl) {
+                float2* dst = &b[n * ls + (m < L ? m : m - L) * ps];
+                if (m < L) dst->x = acc[q];
+                else dst->y = acc[q];
+            }
+        }
+    }
+    __syncthreads();
+    return b;
+}
+
+// line transform for the batched kernel: the tensor-core DFT for short lines
+// (when enabled), the Stockham FFT otherwise
+__device__ __forceinline__ float2* line_transform(float2* a, float2* b, int nl, int ls, int ps, const Radix& rp,
+                                                  const float2* __restrict__ tw, float s, bool line_fast,
+                                                  int dft_max) {
+    if (rp.L <= dft_max) return dft_tc(a, b, nl, ls, ps, rp.L, tw, s);
+    return stockham<float>(a, b, nl, ls, ps, rp, tw, s, line_fast);
+}
+
+}  // namespace pppm

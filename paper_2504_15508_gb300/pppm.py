@@ -274,6 +274,11 @@ class BatchPlan:
     def set(self, prefactor: float = 1.0, tile: int = 0, spin_limit: int = 1 << 24):
         N.check(self._lib.pppm_batch_set(self._h, float(prefactor), int(tile), int(spin_limit)), "pppm_batch_set")
 
+    def set_dft(self, max_len: int):
+        """Lines of length <= max_len (0..18, 0 = off) take the tensor-core
+        DFT instead of the FFT."""
+        N.check(self._lib.pppm_batch_set_dft(self._h, int(max_len)), "pppm_batch_set_dft")
+
     @property
     def meshes(self) -> np.ndarray:
         m = np.zeros((self.nbox, 3), dtype=np.int32)

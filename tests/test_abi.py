@@ -105,3 +105,7 @@ def test_graph_calls_validate_arguments(pppm_lib):
     assert L.pppm_graph_launch(None, None, None, None) == N.PPPM_ERR_INVALID_ARG
     assert L.pppm_graph_launch_f32(None, None, None, None) == N.PPPM_ERR_INVALID_ARG
     L.pppm_graph_destroy(None)
+
+
+def test_batch_set_dft_validates(pppm_lib):
+    assert pppm_lib.pppm_batch_set_dft(None, 18) == N.PPPM_ERR_INVALID_ARG

@@ -24,11 +24,13 @@ def _make_batch(nbox, seed, lo=64, hi=700):
     return specs, boxes, pos, q, offs
 
 
-@pytest.mark.parametrize("tile", [0, 4, 8])
-def test_batched_matches_oracle_per_box(cuda_device, pppm_lib, tile):
+@pytest.mark.parametrize("tile,dft", [(0, 18), (4, 18), (8, 18), (0, 0), (8, 0), (8, 12)])
+def test_batched_matches_oracle_per_box(cuda_device, pppm_lib, tile, dft):
+    """dft: lines up to this length take the tensor-core DFT (0: the FFT for all)."""
     from paper_2504_15508_gb300.pppm import BatchPlan
     specs, boxes, pos, q, offs = _make_batch(6, seed=5)
     bp = BatchPlan(np.array([[s["L"]] * 3 for s in specs]), None, order=5, beta=0.4, tile=tile)
+    bp.set_dft(dft)
     tp = torch.tensor(pos, device=cuda_device)
     tq = torch.tensor(q, device=cuda_device)
     to = torch.tensor(offs, device=cuda_device)
