@@ -730,7 +730,7 @@ __device__ void st_gather(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
 
 // ------------------------------------------------------------------ the persistent kernel
 template <int P, int TILE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)  // two resident blocks per SM: 16 warps to hide latency
 k_batched(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, int nitems, unsigned int* head,
           int* done, Bufs B, long long spin_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
