@@ -229,13 +229,16 @@ __device__ void st_scatter(const BoxDesc& D, int idx, const Bufs& B) {
 }
 
 template <int P, int TILE>
-struct SpreadSmem {
+struct __align__(16) SpreadSmem {  // 16-byte aligned: staged rows take vector stores
     static constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
     static constexpr int WSP = wstride(P) + 4;
-    float st_w[32][WSP];
+    union {
+        int keys[kKeyCap];     // original indices, while ranking
+        float st_w[32][WSP];   // staged weights, while spreading
+    } u;
     float pt[PSIZE];
     int st_cell[32];
-    int2 keys[kKeyCap];
+    short perm[kKeyCap];  // canonical position -> slot in the tile
 };
 
 // One warp per tile, as the single-box fast spread (canonical site order,
@@ -249,27 +252,25 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
     const int tile = idx * kSpreadTiles + warp;
     if (tile >= D.g.ntiles) return;
     W_t& W = reinterpret_cast<W_t*>(smem)[warp];
-    for (int i = lane; i < PSIZE; i += 32) W.pt[i] = 0.f;
+    constexpr int NV = WS / 4;  // 16-byte vectors per weight row
     const int s0 = ldcg(&B.tile_start[D.ts0 + tile]);
     const int c = ldcg(&B.tile_start[D.ts0 + tile + 1]) - s0;
     const long long sb = D.site0 + s0;
-    const bool sorted = c > 1 && c <= kKeyCap;
-    if (sorted) {
-        int cp = 2;
-        while (cp < c) cp <<= 1;
-        for (int i = lane; i < cp; i += 32) W.keys[i] = i < c ? make_int2(ldcg(&B.sorig[sb + i]), i) : make_int2(INT_MAX, -1);
-        __syncwarp();
-        for (int k = 2; k <= cp; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = lane; i < cp; i += 32) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const int2 a = W.keys[i], b = W.keys[ixj];
-                        if ((a.x > b.x) == ((i & k) == 0)) { W.keys[i] = b; W.keys[ixj] = a; }
-                    }
-                }
-                __syncwarp();
-            }
+    // canonical order (by original index) by counting ranks, as the single-box spread
+    const bool ranked = c > 1 && c <= kKeyCap;
+    if (ranked) {
+        for (int i = lane; i < c; i += 32) W.u.keys[i] = ldcg(&B.sorig[sb + i]);
+    }
+    for (int i = lane; i < PSIZE; i += 32) W.pt[i] = 0.f;
+    __syncwarp();
+    if (ranked) {
+        // rank of item i = number of items with a smaller original index
+        for (int i = lane; i < c; i += 32) {
+            const int ki = W.u.keys[i];
+            int r = 0;
+            for (int j = 0; j < c; ++j) r += W.u.keys[j] < ki;
+            W.perm[r] = (short)i;
+        }
     }
     __syncwarp();
     constexpr int NR = (P * P + 31) / 32;
@@ -283,26 +284,40 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
         riz[j] = ract[j] ? row % P : 0;
         roff[j] = riy[j] * PZ + riz[j];
     }
+    // the next batch's weights and cell, in flight while the current one is spread
+    float4 nw[NV];
+    int ncell = 0;
+    auto fetch = [&](int t0) {
+        if (t0 + lane < c) {
+            const long long st = sb + (ranked ? (int)W.perm[t0 + lane] : t0 + lane);
+            const float4* src = reinterpret_cast<const float4*>(B.swt + st * WS);
+#pragma unroll
+            for (int a = 0; a < NV; ++a) nw[a] = __ldcg(&src[a]);
+            ncell = ldcg(&B.scell[st]);
+        }
+    };
+    fetch(0);
     for (int t0 = 0; t0 < c; t0 += 32) {
         const int nb = min(32, c - t0);
         if (lane < nb) {
-            const long long s = sb + (sorted ? W.keys[t0 + lane].y : t0 + lane);
+            float4* dst = reinterpret_cast<float4*>(&W.u.st_w[lane][0]);
 #pragma unroll
-            for (int a = 0; a < WS; ++a) W.st_w[lane][a] = ldcg(&B.swt[s * WS + a]);
-            W.st_cell[lane] = ldcg(&B.scell[s]);
+            for (int a = 0; a < NV; ++a) dst[a] = nw[a];
+            W.st_cell[lane] = ncell;
         }
         __syncwarp();
+        fetch(t0 + 32);
         for (int j = 0; j < nb; ++j) {
             const int cl = W.st_cell[j];
             const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
             float wxq[P];
 #pragma unroll
-            for (int a = 0; a < P; ++a) wxq[a] = W.st_w[j][a];
+            for (int a = 0; a < P; ++a) wxq[a] = W.u.st_w[j][a];
             float* base0 = W.pt + lx * PLANE + ly * PZ + lz;
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr) {
                 if (ract[jr]) {
-                    const float wyz = W.st_w[j][P + riy[jr]] * W.st_w[j][2 * P + riz[jr]];
+                    const float wyz = W.u.st_w[j][P + riy[jr]] * W.u.st_w[j][2 * P + riz[jr]];
                     float* b = base0 + roff[jr];
 #pragma unroll
                     for (int a = 0; a < P; ++a) b[a * PLANE] += wxq[a] * wyz;

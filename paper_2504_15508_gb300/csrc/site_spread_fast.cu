@@ -71,21 +71,12 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
     __syncwarp();
     if (ranked) {
         // rank of item i = number of items with a smaller original index
-        constexpr int MI = kFastCap / 32;
-        int key[MI], rank[MI];
-#pragma unroll
-        for (int m = 0; m < MI; ++m) {
-            key[m] = lane + 32 * m < c ? W.u.keys[lane + 32 * m] : INT_MAX;
-            rank[m] = 0;
+        for (int i = lane; i < c; i += 32) {
+            const int ki = W.u.keys[i];
+            int r = 0;
+            for (int j = 0; j < c; ++j) r += W.u.keys[j] < ki;
+            W.perm[r] = (short)i;
         }
-        for (int j = 0; j < c; ++j) {
-            const int kj = W.u.keys[j];
-#pragma unroll
-            for (int m = 0; m < MI; ++m) rank[m] += kj < key[m];
-        }
-#pragma unroll
-        for (int m = 0; m < MI; ++m)
-            if (lane + 32 * m < c) W.perm[rank[m]] = (short)(lane + 32 * m);
     }
     __syncwarp();
     // lane -> stencil rows (iy, iz); orders above 5 have more rows than lanes
