@@ -119,27 +119,39 @@ cudaError_t launch_bin(cudaStream_t s, const Geo& g, const In* pos, const In* q,
 }
 
 // Exclusive scan of the per-tile counts by one block: start[0..ntiles].
+// Each thread sums a contiguous chunk; warps scan their chunk sums with
+// shuffles; one warp scans the 32 warp totals; two barriers in all.
 __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, int ntiles, int* __restrict__ start) {
-    __shared__ int part[1024];
-    const int tid = threadIdx.x;
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int chunk = (ntiles + 1023) / 1024;
     const int b = tid * chunk, e = min(b + chunk, ntiles);
     int sum = 0;
     for (int i = b; i < e; ++i) sum += count[i];
-    part[tid] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        int v = tid >= off ? part[tid - off] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
+    int incl = sum;  // inclusive scan within the warp
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
     }
-    int run = part[tid] - sum;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = wsum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += v;
+        }
+        wsum[lane] = w;  // inclusive totals of warps 0..lane
+    }
+    __syncthreads();
+    int run = (warp > 0 ? wsum[warp - 1] : 0) + incl - sum;
     for (int i = b; i < e; ++i) {
         start[i] = run;
         run += count[i];
     }
-    if (tid == 1023) start[ntiles] = part[1023];
+    if (tid == 1023) start[ntiles] = wsum[31];
 }
 
 cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int* start) {
