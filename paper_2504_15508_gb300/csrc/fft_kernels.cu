@@ -340,7 +340,7 @@ cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, cons
 // ------------------------------------------------------------------ strided-line C2C
 // axis 1: lines along y (outer index x); axis 0: lines along x (outer index y).
 template <typename R, typename Eng, int SIGN>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, 5)  // one wave of bundles at the workload sizes
 k_fft_bundle(Geo g, int axis, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ data) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -410,7 +410,9 @@ __device__ __forceinline__ void two_sum_pair(R& h, R& l, R h2, R l2) {
 }
 
 template <typename R, typename Eng>
-__global__ void __launch_bounds__(kFftThreads, 4)
+// five resident blocks (one wave at 128: three line buffers fit) where the
+// buffers allow it; at longer lines shared memory caps it at four anyway
+__global__ void __launch_bounds__(kFftThreads, (Eng::kLen > 0 && Eng::kLen <= 128) ? 5 : 4)
 k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R e_scale, R c_field,
                   typename CT<R>::C* __restrict__ S, typename CT<R>::C* __restrict__ Bx, R* __restrict__ partial,
                   unsigned int* __restrict__ counter, double prefactor, double* __restrict__ energy,
@@ -585,20 +587,27 @@ k_fft_y_inverse3(Geo g, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ A, t
     const int kz0 = bi * B;
     const int nl = min(B, Hz - kz0);
     const int64_t off = (int64_t)x * Ny * Hz + kz0;
-    C* buf = reinterpret_cast<C*>(smem_raw);
+    // four line buffers: the three inputs and a scratch that rotates, each
+    // transform leaving its result in one of the two it used
     const int sz = Ny * B;
+    C* p0 = reinterpret_cast<C*>(smem_raw);
+    C* p1 = p0 + sz;
+    C* p2 = p1 + sz;
+    C* scr = p2 + sz;
     BUNDLE_LOOP(t, l, Ny, nl) {
         const C va = A[off + (int64_t)t * Hz + l];
         const int my = t <= Ny / 2 ? t : t - Ny;
         const R kyd = ((Ny % 2 == 0) && (t == Ny / 2)) ? R(0) : kfac<R>(g, 1) * my;
-        buf[t * B + l] = va;
-        buf[2 * sz + t * B + l] = CT<R>::mk(kyd * va.y, -kyd * va.x);
-        buf[4 * sz + t * B + l] = Bx[off + (int64_t)t * Hz + l];
+        p0[t * B + l] = va;
+        p1[t * B + l] = CT<R>::mk(kyd * va.y, -kyd * va.x);
+        p2[t * B + l] = Bx[off + (int64_t)t * Hz + l];
     }
     __syncthreads();
-    C* rC = eng.template run<1, true>(buf, buf + sz, nl, 1, B);
-    C* rD = eng.template run<1, true>(buf + 2 * sz, buf + 3 * sz, nl, 1, B);
-    C* rE = eng.template run<1, true>(buf + 4 * sz, buf + 5 * sz, nl, 1, B);
+    C* rC = eng.template run<1, true>(p0, scr, nl, 1, B);
+    if (rC == scr) scr = p0;
+    C* rD = eng.template run<1, true>(p1, scr, nl, 1, B);
+    if (rD == scr) scr = p1;
+    C* rE = eng.template run<1, true>(p2, scr, nl, 1, B);
     BUNDLE_LOOP(t, l, Ny, nl) {
         A[off + (int64_t)t * Hz + l] = rC[t * B + l];
         D[off + (int64_t)t * Hz + l] = rD[t * B + l];
@@ -610,7 +619,7 @@ template <typename T>
 cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry, const Bundle& bd,
                                   const typename Cx<T>::t* tw, typename Cx<T>::t* A, typename Cx<T>::t* Bx,
                                   typename Cx<T>::t* D) {
-    const size_t smem = 6ull * g.N[1] * bd.B * sizeof(typename Cx<T>::t);
+    const size_t smem = 4ull * g.N[1] * bd.B * sizeof(typename Cx<T>::t);
     return with_engine<T>(ry, tw, [&](auto eng) {
         auto kern = k_fft_y_inverse3<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
@@ -637,7 +646,7 @@ __device__ __forceinline__ X pick4(const X (&a)[4], int f) {
 }
 
 template <typename R, typename Eng>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, 6)  // six resident blocks: two rounds instead of three
 k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
