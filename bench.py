@@ -164,9 +164,7 @@ def step_algorithmic_bytes(n: int, mesh: int) -> int:
 # one ncu --set full capture of the kernel as it stands, on this workload; an
 # entry is removed whenever its kernel changes.
 NCU_TRAFFIC = {
-    ("spread", 128): 20.86e6,
     ("gather", 128): 48.48e6,
-    ("fft_x_influence", 128): 12.87e6,
 }
 
 
