@@ -17,6 +17,7 @@ constexpr int kSpreadWarps = 4;
 // general path for meshes smaller than a tile.
 
 constexpr int kFastCap = 256;  // sites per tile ordered by index in the fast spread
+constexpr int kStage = 32;     // sites staged per batch (one per lane)
 
 // Spread: as k_spread, with the tile's records staged through shared memory in
 // batches of 32 (the next batch's weights are loaded into registers, as
@@ -41,10 +42,10 @@ struct __align__(16) SpreadWarpSmem {  // 16-byte aligned: staged rows take vect
     static constexpr int WSP = wstride(P) + 4;  // staging row pitch (conflict-free 16-byte stores)
     union {
         int keys[kFastCap];  // original indices, while ranking
-        T st_w[32][WSP];     // staged weights, while spreading
+        T st_w[kStage][WSP];  // staged weights, while spreading
     } u;
     T pt[PSIZE];
-    int st_cell[32];
+    int st_cell[kStage];
     short perm[kFastCap];  // canonical position -> slot in the tile
 };
 
@@ -95,7 +96,7 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
     V nw[NV];
     int ncell = 0;
     auto fetch = [&](int t0) {
-        if (t0 + lane < c) {
+        if (lane < kStage && t0 + lane < c) {
             const int s = s0 + (ranked ? (int)W.perm[t0 + lane] : t0 + lane);
             const V* src = reinterpret_cast<const V*>(swt + (size_t)s * WS);
 #pragma unroll
@@ -104,8 +105,8 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
         }
     };
     fetch(0);
-    for (int t0 = 0; t0 < c; t0 += 32) {
-        const int nb = min(32, c - t0);
+    for (int t0 = 0; t0 < c; t0 += kStage) {
+        const int nb = min(kStage, c - t0);
         if (lane < nb) {
             V* dst = reinterpret_cast<V*>(&W.u.st_w[lane][0]);
 #pragma unroll
@@ -113,7 +114,7 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
             W.st_cell[lane] = ncell;
         }
         __syncwarp();
-        fetch(t0 + 32);  // in flight while this batch is spread
+        fetch(t0 + kStage);  // in flight while this batch is spread
         for (int j = 0; j < nb; ++j) {
             const int cl = W.st_cell[j];
             const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
