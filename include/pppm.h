@@ -40,7 +40,9 @@
  *   lengths from the origin) are detected on the device: the affected sites
  *   are placed at the origin so that every access stays in bounds, and the
  *   plan's status word records PPPM_ERR_NONFINITE; pppm_status() reads and
- *   clears it (it synchronizes the stream).
+ *   clears it (it synchronizes the stream).  The gather's wait for its tile
+ *   copies is bounded: one that runs out records PPPM_ERR_TIMEOUT instead,
+ *   and that call's forces are invalid.
  */
 #ifndef PPPM_H
 #define PPPM_H

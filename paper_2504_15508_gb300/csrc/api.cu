@@ -444,8 +444,9 @@ int compute_host(pppm_plan* P, const In* pos, const In* q, int64_t n, double* en
     CK(cudaMemcpyAsync(P->h_status, P->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));  // one synchronization for the outputs and the status word
     if (*P->h_status) {
+        const int st = *P->h_status;
         CK(cudaMemset(P->status, 0, sizeof(int)));
-        return PPPM_ERR_NONFINITE;
+        return (st & 2) ? PPPM_ERR_TIMEOUT : PPPM_ERR_NONFINITE;
     }
     return PPPM_OK;
 }
@@ -685,6 +686,8 @@ int pppm_status(pppm_plan* P) {
     int st = 0;
     CK(cudaMemcpy(&st, P->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st) CK(cudaMemset(P->status, 0, sizeof(int)));
+    // bit 0: a non-finite site; bit 1: the gather's bounded tile-copy wait ran out
+    if (st & 2) return PPPM_ERR_TIMEOUT;
     return st ? PPPM_ERR_NONFINITE : PPPM_OK;
 }
 
