@@ -284,9 +284,11 @@ int run_sites_to_patches(pppm_plan* P, cudaStream_t s, const In* pos, const In* 
       CK((launch_bin<T, In>(s, g, pos, q, (int)n, P->tile_count, P->tile_of, P->slot_of, (Rec<T>*)P->rec, P->cell,
                             P->status))); }
     { PROF(K_SCAN); CK(launch_scan(s, P->tile_count, g.ntiles, P->tile_start)); }
+    // the fast spread and the TMA gather read only cells, indices and weights
+    const bool need_rec = !fast_tiles(g) || !P->fmap_ok;
     { PROF(K_SCATTER);
       CK(launch_scatter<T>(s, g, (int)n, P->tile_of, P->slot_of, P->tile_start, (const Rec<T>*)P->rec, P->cell,
-                           (Rec<T>*)P->srec, P->scell, P->sorig, (T*)P->swt)); }
+                           need_rec ? (Rec<T>*)P->srec : nullptr, P->scell, P->sorig, (T*)P->swt)); }
     { PROF(K_SPREAD);
       CK(launch_spread<T>(s, g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig, (const T*)P->swt,
                           (T*)P->patch)); }

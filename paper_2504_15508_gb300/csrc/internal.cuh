@@ -90,6 +90,11 @@ struct Bundle {
     int nb;          // bundles per outer index = ceil(Hz / B)
 };
 
+// The fast spread and gather need full tiles on every axis and a tile edge of 4 or 8.
+inline bool fast_tiles(const Geo& g) {
+    return (g.T == 4 || g.T == 8) && g.Tt[0] == g.T && g.Tt[1] == g.T && g.Tt[2] == g.T;
+}
+
 // ------------------------------------------------------------------ launchers
 // site_kernels.cu
 template <typename T, typename In>

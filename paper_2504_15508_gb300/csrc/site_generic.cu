@@ -118,10 +118,6 @@ static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int* tile_start,
     return cudaGetLastError();
 }
 
-// The fast kernels need full tiles on every axis and a tile edge of 4 or 8.
-static bool fast_tiles(const Geo& g) {
-    return (g.T == 4 || g.T == 8) && g.Tt[0] == g.T && g.Tt[1] == g.T && g.Tt[2] == g.T;
-}
 
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,

@@ -173,7 +173,7 @@ __global__ void k_scatter(int n, const int* __restrict__ tile_of, const int* __r
     if (i >= n) return;
     const int dst = tile_start[tile_of[i]] + slot_of[i];
     const Rec<T> r = rec[i];
-    srec[dst] = r;
+    if (srec) srec[dst] = r;  // only the generic spread and gather read the records
     scell[dst] = cell[i];
     sorig[dst] = i;
     BspCoef<T, P> co;
