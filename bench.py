@@ -457,16 +457,29 @@ def run_ours(args):
 
 # --------------------------------------------------------------------- batched form
 def run_batched(args):
-    """96 independent water boxes (64 to 8,192 molecules, log-uniform, 29.9 A^3
-    per molecule, meshes at <= 1.2 A spacing) in one persistent launch replayed
-    from a CUDA graph, against the same boxes as 96 single-box calls."""
+    """96 independent water boxes per GPU (64 to 8,192 molecules, log-uniform,
+    29.9 A^3 per molecule, meshes at <= 1.2 A spacing) in one persistent launch
+    replayed from a CUDA graph.  On one GPU it is compared with the same boxes
+    as 96 single-box calls; with N GPUs (torchrun) 96 N boxes are split across
+    the ranks by cost (weak scaling, no collective in the data path)."""
     import torch
+    import torch.distributed as dist
 
     from paper_2504_15508_gb300.pppm import BatchPlan, Plan
+    from paper_2504_15508_gb300.shard import box_costs, gather_by_box, partition, slowest
     from workloads.water import batched_boxes, make_water
 
-    dev = torch.device("cuda", 0)
-    specs = batched_boxes(nbox=96, seed=5)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    all_specs = batched_boxes(nbox=96 * world, seed=5)
+    mine = partition(box_costs([4 * s["n_mol"] for s in all_specs], [s["mesh"] for s in all_specs]), world)[rank]
+    specs = [all_specs[b] for b in mine]
+    nb = len(specs)
     boxes = [make_water(s["n_mol"], s["L"], s["seed"]) for s in specs]
     pos = np.concatenate([b.pos for b in boxes]).astype(np.float32)
     q = np.concatenate([b.q for b in boxes]).astype(np.float32)
@@ -476,8 +489,8 @@ def run_batched(args):
     tq = torch.tensor(q, device=dev)
     to = torch.tensor(offs, device=dev)
     bp = BatchPlan(np.array([[s["L"]] * 3 for s in specs]), None, order=5, beta=0.4)
-    out = (torch.empty(96, dtype=torch.float64, device=dev), torch.empty((n, 3), dtype=torch.float32, device=dev),
-           torch.empty((96, 6), dtype=torch.float64, device=dev))
+    out = (torch.empty(nb, dtype=torch.float64, device=dev), torch.empty((n, 3), dtype=torch.float32, device=dev),
+           torch.empty((nb, 6), dtype=torch.float64, device=dev))
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     for k in range(max(3, args.warmup)):
@@ -487,6 +500,8 @@ def run_batched(args):
 
     def timed(fn):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         for k in range(K):
             flush.fill_(float(k))
@@ -496,51 +511,61 @@ def run_batched(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs) / K
 
-    ms_batched = timed(lambda: bp.compute(tp, tq, to, out=out, stream=stream))
-    # the same batch with lines of length <= 18 as a DFT on the tensor cores
-    f_fft = out[1].clone()
-    bp.set_dft(18)
-    for k in range(3):
-        bp.compute(tp, tq, to, out=out, stream=stream)
-    ms_dft = timed(lambda: bp.compute(tp, tq, to, out=out, stream=stream))
-    torch.cuda.synchronize()
-    dft_vs_fft = float(torch.linalg.norm(out[1].double() - f_fft.double()) / torch.linalg.norm(f_fft.double()))
-    bp.set_dft(0)
-    for k in range(3):
-        bp.compute(tp, tq, to, out=out, stream=stream)
-    meshes = bp.meshes
-    plans = [Plan(b.box, meshes[i], 5, 0.4, precision="fp32") for i, b in enumerate(boxes)]
-    sl = [slice(int(offs[i]), int(offs[i + 1])) for i in range(96)]
-    pv = [(tp[s].contiguous(), tq[s].contiguous()) for s in sl]
-    outs = [(torch.empty(1, dtype=torch.float64, device=dev), torch.empty((s.stop - s.start, 3), dtype=torch.float32,
-             device=dev), torch.empty(6, dtype=torch.float64, device=dev)) for s in sl]
-
-    def singles():
-        for i in range(96):
-            plans[i].compute(pv[i][0], pv[i][1], out=outs[i], stream=stream)
-
-    for _ in range(3):
-        singles()
-    Ks, K = K, min(K, 50)
-    ms_single = timed(singles)
-    K = Ks
-    torch.cuda.synchronize()
-    diff = max(float(torch.linalg.norm(out[1][sl[i]].double() - outs[i][1].double()) /
-                     torch.linalg.norm(outs[i][1].double())) for i in range(96))
-    ediff = max(abs(out[0][i].item() - outs[i][0].item()) / abs(outs[i][0].item()) for i in range(96))
+    ms_batched = slowest(timed(lambda: bp.compute(tp, tq, to, out=out, stream=stream)))
+    energies = gather_by_box(len(all_specs), mine, out[0].cpu().numpy())
     line = {
-        "metric": "batched PPPM evals/s, 96 water boxes of 64-8,192 molecules", "value": 1e3 / ms_batched,
-        "unit": "batch-evals/s", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms_batched,
+        "metric": "batched PPPM evals/s, 96 water boxes of 64-8,192 molecules", "value": world * 1e3 / ms_batched,
+        "unit": "batch-evals/s", "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms_batched,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batched96: 96 cubic water boxes, {int(sum(s['n_mol'] for s in specs))} molecules, "
-                               f"{n} sites, meshes {int(meshes.min())}^3..{int(meshes.max())}^3 at <= 1.2 A, order 5",
+        "config": {"workload": f"batched96: 96 cubic water boxes per GPU ({len(all_specs)} in all, split by cost), "
+                               f"meshes at <= 1.2 A, order 5; this rank: {nb} boxes, "
+                               f"{int(sum(s['n_mol'] for s in specs))} molecules, {n} sites",
                    "tile": bp.tile, "l2": "flushed between timed steps"},
-        "single_box_calls_ms": ms_single, "speedup_vs_single_box_calls": ms_single / ms_batched,
-        "tensor_core_dft_ms": ms_dft, "tensor_core_dft_speedup": ms_batched / ms_dft,
-        "force_rel_diff_dft_vs_fft": dft_vs_fft,
-        "max_force_rel_diff_vs_single": diff, "max_energy_rel_diff_vs_single": ediff,
+        "energy_sum_all_boxes": float(np.sum(energies)),
     }
-    print(json.dumps(line), flush=True)
+    if world == 1:
+        # the same batch with lines of length <= 18 as a DFT on the tensor cores
+        f_fft = out[1].clone()
+        bp.set_dft(18)
+        for k in range(3):
+            bp.compute(tp, tq, to, out=out, stream=stream)
+        ms_dft = timed(lambda: bp.compute(tp, tq, to, out=out, stream=stream))
+        torch.cuda.synchronize()
+        dft_vs_fft = float(torch.linalg.norm(out[1].double() - f_fft.double()) / torch.linalg.norm(f_fft.double()))
+        bp.set_dft(0)
+        for k in range(3):
+            bp.compute(tp, tq, to, out=out, stream=stream)
+        meshes = bp.meshes
+        plans = [Plan(b.box, meshes[i], 5, 0.4, precision="fp32") for i, b in enumerate(boxes)]
+        sl = [slice(int(offs[i]), int(offs[i + 1])) for i in range(nb)]
+        pv = [(tp[x].contiguous(), tq[x].contiguous()) for x in sl]
+        outs = [(torch.empty(1, dtype=torch.float64, device=dev), torch.empty((x.stop - x.start, 3),
+                 dtype=torch.float32, device=dev), torch.empty(6, dtype=torch.float64, device=dev)) for x in sl]
+
+        def singles():
+            for i in range(nb):
+                plans[i].compute(pv[i][0], pv[i][1], out=outs[i], stream=stream)
+
+        for _ in range(3):
+            singles()
+        Ks, K = K, min(K, 50)
+        ms_single = timed(singles)
+        K = Ks
+        bp.compute(tp, tq, to, out=out, stream=stream)
+        torch.cuda.synchronize()
+        diff = max(float(torch.linalg.norm(out[1][sl[i]].double() - outs[i][1].double()) /
+                         torch.linalg.norm(outs[i][1].double())) for i in range(nb))
+        ediff = max(abs(out[0][i].item() - outs[i][0].item()) / abs(outs[i][0].item()) for i in range(nb))
+        line.update({
+            "single_box_calls_ms": ms_single, "speedup_vs_single_box_calls": ms_single / ms_batched,
+            "tensor_core_dft_ms": ms_dft, "tensor_core_dft_speedup": ms_batched / ms_dft,
+            "force_rel_diff_dft_vs_fft": dft_vs_fft,
+            "max_force_rel_diff_vs_single": diff, "max_energy_rel_diff_vs_single": ediff,
+        })
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 # --------------------------------------------------------------------- learned form
