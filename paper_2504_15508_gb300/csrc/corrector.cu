@@ -81,13 +81,17 @@ __device__ __forceinline__ void bspline_all(float x0, float w[P]) {
 
 // One thread per site.  The 27 samples share the site's weights; with the
 // (p+2)^3 mesh values around the site they are three separable contractions.
+// Thread t takes site perm[t]: with the solve's tile order as perm, the sites
+// of a warp lie in one tile and their mesh rows overlap, so a warp's loads
+// touch a few rows instead of 32 scattered ones.
 template <int P>
 __global__ void k_features(Geo g, FieldLayout fl, const float* __restrict__ phi, const float* __restrict__ pos,
-                           const signed char* __restrict__ types, int n, float s_in,
+                           const signed char* __restrict__ types, const int* __restrict__ perm, int n, float s_in,
                            __nv_bfloat16* __restrict__ feat) {
     constexpr int W = P + 2;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int i = perm ? __ldg(&perm[t]) : t;
     const bool odd = (g.order & 1) != 0;
     int gc[3];
     float w[3][P];
@@ -150,9 +154,9 @@ __global__ void k_features(Geo g, FieldLayout fl, const float* __restrict__ phi,
     float v[NIN];
 #pragma unroll
     for (int k = 0; k < 27; ++k) v[k] = F[k] * s_in;
-    const int t = types[i];
+    const int ty = types[i];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[27 + k] = t == k ? 1.f : 0.f;
+    for (int k = 0; k < 3; ++k) v[27 + k] = ty == k ? 1.f : 0.f;
 #pragma unroll
     for (int d = 0; d < 3; ++d) sincospif(2.f * dfrac[d], &v[30 + 2 * d], &v[31 + 2 * d]);
 #pragma unroll
@@ -577,15 +581,24 @@ cudaError_t launch_features(pppm_corr* C, cudaStream_t s, const float* pos, cons
                             __nv_bfloat16* feat) {
     pppm_plan* P = C->plan;
     const float* phi = (const float*)P->fields + 3 * P->flayout.fstride;
+    // every caller runs this right after a solve of the same n sites on the
+    // same stream, whose scatter left the tile order (a permutation of 0..n-1)
+    // in the plan
+    const int* perm = n <= P->cap ? P->sorig : nullptr;
     const int blocks = (int)((n + 127) / 128);
+#define PPPM_FEAT(PP)                                                                                      \
+    case PP:                                                                                               \
+        k_features<PP><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, perm, (int)n, C->s_in, feat); \
+        break;
     switch (P->order) {
-        case 3: k_features<3><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
-        case 4: k_features<4><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
-        case 5: k_features<5><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
-        case 6: k_features<6><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
-        case 7: k_features<7><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, (int)n, C->s_in, feat); break;
+        PPPM_FEAT(3)
+        PPPM_FEAT(4)
+        PPPM_FEAT(5)
+        PPPM_FEAT(6)
+        PPPM_FEAT(7)
         default: return cudaErrorInvalidValue;
     }
+#undef PPPM_FEAT
     return cudaGetLastError();
 }
 
