@@ -164,11 +164,9 @@ def step_algorithmic_bytes(n: int, mesh: int) -> int:
 # one ncu --set full capture of the kernel as it stands, on this workload; an
 # entry is removed whenever its kernel changes.
 NCU_TRAFFIC = {
-    ("gather", 128): 48.48e6,
     ("spread", 128): 20.83e6,
     ("fft_x_influence", 128): 13.42e6,
     ("fft_y_inverse3", 128): 17.11e6,
-    ("fft_z_c2r", 128): 25.60e6,
 }
 
 

@@ -257,15 +257,17 @@ int build_field_map(pppm_plan* P) {
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     const FieldLayout& fl = P->flayout;
-    const int E = P->g.T + P->order - 1, EZ = (E + 3) & ~3;
-    const cuuint64_t dims[4] = {(cuuint64_t)fl.Zp, (cuuint64_t)fl.Yp, (cuuint64_t)fl.Xp, 3};
-    const cuuint64_t strides[3] = {(cuuint64_t)fl.Zp * P->esz, (cuuint64_t)fl.Zp * fl.Yp * P->esz,
-                                   (cuuint64_t)fl.fstride * P->esz};
-    const cuuint32_t box[4] = {(cuuint32_t)EZ, (cuuint32_t)E, (cuuint32_t)E, 3};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const int E = P->g.T + P->order - 1, EZ = gather_box_z(P->order, P->g.T);
+    // (4 z + component, y, x) of the interleaved padded fields: a z row of
+    // points is one contiguous run, copied as one box row
+    const cuuint64_t row = (cuuint64_t)fl.pstride * fl.Zp;  // elements per z row
+    const cuuint64_t dims[3] = {row, (cuuint64_t)fl.Yp, (cuuint64_t)fl.Xp};
+    const cuuint64_t strides[2] = {row * P->esz, row * fl.Yp * P->esz};
+    const cuuint32_t box[3] = {(cuuint32_t)(fl.pstride * EZ), (cuuint32_t)E, (cuuint32_t)E};
+    const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(&P->fmap, P->precision == PPPM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                        4, P->fields, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        3, P->fields, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     P->fmap_ok = (r == CUDA_SUCCESS);
@@ -343,6 +345,7 @@ int run_solve(pppm_plan* P, cudaStream_t s, double* energy, double* virial, T* f
     } else {
         fl.padded = 0;
         fl.fstride = N3;
+        fl.pstride = 1;
     }
     T* out[4] = {fields_out, fields_out + fl.fstride, fields_out + 2 * fl.fstride, fields_out + 3 * fl.fstride};
     const int nf = (P->potential && fields_out == (T*)P->fields) ? 4 : 3;
@@ -554,9 +557,10 @@ int pppm_create(const double box[3], const int mesh[3], int order, double beta, 
         fl.padded = 1;
         fl.Xp = mesh[0] + order - 1;
         fl.Yp = mesh[1] + order - 1;
-        fl.Zp = (mesh[2] + order - 1 + 3) & ~3;
-        fl.fstride = (int64_t)fl.Xp * fl.Yp * fl.Zp;
-        if ((rc = dalloc(&P->fields, 4 * P->esz * fl.fstride)) != PPPM_OK) return fail(rc);
+        fl.Zp = mesh[2] + order - 1;
+        fl.fstride = 1;
+        fl.pstride = 4;
+        if ((rc = dalloc(&P->fields, 4 * P->esz * (size_t)fl.Xp * fl.Yp * fl.Zp)) != PPPM_OK) return fail(rc);
     }
     const int nblk = x_influence_blocks(g, P->bd);
     if ((rc = dalloc(&P->partial, 14 * P->esz * (size_t)nblk)) != PPPM_OK) return fail(rc);
@@ -762,6 +766,7 @@ int pppm_fft_c2r(pppm_plan* P, void* stream, const void* in, void* out) {
         float* o[1] = {(float*)out};
         FieldLayout fl{};
         fl.fstride = mesh_points(P);
+        fl.pstride = 1;
         CK(launch_fft_z_c2r<float>(s, P->g, P->rad[2], (const float2*)P->tw[2], 1, src, mk, o, fl));
     } else {
         double2* c0 = (double2*)P->cx[0];
@@ -771,6 +776,7 @@ int pppm_fft_c2r(pppm_plan* P, void* stream, const void* in, void* out) {
         double* o[1] = {(double*)out};
         FieldLayout fl{};
         fl.fstride = mesh_points(P);
+        fl.pstride = 1;
         CK(launch_fft_z_c2r<double>(s, P->g, P->rad[2], (const double2*)P->tw[2], 1, src, mk, o, fl));
     }
     return PPPM_OK;

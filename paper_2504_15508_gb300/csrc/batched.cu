@@ -1017,6 +1017,7 @@ int build_layout(pppm_batch* P, int li, int T) {
         D.fl.Yp = N[1] + p - 1;
         D.fl.Zp = (N[2] + p - 1 + 3) & ~3;
         D.fl.fstride = (long long)D.fl.Xp * D.fl.Yp * D.fl.Zp;
+        D.fl.pstride = 1;
         D.site0 = P->offsets[b];
         D.nsite = (int)(P->offsets[b + 1] - P->offsets[b]);
         D.tile0 = tile0;

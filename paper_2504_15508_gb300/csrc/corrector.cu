@@ -120,10 +120,10 @@ __global__ void k_features(Geo g, FieldLayout fl, const float* __restrict__ phi,
         for (int k = 0; k < 9; ++k) Sy[k] = 0.f;
 #pragma unroll
         for (int b = 0; b < W; ++b) {  // y offset
-            const float* row = phi + ((int64_t)idx[0][a] * fl.Yp + idx[1][b]) * fl.Zp;
+            const float* row = phi + ((int64_t)idx[0][a] * fl.Yp + idx[1][b]) * fl.Zp * fl.pstride;
             float v[W];
 #pragma unroll
-            for (int c = 0; c < W; ++c) v[c] = __ldg(&row[idx[2][c]]);
+            for (int c = 0; c < W; ++c) v[c] = __ldg(&row[idx[2][c] * fl.pstride]);
             float Sz[3];
 #pragma unroll
             for (int dz = 0; dz < 3; ++dz) {
@@ -580,7 +580,7 @@ int refresh_bf16(pppm_corr* C, cudaStream_t s) {
 cudaError_t launch_features(pppm_corr* C, cudaStream_t s, const float* pos, const signed char* types, int64_t n,
                             __nv_bfloat16* feat) {
     pppm_plan* P = C->plan;
-    const float* phi = (const float*)P->fields + 3 * P->flayout.fstride;
+    const float* phi = (const float*)P->fields + 3 * P->flayout.fstride;  // the fourth field
     // every caller runs this right after a solve of the same n sites on the
     // same stream, whose scatter left the tile order (a permutation of 0..n-1)
     // in the plan

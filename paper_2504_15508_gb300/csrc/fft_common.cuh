@@ -9,13 +9,21 @@ namespace pppm {
 
 // ------------------------------------------------------------------ complex helpers
 template <typename R> struct CT;
+// four reals of one mesh point, stored with one vector store
+struct __align__(32) Real4d {
+    double x, y, z, w;
+};
 template <> struct CT<float> {
     typedef float2 C;
+    typedef float4 C4;
     static __device__ __forceinline__ C mk(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ C4 mk4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
 };
 template <> struct CT<double> {
     typedef double2 C;
+    typedef Real4d C4;
     static __device__ __forceinline__ C mk(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ C4 mk4(double a, double b, double c, double d) { return Real4d{a, b, c, d}; }
 };
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }

@@ -696,38 +696,45 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
         }
         return;
     }
-    // padded: every output row also lands on its periodic ghost images, and
-    // each row is extended by p - 1 ghost points along z
+    // padded: the fields of a point are interleaved (E_x, E_y, E_z, phi) and
+    // stored with one vector store; every output row also lands on its
+    // periodic ghost images, and each row is extended by p - 1 ghost points
+    // along z.  One warp per output row, lanes along z.
     const FieldLayout& fl = zo.fl;
-    const int Ny = g.N[1], Nx = g.N[0], kmin = g.kmin;
+    const int Ny = g.N[1], kmin = g.kmin;
     const int zlen = Nz + g.order - 1;
-    for (int line = threadIdx.x >> 5; line < nlines; line += kFftThreads >> 5) {
-        const int f = line / np, p = line - f * np;
-        R* out = reinterpret_cast<R*>(pick4(zo.out, f));
-        const C* rrow = res + line;  // point z of this line at rrow[z * PL]
-        for (int half = 0; half < 2; ++half) {
-            const int r = 2 * (pair0 + p) + half;
-            if (r >= rows) break;
-            const int x = r / Ny, y = r - x * Ny;
-            const int px0 = x - kmin, py0 = y - kmin;
-            // at most one ghost image per axis (Xp < 2 Nx)
-            const int pxg = px0 + Nx < fl.Xp ? px0 + Nx : (px0 - Nx >= 0 ? px0 - Nx : -1);
-            const int pyg = py0 + Ny < fl.Yp ? py0 + Ny : (py0 - Ny >= 0 ? py0 - Ny : -1);
-            R* o00 = out + ((int64_t)px0 * fl.Yp + py0) * fl.Zp;
-            R* o10 = pxg >= 0 ? out + ((int64_t)pxg * fl.Yp + py0) * fl.Zp : nullptr;
-            R* o01 = pyg >= 0 ? out + ((int64_t)px0 * fl.Yp + pyg) * fl.Zp : nullptr;
-            R* o11 = (pxg >= 0 && pyg >= 0) ? out + ((int64_t)pxg * fl.Yp + pyg) * fl.Zp : nullptr;
-            for (int pz = threadIdx.x & 31; pz < zlen; pz += 32) {
-                int zz = pz + kmin;
-                zz += zz < 0 ? Nz : 0;
-                zz -= zz >= Nz ? Nz : 0;
-                const C zv = rrow[zz * PL];
-                const R v = half ? zv.y : zv.x;
-                o00[pz] = v;
-                if (o10) o10[pz] = v;
-                if (o01) o01[pz] = v;
-                if (o11) o11[pz] = v;
+    typedef typename CT<R>::C4 V4;
+    V4* out = reinterpret_cast<V4*>(zo.out[0]);
+    for (int pr = threadIdx.x >> 5; pr < 2 * np; pr += kFftThreads >> 5) {
+        const int p = pr >> 1, half = pr & 1;
+        const int r = 2 * (pair0 + p) + half;
+        if (r >= rows) continue;
+        const int x = r / Ny, y = r - x * Ny;
+        const int px0 = x - kmin, py0 = y - kmin;
+        // at most one ghost image per axis (Xp < 2 Nx)
+        const int Nx = g.N[0];
+        const int pxg = px0 + Nx < fl.Xp ? px0 + Nx : (px0 - Nx >= 0 ? px0 - Nx : -1);
+        const int pyg = py0 + Ny < fl.Yp ? py0 + Ny : (py0 - Ny >= 0 ? py0 - Ny : -1);
+        V4* o00 = out + ((int64_t)px0 * fl.Yp + py0) * fl.Zp;
+        V4* o10 = pxg >= 0 ? out + ((int64_t)pxg * fl.Yp + py0) * fl.Zp : nullptr;
+        V4* o01 = pyg >= 0 ? out + ((int64_t)px0 * fl.Yp + pyg) * fl.Zp : nullptr;
+        V4* o11 = (pxg >= 0 && pyg >= 0) ? out + ((int64_t)pxg * fl.Yp + pyg) * fl.Zp : nullptr;
+        for (int pz = threadIdx.x & 31; pz < zlen; pz += 32) {
+            int zz = pz + kmin;
+            zz += zz < 0 ? Nz : 0;
+            zz -= zz >= Nz ? Nz : 0;
+            const C* rz = res + zz * PL + p;  // field f of this pair at rz[f * np]
+            R v[4];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const C zv = f < nf ? rz[f * np] : CT<R>::mk(R(0), R(0));
+                v[f] = half ? zv.y : zv.x;
             }
+            const V4 w = CT<R>::mk4(v[0], v[1], v[2], v[3]);
+            o00[pz] = w;
+            if (o10) o10[pz] = w;
+            if (o01) o01[pz] = w;
+            if (o11) o11[pz] = w;
         }
     }
 }

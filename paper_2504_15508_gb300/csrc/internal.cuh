@@ -71,17 +71,25 @@ template <typename R> __host__ __device__ __forceinline__ R kfac(const Geo& g, i
 template <> __host__ __device__ __forceinline__ float kfac<float>(const Geo& g, int d) { return g.kfac_f[d]; }
 template <> __host__ __device__ __forceinline__ double kfac<double>(const Geo& g, int d) { return g.kfac_d[d]; }
 
-// Layout of the three field meshes E_x, E_y, E_z.  Unpadded: three
-// consecutive Nx x Ny x Nz meshes.  Padded ("ghosted"): each mesh extended by
-// p - 1 periodic ghost points per axis, so that a tile's stencil patch is one
-// contiguous box: padded index = mesh index - kmin, extents Xp = Nx + p - 1,
-// Yp = Ny + p - 1, Zp = Nz + p - 1 rounded up to a multiple of 4 (TMA needs
-// 16-byte row strides).
+// Layout of the field meshes E_x, E_y, E_z (and the potential phi).
+// Unpadded: consecutive Nx x Ny x Nz meshes, one per field (fstride = N,
+// pstride = 1).  Padded ("ghosted"): the mesh extended by p - 1 periodic ghost
+// points per axis, so that a tile's stencil patch is one contiguous box
+// (padded index = mesh index - kmin, extents Xp = Nx + p - 1, Yp = Ny + p - 1,
+// Zp = Nz + p - 1), with the four values of a point interleaved as
+// (E_x, E_y, E_z, phi) in 4 consecutive elements (fstride = 1, pstride = 4):
+// the force interpolation reads a point's three fields with one 16-byte load.
 struct FieldLayout {
     int padded;
     int Xp, Yp, Zp;
-    int64_t fstride;  // elements between consecutive fields
+    int64_t fstride;  // elements between the same point of consecutive fields
+    int64_t pstride;  // elements between consecutive mesh points
 };
+
+// z extent (in points) of the TMA box of field patches: at least the patch
+// edge T + p - 1, and odd, so that the 16-byte points of the stencil rows of a
+// site fall on distinct bank groups (see k_gather_tma)
+__host__ __device__ constexpr int gather_box_z(int p, int t) { return (t + p - 1) | 1; }
 
 // Bundle shape of a strided-line FFT pass (lines along y or x, B adjacent kz
 // columns per block).

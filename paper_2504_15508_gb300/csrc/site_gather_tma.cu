@@ -10,9 +10,10 @@ namespace pppm {
 
 constexpr int kGatherWarps = 4;
 
-// Gather with TMA staging: the three padded field meshes form one 4D tensor
-// (z, y, x, field); the tile's stencil patch is the box starting at padded
-// coordinates (tz T, ty T, tx T, 0), fetched by a single cp.async.bulk.tensor
+// Gather with TMA staging: the interleaved padded fields form one 3D tensor
+// (4 z + component, y, x), the components of a z row being contiguous; the
+// tile's stencil patch is the box starting at padded coordinates
+// (4 tz T, ty T, tx T), fetched by a single cp.async.bulk.tensor
 // issued by one thread and waited on through an mbarrier.  The wait is
 // bounded: if it runs out the block records PPPM_ERR_TIMEOUT in the status
 // word (bit 2) and returns without touching the patch.
@@ -33,20 +34,68 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase)
     return false;
 }
 
+// One mesh point of the interleaved padded fields (E_x, E_y, E_z, phi) in
+// shared memory, read with 16-byte loads.
+template <typename T>
+struct Point4;
+template <>
+struct Point4<float> {
+    static __device__ __forceinline__ void load(const float* p, float& x, float& y, float& z) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        x = v.x;
+        y = v.y;
+        z = v.z;
+    }
+};
+template <>
+struct Point4<double> {
+    static __device__ __forceinline__ void load(const double* p, double& x, double& y, double& z) {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        x = a.x;
+        y = a.y;
+        z = p[2];
+    }
+};
+
+// Lane order of the p^2 stencil rows (iy, iz) of a site.  A warp's 16-byte
+// shared loads are served a quarter-warp (8 lanes) at a time, one 16-byte
+// bank group per lane; row (iy, iz) starts in group (iy EZ + iz) mod 8 (plus
+// the same site offset for every row).  Rows are ordered by (k, group), k
+// counting the earlier rows of the same group, so that consecutive lanes walk
+// the groups round-robin: with EZ = 13 and p = 5 each quarter-warp touches 8
+// distinct groups.  Computed on the host, passed as a kernel parameter.
+struct LaneRows {
+    unsigned char row[64];  // slot (lane + 32 j) -> row iy p + iz
+};
+
+static LaneRows order_rows(int p, int ez) {
+    auto grp = [&](int r) { return ((r / p) * ez + r % p) & 7; };
+    int key[64];
+    int seen[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < p * p; ++i) key[i] = (seen[grp(i)]++) * 8 + grp(i);
+    LaneRows lr{};
+    for (int i = 0; i < p * p; ++i) {
+        int pos = 0;
+        for (int j = 0; j < p * p; ++j) pos += key[j] < key[i] || (key[j] == key[i] && j < i);
+        lr.row[pos] = (unsigned char)i;
+    }
+    return lr;
+}
+
 template <typename T, int P, int TILE, typename Out>
 __global__ void __launch_bounds__(kGatherWarps * 32)
 k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
              const int* __restrict__ sorig, const T* __restrict__ swt, const __grid_constant__ CUtensorMap tmap,
-             double prefactor, Out* __restrict__ forces, int* __restrict__ status) {
-    constexpr int E = TILE + P - 1, EZ = (E + 3) & ~3, PLANE = E * EZ, PSIZE = E * PLANE;
+             const __grid_constant__ LaneRows lanes, double prefactor, Out* __restrict__ forces,
+             int* __restrict__ status) {
+    // TMA box: [x][y][z][component], z extent EZ points, 4 components a point
+    constexpr int E = TILE + P - 1, EZ = gather_box_z(P, TILE), PLANE = E * EZ, PSIZE = E * PLANE;
     constexpr int WS = wstride(P), WSP = WS + 4;
-    constexpr uint32_t TX_BYTES = 3u * PSIZE * sizeof(T);
-    constexpr size_t FIELD_BYTES = (3 * PSIZE * sizeof(T) + 127) / 128 * 128;
+    constexpr uint32_t TX_BYTES = 4u * PSIZE * sizeof(T);
+    constexpr size_t FIELD_BYTES = (4 * PSIZE * sizeof(T) + 127) / 128 * 128;
     constexpr size_t STAGE_BYTES = (kGatherWarps * 8 * WSP * sizeof(T) + 31) / 32 * 32;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T* fx = reinterpret_cast<T*>(smem_raw);  // TMA box: [field][x][y][z]
-    T* fy = fx + PSIZE;
-    T* fz = fy + PSIZE;
+    const T* fbox = reinterpret_cast<const T*>(smem_raw);
     T* st_w = reinterpret_cast<T*>(smem_raw + FIELD_BYTES);  // [warps][8][WSP]
     int* st_cell = reinterpret_cast<int*>(smem_raw + FIELD_BYTES + STAGE_BYTES);
     int* st_orig = st_cell + kGatherWarps * 8;
@@ -66,14 +115,14 @@ k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ 
         const int tx = tile / (g.nt[1] * g.nt[2]);
         const int ty = (tile / g.nt[2]) % g.nt[1];
         const int tz = tile % g.nt[2];
-        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(fx);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_raw);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_s), "r"(TX_BYTES)
                      : "memory");
+        // innermost coordinate 4 tz T elements: a whole number of 16-byte points
         asm volatile(
-            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-            "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(tz * TILE), "r"(ty * TILE), "r"(tx * TILE), "r"(0),
-            "r"(mbar_s)
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(4 * tz * TILE), "r"(ty * TILE), "r"(tx * TILE), "r"(mbar_s)
             : "memory");
     }
     constexpr int NR = (P * P + 31) / 32;
@@ -81,11 +130,12 @@ k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ 
     bool ract[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-        const int row = lane + 32 * j;
-        ract[j] = row < P * P;
-        riy[j] = ract[j] ? row / P : 0;
-        riz[j] = ract[j] ? row % P : 0;
-        roff[j] = riy[j] * EZ + riz[j];
+        const int slot = lane + 32 * j;
+        ract[j] = slot < P * P;
+        const int row = ract[j] ? (int)lanes.row[slot] : 0;
+        riy[j] = row / P;
+        riz[j] = row % P;
+        roff[j] = 4 * (riy[j] * EZ + riz[j]);
     }
     T* ww = st_w + warp * 8 * WSP;
     int* wcell = st_cell + warp * 8;
@@ -141,19 +191,23 @@ k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ 
                 const int cl = wcell[j];
                 const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
                 const T* wj = ww + j * WSP;
-                const int base0 = lx * PLANE + ly * EZ + lz;
+                T wx[P];
+#pragma unroll
+                for (int a = 0; a < P; ++a) wx[a] = wj[a];
+                const T* base0 = fbox + 4 * (lx * PLANE + ly * EZ + lz);
 #pragma unroll
                 for (int jr = 0; jr < NR; ++jr) {
                     if (ract[jr]) {
                         const T wyz = wj[P + riy[jr]] * wj[2 * P + riz[jr]];
-                        const int o0 = base0 + roff[jr];
+                        const T* o0 = base0 + roff[jr];
 #pragma unroll
                         for (int a = 0; a < P; ++a) {
-                            const T w = wj[a] * wyz;
-                            const int o = o0 + a * PLANE;
-                            v[4 * j] += w * fx[o];
-                            v[4 * j + 1] += w * fy[o];
-                            v[4 * j + 2] += w * fz[o];
+                            const T w = wx[a] * wyz;
+                            T ex, ey, ez;
+                            Point4<T>::load(o0 + 4 * a * PLANE, ex, ey, ez);
+                            v[4 * j] += w * ex;
+                            v[4 * j + 1] += w * ey;
+                            v[4 * j + 2] += w * ez;
                         }
                     }
                 }
@@ -179,15 +233,17 @@ template <typename T, int P, int TILE, typename Out>
 static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
                               const int* sorig, const T* swt, const void* tmap, double prefactor, Out* forces,
                               int* status) {
-    constexpr int E = TILE + P - 1, EZ = (E + 3) & ~3, WSP = wstride(P) + 4;
-    const size_t smem = (3 * (size_t)E * E * EZ * sizeof(T) + 127) / 128 * 128 +
+    constexpr int E = TILE + P - 1, EZ = gather_box_z(P, TILE), WSP = wstride(P) + 4;
+    const size_t smem = (4 * (size_t)E * E * EZ * sizeof(T) + 127) / 128 * 128 +
                         (kGatherWarps * 8 * WSP * sizeof(T) + 31) / 32 * 32 + kGatherWarps * 8 * 2 * sizeof(int) +
-                        16;
+                        8;
     cudaError_t e = cudaFuncSetAttribute(k_gather_tma<T, P, TILE, Out>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    static const LaneRows lanes = order_rows(P, EZ);
     k_gather_tma<T, P, TILE, Out><<<g.ntiles, kGatherWarps * 32, smem, s>>>(
-        g, tile_start, scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), prefactor, forces, status);
+        g, tile_start, scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), lanes, prefactor, forces,
+        status);
     return cudaGetLastError();
 }
 

@@ -250,8 +250,9 @@ k_gather(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
         int mx = (ox + cx) % g.N[0]; mx += mx < 0 ? g.N[0] : 0;
         int my = (oy + cy) % g.N[1]; my += my < 0 ? g.N[1] : 0;
         int mz = (oz + cz) % g.N[2]; mz += mz < 0 ? g.N[2] : 0;
-        const int64_t f = fl.padded ? ((int64_t)(mx - g.kmin) * fl.Yp + (my - g.kmin)) * fl.Zp + (mz - g.kmin)
-                                    : ((int64_t)mx * g.N[1] + my) * g.N[2] + mz;
+        const int64_t f = fl.pstride * (fl.padded ? ((int64_t)(mx - g.kmin) * fl.Yp + (my - g.kmin)) * fl.Zp +
+                                                        (mz - g.kmin)
+                                                  : ((int64_t)mx * g.N[1] + my) * g.N[2] + mz);
         fx[i] = fields[f];
         fy[i] = fields[fl.fstride + f];
         fz[i] = fields[2 * fl.fstride + f];
