@@ -25,6 +25,10 @@
 
 using namespace pppm;
 
+namespace pppm {
+thread_local bool g_pdl = false;
+}
+
 namespace {
 
 enum Slot { K_BIN, K_SCAN, K_SCATTER, K_SPREAD, K_FOLD, K_FFT_Z_R2C, K_FFT_Y, K_FFT_X_INFLUENCE, K_FFT_Y_INV3,
@@ -360,6 +364,9 @@ int run_compute(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_
     if ((rc = setup_tiles(P, choose_tile(P, n))) != PPPM_OK) return rc;
     if ((rc = reserve_sites(P, n)) != PPPM_OK) return rc;
     P->last = s;
+    // the kernels of the sequence overlap their launches (not under per-kernel
+    // event timing, whose events must bracket each kernel)
+    PdlScope pdl(!P->prof_on);
     // with a two-slot cover table the forward z FFT folds the patches itself
     T* rho = P->cov2 ? (T*)nullptr : (T*)P->rho;
     if ((rc = run_sites_to_patches<T, In>(P, s, pos, q, n, rho, T(1))) != PPPM_OK) return rc;

@@ -267,6 +267,7 @@ template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads)
 k_fft_z_r2c(Geo g, Eng eng, const R* __restrict__ in, typename CT<R>::C* __restrict__ out, int rows, int pairs,
             PatchSrc<R> ps) {
+    pdl_enter();
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // lines interleaved in shared memory: point t of line p at a[t * pairs + p]
@@ -332,8 +333,8 @@ cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, cons
         auto kern = k_fft_z_r2c<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        kern<<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, eng, in, out, rows, pairs, ps);
-        return cudaGetLastError();
+        return launch_k(kern, dim3((npairs + pairs - 1) / pairs), dim3(kFftThreads), smem, s, g, eng, in, out, rows,
+                        pairs, ps);
     });
 }
 
@@ -342,6 +343,7 @@ cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, cons
 template <typename R, typename Eng, int SIGN>
 __global__ void __launch_bounds__(kFftThreads, 5)  // one wave of bundles at the workload sizes
 k_fft_bundle(Geo g, int axis, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ data) {
+    pdl_enter();
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Hz = g.Hz, L = eng.len(), B = bd.B;
@@ -368,8 +370,7 @@ cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, 
         auto kern = sign < 0 ? k_fft_bundle<T, decltype(eng), -1> : k_fft_bundle<T, decltype(eng), 1>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        kern<<<outer * bd.nb, kFftThreads, smem, s>>>(g, axis, bd, eng, data);
-        return cudaGetLastError();
+        return launch_k(kern, dim3(outer * bd.nb), dim3(kFftThreads), smem, s, g, axis, bd, eng, data);
     });
 }
 
@@ -417,6 +418,7 @@ k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R 
                   typename CT<R>::C* __restrict__ S, typename CT<R>::C* __restrict__ Bx, R* __restrict__ partial,
                   unsigned int* __restrict__ counter, double prefactor, double* __restrict__ energy,
                   double* __restrict__ virial) {
+    pdl_enter();
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ R red[kFftThreads / 32][14];
@@ -568,9 +570,8 @@ cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx
         auto kern = k_fft_x_influence<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        kern<<<x_influence_blocks(g, bd), kFftThreads, smem, s>>>(g, bd, eng, G, (T)beta, (T)e_scale, (T)c_field, S,
-                                                                 Bx, partial, counter, prefactor, energy, virial);
-        return cudaGetLastError();
+        return launch_k(kern, dim3(x_influence_blocks(g, bd)), dim3(kFftThreads), smem, s, g, bd, eng, G, (T)beta,
+                        (T)e_scale, (T)c_field, S, Bx, partial, counter, prefactor, energy, virial);
     });
 }
 
@@ -580,6 +581,7 @@ template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads)
 k_fft_y_inverse3(Geo g, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ A, typename CT<R>::C* __restrict__ Bx,
                  typename CT<R>::C* __restrict__ D) {
+    pdl_enter();
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ny = eng.len(), Hz = g.Hz, B = bd.B;
@@ -624,8 +626,7 @@ cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry,
         auto kern = k_fft_y_inverse3<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        kern<<<g.N[0] * bd.nb, kFftThreads, smem, s>>>(g, bd, eng, A, Bx, D);
-        return cudaGetLastError();
+        return launch_k(kern, dim3(g.N[0] * bd.nb), dim3(kFftThreads), smem, s, g, bd, eng, A, Bx, D);
     });
 }
 
@@ -648,6 +649,7 @@ __device__ __forceinline__ X pick4(const X (&a)[4], int f) {
 template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads, 6)  // six resident blocks: two rounds instead of three
 k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
+    pdl_enter();
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // lines interleaved in shared memory: point t of line L at a[t * PL + L],
@@ -762,8 +764,7 @@ cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, cons
         auto kern = k_fft_z_c2r<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        kern<<<(npairs + pairs - 1) / pairs, kFftThreads, smem, s>>>(g, eng, zo, rows, pairs);
-        return cudaGetLastError();
+        return launch_k(kern, dim3((npairs + pairs - 1) / pairs), dim3(kFftThreads), smem, s, g, eng, zo, rows, pairs);
     });
 }
 

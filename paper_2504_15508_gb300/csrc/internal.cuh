@@ -86,6 +86,46 @@ struct FieldLayout {
     int64_t pstride;  // elements between consecutive mesh points
 };
 
+// Programmatic dependent launch.  Within a plan's solve sequence each kernel
+// is launched with programmatic stream serialization: its blocks may be
+// scheduled while the previous kernel's last blocks still run, and it waits
+// (griddepcontrol.wait, the first statement of every such kernel) until that
+// kernel has completed and its writes are visible before touching memory.
+// Each kernel also allows its successor to be scheduled as soon as all of its
+// own blocks have started.  Outside the sequence (or with per-kernel event
+// timing on) launches are plain; the wait is then a no-op.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+extern thread_local bool g_pdl;  // launches of this host thread use PDL
+
+struct PdlScope {
+    bool old;
+    explicit PdlScope(bool on) : old(g_pdl) { g_pdl = on; }
+    ~PdlScope() { g_pdl = old; }
+};
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    if (!g_pdl) {
+        kern<<<grid, block, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // z extent (in points) of the TMA box of field patches: at least the patch
 // edge T + p - 1, and odd, so that the 16-byte points of the stencil rows of a
 // site fall on distinct bank groups (see k_gather_tma)

@@ -57,6 +57,25 @@ struct Point4<double> {
     }
 };
 
+// The first P entries of a 16-byte-aligned shared row (the x weights of a
+// site): 16-byte loads where the type allows.
+template <typename T, int P>
+__device__ __forceinline__ void load_row(const T* w, T (&out)[P]) {
+    int a = 0;
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (; a + 4 <= P; a += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(w + a);
+            out[a] = q.x;
+            out[a + 1] = q.y;
+            out[a + 2] = q.z;
+            out[a + 3] = q.w;
+        }
+    }
+#pragma unroll
+    for (; a < P; ++a) out[a] = w[a];
+}
+
 // Lane order of the p^2 stencil rows (iy, iz) of a site.  A warp's 16-byte
 // shared loads are served a quarter-warp (8 lanes) at a time, one 16-byte
 // bank group per lane; row (iy, iz) starts in group (iy EZ + iz) mod 8 (plus
@@ -83,11 +102,12 @@ static LaneRows order_rows(int p, int ez) {
 }
 
 template <typename T, int P, int TILE, typename Out>
-__global__ void __launch_bounds__(kGatherWarps * 32)
+__global__ void __launch_bounds__(kGatherWarps * 32, 6)  // shared memory holds six blocks an SM
 k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
              const int* __restrict__ sorig, const T* __restrict__ swt, const __grid_constant__ CUtensorMap tmap,
              const __grid_constant__ LaneRows lanes, double prefactor, Out* __restrict__ forces,
              int* __restrict__ status) {
+    pdl_enter();
     // TMA box: [x][y][z][component], z extent EZ points, 4 components a point
     constexpr int E = TILE + P - 1, EZ = gather_box_z(P, TILE), PLANE = E * EZ, PSIZE = E * PLANE;
     constexpr int WS = wstride(P), WSP = WS + 4;
@@ -185,33 +205,37 @@ k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ 
         T v[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = T(0);
+        auto interp = [&](int j) {  // site j of the batch into v[4 j .. 4 j + 2]
+            const int cl = wcell[j];
+            const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+            const T* wj = ww + j * WSP;
+            T wx[P];
+            load_row<T, P>(wj, wx);
+            const T* base0 = fbox + 4 * (lx * PLANE + ly * EZ + lz);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (j < nb) {
-                const int cl = wcell[j];
-                const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
-                const T* wj = ww + j * WSP;
-                T wx[P];
+            for (int jr = 0; jr < NR; ++jr) {
+                if (ract[jr]) {
+                    const T wyz = wj[P + riy[jr]] * wj[2 * P + riz[jr]];
+                    const T* o0 = base0 + roff[jr];
 #pragma unroll
-                for (int a = 0; a < P; ++a) wx[a] = wj[a];
-                const T* base0 = fbox + 4 * (lx * PLANE + ly * EZ + lz);
-#pragma unroll
-                for (int jr = 0; jr < NR; ++jr) {
-                    if (ract[jr]) {
-                        const T wyz = wj[P + riy[jr]] * wj[2 * P + riz[jr]];
-                        const T* o0 = base0 + roff[jr];
-#pragma unroll
-                        for (int a = 0; a < P; ++a) {
-                            const T w = wx[a] * wyz;
-                            T ex, ey, ez;
-                            Point4<T>::load(o0 + 4 * a * PLANE, ex, ey, ez);
-                            v[4 * j] += w * ex;
-                            v[4 * j + 1] += w * ey;
-                            v[4 * j + 2] += w * ez;
-                        }
+                    for (int a = 0; a < P; ++a) {
+                        const T w = wx[a] * wyz;
+                        T ex, ey, ez;
+                        Point4<T>::load(o0 + 4 * a * PLANE, ex, ey, ez);
+                        v[4 * j] += w * ex;
+                        v[4 * j + 1] += w * ey;
+                        v[4 * j + 2] += w * ez;
                     }
                 }
             }
+        };
+        if (nb == 8) {  // no per-site branch: the loads of a site can overlap the previous one's arithmetic
+#pragma unroll
+            for (int j = 0; j < 8; ++j) interp(j);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < nb) interp(j);
         }
 #pragma unroll
         for (int h = 16; h >= 1; h >>= 1) {
@@ -241,10 +265,8 @@ static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_star
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     static const LaneRows lanes = order_rows(P, EZ);
-    k_gather_tma<T, P, TILE, Out><<<g.ntiles, kGatherWarps * 32, smem, s>>>(
-        g, tile_start, scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), lanes, prefactor, forces,
-        status);
-    return cudaGetLastError();
+    return launch_k(k_gather_tma<T, P, TILE, Out>, dim3(g.ntiles), dim3(kGatherWarps * 32), smem, s, g, tile_start,
+                    scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), lanes, prefactor, forces, status);
 }
 
 #define PPPM_FAST_SWITCH_G(FN, T_, O_, ...)                                                       \

@@ -33,6 +33,7 @@ template <typename T, int P>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
          const int* __restrict__ scell, const int* __restrict__ sorig, T* __restrict__ patch) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x * kSpreadWarps + warp;
@@ -114,8 +115,8 @@ static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int* tile_start,
     cudaError_t e = cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
-    k_spread<T, P><<<blocks, kSpreadWarps * 32, smem, s>>>(g, tile_start, srec, scell, sorig, patch);
-    return cudaGetLastError();
+    return launch_k(k_spread<T, P>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tile_start, srec, scell, sorig,
+                    patch);
 }
 
 
@@ -147,6 +148,7 @@ cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, c
 template <typename T>
 __global__ void k_fold(Geo g, const T* __restrict__ patch, const int* __restrict__ cov_off,
                        const int2* __restrict__ cov_ent, int nmax1, T scale, T* __restrict__ rho) {
+    pdl_enter();
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2];
     if (idx >= total) return;
@@ -177,6 +179,7 @@ __global__ void k_fold(Geo g, const T* __restrict__ patch, const int* __restrict
 template <typename T>
 __global__ void k_fold_rows(Geo g, const T* __restrict__ patch, const int* __restrict__ cov_off,
                             const int2* __restrict__ cov_ent, int nmax1, T scale, T* __restrict__ rho) {
+    pdl_enter();
     const int row = blockIdx.x;
     const int x = row / g.N[1], y = row - x * g.N[1];
     const int* ox = cov_off;
@@ -212,11 +215,11 @@ cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int*
     int nmax1 = 1 + (g.N[0] > g.N[1] ? (g.N[0] > g.N[2] ? g.N[0] : g.N[2]) : (g.N[1] > g.N[2] ? g.N[1] : g.N[2]));
     if (g.N[2] >= 32) {
         const int threads = g.N[2] >= 128 ? 128 : (g.N[2] >= 64 ? 64 : 32);
-        k_fold_rows<T><<<g.N[0] * g.N[1], threads, 0, s>>>(g, patch, cov_off, cov_ent, nmax1, scale, rho);
-        return cudaGetLastError();
+        return launch_k(k_fold_rows<T>, dim3(g.N[0] * g.N[1]), dim3(threads), 0, s, g, patch, cov_off, cov_ent, nmax1,
+                        scale, rho);
     }
-    k_fold<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, patch, cov_off, cov_ent, nmax1, scale, rho);
-    return cudaGetLastError();
+    return launch_k(k_fold<T>, dim3((unsigned)((total + 255) / 256)), dim3(256), 0, s, g, patch, cov_off, cov_ent, nmax1,
+                    scale, rho);
 }
 
 // ------------------------------------------------------------------ gather
@@ -231,6 +234,7 @@ __global__ void __launch_bounds__(kGatherThreads)
 k_gather(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
          const int* __restrict__ scell, const int* __restrict__ sorig, const T* __restrict__ fields, FieldLayout fl,
          double prefactor, Out* __restrict__ forces) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = blockIdx.x;
     const int s0 = tile_start[tile], s1 = tile_start[tile + 1];
@@ -299,9 +303,8 @@ static cudaError_t gather_p(cudaStream_t s, const Geo& g, const int* tile_start,
     size_t smem = 3ull * g.E[0] * g.E[1] * g.E[2] * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_gather<T, P, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gather<T, P, Out><<<g.ntiles, kGatherThreads, smem, s>>>(g, tile_start, srec, scell, sorig, fields, fl,
-                                                               prefactor, forces);
-    return cudaGetLastError();
+    return launch_k(k_gather<T, P, Out>, dim3(g.ntiles), dim3(kGatherThreads), smem, s, g, tile_start, srec, scell,
+                    sorig, fields, fl, prefactor, forces);
 }
 
 template <typename T, typename Out>

@@ -64,6 +64,7 @@ template <typename T, typename In>
 __global__ void k_bin(Geo g, const In* __restrict__ pos, const In* __restrict__ q, int n,
                       int* __restrict__ tile_count, int* __restrict__ tile_of, int* __restrict__ slot_of,
                       Rec<T>* __restrict__ rec, int* __restrict__ cell, int* __restrict__ status) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
     const int lane = threadIdx.x & 31;
@@ -122,6 +123,7 @@ cudaError_t launch_bin(cudaStream_t s, const Geo& g, const In* pos, const In* q,
 // Each thread sums a contiguous chunk; warps scan their chunk sums with
 // shuffles; one warp scans the 32 warp totals; two barriers in all.
 __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, int ntiles, int* __restrict__ start) {
+    pdl_enter();
     __shared__ int wsum[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int chunk = (ntiles + 1023) / 1024;
@@ -155,8 +157,7 @@ __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, in
 }
 
 cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int* start) {
-    k_scan<<<1, 1024, 0, s>>>(count, ntiles, start);
-    return cudaGetLastError();
+    return launch_k(k_scan, dim3(1), dim3(1024), 0, s, count, ntiles, start);
 }
 
 // Scatter to tile order.  Each site's B-spline weights are evaluated here,
@@ -168,6 +169,7 @@ __global__ void k_scatter(int n, const int* __restrict__ tile_of, const int* __r
                           const int* __restrict__ tile_start, const Rec<T>* __restrict__ rec,
                           const int* __restrict__ cell, Rec<T>* __restrict__ srec, int* __restrict__ scell,
                           int* __restrict__ sorig, T* __restrict__ swt) {
+    pdl_enter();
     constexpr int WS = wstride(P);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -211,9 +213,8 @@ cudaError_t launch_scatter(cudaStream_t s, const Geo& g, int n, const int* tile_
     const int blocks = (n + 255) / 256;
 #define PPPM_SCATTER_P(PP)                                                                                  \
     case PP:                                                                                                \
-        k_scatter<T, PP><<<blocks, 256, 0, s>>>(n, tile_of, slot_of, tile_start, rec, cell, srec, scell, sorig, \
-                                                swt);                                                       \
-        break;
+        return launch_k(k_scatter<T, PP>, dim3(blocks), dim3(256), 0, s, n, tile_of, slot_of, tile_start, rec,   \
+                        cell, srec, scell, sorig, swt);
     switch (g.order) {
         PPPM_SCATTER_P(2)
         PPPM_SCATTER_P(3)

@@ -53,6 +53,7 @@ template <typename T, int P, int TILE>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
               const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch) {
+    pdl_enter();
     typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
     typedef typename Vec16T<T>::t V;
     constexpr int E = WarpSmem::E, PZ = WarpSmem::PZ, PLANE = WarpSmem::PLANE, PSIZE = WarpSmem::PSIZE;
@@ -147,8 +148,8 @@ static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_sta
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
-    k_spread_fast<T, P, TILE><<<blocks, kSpreadWarps * 32, smem, s>>>(g, tile_start, scell, sorig, swt, patch);
-    return cudaGetLastError();
+    return launch_k(k_spread_fast<T, P, TILE>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tile_start, scell,
+                    sorig, swt, patch);
 }
 
 
