@@ -392,6 +392,22 @@ int compute_dispatch(pppm_plan* P, void* stream, const In* pos, const In* q, int
     return run_compute<double, In>(P, s, pos, q, n, energy, forces, virial, nullptr);
 }
 
+// The device address of a pinned, device-mapped host array, else nullptr.
+const void* mapped_host(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+void drop_host_graph(pppm_plan* P) {
+    if (P->host_g) pppm_graph_destroy(P->host_g);
+    P->host_g = nullptr;
+    P->host_graph_n = -1;
+}
+
 template <typename In>
 int compute_host(pppm_plan* P, const In* pos, const In* q, int64_t n, double* energy, In* forces, double* virial) {
     if (!P || n < 0 || !energy || !virial) return PPPM_ERR_INVALID_ARG;
@@ -399,64 +415,79 @@ int compute_host(pppm_plan* P, const In* pos, const In* q, int64_t n, double* en
     CK(cudaSetDevice(P->device));
     const size_t need = sizeof(In) * (size_t)(7 * n) + 8 * sizeof(double) + 256;
     if (need > P->h_stage_bytes) {
+        drop_host_graph(P);  // it was captured on the old staging buffers
         dfree(P->h_stage);
-    if (P->h_status) cudaFreeHost(P->h_status);
-    if (P->host_graph) cudaGraphExecDestroy(P->host_graph);
         P->h_stage_bytes = 0;
         int rc;
         if ((rc = dalloc(&P->h_stage, need)) != PPPM_OK) return rc;
         P->h_stage_bytes = need;
     }
+    if (!P->h_tail) CK(cudaMallocHost((void**)&P->h_tail, 8 * sizeof(double)));
+    // staging: energy, virial[6], a copy of the status word, then the sites
     double* d_e = (double*)P->h_stage;
     double* d_v = d_e + 1;
+    int* d_st = reinterpret_cast<int*>(d_e + 7);
     In* d_pos = (In*)(d_e + 8);
     In* d_q = d_pos + 3 * n;
     In* d_f = d_q + n;
     cudaStream_t s = P->own;
+    // pinned (device-mapped) host arrays are read in place by the binning
+    // kernel, which then overlaps the transfer; others are copied first
+    const In* use_pos = d_pos;
+    const In* use_q = d_q;
     if (n > 0) {
-        CK(cudaMemcpyAsync(d_pos, pos, sizeof(In) * 3 * n, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(d_q, q, sizeof(In) * n, cudaMemcpyHostToDevice, s));
+        const In* mp = (const In*)mapped_host(pos);
+        const In* mq = (const In*)mapped_host(q);
+        if (mp && mq) {
+            use_pos = mp;
+            use_q = mq;
+        } else {
+            CK(cudaMemcpyAsync(d_pos, pos, sizeof(In) * 3 * n, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(d_q, q, sizeof(In) * n, cudaMemcpyHostToDevice, s));
+        }
     }
     // the device part replays a graph captured on an earlier call with the
-    // same site count and plan state (its buffers are the plan's own)
-    const bool fits = P->host_graph && P->host_graph_n == n && P->host_graph_in == (int)sizeof(In) &&
+    // same site count and plan state; the site pointers are patched per call
+    int rc = PPPM_OK;
+    const bool fits = P->host_g && P->host_graph_n == n && P->host_graph_in == (int)sizeof(In) &&
                       P->host_graph_gen == P->gen && !P->prof_on;
     if (fits) {
-        CK(cudaGraphLaunch(P->host_graph, s));
-        P->last = s;
-    } else {
-        int rc = compute_dispatch<In>(P, s, d_pos, d_q, n, d_e, d_f, d_v);
+        rc = sizeof(In) == 4 ? pppm_graph_launch_f32(P->host_g, s, (const float*)use_pos, (const float*)use_q)
+                             : pppm_graph_launch(P->host_g, s, (const double*)use_pos, (const double*)use_q);
         if (rc != PPPM_OK) return rc;
-        if (P->host_graph) {
-            cudaGraphExecDestroy(P->host_graph);
-            P->host_graph = nullptr;
-        }
-        if (n > 0 && !P->prof_on) {  // capture the same call for the next ones
-            cudaGraph_t gr = nullptr;
-            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                rc = compute_dispatch<In>(P, s, d_pos, d_q, n, d_e, d_f, d_v);
-                const cudaError_t ce = cudaStreamEndCapture(s, &gr);
-                if (rc == PPPM_OK && ce == cudaSuccess && gr &&
-                    cudaGraphInstantiate(&P->host_graph, gr, 0) == cudaSuccess) {
-                    P->host_graph_n = n;
-                    P->host_graph_in = (int)sizeof(In);
-                    P->host_graph_gen = P->gen;
-                } else {
-                    P->host_graph = nullptr;
-                }
-                if (gr) cudaGraphDestroy(gr);
-                cudaGetLastError();  // a failed capture leaves no sticky error; the eager result stands
+    } else {
+        drop_host_graph(P);
+        if (n > 0 && !P->prof_on) {
+            // an eager evaluation (this call's result), then the capture for the next calls
+            rc = sizeof(In) == 4 ? pppm_graph_create_f32(P, s, (const float*)use_pos, (const float*)use_q, n, d_e,
+                                                         (float*)d_f, d_v, &P->host_g)
+                                 : pppm_graph_create(P, s, (const double*)use_pos, (const double*)use_q, n, d_e,
+                                                     (double*)d_f, d_v, &P->host_g);
+            if (rc == PPPM_OK) {
+                P->host_graph_n = n;
+                P->host_graph_in = (int)sizeof(In);
+                P->host_graph_gen = P->gen;
+            } else {
+                P->host_g = nullptr;
+                cudaGetLastError();  // a failed capture leaves no sticky error
+                rc = compute_dispatch<In>(P, s, use_pos, use_q, n, d_e, d_f, d_v);
             }
+        } else {
+            rc = compute_dispatch<In>(P, s, use_pos, use_q, n, d_e, d_f, d_v);
         }
+        if (rc != PPPM_OK) return rc;
+        P->last = s;
     }
-    if (!P->h_status) CK(cudaMallocHost((void**)&P->h_status, sizeof(int)));
-    CK(cudaMemcpyAsync(energy, d_e, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(virial, d_v, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    // one small read-back (energy, virial, status) and the forces
+    CK(cudaMemcpyAsync(d_st, P->status, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(P->h_tail, d_e, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (n > 0) CK(cudaMemcpyAsync(forces, d_f, sizeof(In) * 3 * n, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(P->h_status, P->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));  // one synchronization for the outputs and the status word
-    if (*P->h_status) {
-        const int st = *P->h_status;
+    CK(cudaStreamSynchronize(s));  // one synchronization for all outputs
+    energy[0] = P->h_tail[0];
+    for (int k = 0; k < 6; ++k) virial[k] = P->h_tail[1 + k];
+    int st = 0;
+    std::memcpy(&st, &P->h_tail[7], sizeof(int));
+    if (st) {
         CK(cudaMemset(P->status, 0, sizeof(int)));
         return (st & 2) ? PPPM_ERR_TIMEOUT : PPPM_ERR_NONFINITE;
     }
@@ -643,9 +674,9 @@ void pppm_destroy(pppm_plan* P) {
     dfree(P->scell);
     dfree(P->sorig);
     dfree(P->swt);
+    drop_host_graph(P);
     dfree(P->h_stage);
-    if (P->h_status) cudaFreeHost(P->h_status);
-    if (P->host_graph) cudaGraphExecDestroy(P->host_graph);
+    if (P->h_tail) cudaFreeHost(P->h_tail);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : P->pend_a) cudaEventDestroy(e);
     for (cudaEvent_t e : P->pend_b) cudaEventDestroy(e);

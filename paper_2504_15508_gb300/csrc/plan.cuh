@@ -56,12 +56,12 @@ struct pppm_plan {
     cudaStream_t own = nullptr;
     void* h_stage = nullptr;  // device buffers of the host-pointer calls
     size_t h_stage_bytes = 0;
-    int* h_status = nullptr;  // pinned host copy of the status word
+    double* h_tail = nullptr;  // pinned read-back: energy, virial[6], status word
     // bumped whenever a workspace buffer is reallocated or an option changes:
     // a captured graph older than this no longer matches the plan
     uint64_t gen = 1;
     // graph of the device part of the host-pointer call (its buffers are fixed)
-    cudaGraphExec_t host_graph = nullptr;
+    pppm_graph* host_g = nullptr;
     int64_t host_graph_n = -1;
     int host_graph_in = 0;
     uint64_t host_graph_gen = 0;

@@ -87,3 +87,49 @@ def test_host_call_replays_its_graph_bitwise(cuda_device):
     plan.set_options(prefactor=2.0)
     e, f, v = plan.compute_host(hp, hq, out=out)
     assert np.allclose(f, 2.0 * f0.cpu().numpy(), rtol=1e-6, atol=0)
+
+
+def _pinned(a):
+    t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    return t, t.numpy()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_host_call_pinned_and_pageable_inputs(cuda_device, prec):
+    """Pinned host arrays are read in place by the device, pageable ones are
+    copied first; either kind, at any address, through the same replayed
+    graph, gives the device call's result bitwise."""
+    plan, pos, q = _setup("water4096", prec)
+    dt = np.float32 if prec == "fp32" else np.float64
+    rng = np.random.default_rng(3)
+    frames = [pos.cpu().numpy()]
+    frames.append((frames[0] + rng.normal(0, 0.05, size=frames[0].shape)).astype(dt))
+    hq = q.cpu().numpy()
+    keep = []
+    for k, (fr, pinned) in enumerate([(0, True), (1, True), (0, False), (1, True), (1, False)]):
+        if pinned:
+            tp, hp = _pinned(frames[fr])
+            tq, hqq = _pinned(hq)
+            keep += [tp, tq]  # distinct pinned buffers at new addresses every call
+        else:
+            hp, hqq = frames[fr].copy(), hq.copy()
+        out = (np.zeros(1), np.zeros(frames[fr].shape, dt), np.zeros(6))
+        e, f, v = plan.compute_host(hp, hqq, out=out)
+        e0, f0, v0 = plan.compute(torch.tensor(frames[fr], device="cuda"), q)
+        torch.cuda.synchronize()
+        assert e == e0.item(), (k, pinned)
+        assert np.array_equal(f, f0.cpu().numpy()) and np.array_equal(v, v0.cpu().numpy()), (k, pinned)
+
+
+def test_host_call_site_count_changes(cuda_device):
+    """Growing the site count reallocates the host-call staging and drops its
+    graph; smaller and larger calls in any order stay exact."""
+    plan, pos, q = _setup("water4096", "fp32")
+    hp, hq = pos.cpu().numpy(), q.cpu().numpy()
+    big_p = np.concatenate([hp, hp + 0.5]).astype(np.float32)
+    big_q = np.concatenate([hq, hq]).astype(np.float32)
+    for p_, q_ in [(hp, hq), (big_p, big_q), (hp, hq), (big_p, big_q)]:
+        e, f, v = plan.compute_host(p_, q_)
+        e0, f0, v0 = plan.compute(torch.tensor(p_, device="cuda"), torch.tensor(q_, device="cuda"))
+        torch.cuda.synchronize()
+        assert e == e0.item() and np.array_equal(f, f0.cpu().numpy()) and np.array_equal(v, v0.cpu().numpy())
