@@ -335,11 +335,11 @@ int run_solve(pppm_plan* P, cudaStream_t s, double* energy, double* virial, T* f
           CK(launch_fft_z_r2c<T>(s, g, P->rad[2], (const C*)P->tw[2], nullptr, c0, patch_source<T>(P)));
       else
           CK(launch_fft_z_r2c<T>(s, g, P->rad[2], (const C*)P->tw[2], (const T*)P->rho, c0, PatchSrc<T>{})); }
-    { PROF(K_FFT_Y); CK(launch_fft_bundle<T>(s, g, 1, -1, P->rad[1], P->bd, (const C*)P->tw[1], c0)); }
+    { PROF(K_FFT_Y); CK(launch_fft_bundle<T>(s, g, 1, -1, P->rad[1], P->lb[LB_Y], (const C*)P->tw[1], c0)); }
     { PROF(K_FFT_X_INFLUENCE);
-      CK(launch_fft_x_influence<T>(s, g, P->rad[0], P->bd, (const C*)P->tw[0], (const T*)P->G, P->beta, e_scale,
+      CK(launch_fft_x_influence<T>(s, g, P->rad[0], P->lb[LB_X_INFLUENCE], (const C*)P->tw[0], (const T*)P->G, P->beta, e_scale,
                                    c_field, c0, c1, (T*)P->partial, P->counter, P->opt.prefactor, energy, virial)); }
-    { PROF(K_FFT_Y_INV3); CK(launch_fft_y_inverse3<T>(s, g, P->rad[1], P->bd, (const C*)P->tw[1], c0, c1, c2)); }
+    { PROF(K_FFT_Y_INV3); CK(launch_fft_y_inverse3<T>(s, g, P->rad[1], P->lb[LB_Y_INVERSE3], (const C*)P->tw[1], c0, c1, c2)); }
     const int64_t N3 = mesh_points(P);
     const C* src[4] = {c1, c2, c0, c0};
     const int mk[4] = {0, 0, 1, 0};
@@ -561,22 +561,21 @@ int pppm_create(const double box[3], const int mesh[3], int order, double beta, 
     g.Hz = mesh[2] / 2 + 1;
     g.order = order;
     g.kmin = (order % 2) ? -(order - 1) / 2 : -order / 2 + 1;
-    // bundle: about 16 kz columns per block, fewer if shared memory would not hold 6 line buffers
-    {
-        const int Lmax = mesh[0] > mesh[1] ? mesh[0] : mesh[1];
-        int bmax = (int)((200 * 1024) / (6 * (size_t)Lmax * 2 * P->esz));
-        if (bmax < 1) bmax = 1;
-        if (bmax > 16) bmax = 16;
-        int nb = (g.Hz + bmax - 1) / bmax;
-        P->bd.B = (g.Hz + nb - 1) / nb;
-        P->bd.nb = (g.Hz + P->bd.B - 1) / P->bd.B;  // no empty bundle
-    }
     int rc = PPPM_OK;
     auto fail = [&](int code) {
         pppm_destroy(P);
         return code;
     };
     if (cudaStreamCreateWithFlags(&P->own, cudaStreamNonBlocking) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    {
+        // lines per block of the strided FFT passes, sized to whole waves on this device
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess || nsm < 1)
+            return fail(PPPM_ERR_CUDA);
+        const cudaError_t e = precision == PPPM_FP32 ? choose_line_blocks<float>(g, P->rad, nsm, P->lb)
+                                                     : choose_line_blocks<double>(g, P->rad, nsm, P->lb);
+        if (e != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    }
     upload_bspline_coefficients();
     const int64_t N3 = mesh_points(P), NH = half_points(P);
     if ((rc = dalloc(&P->G64, sizeof(double) * NH)) != PPPM_OK) return fail(rc);
@@ -600,7 +599,7 @@ int pppm_create(const double box[3], const int mesh[3], int order, double beta, 
         fl.pstride = 4;
         if ((rc = dalloc(&P->fields, 4 * P->esz * (size_t)fl.Xp * fl.Yp * fl.Zp)) != PPPM_OK) return fail(rc);
     }
-    const int nblk = x_influence_blocks(g, P->bd);
+    const int nblk = x_influence_blocks(P->lb[LB_X_INFLUENCE]);
     if ((rc = dalloc(&P->partial, 14 * P->esz * (size_t)nblk)) != PPPM_OK) return fail(rc);
     if ((rc = dalloc(&P->counter, sizeof(unsigned int))) != PPPM_OK) return fail(rc);
     if ((rc = dalloc(&P->status, sizeof(int))) != PPPM_OK) return fail(rc);
@@ -778,13 +777,13 @@ int pppm_fft_r2c(pppm_plan* P, void* stream, const void* in, void* out) {
     if (P->precision == PPPM_FP32) {
         CK(launch_fft_z_r2c<float>(s, P->g, P->rad[2], (const float2*)P->tw[2], (const float*)in, (float2*)out,
                                    PatchSrc<float>{}));
-        CK(launch_fft_bundle<float>(s, P->g, 1, -1, P->rad[1], P->bd, (const float2*)P->tw[1], (float2*)out));
-        CK(launch_fft_bundle<float>(s, P->g, 0, -1, P->rad[0], P->bd, (const float2*)P->tw[0], (float2*)out));
+        CK(launch_fft_bundle<float>(s, P->g, 1, -1, P->rad[1], P->lb[LB_Y], (const float2*)P->tw[1], (float2*)out));
+        CK(launch_fft_bundle<float>(s, P->g, 0, -1, P->rad[0], P->lb[LB_X], (const float2*)P->tw[0], (float2*)out));
     } else {
         CK(launch_fft_z_r2c<double>(s, P->g, P->rad[2], (const double2*)P->tw[2], (const double*)in,
                                     (double2*)out, PatchSrc<double>{}));
-        CK(launch_fft_bundle<double>(s, P->g, 1, -1, P->rad[1], P->bd, (const double2*)P->tw[1], (double2*)out));
-        CK(launch_fft_bundle<double>(s, P->g, 0, -1, P->rad[0], P->bd, (const double2*)P->tw[0], (double2*)out));
+        CK(launch_fft_bundle<double>(s, P->g, 1, -1, P->rad[1], P->lb[LB_Y], (const double2*)P->tw[1], (double2*)out));
+        CK(launch_fft_bundle<double>(s, P->g, 0, -1, P->rad[0], P->lb[LB_X], (const double2*)P->tw[0], (double2*)out));
     }
     return PPPM_OK;
 }
@@ -798,8 +797,8 @@ int pppm_fft_c2r(pppm_plan* P, void* stream, const void* in, void* out) {
     const int mk[1] = {0};
     if (P->precision == PPPM_FP32) {
         float2* c0 = (float2*)P->cx[0];
-        CK(launch_fft_bundle<float>(s, P->g, 0, 1, P->rad[0], P->bd, (const float2*)P->tw[0], c0));
-        CK(launch_fft_bundle<float>(s, P->g, 1, 1, P->rad[1], P->bd, (const float2*)P->tw[1], c0));
+        CK(launch_fft_bundle<float>(s, P->g, 0, 1, P->rad[0], P->lb[LB_X], (const float2*)P->tw[0], c0));
+        CK(launch_fft_bundle<float>(s, P->g, 1, 1, P->rad[1], P->lb[LB_Y], (const float2*)P->tw[1], c0));
         const float2* src[1] = {c0};
         float* o[1] = {(float*)out};
         FieldLayout fl{};
@@ -808,8 +807,8 @@ int pppm_fft_c2r(pppm_plan* P, void* stream, const void* in, void* out) {
         CK(launch_fft_z_c2r<float>(s, P->g, P->rad[2], (const float2*)P->tw[2], 1, src, mk, o, fl));
     } else {
         double2* c0 = (double2*)P->cx[0];
-        CK(launch_fft_bundle<double>(s, P->g, 0, 1, P->rad[0], P->bd, (const double2*)P->tw[0], c0));
-        CK(launch_fft_bundle<double>(s, P->g, 1, 1, P->rad[1], P->bd, (const double2*)P->tw[1], c0));
+        CK(launch_fft_bundle<double>(s, P->g, 0, 1, P->rad[0], P->lb[LB_X], (const double2*)P->tw[0], c0));
+        CK(launch_fft_bundle<double>(s, P->g, 1, 1, P->rad[1], P->lb[LB_Y], (const double2*)P->tw[1], c0));
         const double2* src[1] = {c0};
         double* o[1] = {(double*)out};
         FieldLayout fl{};

@@ -341,36 +341,43 @@ cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, cons
 // ------------------------------------------------------------------ strided-line C2C
 // axis 1: lines along y (outer index x); axis 0: lines along x (outer index y).
 template <typename R, typename Eng, int SIGN>
-__global__ void __launch_bounds__(kFftThreads, 5)  // one wave of bundles at the workload sizes
-k_fft_bundle(Geo g, int axis, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ data) {
+__global__ void __launch_bounds__(kFftThreads, 5)  // one wave of blocks at the workload sizes
+k_fft_bundle(Geo g, int axis, LineBlocks lb, Eng eng, typename CT<R>::C* __restrict__ data) {
     pdl_enter();
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Hz = g.Hz, L = eng.len(), B = bd.B;
-    const int outer = blockIdx.x / bd.nb, bi = blockIdx.x - outer * bd.nb;
-    const int kz0 = bi * B;
-    const int nl = min(B, Hz - kz0);
-    const int64_t es = axis == 1 ? (int64_t)Hz : (int64_t)g.N[1] * Hz;
-    const int64_t os = axis == 1 ? (int64_t)g.N[1] * Hz : (int64_t)Hz;
+    const int Hz = g.Hz, L = eng.len(), B = lb.B;
+    const int64_t es = axis == 1 ? (int64_t)Hz : (int64_t)g.N[1] * Hz;  // along the line
+    const int64_t os = axis == 1 ? (int64_t)g.N[1] * Hz : (int64_t)Hz;  // between outer rows
+    const int64_t nlines = (int64_t)(axis == 1 ? g.N[0] : g.N[1]) * Hz;
+    const int64_t f0 = (int64_t)blockIdx.x * B;
+    const int nl = (int)min((int64_t)B, nlines - f0);
+    const int l = threadIdx.x & 15;  // this thread's line (B <= 16)
+    const int64_t fl = f0 + l;
+    const int64_t loff = (fl / Hz) * os + fl % Hz;
     C* a = reinterpret_cast<C*>(smem_raw);
     C* b = a + L * B;
-    C* base = data + outer * os + kz0;
-    BUNDLE_LOOP(t, l, L, nl) a[t * B + l] = base[t * es + l];
+    if (l < nl) {
+#pragma unroll
+        for (int t = threadIdx.x >> 4; t < L; t += kFftThreads >> 4) a[t * B + l] = data[loff + t * es];
+    }
     __syncthreads();
     C* res = eng.template run<SIGN, true>(a, b, nl, 1, B);
-    BUNDLE_LOOP(t, l, L, nl) base[t * es + l] = res[t * B + l];
+    if (l < nl) {
+#pragma unroll
+        for (int t = threadIdx.x >> 4; t < L; t += kFftThreads >> 4) data[loff + t * es] = res[t * B + l];
+    }
 }
 
 template <typename T>
-cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, const Radix& r, const Bundle& bd,
+cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, const Radix& r, const LineBlocks& lb,
                               const typename Cx<T>::t* tw, typename Cx<T>::t* data) {
-    const int outer = axis == 1 ? g.N[0] : g.N[1];
-    const size_t smem = 2ull * r.L * bd.B * sizeof(typename Cx<T>::t);
+    const size_t smem = 2ull * r.L * lb.B * sizeof(typename Cx<T>::t);
     return with_engine<T>(r, tw, [&](auto eng) {
         auto kern = sign < 0 ? k_fft_bundle<T, decltype(eng), -1> : k_fft_bundle<T, decltype(eng), 1>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        return launch_k(kern, dim3(outer * bd.nb), dim3(kFftThreads), smem, s, g, axis, bd, eng, data);
+        return launch_k(kern, dim3(lb.nblk), dim3(kFftThreads), smem, s, g, axis, lb, eng, data);
     });
 }
 
@@ -414,7 +421,7 @@ template <typename R, typename Eng>
 // five resident blocks (one wave at 128: three line buffers fit) where the
 // buffers allow it; at longer lines shared memory caps it at four anyway
 __global__ void __launch_bounds__(kFftThreads, (Eng::kLen > 0 && Eng::kLen <= 128) ? 5 : 4)
-k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R e_scale, R c_field,
+k_fft_x_influence(Geo g, LineBlocks lb, Eng eng, const R* __restrict__ G, R beta, R e_scale, R c_field,
                   typename CT<R>::C* __restrict__ S, typename CT<R>::C* __restrict__ Bx, R* __restrict__ partial,
                   unsigned int* __restrict__ counter, double prefactor, double* __restrict__ energy,
                   double* __restrict__ virial) {
@@ -423,43 +430,44 @@ k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ R red[kFftThreads / 32][14];
     __shared__ bool is_last;
-    const int Nx = eng.len(), Ny = g.N[1], Nz = g.N[2], Hz = g.Hz, B = bd.B;
-    const int y = blockIdx.x / bd.nb, bi = blockIdx.x - y * bd.nb;
-    const int kz0 = bi * B;
-    const int nl = min(B, Hz - kz0);
+    const int Nx = eng.len(), Ny = g.N[1], Nz = g.N[2], Hz = g.Hz, B = lb.B;
+    // lines along x, numbered f = y Hz + kz: a block's B lines are consecutive in memory
     const int64_t es = (int64_t)Ny * Hz;
+    const int64_t f0 = (int64_t)blockIdx.x * B;
+    const int nl = (int)min((int64_t)B, es - f0);
+    const int lt = threadIdx.x & 15;  // this thread's line (B <= 16)
+    const int yl = (int)((f0 + lt) / Hz), kzl = (int)((f0 + lt) - (int64_t)yl * Hz);
     // three line buffers; each transform returns the one holding its result
     // and the others are reused as they free up
     C* a0 = reinterpret_cast<C*>(smem_raw);
     C* a1 = a0 + Nx * B;
     C* b0 = a1 + Nx * B;
-    C* base = S + (int64_t)y * Hz + kz0;
+    C* base = S + f0;
     BUNDLE_LOOP(t, l, Nx, nl) a0[t * B + l] = base[t * es + l];
     // with a compile-time length, each thread's G values are fetched now so
     // that their latency hides behind the forward FFT
     constexpr int NG = Eng::kLen > 0 ? Eng::kLen / (kFftThreads / 16) : 1;
     R gpre[NG];
     if constexpr (Eng::kLen > 0) {
-        const int l = threadIdx.x & 15;
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
             const int t = (threadIdx.x >> 4) + i * (kFftThreads / 16);
-            gpre[i] = l < nl ? __ldg(&G[((int64_t)t * Ny + y) * Hz + kz0 + l]) : R(0);
+            gpre[i] = lt < nl ? __ldg(&G[(int64_t)t * es + f0 + lt]) : R(0);
         }
     }
     __syncthreads();
     C* rh = eng.template run<-1, true>(a0, a1, nl, 1, B);
     C* pbuf = (rh == a0) ? a1 : a0;  // free partner of the result buffer
 
-    const int my = y <= Ny / 2 ? y : y - Ny;
+    const int my = yl <= Ny / 2 ? yl : yl - Ny;
     const R ky = kfac<R>(g, 1) * my;
-    const bool nyq_y = (Ny % 2 == 0) && (y == Ny / 2);
+    const bool nyq_y = (Ny % 2 == 0) && (yl == Ny / 2);
     const R inv4b2 = R(1) / (R(4) * beta * beta);
     R acc_hi[7], acc_lo[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) { acc_hi[q] = R(0); acc_lo[q] = R(0); }
     BUNDLE_LOOP_ROLLED(t, l, Nx, nl) {
-        const int kz = kz0 + l;
+        const int kz = kzl;
         const int mx = t <= Nx / 2 ? t : t - Nx;
         const R kx = kfac<R>(g, 0) * mx;
         const R kzv = kfac<R>(g, 2) * kz;
@@ -472,7 +480,7 @@ k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R 
 #pragma unroll
             for (int q = 1; q < NG; ++q) gk = (i == q) ? gpre[q] : gk;
         } else {
-            gk = G[((int64_t)t * Ny + y) * Hz + kz];
+            gk = G[(int64_t)t * es + f0 + l];
         }
         const C v = rh[t * B + l];
         const bool plane1 = (kz == 0) || ((Nz % 2 == 0) && (kz == Nz / 2));
@@ -501,7 +509,7 @@ k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R 
     C* rA = eng.template run<1, true>(pbuf, rh, nl, 1, B);  // rho_hat is no longer needed: scratch
     C* fr = (rA == pbuf) ? rh : pbuf;
     C* rB = eng.template run<1, true>(b0, fr, nl, 1, B);
-    C* obx = Bx + (int64_t)y * Hz + kz0;
+    C* obx = Bx + f0;
     BUNDLE_LOOP(t, l, Nx, nl) {
         base[t * es + l] = rA[t * B + l];
         obx[t * es + l] = rB[t * B + l];
@@ -558,19 +566,19 @@ k_fft_x_influence(Geo g, Bundle bd, Eng eng, const R* __restrict__ G, R beta, R 
     }
 }
 
-int x_influence_blocks(const Geo& g, const Bundle& bd) { return g.N[1] * bd.nb; }
+int x_influence_blocks(const LineBlocks& lb) { return lb.nblk; }
 
 template <typename T>
-cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx, const Bundle& bd,
+cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx, const LineBlocks& lb,
                                    const typename Cx<T>::t* tw, const T* G, double beta, double e_scale,
                                    double c_field, typename Cx<T>::t* S, typename Cx<T>::t* Bx, T* partial,
                                    unsigned int* counter, double prefactor, double* energy, double* virial) {
-    const size_t smem = 3ull * g.N[0] * bd.B * sizeof(typename Cx<T>::t);
+    const size_t smem = 3ull * g.N[0] * lb.B * sizeof(typename Cx<T>::t);
     return with_engine<T>(rx, tw, [&](auto eng) {
         auto kern = k_fft_x_influence<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        return launch_k(kern, dim3(x_influence_blocks(g, bd)), dim3(kFftThreads), smem, s, g, bd, eng, G, (T)beta,
+        return launch_k(kern, dim3(x_influence_blocks(lb)), dim3(kFftThreads), smem, s, g, lb, eng, G, (T)beta,
                         (T)e_scale, (T)c_field, S, Bx, partial, counter, prefactor, energy, virial);
     });
 }
@@ -579,16 +587,17 @@ cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx
 // C = IFFT_y(A), D = IFFT_y(-i ky' A), Ex' = IFFT_y(Bx); C overwrites A, Ex' overwrites Bx.
 template <typename R, typename Eng>
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_y_inverse3(Geo g, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ A, typename CT<R>::C* __restrict__ Bx,
+k_fft_y_inverse3(Geo g, LineBlocks lb, Eng eng, typename CT<R>::C* __restrict__ A, typename CT<R>::C* __restrict__ Bx,
                  typename CT<R>::C* __restrict__ D) {
     pdl_enter();
     typedef typename CT<R>::C C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Ny = eng.len(), Hz = g.Hz, B = bd.B;
-    const int x = blockIdx.x / bd.nb, bi = blockIdx.x - x * bd.nb;
-    const int kz0 = bi * B;
-    const int nl = min(B, Hz - kz0);
-    const int64_t off = (int64_t)x * Ny * Hz + kz0;
+    const int Ny = eng.len(), Hz = g.Hz, B = lb.B;
+    // lines along y, numbered f = x Hz + kz; line f starts at x Ny Hz + kz
+    const int64_t f0 = (int64_t)blockIdx.x * B;
+    const int nl = (int)min((int64_t)B, (int64_t)g.N[0] * Hz - f0);
+    const int64_t fl = f0 + (threadIdx.x & 15);  // this thread's line (B <= 16)
+    const int64_t loff = (fl / Hz) * ((int64_t)Ny * Hz) + fl % Hz;
     // four line buffers: the three inputs and a scratch that rotates, each
     // transform leaving its result in one of the two it used
     const int sz = Ny * B;
@@ -597,12 +606,12 @@ k_fft_y_inverse3(Geo g, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ A, t
     C* p2 = p1 + sz;
     C* scr = p2 + sz;
     BUNDLE_LOOP(t, l, Ny, nl) {
-        const C va = A[off + (int64_t)t * Hz + l];
+        const C va = A[loff + (int64_t)t * Hz];
         const int my = t <= Ny / 2 ? t : t - Ny;
         const R kyd = ((Ny % 2 == 0) && (t == Ny / 2)) ? R(0) : kfac<R>(g, 1) * my;
         p0[t * B + l] = va;
         p1[t * B + l] = CT<R>::mk(kyd * va.y, -kyd * va.x);
-        p2[t * B + l] = Bx[off + (int64_t)t * Hz + l];
+        p2[t * B + l] = Bx[loff + (int64_t)t * Hz];
     }
     __syncthreads();
     C* rC = eng.template run<1, true>(p0, scr, nl, 1, B);
@@ -611,22 +620,22 @@ k_fft_y_inverse3(Geo g, Bundle bd, Eng eng, typename CT<R>::C* __restrict__ A, t
     if (rD == scr) scr = p1;
     C* rE = eng.template run<1, true>(p2, scr, nl, 1, B);
     BUNDLE_LOOP(t, l, Ny, nl) {
-        A[off + (int64_t)t * Hz + l] = rC[t * B + l];
-        D[off + (int64_t)t * Hz + l] = rD[t * B + l];
-        Bx[off + (int64_t)t * Hz + l] = rE[t * B + l];
+        A[loff + (int64_t)t * Hz] = rC[t * B + l];
+        D[loff + (int64_t)t * Hz] = rD[t * B + l];
+        Bx[loff + (int64_t)t * Hz] = rE[t * B + l];
     }
 }
 
 template <typename T>
-cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry, const Bundle& bd,
+cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry, const LineBlocks& lb,
                                   const typename Cx<T>::t* tw, typename Cx<T>::t* A, typename Cx<T>::t* Bx,
                                   typename Cx<T>::t* D) {
-    const size_t smem = 4ull * g.N[1] * bd.B * sizeof(typename Cx<T>::t);
+    const size_t smem = 4ull * g.N[1] * lb.B * sizeof(typename Cx<T>::t);
     return with_engine<T>(ry, tw, [&](auto eng) {
         auto kern = k_fft_y_inverse3<T, decltype(eng)>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        return launch_k(kern, dim3(g.N[0] * bd.nb), dim3(kFftThreads), smem, s, g, bd, eng, A, Bx, D);
+        return launch_k(kern, dim3(lb.nblk), dim3(kFftThreads), smem, s, g, lb, eng, A, Bx, D);
     });
 }
 
@@ -768,15 +777,68 @@ cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, cons
     });
 }
 
+// B for one pass: the fewest rounds of resident blocks, then the fewest
+// blocks on the busiest SM (a block costs about the same for any B <= 16:
+// its lanes are laid out for 16 lines), then the larger B.
+template <typename K>
+static LineBlocks pick_line_blocks(K kern, size_t bytes_per_line, int64_t lines, int nsm) {
+    int maxB = 16;
+    while (maxB > 1 && bytes_per_line * maxB > 227 * 1024) --maxB;
+    LineBlocks best{1, (int)lines};
+    int64_t best_rounds = -1, best_busy = 0;
+    if (set_smem(kern, bytes_per_line * maxB) != cudaSuccess) {
+        cudaGetLastError();
+        return best;
+    }
+    for (int B = 1; B <= maxB; ++B) {
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kFftThreads, bytes_per_line * B) !=
+                cudaSuccess ||
+            per < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const int64_t blocks = (lines + B - 1) / B;
+        const int64_t rounds = (blocks + (int64_t)per * nsm - 1) / ((int64_t)per * nsm);
+        const int64_t busy = (blocks + nsm - 1) / nsm;
+        if (best_rounds < 0 || rounds < best_rounds || (rounds == best_rounds && busy <= best_busy)) {
+            best_rounds = rounds;
+            best_busy = busy;
+            best = LineBlocks{B, (int)blocks};
+        }
+    }
+    return best;
+}
+
+template <typename T>
+cudaError_t choose_line_blocks(const Geo& g, const Radix rad[3], int nsm, LineBlocks lb[4]) {
+    typedef typename Cx<T>::t C;
+    const int64_t Hz = g.Hz;
+    cudaError_t e = with_engine<T>(rad[1], nullptr, [&](auto eng) {
+        lb[LB_Y] = pick_line_blocks(k_fft_bundle<T, decltype(eng), -1>, 2 * sizeof(C) * rad[1].L, g.N[0] * Hz, nsm);
+        lb[LB_Y_INVERSE3] =
+            pick_line_blocks(k_fft_y_inverse3<T, decltype(eng)>, 4 * sizeof(C) * rad[1].L, g.N[0] * Hz, nsm);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
+    return with_engine<T>(rad[0], nullptr, [&](auto eng) {
+        lb[LB_X_INFLUENCE] =
+            pick_line_blocks(k_fft_x_influence<T, decltype(eng)>, 3 * sizeof(C) * rad[0].L, g.N[1] * Hz, nsm);
+        lb[LB_X] = pick_line_blocks(k_fft_bundle<T, decltype(eng), 1>, 2 * sizeof(C) * rad[0].L, g.N[1] * Hz, nsm);
+        return cudaSuccess;
+    });
+}
+
 #define PPPM_INST_FFT(T)                                                                                           \
     template cudaError_t launch_fft_z_r2c<T>(cudaStream_t, const Geo&, const Radix&, const Cx<T>::t*, const T*,    \
                                              Cx<T>::t*, const PatchSrc<T>&);                                       \
-    template cudaError_t launch_fft_bundle<T>(cudaStream_t, const Geo&, int, int, const Radix&, const Bundle&,     \
+    template cudaError_t choose_line_blocks<T>(const Geo&, const Radix*, int, LineBlocks*);                      \
+    template cudaError_t launch_fft_bundle<T>(cudaStream_t, const Geo&, int, int, const Radix&, const LineBlocks&, \
                                               const Cx<T>::t*, Cx<T>::t*);                                         \
-    template cudaError_t launch_fft_x_influence<T>(cudaStream_t, const Geo&, const Radix&, const Bundle&,          \
+    template cudaError_t launch_fft_x_influence<T>(cudaStream_t, const Geo&, const Radix&, const LineBlocks&,      \
                                                    const Cx<T>::t*, const T*, double, double, double, Cx<T>::t*,   \
                                                    Cx<T>::t*, T*, unsigned int*, double, double*, double*);        \
-    template cudaError_t launch_fft_y_inverse3<T>(cudaStream_t, const Geo&, const Radix&, const Bundle&,           \
+    template cudaError_t launch_fft_y_inverse3<T>(cudaStream_t, const Geo&, const Radix&, const LineBlocks&,       \
                                                   const Cx<T>::t*, Cx<T>::t*, Cx<T>::t*, Cx<T>::t*);               \
     template cudaError_t launch_fft_z_c2r<T>(cudaStream_t, const Geo&, const Radix&, const Cx<T>::t*, int,         \
                                              const Cx<T>::t* const*, const int*, T* const*, const FieldLayout&);

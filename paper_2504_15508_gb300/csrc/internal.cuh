@@ -131,12 +131,23 @@ cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
 // site fall on distinct bank groups (see k_gather_tma)
 __host__ __device__ constexpr int gather_box_z(int p, int t) { return (t + p - 1) | 1; }
 
-// Bundle shape of a strided-line FFT pass (lines along y or x, B adjacent kz
-// columns per block).
+// Bundle shape of a strided-line FFT pass in the batched kernel (lines along
+// y or x, B adjacent kz columns per block).
 struct Bundle {
     int B;           // lines per block
     int nb;          // bundles per outer index = ceil(Hz / B)
 };
+
+// Blocks of a strided-line FFT pass of a plan: the lines (along y or x) are
+// numbered f = outer Hz + kz over the other two indices, and a block takes B
+// consecutive f (it may span two outer rows), so B can be chosen per pass to
+// fill whole waves of resident blocks (choose_line_blocks).
+struct LineBlocks {
+    int B;     // lines per block, at most 16
+    int nblk;  // blocks = ceil(outer Hz / B)
+};
+// the passes of a plan
+enum { LB_Y = 0, LB_X_INFLUENCE = 1, LB_Y_INVERSE3 = 2, LB_X = 3 };
 
 // The fast spread and gather need full tiles on every axis and a tile edge of 4 or 8.
 inline bool fast_tiles(const Geo& g) {
@@ -178,15 +189,15 @@ template <typename T>
 cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw,
                              const T* in, typename Cx<T>::t* out, const PatchSrc<T>& ps);
 template <typename T>
-cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, const Radix& r, const Bundle& bd,
+cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, const Radix& r, const LineBlocks& lb,
                               const typename Cx<T>::t* tw, typename Cx<T>::t* data);
 template <typename T>
-cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx, const Bundle& bd,
+cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx, const LineBlocks& lb,
                                    const typename Cx<T>::t* tw, const T* G, double beta, double e_scale,
                                    double c_field, typename Cx<T>::t* S, typename Cx<T>::t* Bx, T* partial,
                                    unsigned int* counter, double prefactor, double* energy, double* virial);
 template <typename T>
-cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry, const Bundle& bd,
+cudaError_t launch_fft_y_inverse3(cudaStream_t s, const Geo& g, const Radix& ry, const LineBlocks& lb,
                                   const typename Cx<T>::t* tw, typename Cx<T>::t* A, typename Cx<T>::t* Bx,
                                   typename Cx<T>::t* D);
 // nf fields: out[f] = C2R_z(src[f] * (mulkz[f] ? -i kz' : 1)); src/out arrays of nf pointers
@@ -194,7 +205,10 @@ template <typename T>
 cudaError_t launch_fft_z_c2r(cudaStream_t s, const Geo& g, const Radix& rz, const typename Cx<T>::t* tw, int nf,
                              const typename Cx<T>::t* const* src, const int* mulkz, T* const* out,
                              const FieldLayout& fl);
-int x_influence_blocks(const Geo& g, const Bundle& bd);
+int x_influence_blocks(const LineBlocks& lb);
+// B of each pass (LB_*), from the resident blocks per SM of its kernel
+template <typename T>
+cudaError_t choose_line_blocks(const Geo& g, const Radix rad[3], int nsm, LineBlocks lb[4]);
 
 // influence.cu
 cudaError_t launch_influence(cudaStream_t s, const Geo& g, double beta, int alias, double* G);

@@ -18,7 +18,7 @@ struct pppm_plan {
     pppm_options opt{};
     pppm::Geo g{};
     pppm::Radix rad[3]{};
-    pppm::Bundle bd{};
+    pppm::LineBlocks lb[4]{};  // strided-line FFT passes (LB_*)
     size_t esz = 4;  // sizeof(real)
     // mesh workspace
     double* G64 = nullptr;
