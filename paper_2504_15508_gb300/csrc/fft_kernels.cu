@@ -340,8 +340,10 @@ cudaError_t launch_fft_z_r2c(cudaStream_t s, const Geo& g, const Radix& rz, cons
 
 // ------------------------------------------------------------------ strided-line C2C
 // axis 1: lines along y (outer index x); axis 0: lines along x (outer index y).
+// Four resident blocks (64 registers): with the lines per block chosen for it,
+// the strided passes run in one round of blocks at the workload sizes.
 template <typename R, typename Eng, int SIGN>
-__global__ void __launch_bounds__(kFftThreads, 5)  // one wave of blocks at the workload sizes
+__global__ void __launch_bounds__(kFftThreads, 4)
 k_fft_bundle(Geo g, int axis, LineBlocks lb, Eng eng, typename CT<R>::C* __restrict__ data) {
     pdl_enter();
     typedef typename CT<R>::C C;
@@ -418,9 +420,7 @@ __device__ __forceinline__ void two_sum_pair(R& h, R& l, R h2, R l2) {
 }
 
 template <typename R, typename Eng>
-// five resident blocks (one wave at 128: three line buffers fit) where the
-// buffers allow it; at longer lines shared memory caps it at four anyway
-__global__ void __launch_bounds__(kFftThreads, (Eng::kLen > 0 && Eng::kLen <= 128) ? 5 : 4)
+__global__ void __launch_bounds__(kFftThreads, 4)
 k_fft_x_influence(Geo g, LineBlocks lb, Eng eng, const R* __restrict__ G, R beta, R e_scale, R c_field,
                   typename CT<R>::C* __restrict__ S, typename CT<R>::C* __restrict__ Bx, R* __restrict__ partial,
                   unsigned int* __restrict__ counter, double prefactor, double* __restrict__ energy,
@@ -586,7 +586,7 @@ cudaError_t launch_fft_x_influence(cudaStream_t s, const Geo& g, const Radix& rx
 // ------------------------------------------------------------------ y inverse, three outputs
 // C = IFFT_y(A), D = IFFT_y(-i ky' A), Ex' = IFFT_y(Bx); C overwrites A, Ex' overwrites Bx.
 template <typename R, typename Eng>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, 4)
 k_fft_y_inverse3(Geo g, LineBlocks lb, Eng eng, typename CT<R>::C* __restrict__ A, typename CT<R>::C* __restrict__ Bx,
                  typename CT<R>::C* __restrict__ D) {
     pdl_enter();
