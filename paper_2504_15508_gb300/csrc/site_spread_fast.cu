@@ -120,8 +120,18 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
             const int cl = W.st_cell[j];
             const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
             T wxq[P];
+            if constexpr (sizeof(T) == 4 && P >= 4) {  // staged rows are 16-byte aligned
+                const float4 q4 = *reinterpret_cast<const float4*>(&W.u.st_w[j][0]);
+                wxq[0] = q4.x;
+                wxq[1] = q4.y;
+                wxq[2] = q4.z;
+                wxq[3] = q4.w;
 #pragma unroll
-            for (int a = 0; a < P; ++a) wxq[a] = W.u.st_w[j][a];
+                for (int a = 4; a < P; ++a) wxq[a] = W.u.st_w[j][a];
+            } else {
+#pragma unroll
+                for (int a = 0; a < P; ++a) wxq[a] = W.u.st_w[j][a];
+            }
             T* base0 = W.pt + lx * PLANE + ly * PZ + lz;
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr) {
