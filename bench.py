@@ -703,8 +703,9 @@ class ShortRangeStandIn:
 def run_overlap(args):
     """The 128^3 force evaluation (one captured graph) and the short-range
     stand-in, alone, back to back on one stream, and concurrently on two
-    streams (the long-range one at high priority), as in the paper's overlap
-    of long- and short-range forces (Section "Long-range and Short-range Force
+    streams (long range at high or at equal priority; PPPM kernels with and
+    without programmatic dependent launch), as in the paper's overlap of long-
+    and short-range forces (Section "Long-range and Short-range Force
     Overlap")."""
     import torch
 
@@ -720,7 +721,7 @@ def run_overlap(args):
     plan.reserve(n)
     lo = torch.cuda.Stream(device=dev, priority=0)
     hi = torch.cuda.Stream(device=dev, priority=-1)
-    g = plan.graph(pos, q)
+    lo2 = torch.cuda.Stream(device=dev, priority=0)
     sr = ShortRangeStandIn(3 * wb.n_mol, dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     main = torch.cuda.current_stream()
@@ -739,19 +740,7 @@ def run_overlap(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs) / K
 
-    def lr_alone():
-        g.launch(pos, q, stream=main)
-
-    def sr_alone():
-        sr()
-
-    def sequential():
-        g.launch(pos, q, stream=main)
-        sr()
-
-    lo2 = torch.cuda.Stream(device=dev, priority=0)
-
-    def concurrent(lr_stream, sr_stream):
+    def concurrent(g, lr_stream, sr_stream):
         def body():
             start = torch.cuda.Event()
             start.record(main)
@@ -767,32 +756,55 @@ def run_overlap(args):
             main.wait_event(done_sr)
         return body
 
-    t_lr = timed(lr_alone)
-    t_sr = timed(sr_alone)
-    t_seq = timed(sequential)
-    t_par = timed(concurrent(hi, lo))      # long range on the high-priority stream
-    t_par_eq = timed(concurrent(lo2, lo))  # both at the same priority
-    f_ref = g.out[1].clone()
-    # results under overlap are those of the step alone
-    g.launch(pos, q, stream=main)
-    torch.cuda.synchronize()
-    same = bool(torch.equal(g.out[1], f_ref))
+    t_sr = timed(lambda: sr())
+    # with and without programmatic dependent launch between the PPPM kernels:
+    # its early-scheduled blocks hold SM resources the concurrent work could use
+    runs = {}
+    f_ref = None
+    same = True
+    for pdl in (True, False):
+        plan.set_dependent_launch(pdl)
+        g = plan.graph(pos, q)
+        r = {"long_range_alone": timed(lambda: g.launch(pos, q, stream=main))}
+
+        def sequential():
+            g.launch(pos, q, stream=main)
+            sr()
+
+        r["sequential"] = timed(sequential)
+        r["concurrent"] = timed(concurrent(g, hi, lo))  # long range on the high-priority stream
+        r["concurrent_equal_priority"] = timed(concurrent(g, lo2, lo))
+        # results under overlap are those of the step alone, with either launch mode
+        g.launch(pos, q, stream=main)
+        torch.cuda.synchronize()
+        if f_ref is None:
+            f_ref = g.out[1].clone()
+        same = same and bool(torch.equal(g.out[1], f_ref))
+        g.close()
+        runs["dependent_launch_on" if pdl else "dependent_launch_off"] = r
+    plan.set_dependent_launch(True)
+    # the headline: the best concurrent configuration, against the best back-to-back one
+    best_key, best_mode = min(((m, k) for k in runs for m in ("concurrent", "concurrent_equal_priority")),
+                              key=lambda mk: runs[mk[1]][mk[0]])
+    t_par = runs[best_mode][best_key]
+    t_seq = min(r["sequential"] for r in runs.values())
+    t_lr = min(r["long_range_alone"] for r in runs.values())
     line = {
         "metric": "long-range step concurrent with a short-range load", "value": 1e3 / t_par,
         "unit": "steps/s", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": t_par,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
-        "config": {"workload": f"overlap: water72192 ({n} sites) PPPM on 128^3 (captured graph, high-priority "
-                               f"stream) with a {3 * wb.n_mol}-atom 128-240-240-240-1 BF16 MLP stand-in "
+        "config": {"workload": f"overlap: water72192 ({n} sites) PPPM on 128^3 (captured graph) with a "
+                               f"{3 * wb.n_mol}-atom 128-240-240-240-1 BF16 MLP stand-in "
                                f"({sr.flops / 1e9:.1f} GFLOP) on a second stream",
+                   "best": {"streams": "long range at high priority" if best_key == "concurrent"
+                            else "equal priorities", "pppm_launch": best_mode},
                    "l2": "flushed between timed steps"},
-        "ms": {"long_range_alone": t_lr, "short_range_alone": t_sr, "sequential": t_seq, "concurrent": t_par,
-               "concurrent_equal_priority": t_par_eq},
+        "ms": {"short_range_alone": t_sr, **{k: v for k, v in runs.items()}},
         "speedup_vs_sequential": t_seq / t_par,
         "hidden_fraction_of_shorter": (t_lr + t_sr - t_par) / min(t_lr, t_sr),
         "short_range_tflops_alone": sr.flops / (t_sr * 1e-3) / 1e12,
         "pppm_results_unchanged": same,
     }
-    g.close()
     print(json.dumps(line), flush=True)
 
 

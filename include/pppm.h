@@ -32,7 +32,9 @@
  *   (a cudaStream_t passed as void*, NULL = legacy default stream) and write
  *   energy and virial to device memory, so a call can be captured in a CUDA
  *   graph once the plan's site capacity covers n (pppm_reserve).
- *   A plan is not thread-safe: one compute at a time per plan.
+ *   A plan is not thread-safe: one compute at a time per plan.  Its calls
+ *   share the workspace, so calls on different streams must be ordered by
+ *   the caller (a synchronization or an event wait between them).
  *
  * Errors
  *   Every call returns PPPM_OK (0) or a negative PPPM_ERR_* code; nothing
@@ -238,10 +240,24 @@ int pppm_spread_noalloc(const double box[3], const int mesh[3], int order, void 
  * pppm_set_potential -- when on (nonzero), every later compute call of an FP32
  * plan also writes the mesh potential phi (the inverse FFT of G(k) rho_hat(k),
  * Eq. DPLR:EGt's reciprocal-space potential, same scaling as the field meshes)
- * into the plan's own workspace as a fourth padded mesh; it costs one more
- * inverse z pass.  Used by the correction network below.  Off by default.
+ * into a padded mesh of the plan's own workspace (allocated by the first call
+ * with on; PPPM_ERR_CUDA if that fails); it costs one more inverse z
+ * transform.  Used by the correction network below.  Off by default.
  */
 int pppm_set_potential(pppm_plan *plan, int on);
+
+/*
+ * pppm_set_dependent_launch -- when on (nonzero, the default), the kernels of
+ * one evaluation are launched with programmatic dependent launch: each may be
+ * scheduled while its predecessor's last blocks run and waits on the device
+ * for the predecessor to complete before touching memory.  That removes the
+ * gaps between kernels of a plan running alone; when other work shares the
+ * GPU concurrently (another stream), the early-scheduled blocks hold SM
+ * resources that work could use, and off may overlap better.  Results are
+ * identical either way.  A graph captured before the change no longer
+ * matches the plan (pppm_graph_launch refuses it).
+ */
+int pppm_set_dependent_launch(pppm_plan *plan, int on);
 
 /*
  * Learned coarse-mesh correction.  A coarse-mesh FP32 PPPM is corrected per

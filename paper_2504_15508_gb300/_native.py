@@ -77,6 +77,7 @@ SIGNATURES = {
     "pppm_batch_status": (cint, [vp]),
     "pppm_batch_destroy": (None, [vp]),
     "pppm_set_potential": (cint, [vp, cint]),
+    "pppm_set_dependent_launch": (cint, [vp, cint]),
     "pppm_corr_create": (cint, [vp, ctypes.POINTER(vp)]),
     "pppm_corr_nparams": (cint, []),
     "pppm_corr_set_weights": (cint, [vp, vp, dbl, dbl]),

@@ -352,7 +352,8 @@ int run_solve(pppm_plan* P, cudaStream_t s, double* energy, double* virial, T* f
         fl.pstride = 1;
     }
     T* out[4] = {fields_out, fields_out + fl.fstride, fields_out + 2 * fl.fstride, fields_out + 3 * fl.fstride};
-    const int nf = (P->potential && fields_out == (T*)P->fields) ? 4 : 3;
+    const int nf = (P->potential && P->phi && fields_out == (T*)P->fields) ? 4 : 3;
+    if (nf == 4) out[3] = (T*)P->phi;  // the potential goes to its own padded mesh
     { PROF(K_FFT_Z_C2R); CK(launch_fft_z_c2r<T>(s, g, P->rad[2], (const C*)P->tw[2], nf, src, mk, out, fl)); }
     return PPPM_OK;
 }
@@ -366,7 +367,7 @@ int run_compute(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_
     P->last = s;
     // the kernels of the sequence overlap their launches (not under per-kernel
     // event timing, whose events must bracket each kernel)
-    PdlScope pdl(!P->prof_on);
+    PdlScope pdl(P->pdl && !P->prof_on);
     // with a two-slot cover table the forward z FFT folds the patches itself
     T* rho = P->cov2 ? (T*)nullptr : (T*)P->rho;
     if ((rc = run_sites_to_patches<T, In>(P, s, pos, q, n, rho, T(1))) != PPPM_OK) return rc;
@@ -674,6 +675,7 @@ void pppm_destroy(pppm_plan* P) {
     dfree(P->sorig);
     dfree(P->swt);
     drop_host_graph(P);
+    dfree(P->phi);
     dfree(P->h_stage);
     if (P->h_tail) cudaFreeHost(P->h_tail);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
@@ -685,8 +687,21 @@ void pppm_destroy(pppm_plan* P) {
 
 int pppm_set_potential(pppm_plan* P, int on) {
     if (!P) return PPPM_ERR_INVALID_ARG;
+    if (on && !P->phi) {
+        CK(cudaSetDevice(P->device));
+        const FieldLayout& fl = P->flayout;
+        int rc = dalloc(&P->phi, P->esz * (size_t)fl.Xp * fl.Yp * fl.Zp);
+        if (rc != PPPM_OK) return rc;
+    }
     ++P->gen;
     P->potential = on != 0;
+    return PPPM_OK;
+}
+
+int pppm_set_dependent_launch(pppm_plan* P, int on) {
+    if (!P) return PPPM_ERR_INVALID_ARG;
+    ++P->gen;
+    P->pdl = on != 0;
     return PPPM_OK;
 }
 

@@ -580,7 +580,10 @@ int refresh_bf16(pppm_corr* C, cudaStream_t s) {
 cudaError_t launch_features(pppm_corr* C, cudaStream_t s, const float* pos, const signed char* types, int64_t n,
                             __nv_bfloat16* feat) {
     pppm_plan* P = C->plan;
-    const float* phi = (const float*)P->fields + 3 * P->flayout.fstride;  // the fourth field
+    const float* phi = (const float*)P->phi;  // padded, one value a point
+    FieldLayout pl = P->flayout;
+    pl.fstride = 0;
+    pl.pstride = 1;
     // every caller runs this right after a solve of the same n sites on the
     // same stream, whose scatter left the tile order (a permutation of 0..n-1)
     // in the plan
@@ -588,7 +591,7 @@ cudaError_t launch_features(pppm_corr* C, cudaStream_t s, const float* pos, cons
     const int blocks = (int)((n + 127) / 128);
 #define PPPM_FEAT(PP)                                                                                      \
     case PP:                                                                                               \
-        k_features<PP><<<blocks, 128, 0, s>>>(P->g, P->flayout, phi, pos, types, perm, (int)n, C->s_in, feat); \
+        k_features<PP><<<blocks, 128, 0, s>>>(P->g, pl, phi, pos, types, perm, (int)n, C->s_in, feat);         \
         break;
     switch (P->order) {
         PPPM_FEAT(3)
@@ -654,11 +657,12 @@ int pppm_corr_create(pppm_plan* coarse, pppm_corr** out) {
     pppm_corr* C = new (std::nothrow) pppm_corr();
     if (!C) return PPPM_ERR_CUDA;
     C->plan = coarse;
-    coarse->potential = true;
     auto fail = [&](int code) {
         pppm_corr_destroy(C);
         return code;
     };
+    const int prc = pppm_set_potential(coarse, 1);
+    if (prc != PPPM_OK) return fail(prc);
     if (cudaMalloc((void**)&C->master, sizeof(float) * NPARAM) != cudaSuccess) return fail(PPPM_ERR_CUDA);
     if (cudaMalloc((void**)&C->m1, sizeof(float) * NPARAM) != cudaSuccess) return fail(PPPM_ERR_CUDA);
     if (cudaMalloc((void**)&C->m2, sizeof(float) * NPARAM) != cudaSuccess) return fail(PPPM_ERR_CUDA);

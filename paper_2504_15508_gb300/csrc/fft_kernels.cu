@@ -707,8 +707,9 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
         }
         return;
     }
-    // padded: the fields of a point are interleaved (E_x, E_y, E_z, phi) and
-    // stored with one vector store; every output row also lands on its
+    // padded: the fields of a point are interleaved (E_x, E_y, E_z, 0) and
+    // stored with one vector store, the potential (a fourth output) goes to
+    // its own padded mesh; every output row also lands on its
     // periodic ghost images, and each row is extended by p - 1 ghost points
     // along z.  One warp per output row, lanes along z.
     const FieldLayout& fl = zo.fl;
@@ -716,6 +717,7 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
     const int zlen = Nz + g.order - 1;
     typedef typename CT<R>::C4 V4;
     V4* out = reinterpret_cast<V4*>(zo.out[0]);
+    R* phi = nf == 4 ? reinterpret_cast<R*>(zo.out[3]) : nullptr;  // padded potential, one value a point
     for (int pr = threadIdx.x >> 5; pr < 2 * np; pr += kFftThreads >> 5) {
         const int p = pr >> 1, half = pr & 1;
         const int r = 2 * (pair0 + p) + half;
@@ -726,10 +728,10 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
         const int Nx = g.N[0];
         const int pxg = px0 + Nx < fl.Xp ? px0 + Nx : (px0 - Nx >= 0 ? px0 - Nx : -1);
         const int pyg = py0 + Ny < fl.Yp ? py0 + Ny : (py0 - Ny >= 0 ? py0 - Ny : -1);
-        V4* o00 = out + ((int64_t)px0 * fl.Yp + py0) * fl.Zp;
-        V4* o10 = pxg >= 0 ? out + ((int64_t)pxg * fl.Yp + py0) * fl.Zp : nullptr;
-        V4* o01 = pyg >= 0 ? out + ((int64_t)px0 * fl.Yp + pyg) * fl.Zp : nullptr;
-        V4* o11 = (pxg >= 0 && pyg >= 0) ? out + ((int64_t)pxg * fl.Yp + pyg) * fl.Zp : nullptr;
+        const int64_t r00 = ((int64_t)px0 * fl.Yp + py0) * fl.Zp;  // first point of each image row
+        const int64_t r10 = pxg >= 0 ? ((int64_t)pxg * fl.Yp + py0) * fl.Zp : -1;
+        const int64_t r01 = pyg >= 0 ? ((int64_t)px0 * fl.Yp + pyg) * fl.Zp : -1;
+        const int64_t r11 = (pxg >= 0 && pyg >= 0) ? ((int64_t)pxg * fl.Yp + pyg) * fl.Zp : -1;
         for (int pz = threadIdx.x & 31; pz < zlen; pz += 32) {
             int zz = pz + kmin;
             zz += zz < 0 ? Nz : 0;
@@ -741,11 +743,17 @@ k_fft_z_c2r(Geo g, Eng eng, ZOut zo, int rows, int pairs) {
                 const C zv = f < nf ? rz[f * np] : CT<R>::mk(R(0), R(0));
                 v[f] = half ? zv.y : zv.x;
             }
-            const V4 w = CT<R>::mk4(v[0], v[1], v[2], v[3]);
-            o00[pz] = w;
-            if (o10) o10[pz] = w;
-            if (o01) o01[pz] = w;
-            if (o11) o11[pz] = w;
+            const V4 w = CT<R>::mk4(v[0], v[1], v[2], R(0));
+            out[r00 + pz] = w;
+            if (r10 >= 0) out[r10 + pz] = w;
+            if (r01 >= 0) out[r01 + pz] = w;
+            if (r11 >= 0) out[r11 + pz] = w;
+            if (phi) {
+                phi[r00 + pz] = v[3];
+                if (r10 >= 0) phi[r10 + pz] = v[3];
+                if (r01 >= 0) phi[r01 + pz] = v[3];
+                if (r11 >= 0) phi[r11 + pz] = v[3];
+            }
         }
     }
 }

@@ -76,9 +76,11 @@ template <> __host__ __device__ __forceinline__ double kfac<double>(const Geo& g
 // pstride = 1).  Padded ("ghosted"): the mesh extended by p - 1 periodic ghost
 // points per axis, so that a tile's stencil patch is one contiguous box
 // (padded index = mesh index - kmin, extents Xp = Nx + p - 1, Yp = Ny + p - 1,
-// Zp = Nz + p - 1), with the four values of a point interleaved as
-// (E_x, E_y, E_z, phi) in 4 consecutive elements (fstride = 1, pstride = 4):
+// Zp = Nz + p - 1), with the values of a point interleaved as
+// (E_x, E_y, E_z, 0) in 4 consecutive elements (fstride = 1, pstride = 4):
 // the force interpolation reads a point's three fields with one 16-byte load.
+// The potential, when produced, has a padded mesh of its own (one value a
+// point).
 struct FieldLayout {
     int padded;
     int Xp, Yp, Zp;

@@ -28,7 +28,9 @@ struct pppm_plan {
     void* cx[3] = {nullptr, nullptr, nullptr};
     void* fields = nullptr;  // padded (ghosted) field meshes, see FieldLayout
     pppm::FieldLayout flayout{};
-    bool potential = false;  // also produce the mesh potential as a 4th padded field
+    bool potential = false;  // also produce the mesh potential (padded, planar: phi)
+    void* phi = nullptr;     // padded potential mesh, Xp x Yp x Zp (allocated on demand)
+    bool pdl = true;         // programmatic dependent launch between the kernels of a solve
     CUtensorMap fmap;        // 4D TMA descriptor of the padded fields
     bool fmap_ok = false;
     void* partial = nullptr;

@@ -80,6 +80,11 @@ class Plan:
             opt.tile = int(tile)
         N.check(self._lib.pppm_set_options(self._h, ctypes.byref(opt)), "pppm_set_options")
 
+    def set_dependent_launch(self, on: bool = True):
+        """Programmatic dependent launch between the kernels of an evaluation
+        (default on; off may overlap better with concurrent work)."""
+        N.check(self._lib.pppm_set_dependent_launch(self._h, int(bool(on))), "pppm_set_dependent_launch")
+
     def reserve(self, n: int):
         N.check(self._lib.pppm_reserve(self._h, int(n)), "pppm_reserve")
 
@@ -213,6 +218,9 @@ class StepGraph:
         if stream is None:
             stream = torch.cuda.Stream(device=pos.device)
         self.stream = stream
+        # the capture's warm-up call uses the plan's workspace: order it after
+        # the caller's work on the current stream
+        stream.wait_stream(torch.cuda.current_stream(pos.device))
         h = ctypes.c_void_p()
         fn = L.pppm_graph_create_f32 if pos.dtype == torch.float32 else L.pppm_graph_create
         N.check(fn(plan.handle, _stream(stream), _ptr(pos), _ptr(q), n, _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),

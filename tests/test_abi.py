@@ -75,6 +75,7 @@ def test_corrector_calls_validate_arguments(pppm_lib):
     assert L.pppm_corr_create(None, ctypes.byref(h)) == N.PPPM_ERR_INVALID_ARG
     assert L.pppm_corr_create(None, None) == N.PPPM_ERR_INVALID_ARG
     assert L.pppm_set_potential(None, 1) == N.PPPM_ERR_INVALID_ARG
+    assert L.pppm_set_dependent_launch(None, 1) == N.PPPM_ERR_INVALID_ARG
     assert L.pppm_corr_set_weights(None, None, 1.0, 1.0) == N.PPPM_ERR_INVALID_ARG
     assert L.pppm_corr_get_weights(None, None, None, None) == N.PPPM_ERR_INVALID_ARG
     assert L.pppm_corr_features(None, None, None, None, None, 0, None, None) == N.PPPM_ERR_INVALID_ARG

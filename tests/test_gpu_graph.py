@@ -133,3 +133,26 @@ def test_host_call_site_count_changes(cuda_device):
         e0, f0, v0 = plan.compute(torch.tensor(p_, device="cuda"), torch.tensor(q_, device="cuda"))
         torch.cuda.synchronize()
         assert e == e0.item() and np.array_equal(f, f0.cpu().numpy()) and np.array_equal(v, v0.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_dependent_launch_switch(cuda_device, prec):
+    """Programmatic dependent launch between the kernels changes no result
+    bit; switching it invalidates a graph captured before."""
+    from paper_2504_15508_gb300 import _native as N
+    plan, pos, q = _setup("water4096", prec)
+    e1, f1, v1 = (t.clone() for t in plan.compute(pos, q))
+    g = plan.graph(pos, q)
+    plan.set_dependent_launch(False)
+    e0, f0, v0 = (t.clone() for t in plan.compute(pos, q))
+    torch.cuda.synchronize()
+    assert torch.equal(f0, f1) and torch.equal(e0, e1) and torch.equal(v0, v1)
+    with pytest.raises(N.PPPMError):
+        g.launch(pos, q)
+    g.close()
+    g = plan.graph(pos, q)
+    e2, f2, v2 = (t.clone() for t in g.launch(pos, q, stream=torch.cuda.current_stream()))
+    torch.cuda.synchronize()
+    assert torch.equal(f2, f1) and torch.equal(e2, e1)
+    g.close()
+    plan.set_dependent_launch(True)
