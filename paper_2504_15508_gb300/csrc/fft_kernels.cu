@@ -8,7 +8,7 @@
 // with a self-sorting (Stockham) mixed-radix FFT between two shared buffers,
 // and writes them back:
 //   z forward   real rows, two per complex FFT (a + i b), unpacked to two half rows;
-//   y, x        strided lines, a bundle of B adjacent kz columns per block;
+//   y, x        strided lines, B consecutive (outer, kz) lines per block;
 //   x + G       forward x FFT, multiply by the influence function with the
 //               energy/virial reduction, and the inverse x FFTs of G rho and
 //               -i kx G rho in one block (Poisson-ik, Section 3.1 of the paper);
@@ -385,7 +385,7 @@ cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, 
 
 // ------------------------------------------------------------------ x + influence
 //
-// Per block: one y index and B adjacent kz columns, lines along x.
+// Per block: B consecutive lines along x, numbered y Hz + kz.
 //   1. forward FFT along x  -> rho_hat(k) up to the 1/h^3 factor;
 //   2. per mode: G, the energy term e = w G |rho_hat|^2 V/(2 N^2) and the virial
 //      terms e (delta_ab - 2 (1 + k^2/(4 beta^2)) k_a k_b / k^2), accumulated per
