@@ -75,7 +75,8 @@ def test_influence_table(cuda_device, pppm_lib, mesh):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("mesh", [(32, 32, 32), (30, 36, 40), (27, 25, 45), (12, 15, 16), (160, 8, 6)])
+@pytest.mark.parametrize("mesh", [(32, 32, 32), (30, 36, 40), (27, 25, 45), (12, 15, 16), (160, 8, 6),
+                                  (64, 128, 32), (128, 160, 64)])
 def test_fft_r2c_c2r(cuda_device, pppm_lib, prec, mesh):
     plan = _plan((10.0, 11.0, 12.0), mesh, 5, 0.4, precision=prec)
     rng = np.random.default_rng(sum(mesh))
@@ -148,7 +149,8 @@ def test_water72192_fp32(cuda_device, pppm_lib, mesh):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["rect_odd", "order3", "order4", "order7", "tiny_mesh", "tile4", "coarse"])
+@pytest.mark.parametrize("case", ["rect_odd", "order3", "order4", "order7", "tiny_mesh", "tile4", "coarse",
+                                  "mixed_lengths"])
 def test_geometries(cuda_device, pppm_lib, prec, case):
     box = np.array([9.0, 10.5, 12.0])
     mesh, order, beta, n, tile = (30, 36, 40), 5, 0.5, 300, 0
@@ -166,6 +168,10 @@ def test_geometries(cuda_device, pppm_lib, prec, case):
         tile = 4
     elif case == "coarse":
         mesh, n = (8, 9, 10), 3000  # dense: many sites per tile
+    elif case == "mixed_lengths":
+        # three different compile-time FFT lengths: the x and y passes number
+        # their lines over different outer counts (Ny Hz vs Nx Hz)
+        mesh, n = (64, 128, 32), 2000
     pos, q = _random_neutral(n, box, seed=11)
     tp, tq, pos_r, q_r = _sites(pos, q, prec, cuda_device)
     plan = _plan(box, mesh, order, beta, precision=prec, tile=tile)
