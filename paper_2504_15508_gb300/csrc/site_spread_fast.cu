@@ -68,15 +68,23 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
     const bool ranked = c > 1 && c <= kFastCap;
     if (ranked) {
         for (int i = lane; i < c; i += 32) W.u.keys[i] = __ldg(&sorig[s0 + i]);
+        // pad to a multiple of 4 with keys larger than every site index
+        if (lane < ((c + 3) & ~3) - c) W.u.keys[c + lane] = INT_MAX;
     }
     for (int i = lane; i < PSIZE; i += 32) W.pt[i] = T(0);
     __syncwarp();
     if (ranked) {
         // rank of item i = number of items with a smaller original index
+        // (keys compared four at a time, from 16-byte broadcast loads)
+        const int c4 = (c + 3) >> 2;
+        const int4* k4 = reinterpret_cast<const int4*>(W.u.keys);
         for (int i = lane; i < c; i += 32) {
             const int ki = W.u.keys[i];
             int r = 0;
-            for (int j = 0; j < c; ++j) r += W.u.keys[j] < ki;
+            for (int j = 0; j < c4; ++j) {
+                const int4 kk = k4[j];
+                r += (kk.x < ki) + (kk.y < ki) + (kk.z < ki) + (kk.w < ki);
+            }
             W.perm[r] = (short)i;
         }
     }
