@@ -383,6 +383,11 @@ cudaError_t launch_fft_bundle(cudaStream_t s, const Geo& g, int axis, int sign, 
     });
 }
 
+// a / b for the virial coefficient: in FP32 the 2-ulp hardware quotient (the
+// coefficient enters sums that are accurate to ~1e-7 anyway), in FP64 exact
+__device__ __forceinline__ float div_approx(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_approx(double a, double b) { return a / b; }
+
 // ------------------------------------------------------------------ x + influence
 //
 // Per block: B consecutive lines along x, numbered y Hz + kz.
@@ -474,11 +479,11 @@ k_fft_x_influence(Geo g, LineBlocks lb, Eng eng, const R* __restrict__ G, R beta
         const bool nyq_x = (Nx % 2 == 0) && (t == Nx / 2);
         R gk;
         if constexpr (Eng::kLen > 0) {
-            // t = (threadIdx.x >> 4) + i (kFftThreads / 16): pick gpre[i] by selects
-            const int i = (t - (threadIdx.x >> 4)) / (kFftThreads / 16);
+            // the rows come in the order their values were fetched: take the
+            // first and move the rest down
             gk = gpre[0];
 #pragma unroll
-            for (int q = 1; q < NG; ++q) gk = (i == q) ? gpre[q] : gk;
+            for (int q = 0; q + 1 < NG; ++q) gpre[q] = gpre[q + 1];
         } else {
             gk = G[(int64_t)t * es + f0 + l];
         }
@@ -488,7 +493,7 @@ k_fft_x_influence(Geo g, LineBlocks lb, Eng eng, const R* __restrict__ G, R beta
         const R k2 = kx * kx + ky * ky + kzv * kzv;
         if (k2 > R(0)) {
             const R e = w * e_scale * gk * (v.x * v.x + v.y * v.y);
-            const R c = R(2) * (R(1) + k2 * inv4b2) / k2;
+            const R c = div_approx(R(2) * (R(1) + k2 * inv4b2), k2);
             const R fxy = (plane1 || (nyq_x == nyq_y)) ? R(1) : R(0);
             const R fxz = (plane1 || !nyq_x) ? R(1) : R(0);
             const R fyz = (plane1 || !nyq_y) ? R(1) : R(0);
