@@ -150,7 +150,7 @@ def test_water72192_fp32(cuda_device, pppm_lib, mesh):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", ["rect_odd", "order3", "order4", "order7", "tiny_mesh", "tile4", "coarse",
-                                  "mixed_lengths"])
+                                  "mixed_lengths", "box_beyond_mesh"])
 def test_geometries(cuda_device, pppm_lib, prec, case):
     box = np.array([9.0, 10.5, 12.0])
     mesh, order, beta, n, tile = (30, 36, 40), 5, 0.5, 300, 0
@@ -168,6 +168,10 @@ def test_geometries(cuda_device, pppm_lib, prec, case):
         tile = 4
     elif case == "coarse":
         mesh, n = (8, 9, 10), 3000  # dense: many sites per tile
+    elif case == "box_beyond_mesh":
+        # 8-cell tiles on an 8^3 mesh: the padded z extent (12 points) is
+        # shorter than the field box's odd z pitch (13)
+        mesh, n, tile = (8, 8, 8), 100, 8
     elif case == "mixed_lengths":
         # three different compile-time FFT lengths: the x and y passes number
         # their lines over different outer counts (Ny Hz vs Nx Hz)
