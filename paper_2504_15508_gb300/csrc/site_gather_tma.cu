@@ -1,5 +1,6 @@
-// Force interpolation with TMA-staged field patches (padded field meshes,
-// compile-time tile edge and order, precomputed per-site weights).
+// Force interpolation with TMA-staged field patches (padded field meshes with
+// the three fields of a point interleaved in 16 bytes, compile-time tile edge
+// and order, precomputed per-site weights).
 #include <climits>
 
 #include <cuda.h>
