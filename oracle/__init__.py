@@ -17,4 +17,7 @@ Contents:
   mlp.py              FP64 features, forward/backward and Adam of the
                       coarse-mesh correction network.
   wc_fold.py          FP64 fold of WC forces onto atoms (Eq. DPLR:F_final).
+  dft_quant.py        the DFT with int32-quantised per-node partial sums of
+                      the paper's hardware-offloaded FFT, and the PPPM that
+                      uses it for every transform.
 """

@@ -142,6 +142,9 @@ def smooth_at_least(x: float) -> int:
 
 WORKLOADS = {
     "water64": dict(n_mol=64, L=12.42, mesh=(32, 32, 32), order=5, beta=0.4, seed=1),
+    # 128 waters in a ~16 A box, the system of the paper's accuracy table; its
+    # int32 runs use the meshes 8x12x8, 10x15x10 and 12x18x12
+    "water128": dict(n_mol=128, L=15.64, mesh=(12, 18, 12), order=5, beta=0.4, seed=4),
     "water4096": dict(n_mol=4096, L=49.7, mesh=(64, 64, 64), order=5, beta=0.4, seed=2),
     "water72192_m128": dict(n_mol=72192, L=129.3, mesh=(128, 128, 128), order=5, beta=0.4, seed=3),
     "water72192_m160": dict(n_mol=72192, L=129.3, mesh=(160, 160, 160), order=5, beta=0.4, seed=3),
