@@ -70,16 +70,84 @@ def test_linear_axis_order_and_roundtrip():
     assert np.max(np.abs(b / 12 - x)) <= 2 * 3 * 0.5 / SCALE + 1e-12
 
 
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.mark.parametrize("spectrum", ["half", "full"])
 @pytest.mark.parametrize("mesh,g", [((8, 12, 8), 4), ((10, 15, 10), 5), ((12, 18, 12), 6)])
-def test_quantised_pppm_keeps_the_accuracy(mesh, g):
+def test_quantised_pppm_keeps_the_accuracy(mesh, g, spectrum):
     """The paper's int32 runs on 128 waters: quantising every transform at
     10^7 changes the forces by far less than the discretisation error, and
     nothing saturates."""
     wb, w = make_workload("water128")
     o = OraclePPPM(wb.box, mesh, w["order"], w["beta"])
     ref = o.compute(wb.pos, wb.q)
-    r = pppm_quantized(o, wb.pos, wb.q, g)
+    r = pppm_quantized(o, wb.pos, wb.q, g, spectrum=spectrum)
     assert not r["saturated"]
-    d = np.linalg.norm(r["forces"] - ref["forces"]) / np.linalg.norm(ref["forces"])
+    d = _rel(r["forces"], ref["forces"])
     assert d < 1e-5, d
     assert abs(r["energy"] - ref["energy"]) / abs(ref["energy"]) < 1e-6
+    assert _rel(r["virial"], ref["virial"]) < 1e-5
+
+
+@pytest.mark.parametrize("spectrum", ["half", "full"])
+@pytest.mark.parametrize("mesh", [(12, 18, 12), (10, 15, 9), (9, 12, 16)])
+def test_with_no_axis_quantised_it_is_the_pppm(mesh, spectrum):
+    """Exact transforms everywhere: both readings reproduce oracle.pppm, which
+    pins the half-spectrum bookkeeping (the Hermitian extension along z, the
+    mirrored spectrum for the energy and virial, odd and even meshes)."""
+    wb, w = make_workload("water128")
+    o = OraclePPPM(wb.box, mesh, w["order"], w["beta"])
+    ref = o.compute(wb.pos, wb.q)
+    r = pppm_quantized(o, wb.pos, wb.q, 3, axes=(), spectrum=spectrum)
+    assert _rel(r["forces"], ref["forces"]) < 1e-13
+    assert abs(r["energy"] - ref["energy"]) <= 1e-13 * abs(ref["energy"])
+    assert _rel(r["virial"], ref["virial"]) < 1e-13
+
+
+def test_quantised_backward_passes_break_the_mirror_symmetry():
+    """Why the real/complex reading matters: a backward pass splits the
+    frequency index into nodes, and k -> -k maps that split onto another, so
+    the quantised backward DFT of a spectrum with X(-ky, -kz) = conj X(ky, kz)
+    no longer has B(y, -kz) = conj B(y, kz); the exact one does."""
+    rng = np.random.default_rng(11)
+    Ny, Nz = 12, 8
+    X = rng.uniform(-1, 1, (Ny, Nz)) + 1j * rng.uniform(-1, 1, (Ny, Nz))
+    X = 0.5 * (X + np.conj(np.roll(np.flip(X, axis=(0, 1)), 1, axis=(0, 1))))   # Hermitian in both indices
+    def asym(B):
+        return np.max(np.abs(np.roll(np.flip(B, axis=1), 1, axis=1) - np.conj(B)))
+    exact = np.fft.ifft(X, axis=0) * Ny
+    quant, _ = dft_quantized(X, 0, 4, +1, scale=1e4)
+    assert asym(exact) < 1e-13
+    assert asym(quant) > 0.5e-4
+
+
+def test_the_two_readings_differ_at_a_coarse_scale():
+    """At 10^2 the quantisation error is large and the two readings give
+    different forces; at 10^7 both are within the FP32-level bar of the PPPM."""
+    wb, w = make_workload("water128")
+    o = OraclePPPM(wb.box, (12, 18, 12), w["order"], w["beta"])
+    ref = o.compute(wb.pos, wb.q)
+    half = pppm_quantized(o, wb.pos, wb.q, 6, scale=1e2)
+    full = pppm_quantized(o, wb.pos, wb.q, 6, scale=1e2, spectrum="full")
+    effect = _rel(half["forces"], ref["forces"])
+    assert effect > 0.05 and _rel(full["forces"], half["forces"]) > 0.2 * effect
+    # energy: the forward passes preserve the mirror symmetry (they split the
+    # position index), so both readings have the same spectrum up to ties
+    assert abs(full["energy"] - half["energy"]) < 0.2 * abs(half["energy"] - ref["energy"])
+
+
+def test_only_the_chosen_axes_are_quantised():
+    """axes=(1,): the y transforms alone are quantised; the error is then
+    bounded by that axis' passes alone (smaller than all three)."""
+    wb, w = make_workload("water128")
+    o = OraclePPPM(wb.box, (12, 18, 12), w["order"], w["beta"])
+    ref = o.compute(wb.pos, wb.q)
+    y_only = _rel(pppm_quantized(o, wb.pos, wb.q, 9, scale=1e3, axes=(1,))["forces"], ref["forces"])
+    all3 = _rel(pppm_quantized(o, wb.pos, wb.q, 6, scale=1e3)["forces"], ref["forces"])
+    assert 0 < y_only < all3
+    with pytest.raises(ValueError):
+        pppm_quantized(o, wb.pos, wb.q, 9)          # 9 does not divide 12
+    with pytest.raises(ValueError):
+        pppm_quantized(o, wb.pos, wb.q, 6, spectrum="other")
