@@ -195,6 +195,24 @@ int pppm_fields(pppm_plan *plan, void *stream, const double *pos, const double *
  *                      meshes (X = F_N x per axis, as in the paper's DFT
  *                      formulation of its distributed FFT, Section
  *                      "Hardware-offloaded 3D FFT").
+ * pppm_batch_set_quantized
+ *                      group > 0 (1..18; default 0 = off): every line whose
+ *                      length is <= 18 and a multiple of group is transformed
+ *                      as the paper's int32-quantised distributed DFT
+ *                      (Section "Hardware-offloaded 3D FFT", its quantisation
+ *                      panel): the line is split into nodes of group
+ *                      consecutive points, each node's partial sum for every
+ *                      output is computed in FP32, multiplied by scale (the
+ *                      paper's 10^7; 1 .. 1e15), rounded to the nearest
+ *                      integer and clamped to int32, and the nodes' integers
+ *                      are added exactly before dividing by scale.  What is
+ *                      transformed: the charge per mesh point (sum of q W)
+ *                      forward, the field spectra divided by N h^3 backward.
+ *                      It takes precedence over pppm_batch_set_dft.  An
+ *                      accuracy ablation, not a fast path, built for order 5
+ *                      only (another order: PPPM_ERR_INVALID_ARG): a clamped
+ *                      partial sum makes pppm_batch_status return
+ *                      PPPM_ERR_TOO_LARGE.
  * pppm_batch_meshes    copy the nbox x 3 meshes in use to a host array.
  * pppm_batch_tile      tile edge in use (0 before the first call).
  */
@@ -203,6 +221,7 @@ int pppm_batch_create(int nbox, const double *boxes, const int *meshes, int orde
                       pppm_batch **out);
 int pppm_batch_set(pppm_batch *batch, double prefactor, int tile, long long spin_limit);
 int pppm_batch_set_dft(pppm_batch *batch, int max_len);
+int pppm_batch_set_quantized(pppm_batch *batch, int group, double scale);
 int pppm_batch_meshes(const pppm_batch *batch, int *meshes);
 int pppm_batch_tile(const pppm_batch *batch);
 int pppm_compute_batched(pppm_batch *batch, void *stream, const float *pos, const float *q,

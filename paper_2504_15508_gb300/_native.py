@@ -71,6 +71,7 @@ SIGNATURES = {
     "pppm_batch_create": (cint, [cint, ctypes.POINTER(dbl), ctypes.POINTER(cint), cint, dbl, ctypes.POINTER(vp)]),
     "pppm_batch_set": (cint, [vp, dbl, cint, ctypes.c_longlong]),
     "pppm_batch_set_dft": (cint, [vp, cint]),
+    "pppm_batch_set_quantized": (cint, [vp, cint, dbl]),
     "pppm_batch_meshes": (cint, [vp, ctypes.POINTER(cint)]),
     "pppm_batch_tile": (cint, [vp]),
     "pppm_compute_batched": (cint, [vp, vp, vp, vp, vp, vp, vp, vp]),

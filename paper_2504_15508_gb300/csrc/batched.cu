@@ -92,6 +92,8 @@ struct Bufs {
     int* status;
     double prefactor;
     int dft_max;  // lines up to this length take the tensor-core DFT (0: all take the FFT)
+    int qgroup;     // node size of the int32-quantised DFT (0: off)
+    double qscale;  // its scale
 };
 
 // ------------------------------------------------------------------ helpers
@@ -371,7 +373,58 @@ __device__ __forceinline__ float fold_point_b(const BoxDesc& D, const Bufs& B, c
     return sum;
 }
 
+// With the quantised DFT every transform follows the paper's chain literally:
+// each real z line is its own complex line (no two-for-one packing, whose
+// quantised partial sums would mix two lines), and each of the three ik
+// spectra -i k_d phi_hat is formed before the first inverse pass (the default
+// chain multiplies by k_y and k_z after the x pass, which is the same only
+// in exact arithmetic).
+// node size of the quantised DFT along axis d of this box: lines of at most
+// 18 points that the node size divides; 0 = not quantised
+__device__ __forceinline__ int qg(const BoxDesc& D, const Bufs& B, int d) {
+    const int L = D.rad[d].L, g = B.qgroup;
+    return (g > 0 && L <= kDftTcMax && L % g == 0) ? g : 0;
+}
+
+__device__ __forceinline__ bool quant_chain(const BoxDesc& D, const Bufs& B) {
+    return (qg(D, B, 0) | qg(D, B, 1) | qg(D, B, 2)) != 0;
+}
+
+__device__ void st_zr2c_quant(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
+    const Geo& g = D.g;
+    const int Nz = g.N[2], Hz = g.Hz, rows = g.N[0] * g.N[1];
+    float2* a = reinterpret_cast<float2*>(smem);
+    float2* b = a + kZPairs * Nz;
+    const int pair0 = idx * kZPairs;
+    const int np = min(kZPairs, (rows + 1) / 2 - pair0);
+    float2* out = B.cx0 + D.c0;
+    for (int half = 0; half < 2; ++half) {
+        for (int p = threadIdx.x >> 5; p < np; p += kWarps) {
+            const int r = 2 * (pair0 + p) + half;
+            if (r < rows) {
+                const int x = r / g.N[1], y = r - x * g.N[1];
+                const Cover4 cx = load_cover(B, D, 0, x), cy = load_cover(B, D, 1, y);
+                for (int t = threadIdx.x & 31; t < Nz; t += 32)
+                    a[p * Nz + t] = make_float2(fold_point_b(D, B, cx, cy, t), 0.f);
+            } else {
+                for (int t = threadIdx.x & 31; t < Nz; t += 32) a[p * Nz + t] = make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        const float2* res = dft_quant(a, b, np, Nz, 1, Nz, qg(D, B, 2), B.qscale, B.tw + D.tw0[2], -1.f, B.status);
+        for (int p = threadIdx.x >> 5; p < np; p += kWarps) {
+            const int r = 2 * (pair0 + p) + half;
+            if (r < rows)
+                for (int k = threadIdx.x & 31; k < Hz; k += 32) out[(long long)r * Hz + k] = res[p * Nz + k];
+        }
+        __syncthreads();
+    }
+}
+
+template <bool Q>
 __device__ void st_zr2c(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
+    if constexpr (Q)
+        if (qg(D, B, 2) > 0) return st_zr2c_quant(D, idx, B, smem);
     const Geo& g = D.g;
     const int Nz = g.N[2], Hz = g.Hz, rows = g.N[0] * g.N[1];
     float2* a = reinterpret_cast<float2*>(smem);
@@ -392,7 +445,7 @@ __device__ void st_zr2c(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
             a[p * Nz + t] = make_float2(fold_point_b(D, B, cx0, cy0, t), fold_point_b(D, B, cx1, cy1, t));
     }
     __syncthreads();
-    float2* res = line_transform(a, b, np, Nz, 1, D.rad[2], B.tw + D.tw0[2], -1.f, false, B.dft_max);
+    float2* res = line_transform<Q>(a, b, np, Nz, 1, D.rad[2], B.tw + D.tw0[2], -1.f, false, B.dft_max, qg(D, B, 2), B.qscale, B.status);
     float2* out = B.cx0 + D.c0;
     for (int p = threadIdx.x >> 5; p < np; p += kWarps) {
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
@@ -407,6 +460,7 @@ __device__ void st_zr2c(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
 }
 
 // lines along y of the complex spectrum (outer index x), in place
+template <bool Q>
 __device__ void st_yfwd(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
     const Geo& g = D.g;
     const int Hz = g.Hz, L = g.N[1], Bw = D.bd.B;
@@ -420,7 +474,7 @@ __device__ void st_yfwd(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
         a[t * Bw + l] = ldcg(&base[(long long)t * Hz + l]);
     }
     __syncthreads();
-    float2* res = line_transform(a, b, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], -1.f, true, B.dft_max);
+    float2* res = line_transform<Q>(a, b, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], -1.f, true, B.dft_max, qg(D, B, 1), B.qscale, B.status);
     for (int i = threadIdx.x; i < L * nl; i += kThreads) {
         const int t = i / nl, l = i - t * nl;
         base[(long long)t * Hz + l] = res[t * Bw + l];
@@ -436,6 +490,7 @@ __device__ __forceinline__ void tsum_pair(float& h, float& l, float h2, float l2
 
 // x FFT, influence multiply with energy/virial, inverse x FFTs; the last item
 // of a box sums that box's partials (compensated FP32, FP64 final)
+template <bool Q>
 __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsigned char* smem) {
     const Geo& g = D.g;
     const int Nx = g.N[0], Ny = g.N[1], Nz = g.N[2], Hz = g.Hz, Bw = D.bd.B;
@@ -453,7 +508,7 @@ __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsig
         a0[t * Bw + l] = ldcg(&base[t * es + l]);
     }
     __syncthreads();
-    float2* rh = line_transform(a0, a1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], -1.f, true, B.dft_max);
+    float2* rh = line_transform<Q>(a0, a1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], -1.f, true, B.dft_max, qg(D, B, 0), B.qscale, B.status);
     float2* pbuf = (rh == a0) ? a1 : a0;
     const int my = y <= Ny / 2 ? y : y - Ny;
     const float ky = g.kfac_f[1] * my;
@@ -490,13 +545,41 @@ __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsig
         b0[t * Bw + l] = make_float2(kxd * Pv.y, -kxd * Pv.x);
     }
     __syncthreads();
-    float2* rA = line_transform(pbuf, rh, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max);
-    float2* rB = line_transform(b0, b1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max);
-    float2* obx = B.cx1 + D.c0 + (long long)y * Hz + kz0;
-    for (int i = threadIdx.x; i < Nx * nl; i += kThreads) {
-        const int t = i / nl, l = i - t * nl;
-        base[t * es + l] = rA[t * Bw + l];
-        obx[t * es + l] = rB[t * Bw + l];
+    bool chain = false;
+    if constexpr (Q) chain = quant_chain(D, B);
+    if (chain) {
+        float2* obx = B.cx1 + D.c0 + (long long)y * Hz + kz0;
+        // x inverses of -i k_x P (-> cx1), -i k_y P (-> cx2) and -i k_z P (-> cx0)
+        float2* oby = B.cx2 + D.c0 + (long long)y * Hz + kz0;
+        const float kyd = nyq_y ? 0.f : ky;
+        for (int d = 0; d < 3; ++d) {
+            if (d > 0) {
+                for (int i = threadIdx.x; i < Nx * nl; i += kThreads) {
+                    const int t = i / nl, l = i - t * nl, kz = kz0 + l;
+                    const float kd = d == 1 ? kyd : (((Nz % 2 == 0) && (kz == Nz / 2)) ? 0.f : g.kfac_f[2] * kz);
+                    const float2 Pv = pbuf[t * Bw + l];
+                    b0[t * Bw + l] = make_float2(kd * Pv.y, -kd * Pv.x);
+                }
+                __syncthreads();
+            }
+            const float2* r = line_transform<Q>(b0, b1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max,
+                                                qg(D, B, 0), B.qscale, B.status);
+            float2* o = d == 0 ? obx : (d == 1 ? oby : base);
+            for (int i = threadIdx.x; i < Nx * nl; i += kThreads) {
+                const int t = i / nl, l = i - t * nl;
+                o[t * es + l] = r[t * Bw + l];
+            }
+            __syncthreads();
+        }
+    } else {
+        float2* rA = line_transform<Q>(pbuf, rh, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max, qg(D, B, 0), B.qscale, B.status);
+        float2* rB = line_transform<Q>(b0, b1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max, qg(D, B, 0), B.qscale, B.status);
+        float2* obx = B.cx1 + D.c0 + (long long)y * Hz + kz0;
+        for (int i = threadIdx.x; i < Nx * nl; i += kThreads) {
+            const int t = i / nl, l = i - t * nl;
+            base[t * es + l] = rA[t * Bw + l];
+            obx[t * es + l] = rB[t * Bw + l];
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -538,6 +621,7 @@ __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsig
     }
 }
 
+template <bool Q>
 __device__ void st_yinv(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
     const Geo& g = D.g;
     const int Ny = g.N[1], Hz = g.Hz, Bw = D.bd.B;
@@ -552,13 +636,16 @@ __device__ void st_yinv(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
         const int my = t <= Ny / 2 ? t : t - Ny;
         const float kyd = ((Ny % 2 == 0) && (t == Ny / 2)) ? 0.f : g.kfac_f[1] * my;
         buf[t * Bw + l] = va;
-        buf[2 * sz + t * Bw + l] = make_float2(kyd * va.y, -kyd * va.x);
+        bool chain = false;
+        if constexpr (Q) chain = quant_chain(D, B);
+        // the chain mode formed -i k_y P before the x pass, in cx2
+        buf[2 * sz + t * Bw + l] = chain ? ldcg(&B.cx2[off + (long long)t * Hz + l]) : make_float2(kyd * va.y, -kyd * va.x);
         buf[4 * sz + t * Bw + l] = ldcg(&B.cx1[off + (long long)t * Hz + l]);
     }
     __syncthreads();
-    float2* rC = line_transform(buf, buf + sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max);
-    float2* rD = line_transform(buf + 2 * sz, buf + 3 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max);
-    float2* rE = line_transform(buf + 4 * sz, buf + 5 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max);
+    float2* rC = line_transform<Q>(buf, buf + sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max, qg(D, B, 1), B.qscale, B.status);
+    float2* rD = line_transform<Q>(buf + 2 * sz, buf + 3 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max, qg(D, B, 1), B.qscale, B.status);
+    float2* rE = line_transform<Q>(buf + 4 * sz, buf + 5 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max, qg(D, B, 1), B.qscale, B.status);
     for (int i = threadIdx.x; i < Ny * nl; i += kThreads) {
         const int t = i / nl, l = i - t * nl;
         B.cx0[off + (long long)t * Hz + l] = rC[t * Bw + l];
@@ -568,7 +655,74 @@ __device__ void st_yinv(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
 }
 
 // z inverse of (Ex', D, -i kz' C) -> E_x, E_y, E_z into the padded field layout
+// one z line of a field, written into the padded layout with its ghost images
+__device__ __forceinline__ void store_field_row(const BoxDesc& D, const Bufs& B, int f, int r, const float2* line,
+                                                bool imag) {
+    const Geo& g = D.g;
+    const FieldLayout& fl = D.fl;
+    const int Nz = g.N[2], Ny = g.N[1], Nx = g.N[0];
+    const int kmin = g.kmin, zlen = Nz + g.order - 1;
+    float* out = B.fields + D.f0 + f * fl.fstride;
+    const int x = r / Ny, y = r - x * Ny;
+    const int px0 = x - kmin, py0 = y - kmin;
+    const int pxg = px0 + Nx < fl.Xp ? px0 + Nx : (px0 - Nx >= 0 ? px0 - Nx : -1);
+    const int pyg = py0 + Ny < fl.Yp ? py0 + Ny : (py0 - Ny >= 0 ? py0 - Ny : -1);
+    float* o00 = out + ((long long)px0 * fl.Yp + py0) * fl.Zp;
+    float* o10 = pxg >= 0 ? out + ((long long)pxg * fl.Yp + py0) * fl.Zp : nullptr;
+    float* o01 = pyg >= 0 ? out + ((long long)px0 * fl.Yp + pyg) * fl.Zp : nullptr;
+    float* o11 = (pxg >= 0 && pyg >= 0) ? out + ((long long)pxg * fl.Yp + pyg) * fl.Zp : nullptr;
+    for (int pz = threadIdx.x & 31; pz < zlen; pz += 32) {
+        int zz = pz + kmin;
+        zz += zz < 0 ? Nz : 0;
+        zz -= zz >= Nz ? Nz : 0;
+        const float2 zv = line[zz];
+        const float v = imag ? zv.y : zv.x;
+        o00[pz] = v;
+        if (o10) o10[pz] = v;
+        if (o01) o01[pz] = v;
+        if (o11) o11[pz] = v;
+    }
+}
+
+// quantised z inverse: each row's Hermitian line transformed on its own
+// (fields already multiplied by -i k_d), real part kept
+__device__ void st_zc2r_quant(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
+    const Geo& g = D.g;
+    const int Nz = g.N[2], Hz = g.Hz, rows = g.N[0] * g.N[1];
+    const int pair0 = idx * kZPairs;
+    const int np = min(kZPairs, (rows + 1) / 2 - pair0);
+    const int nlines = 3 * np;
+    float2* a = reinterpret_cast<float2*>(smem);
+    float2* b = a + 3 * kZPairs * Nz;
+    const float2* srcs[3] = {B.cx1 + D.c0, B.cx2 + D.c0, B.cx0 + D.c0};
+    for (int half = 0; half < 2; ++half) {
+        for (int line = threadIdx.x >> 5; line < nlines; line += kWarps) {
+            const int f = line / np, p = line - f * np;
+            const int r = 2 * (pair0 + p) + half;
+            for (int t = threadIdx.x & 31; t < Nz; t += 32) {
+                const int kk = t < Hz ? t : Nz - t;
+                float2 h = r < rows ? ldcg(&srcs[f][(long long)r * Hz + kk]) : make_float2(0.f, 0.f);
+                if (t >= Hz) h.y = -h.y;
+                a[line * Nz + t] = h;
+            }
+        }
+        __syncthreads();
+        const float2* res = dft_quant(a, b, nlines, Nz, 1, Nz, qg(D, B, 2), B.qscale, B.tw + D.tw0[2], 1.f, B.status);
+        for (int line = threadIdx.x >> 5; line < nlines; line += kWarps) {
+            const int f = line / np, p = line - f * np;
+            const int r = 2 * (pair0 + p) + half;
+            if (r < rows) store_field_row(D, B, f, r, res + line * Nz, false);
+        }
+        __syncthreads();
+    }
+}
+
+template <bool Q>
 __device__ void st_zc2r(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
+    if constexpr (Q)
+        if (qg(D, B, 2) > 0) return st_zc2r_quant(D, idx, B, smem);
+    bool chain = false;
+    if constexpr (Q) chain = quant_chain(D, B);
     const Geo& g = D.g;
     const int Nz = g.N[2], Hz = g.Hz, rows = g.N[0] * g.N[1], Ny = g.N[1], Nx = g.N[0];
     const int pair0 = idx * kZPairs;
@@ -586,7 +740,7 @@ __device__ void st_zc2r(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
             const int kk = t < Hz ? t : Nz - t;
             float2 h0 = ldcg(&src[(long long)r0 * Hz + kk]);
             float2 h1 = r1 < rows ? ldcg(&src[(long long)r1 * Hz + kk]) : make_float2(0.f, 0.f);
-            if (f == 2) {
+            if (f == 2 && !chain) {
                 const float kzd = (even && kk == Nz / 2) ? 0.f : g.kfac_f[2] * kk;
                 h0 = make_float2(kzd * h0.y, -kzd * h0.x);
                 h1 = make_float2(kzd * h1.y, -kzd * h1.x);
@@ -597,7 +751,7 @@ __device__ void st_zc2r(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
         }
     }
     __syncthreads();
-    float2* res = line_transform(a, b, nlines, Nz, 1, D.rad[2], B.tw + D.tw0[2], 1.f, false, B.dft_max);
+    float2* res = line_transform<Q>(a, b, nlines, Nz, 1, D.rad[2], B.tw + D.tw0[2], 1.f, false, B.dft_max, qg(D, B, 2), B.qscale, B.status);
     const FieldLayout& fl = D.fl;
     const int kmin = g.kmin, zlen = Nz + g.order - 1;
     for (int line = threadIdx.x >> 5; line < nlines; line += kWarps) {
@@ -744,7 +898,7 @@ __device__ void st_gather(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
 }
 
 // ------------------------------------------------------------------ the persistent kernel
-template <int P, int TILE>
+template <int P, int TILE, bool Q>
 __global__ void __launch_bounds__(kThreads, 2)  // two resident blocks per SM: 16 warps to hide latency
 k_batched(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, int nitems, unsigned int* head,
           int* done, Bufs B, long long spin_limit) {
@@ -791,11 +945,11 @@ k_batched(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, int
                 case S_SCAN: st_scan(sbox, B, reinterpret_cast<int*>(smem)); break;
                 case S_SCATTER: st_scatter<P>(sbox, idx, B); break;
                 case S_SPREAD: st_spread<P, TILE>(sbox, idx, B, smem); break;
-                case S_ZR2C: st_zr2c(sbox, idx, B, smem); break;
-                case S_YFWD: st_yfwd(sbox, idx, B, smem); break;
-                case S_XINF: st_xinf(sbox, box, idx, B, smem); break;
-                case S_YINV: st_yinv(sbox, idx, B, smem); break;
-                case S_ZC2R: st_zc2r(sbox, idx, B, smem); break;
+                case S_ZR2C: st_zr2c<Q>(sbox, idx, B, smem); break;
+                case S_YFWD: st_yfwd<Q>(sbox, idx, B, smem); break;
+                case S_XINF: st_xinf<Q>(sbox, box, idx, B, smem); break;
+                case S_YINV: st_yinv<Q>(sbox, idx, B, smem); break;
+                case S_ZC2R: st_zc2r<Q>(sbox, idx, B, smem); break;
                 case S_GATHER: st_gather<P, TILE>(sbox, idx, B, smem); break;
             }
         }
@@ -822,21 +976,21 @@ size_t stage_smem(int maxN, int maxB) {
     return (m + 127) / 128 * 128;
 }
 
-template <int P, int TILE>
+template <int P, int TILE, bool Q>
 cudaError_t launch(cudaStream_t s, const BoxDesc* boxes, const int2* items, int nitems, unsigned int* head, int* done,
                    const Bufs& B, long long spin_limit, int maxN, int maxB, int* grid_out) {
     const size_t smem = stage_smem<P, TILE>(maxN, maxB);
-    cudaError_t e = cudaFuncSetAttribute(k_batched<P, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_batched<P, TILE, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<P, TILE>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<P, TILE, Q>, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int grid = std::min(nsm * per_sm, nitems);
     if (grid_out) *grid_out = grid;
-    k_batched<P, TILE><<<grid, kThreads, smem, s>>>(boxes, items, nitems, head, done, B, spin_limit);
+    k_batched<P, TILE, Q><<<grid, kThreads, smem, s>>>(boxes, items, nitems, head, done, B, spin_limit);
     return cudaGetLastError();
 }
 
@@ -854,6 +1008,8 @@ struct pppm_batch {
     double prefactor = 1.0;
     long long spin_limit = 1ll << 24;
     int dft_max = 0;            // short lines on the tensor cores (off: measured 2 % slower on the batch)
+    int quant_group = 0;        // int32-quantised DFT of short lines (an accuracy ablation; off)
+    double quant_scale = 1e7;
     std::vector<double> boxes;  // nbox * 3
     std::vector<int> meshes;    // nbox * 3
     int tile = 0;               // chosen tile edge (0 = not tuned yet)
@@ -1172,13 +1328,18 @@ int enqueue(pppm_batch* P, cudaStream_t s, int li, const float* pos, const float
     B.status = P->status;
     B.prefactor = P->prefactor;
     B.dft_max = P->dft_max;
+    B.qgroup = P->quant_group;
+    B.qscale = P->quant_scale;
     cudaError_t e = cudaErrorInvalidValue;
     const int n = (int)Y.items.size();
-#define BATCH_CASE(PP, TT)                                                                                       \
-    if (P->order == PP && Y.T == TT)                                                                             \
-        e = launch<PP, TT>(s, Y.d_desc, Y.d_items, n, P->head, P->done, B, P->spin_limit, Y.maxN, Y.maxB,        \
-                           &P->last_grid);
-    BATCH_CASE(3, 4) BATCH_CASE(3, 8) BATCH_CASE(5, 4) BATCH_CASE(5, 8) BATCH_CASE(7, 4) BATCH_CASE(7, 8)
+    const bool quant = P->quant_group > 0;
+#define BATCH_CASE(PP, TT, QQ)                                                                                   \
+    if (P->order == PP && Y.T == TT && quant == QQ)                                                              \
+        e = launch<PP, TT, QQ>(s, Y.d_desc, Y.d_items, n, P->head, P->done, B, P->spin_limit, Y.maxN, Y.maxB,    \
+                               &P->last_grid);
+    BATCH_CASE(3, 4, false) BATCH_CASE(3, 8, false) BATCH_CASE(5, 4, false) BATCH_CASE(5, 8, false)
+    BATCH_CASE(7, 4, false) BATCH_CASE(7, 8, false)
+    BATCH_CASE(5, 4, true) BATCH_CASE(5, 8, true)  // the quantised ablation: order 5 only
 #undef BATCH_CASE
     BK(e);
     return PPPM_OK;
@@ -1349,6 +1510,17 @@ int pppm_batch_set_dft(pppm_batch* P, int max_len) {
     return PPPM_OK;
 }
 
+int pppm_batch_set_quantized(pppm_batch* P, int group, double scale) {
+    if (!P || group < 0 || group > kDftTcMax || (group > 0 && P->order != 5)) return PPPM_ERR_INVALID_ARG;
+    if (!(scale >= 1.0 && scale <= 1e15)) return PPPM_ERR_INVALID_ARG;
+    P->quant_group = group;
+    P->quant_scale = scale;
+    P->tile = P->forced_tile;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    P->exec = nullptr;
+    return PPPM_OK;
+}
+
 int pppm_batch_meshes(const pppm_batch* P, int* meshes) {
     if (!P || !meshes) return PPPM_ERR_INVALID_ARG;
     std::memcpy(meshes, P->meshes.data(), sizeof(int) * 3 * P->nbox);
@@ -1408,6 +1580,7 @@ int pppm_batch_status(pppm_batch* P) {
     if (st) BK(cudaMemset(P->status, 0, sizeof(int)));
     if (st & 4) return PPPM_ERR_TIMEOUT;
     if (st & 1) return PPPM_ERR_NONFINITE;
+    if (st & 8) return PPPM_ERR_TOO_LARGE;  // a quantised partial sum was clamped to int32
     return PPPM_OK;
 }
 

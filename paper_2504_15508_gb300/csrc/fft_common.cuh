@@ -232,11 +232,62 @@ __device__ inline float2* dft_tc(float2* a, float2* b, int nl, int ls, int ps, i
     return b;
 }
 
-// line transform for the batched kernel: the tensor-core DFT for short lines
-// (when enabled), the Stockham FFT otherwise
+// ------------------------------------------------------------------ int32-quantised DFT (ablation)
+// The DFT of nl lines of length L as in the paper's hardware-offloaded FFT
+// (Section "Hardware-offloaded 3D FFT", its data-quantisation panel): the line
+// is split into nodes of `group` consecutive points; each node's partial sum
+// of x_t e^{s 2 pi i k t / L} over its points (FP32) is multiplied by `scale`
+// (the paper's 10^7), rounded to the nearest integer and clamped to int32 (a
+// clamped value sets bit 8 of *status), and the nodes' integers are added
+// exactly; the sum is scaled back.  One thread per output; layout and return
+// as dft_tc.
+__device__ __forceinline__ long long quant_int32(float v, double scale, bool& saturated) {
+    double y = rint((double)v * scale);
+    if (!(fabs(y) <= 2147483647.0)) {  // also catches a non-finite value
+        saturated = true;
+        y = y > 0.0 ? 2147483647.0 : -2147483648.0;
+    }
+    return (long long)y;
+}
+
+__device__ inline float2* dft_quant(const float2* a, float2* b, int nl, int ls, int ps, int L, int group,
+                                    double scale, const float2* __restrict__ tw, float s,
+                                    int* __restrict__ status) {
+    bool saturated = false;
+    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+        const int line = idx / L, k = idx - line * L;
+        const float2* x = a + line * ls;
+        long long ar = 0, ai = 0;
+        for (int t0 = 0; t0 < L; t0 += group) {
+            float pr = 0.f, pi = 0.f;
+            for (int t = t0; t < t0 + group; ++t) {
+                const float2 w = __ldg(&tw[(k * t) % L]);  // e^{-2 pi i k t / L}
+                const float wr = w.x, wi = -s * w.y;      // e^{s 2 pi i k t / L}
+                const float2 v = x[t * ps];
+                pr += v.x * wr - v.y * wi;
+                pi += v.x * wi + v.y * wr;
+            }
+            ar += quant_int32(pr, scale, saturated);
+            ai += quant_int32(pi, scale, saturated);
+        }
+        b[line * ls + k * ps] = make_float2((float)((double)ar / scale), (float)((double)ai / scale));
+    }
+    if (saturated) atomicOr(status, 8);
+    __syncthreads();
+    return b;
+}
+
+// line transform for the batched kernel: the int32-quantised DFT with nodes
+// of qg points (qg > 0: that ablation is on for this axis), the tensor-core
+// DFT for short lines (when enabled), the Stockham FFT otherwise.  Q compiles
+// the quantised branch in (a separate kernel instantiation, so that the
+// default kernel carries none of its registers).
+template <bool Q>
 __device__ __forceinline__ float2* line_transform(float2* a, float2* b, int nl, int ls, int ps, const Radix& rp,
                                                   const float2* __restrict__ tw, float s, bool line_fast,
-                                                  int dft_max) {
+                                                  int dft_max, int qg, double qscale, int* status) {
+    if constexpr (Q)
+        if (qg > 0) return dft_quant(a, b, nl, ls, ps, rp.L, qg, qscale, tw, s, status);
     if (rp.L <= dft_max) return dft_tc(a, b, nl, ls, ps, rp.L, tw, s);
     return stockham<float>(a, b, nl, ls, ps, rp, tw, s, line_fast);
 }

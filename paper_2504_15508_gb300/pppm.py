@@ -287,6 +287,12 @@ class BatchPlan:
         DFT instead of the FFT."""
         N.check(self._lib.pppm_batch_set_dft(self._h, int(max_len)), "pppm_batch_set_dft")
 
+    def set_quantized(self, group: int, scale: float = 1e7):
+        """group > 0: lines of length <= 18 divisible by group take the
+        int32-quantised per-node DFT at `scale` (an accuracy ablation; order
+        5 only); 0 = off."""
+        N.check(self._lib.pppm_batch_set_quantized(self._h, int(group), float(scale)), "pppm_batch_set_quantized")
+
     @property
     def meshes(self) -> np.ndarray:
         m = np.zeros((self.nbox, 3), dtype=np.int32)

@@ -110,3 +110,7 @@ def test_graph_calls_validate_arguments(pppm_lib):
 
 def test_batch_set_dft_validates(pppm_lib):
     assert pppm_lib.pppm_batch_set_dft(None, 18) == N.PPPM_ERR_INVALID_ARG
+
+
+def test_batch_set_quantized_validates(pppm_lib):
+    assert pppm_lib.pppm_batch_set_quantized(None, 4, 1e7) == N.PPPM_ERR_INVALID_ARG
