@@ -1213,7 +1213,10 @@ int build_layout(pppm_batch* P, int li, int T) {
                     else return PPPM_ERR_BAD_MESH;
                 }
             }
-        D.nitems[S_BIN] = (D.nsite + kSiteChunk - 1) / kSiteChunk;
+        // every stage waits only on the one before it, so no stage may be
+        // empty: a box without sites still gets one (idle) binning and one
+        // scatter item, or its spread would not wait for its scan
+        D.nitems[S_BIN] = std::max(1, (D.nsite + kSiteChunk - 1) / kSiteChunk);
         D.nitems[S_SCAN] = 1;
         D.nitems[S_SCATTER] = D.nitems[S_BIN];
         D.nitems[S_SPREAD] = (D.g.ntiles + kSpreadTiles - 1) / kSpreadTiles;
@@ -1226,8 +1229,6 @@ int build_layout(pppm_batch* P, int li, int T) {
         D.nitems[S_GATHER] = (D.g.ntiles + kGatherTiles - 1) / kGatherTiles;
         D.part0 = part0;
         part0 += D.nitems[S_XINF];
-        for (int s = 0; s < NSTAGE; ++s)
-            if (D.nitems[s] == 0) D.nitems[s] = 0;
     }
     // stage-major work list; bigger boxes first within a stage
     std::vector<int> order(P->nbox);

@@ -95,3 +95,44 @@ def test_batched_bounded_wait_times_out_cleanly(cuda_device, pppm_lib):
     sl = slice(offs[0], offs[1])
     ref = OraclePPPM(wb.box, bp.meshes[0], 5, 0.4).compute(pos[sl].astype(np.float64), q[sl].astype(np.float64))
     assert _rel(f[sl].cpu().numpy(), ref["forces"]) <= 1e-5
+
+
+@pytest.mark.parametrize("order,meshes", [
+    (3, [(12, 15, 16), (16, 16, 16), (12, 16, 20), (16, 16, 16)]),
+    (7, [(15, 16, 18), (16, 16, 16), (15, 16, 20), (16, 16, 16)]),
+])
+def test_batched_orders_rectangular_empty_and_single_site(cuda_device, pppm_lib, order, meshes):
+    """Orders 3 and 7; in one launch a water box, a box without sites, a
+    rectangular box of random neutral charges on a mixed mesh and a box with
+    one charge.  Every box equals the oracle; the empty one gives zeros."""
+    from paper_2504_15508_gb300.pppm import BatchPlan
+    rng = np.random.default_rng(order)
+    water = make_water(128, 15.64, 3)
+    rect_box = np.array([14.0, 19.0, 23.5])
+    rect_pos = rng.uniform(0, 1, (300, 3)) * rect_box
+    rect_q = np.where(np.arange(300) % 2 == 0, 0.7, -0.7)
+    one_box = np.array([10.0, 10.0, 10.0])
+    one_pos = rng.uniform(0, 10, (1, 3))
+    one_q = np.array([1.0])
+    boxes = np.array([water.box, [20.0, 20.0, 20.0], rect_box, one_box])
+    sites = [(water.pos, water.q), (np.zeros((0, 3)), np.zeros(0)), (rect_pos, rect_q), (one_pos, one_q)]
+    pos = np.concatenate([p for p, _ in sites]).astype(np.float32)
+    q = np.concatenate([c for _, c in sites]).astype(np.float32)
+    offs = np.concatenate([[0], np.cumsum([len(c) for _, c in sites])]).astype(np.int64)
+    bp = BatchPlan(boxes, np.array(meshes, dtype=np.int32), order=order, beta=0.4)
+    e, f, v = bp.compute(torch.tensor(pos, device=cuda_device), torch.tensor(q, device=cuda_device),
+                         torch.tensor(offs, device=cuda_device))
+    torch.cuda.synchronize()
+    assert bp.status() == 0
+    e, f, v = e.cpu().numpy(), f.cpu().numpy(), v.cpu().numpy()
+    assert e[1] == 0.0 and np.all(v[1] == 0.0)
+    for b in (0, 2, 3):
+        sl = slice(offs[b], offs[b + 1])
+        ref = OraclePPPM(boxes[b], meshes[b], order, 0.4).compute(pos[sl].astype(np.float64),
+                                                                  q[sl].astype(np.float64))
+        assert abs(e[b] - ref["energy"]) <= 1e-6 * abs(ref["energy"]), (b, e[b], ref["energy"])
+        assert _rel(v[b], ref["virial"]) <= 1e-5, b
+        if b == 3:   # a lone charge feels (almost) no force from its own images
+            assert np.max(np.abs(f[sl] - ref["forces"])) <= 1e-5 + 1e-5 * np.max(np.abs(ref["forces"]))
+        else:
+            assert _rel(f[sl], ref["forces"]) <= 1e-5, b
