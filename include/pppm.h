@@ -170,7 +170,9 @@ int pppm_fields(pppm_plan *plan, void *stream, const double *pos, const double *
  *   boxes          nbox x 3 edge lengths (host)
  *   meshes         nbox x 3 mesh sizes (host), or NULL: per axis the smallest
  *                  2^a 3^b 5^c >= L / 1.2 (spacing <= 1.2 Angstrom); every size
- *                  must be 2^a 3^b 5^c in [order + 7, 512]
+ *                  must be 2^a 3^b 5^c in [order + 3, 512]; the tile edge 8
+ *                  needs every axis of every box >= order + 7, else the batch
+ *                  runs with tile edge 4 (forcing 8 then gives PPPM_ERR_BAD_MESH)
  *   order          3, 5 or 7
  *   beta           as in pppm_create
  * pppm_compute_batched

@@ -1355,8 +1355,12 @@ int prepare(pppm_batch* P, const int64_t* offsets) {
         P->offsets = off;
         int rc;
         if ((rc = ensure_sites(P, off[P->nbox])) != PPPM_OK) return rc;
-        for (int li = 0; li < 2; ++li)
-            if ((rc = build_layout(P, li, li == 0 ? 4 : 8)) != PPPM_OK) return rc;
+        if ((rc = build_layout(P, 0, 4)) != PPPM_OK) return rc;
+        // tile edge 8 needs every axis of every box to hold 8 + p - 1 points;
+        // if one does not, only tile edge 4 is available
+        rc = build_layout(P, 1, 8);
+        if (rc == PPPM_ERR_BAD_MESH) P->lay[1].T = 0;
+        else if (rc != PPPM_OK) return rc;
         if (P->exec) cudaGraphExecDestroy(P->exec);
         P->exec = nullptr;
         P->tile = P->forced_tile;
@@ -1374,6 +1378,7 @@ int autotune(pppm_batch* P, const float* pos, const float* q, double* energies, 
     float best = 1e30f;
     int best_T = 8;
     for (int li = 0; li < 2; ++li) {
+        if (P->lay[li].T == 0) continue;  // not available for these meshes
         float ms_sum = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
             if (enqueue(P, s, li, pos, q, energies, forces, virials) != PPPM_OK) { ms_sum = 1e30f; break; }
@@ -1422,7 +1427,7 @@ int pppm_batch_create(int nbox, const double* boxes, const int* meshes, int orde
             const double L = boxes[3 * b + d];
             if (!(L > 0.0) || !std::isfinite(L)) return fail(PPPM_ERR_BAD_BOX);
             int m = meshes ? meshes[3 * b + d] : smooth_at_least_b(L / 1.2);
-            if (!smooth235_b(m) || m < 8 + order - 1 || m > 512) return fail(PPPM_ERR_BAD_MESH);
+            if (!smooth235_b(m) || m < 4 + order - 1 || m > 512) return fail(PPPM_ERR_BAD_MESH);
             P->meshes[3 * b + d] = m;
         }
     // influence functions (FP64 on the device, FP32 copies) and twiddles, per box
@@ -1543,6 +1548,7 @@ int pppm_compute_batched(pppm_batch* P, void* stream, const float* pos, const fl
         if ((rc = autotune(P, pos, q, energies, forces, virials)) != PPPM_OK) return rc;
     }
     const int li = P->tile == 4 ? 0 : 1;
+    if (P->lay[li].T == 0) return PPPM_ERR_BAD_MESH;  // tile edge 8 forced on a mesh too small for it
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     BK(cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone || s == nullptr) return enqueue(P, s, li, pos, q, energies, forces, virials);

@@ -29,9 +29,9 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
 
 
-def _boxes(seeds, extra=()):
+def _boxes(seeds, extra=(), mesh=MESH128):
     boxes = [make_water(128, L128, s) for s in seeds] + [make_water(n, L, s) for (n, L, s) in extra]
-    meshes = [MESH128] * len(seeds) + [(24, 24, 24)] * len(extra)
+    meshes = [mesh] * len(seeds) + [(24, 24, 24)] * len(extra)
     pos = np.concatenate([b.pos for b in boxes]).astype(np.float32)
     q = np.concatenate([b.q for b in boxes]).astype(np.float32)
     offs = np.concatenate([[0], np.cumsum([b.n for b in boxes])]).astype(np.int64)
@@ -49,9 +49,11 @@ def _plan(boxes, meshes):
     return BatchPlan(np.array([b.box for b in boxes]), meshes, order=5, beta=0.4)
 
 
-@pytest.mark.parametrize("group", [6, 3, 2])
-def test_quantized_paper_scale(cuda_device, pppm_lib, group):
-    boxes, meshes, pos, q, offs = _boxes([4, 5, 6])
+@pytest.mark.parametrize("mesh,group", [((8, 12, 8), 4), ((10, 15, 10), 5), (MESH128, 6), (MESH128, 3), (MESH128, 2)])
+def test_quantized_paper_scale(cuda_device, pppm_lib, mesh, group):
+    """The three meshes of the paper's int32 runs (the two coarser ones run
+    with tile edge 4)."""
+    boxes, meshes, pos, q, offs = _boxes([4, 5, 6], mesh=mesh)
     bp = _plan(boxes, meshes)
     _, f0, _ = _run(bp, cuda_device, pos, q, offs)   # switched on after a first run
     bp.set_quantized(group)
@@ -63,7 +65,7 @@ def test_quantized_paper_scale(cuda_device, pppm_lib, group):
     for b, wb in enumerate(boxes):
         sl = slice(offs[b], offs[b + 1])
         p64, q64 = pos[sl].astype(np.float64), q[sl].astype(np.float64)
-        o = OraclePPPM(wb.box, MESH128, 5, 0.4)
+        o = OraclePPPM(wb.box, mesh, 5, 0.4)
         plain = o.compute(p64, q64)
         quant = pppm_quantized(o, p64, q64, group)
         assert not quant["saturated"]
@@ -73,14 +75,16 @@ def test_quantized_paper_scale(cuda_device, pppm_lib, group):
             assert _rel(v[b], ref["virial"]) <= 1e-5
 
 
-@pytest.mark.parametrize("group,axes", [(6, (0, 1, 2)), (2, (0, 1, 2)), (4, (0, 2)), (9, (1,))])
-def test_quantized_coarse_scale_reproduces_oracle_errors(cuda_device, pppm_lib, group, axes):
+@pytest.mark.parametrize("mesh,group,axes", [(MESH128, 6, (0, 1, 2)), (MESH128, 2, (0, 1, 2)), (MESH128, 4, (0, 2)),
+                                             (MESH128, 9, (1,)), ((8, 12, 8), 4, (0, 1, 2)),
+                                             ((10, 15, 10), 5, (0, 1, 2))])
+def test_quantized_coarse_scale_reproduces_oracle_errors(cuda_device, pppm_lib, mesh, group, axes):
     """The library quantises the lines of at most 18 points that the node size
     divides (group 4 on 12 x 18 x 12: x and z; group 9: y).  Left over after
     the match: exact ties (a partial sum of grid values times a twiddle of
     1/2), which FP32 and the oracle's FP64 may round either way."""
     scale = 1e4
-    boxes, meshes, pos, q, offs = _boxes([4, 7])
+    boxes, meshes, pos, q, offs = _boxes([4, 7], mesh=mesh)
     bp = _plan(boxes, meshes)
     e0, f0, v0 = _run(bp, cuda_device, pos, q, offs)          # unquantised, same kernels
     bp.set_quantized(group, scale)
@@ -89,7 +93,7 @@ def test_quantized_coarse_scale_reproduces_oracle_errors(cuda_device, pppm_lib, 
     for b, wb in enumerate(boxes):
         sl = slice(offs[b], offs[b + 1])
         p64, q64 = pos[sl].astype(np.float64), q[sl].astype(np.float64)
-        o = OraclePPPM(wb.box, MESH128, 5, 0.4)
+        o = OraclePPPM(wb.box, mesh, 5, 0.4)
         plain = o.compute(p64, q64)
         quant = pppm_quantized(o, p64, q64, group, scale, axes=axes)
         d_f = _rel(quant["forces"], plain["forces"])
@@ -134,6 +138,20 @@ def test_quantized_saturation_reported_then_recovers(cuda_device, pppm_lib):
     assert bp.status() == 0
     ref = OraclePPPM(boxes[0].box, MESH128, 5, 0.4).compute(pos.astype(np.float64), q.astype(np.float64))
     assert _rel(f, ref["forces"]) <= 1e-5
+
+
+def test_small_meshes_run_with_tile_edge_four(cuda_device, pppm_lib):
+    """8 x 12 x 8 is below the 12 points tile edge 8 needs: the autotuner
+    keeps 4, and forcing 8 is refused."""
+    boxes, meshes, pos, q, offs = _boxes([4], mesh=(8, 12, 8))
+    bp = _plan(boxes, meshes)
+    _run(bp, cuda_device, pos, q, offs)
+    assert bp.status() == 0 and bp.tile == 4
+    bp.set(tile=8)
+    tp, tq, to = (torch.tensor(pos, device=cuda_device), torch.tensor(q, device=cuda_device),
+                  torch.tensor(offs, device=cuda_device))
+    with pytest.raises(Exception):
+        bp.compute(tp, tq, to)
 
 
 def test_quantized_argument_checks(cuda_device, pppm_lib):
