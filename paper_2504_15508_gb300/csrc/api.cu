@@ -297,7 +297,7 @@ int run_sites_to_patches(pppm_plan* P, cudaStream_t s, const In* pos, const In* 
                            need_rec ? (Rec<T>*)P->srec : nullptr, P->scell, P->sorig, (T*)P->swt)); }
     { PROF(K_SPREAD);
       CK(launch_spread<T>(s, g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig, (const T*)P->swt,
-                          (T*)P->patch)); }
+                          (T*)P->patch, P->slot_of)); }
     if (rho_out) {
         PROF(K_FOLD);
         CK(launch_fold<T>(s, g, (const T*)P->patch, P->cov_off, P->cov_ent, scale, rho_out));

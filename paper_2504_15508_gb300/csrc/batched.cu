@@ -260,6 +260,7 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
     const long long sb = D.site0 + s0;
     // canonical order (by original index) by counting ranks, as the single-box spread
     const bool ranked = c > 1 && c <= kKeyCap;
+    const bool dense = c > kKeyCap;  // ranked from global memory instead
     if (ranked) {
         for (int i = lane; i < c; i += 32) W.u.keys[i] = ldcg(&B.sorig[sb + i]);
     }
@@ -275,6 +276,7 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
         }
     }
     __syncwarp();
+    if (dense) rank_dense_tile(B.sorig + sb, c, B.slot_of + sb);  // the slots are dead after the scatter
     constexpr int NR = (P * P + 31) / 32;
     int roff[NR], riy[NR], riz[NR];
     bool ract[NR];
@@ -291,7 +293,7 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
     int ncell = 0;
     auto fetch = [&](int t0) {
         if (t0 + lane < c) {
-            const long long st = sb + (ranked ? (int)W.perm[t0 + lane] : t0 + lane);
+            const long long st = sb + (ranked ? (int)W.perm[t0 + lane] : (dense ? ldcg(&B.slot_of[sb + t0 + lane]) : t0 + lane));
             const float4* src = reinterpret_cast<const float4*>(B.swt + st * WS);
 #pragma unroll
             for (int a = 0; a < NV; ++a) nw[a] = __ldcg(&src[a]);

@@ -101,6 +101,22 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Canonical order of a tile that holds more sites than a spread kernel ranks
+// in shared memory: rank of the tile's site i = how many of its sites have a
+// smaller original index, counted over keys[0 .. c) in global memory (O(c^2),
+// only for such tiles; L2 loads, so keys written earlier in the same kernel
+// are seen); order[rank] = i.  One warp, every lane; ends with __syncwarp, after
+// which every lane of the warp may read order[] (with L2 loads).
+__device__ __forceinline__ void rank_dense_tile(const int* keys, int c, int* order) {
+    for (int i = (int)(threadIdx.x & 31); i < c; i += 32) {
+        const int ki = __ldcg(&keys[i]);
+        int r = 0;
+        for (int j = 0; j < c; ++j) r += __ldcg(&keys[j]) < ki;
+        order[r] = i;
+    }
+    __syncwarp();
+}
+
 extern thread_local bool g_pdl;  // launches of this host thread use PDL
 
 struct PdlScope {
@@ -167,9 +183,11 @@ template <typename T>
 cudaError_t launch_scatter(cudaStream_t s, const Geo& g, int n, const int* tile_of, const int* slot_of,
                            const int* tile_start, const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell,
                            int* sorig, T* swt);
+// order: n ints of scratch in tile order (the binning's slot array, dead once
+// the scatter has run), used for tiles denser than the shared-memory ranking
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, T* patch);
+                          const int* scell, const int* sorig, const T* swt, T* patch, int* order);
 template <typename T>
 cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
                         T scale, T* rho);
@@ -181,7 +199,7 @@ void upload_bspline_coefficients();
 // full-tile fast paths (cudaErrorNotSupported when the order/tile has none)
 template <typename T>
 cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
-                               const int* sorig, const T* swt, T* patch);
+                               const int* sorig, const T* swt, T* patch, int* order);
 template <typename T, typename Out>
 cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell, const int* sorig,
                               const T* swt, const void* tmap, double prefactor, Out* forces, int* status);

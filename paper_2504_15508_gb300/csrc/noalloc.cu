@@ -183,7 +183,7 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     NA_CK((launch_bin<float, double>(s, g, pos, q, (int)n, tile_count, tile_of, slot_of, rec, cell, status)));
     NA_CK(launch_scan(s, tile_count, g.ntiles, tile_start));
     NA_CK(launch_scatter<float>(s, g, (int)n, tile_of, slot_of, tile_start, rec, cell, srec, scell, sorig, swt));
-    NA_CK(launch_spread<float>(s, g, tile_start, srec, scell, sorig, swt, patch));
+    NA_CK(launch_spread<float>(s, g, tile_start, srec, scell, sorig, swt, patch, slot_of));
     NA_CK(launch_fold<float>(s, g, patch, cov_off, cov_ent, (float)(1.0 / h3), rho));
 #undef NA_CK
     return PPPM_OK;

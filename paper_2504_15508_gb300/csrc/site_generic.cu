@@ -32,7 +32,7 @@ constexpr int kSpreadCap = 512;
 template <typename T, int P>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
-         const int* __restrict__ scell, const int* __restrict__ sorig, T* __restrict__ patch) {
+         const int* __restrict__ scell, const int* __restrict__ sorig, T* __restrict__ patch, int* order) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -67,6 +67,8 @@ k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
             }
     }
     __syncwarp();
+    const bool dense = c > kSpreadCap;  // ranked from global memory instead
+    if (dense) rank_dense_tile(sorig + s0, c, order + s0);
 
     // lane -> stencil rows (iy, iz); orders above 5 have more rows than lanes
     constexpr int NR = (P * P + 31) / 32;
@@ -85,7 +87,7 @@ k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
         roff[j] = iy * Pz + iz;
     }
     for (int t = 0; t < c; ++t) {
-        const int s = sorted ? keys[t].y : s0 + t;
+        const int s = sorted ? keys[t].y : s0 + (dense ? __ldcg(&order[s0 + t]) : t);
         const Rec<T> r = srec[s];
         const int cl = scell[s];
         const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
@@ -109,31 +111,31 @@ k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
 
 template <typename T, int P>
 static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                            const int* scell, const int* sorig, T* patch) {
+                            const int* scell, const int* sorig, T* patch, int* order) {
     const int psize = g.E[0] * g.E[1] * g.Pz;
     size_t smem = (size_t)kSpreadWarps * psize * sizeof(T) + (size_t)kSpreadWarps * kSpreadCap * sizeof(int2);
     cudaError_t e = cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
     return launch_k(k_spread<T, P>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tile_start, srec, scell, sorig,
-                    patch);
+                    patch, order);
 }
 
 
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, T* patch) {
+                          const int* scell, const int* sorig, const T* swt, T* patch, int* order) {
     if (fast_tiles(g)) {
-        cudaError_t e = launch_spread_fast<T>(s, g, tile_start, scell, sorig, swt, patch);
+        cudaError_t e = launch_spread_fast<T>(s, g, tile_start, scell, sorig, swt, patch, order);
         if (e != cudaErrorNotSupported) return e;
     }
     switch (g.order) {
-        case 2: return spread_p<T, 2>(s, g, tile_start, srec, scell, sorig, patch);
-        case 3: return spread_p<T, 3>(s, g, tile_start, srec, scell, sorig, patch);
-        case 4: return spread_p<T, 4>(s, g, tile_start, srec, scell, sorig, patch);
-        case 5: return spread_p<T, 5>(s, g, tile_start, srec, scell, sorig, patch);
-        case 6: return spread_p<T, 6>(s, g, tile_start, srec, scell, sorig, patch);
-        case 7: return spread_p<T, 7>(s, g, tile_start, srec, scell, sorig, patch);
+        case 2: return spread_p<T, 2>(s, g, tile_start, srec, scell, sorig, patch, order);
+        case 3: return spread_p<T, 3>(s, g, tile_start, srec, scell, sorig, patch, order);
+        case 4: return spread_p<T, 4>(s, g, tile_start, srec, scell, sorig, patch, order);
+        case 5: return spread_p<T, 5>(s, g, tile_start, srec, scell, sorig, patch, order);
+        case 6: return spread_p<T, 6>(s, g, tile_start, srec, scell, sorig, patch, order);
+        case 7: return spread_p<T, 7>(s, g, tile_start, srec, scell, sorig, patch, order);
     }
     return cudaErrorInvalidValue;
 }
@@ -328,7 +330,7 @@ cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, c
 
 #define PPPM_INST_T(T)                                                                                          \
     template cudaError_t launch_spread<T>(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*,       \
-                                          const int*, const T*, T*);                                             \
+                                          const int*, const T*, T*, int*);                                       \
     template cudaError_t launch_fold<T>(cudaStream_t, const Geo&, const T*, const int*, const int2*, T, T*);
 PPPM_INST_T(float)
 PPPM_INST_T(double)

@@ -52,7 +52,7 @@ struct __align__(16) SpreadWarpSmem {  // 16-byte aligned: staged rows take vect
 template <typename T, int P, int TILE>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
-              const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch) {
+              const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch, int* order) {
     pdl_enter();
     typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
     typedef typename Vec16T<T>::t V;
@@ -89,6 +89,8 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
         }
     }
     __syncwarp();
+    const bool dense = c > kFastCap;  // ranked from global memory instead
+    if (dense) rank_dense_tile(sorig + s0, c, order + s0);
     // lane -> stencil rows (iy, iz); orders above 5 have more rows than lanes
     constexpr int NR = (P * P + 31) / 32;
     int roff[NR], riy[NR], riz[NR];
@@ -106,7 +108,7 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
     int ncell = 0;
     auto fetch = [&](int t0) {
         if (lane < kStage && t0 + lane < c) {
-            const int s = s0 + (ranked ? (int)W.perm[t0 + lane] : t0 + lane);
+            const int s = s0 + (ranked ? (int)W.perm[t0 + lane] : (dense ? __ldcg(&order[s0 + t0 + lane]) : t0 + lane));
             const V* src = reinterpret_cast<const V*>(swt + (size_t)s * WS);
 #pragma unroll
             for (int a = 0; a < NV; ++a) nw[a] = __ldg(&src[a]);
@@ -160,14 +162,14 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
 
 template <typename T, int P, int TILE>
 static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
-                               const int* sorig, const T* swt, T* patch) {
+                               const int* sorig, const T* swt, T* patch, int* order) {
     const size_t smem = kSpreadWarps * sizeof(SpreadWarpSmem<T, P, TILE>);
     cudaError_t e = cudaFuncSetAttribute(k_spread_fast<T, P, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
     return launch_k(k_spread_fast<T, P, TILE>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tile_start, scell,
-                    sorig, swt, patch);
+                    sorig, swt, patch, order);
 }
 
 
@@ -190,14 +192,14 @@ static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_sta
 
 template <typename T>
 cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
-                               const int* sorig, const T* swt, T* patch) {
-    PPPM_FAST_SWITCH(spread_fast, T, s, g, tile_start, scell, sorig, swt, patch)
+                               const int* sorig, const T* swt, T* patch, int* order) {
+    PPPM_FAST_SWITCH(spread_fast, T, s, g, tile_start, scell, sorig, swt, patch, order)
     return cudaErrorNotSupported;
 }
 
 template cudaError_t launch_spread_fast<float>(cudaStream_t, const Geo&, const int*, const int*, const int*,
-                                               const float*, float*);
+                                               const float*, float*, int*);
 template cudaError_t launch_spread_fast<double>(cudaStream_t, const Geo&, const int*, const int*, const int*,
-                                                const double*, double*);
+                                                const double*, double*, int*);
 
 }  // namespace pppm

@@ -212,6 +212,27 @@ def test_deterministic(cuda_device, pppm_lib):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("mesh,n,tile", [((8, 8, 8), 3000, 4), ((8, 9, 10), 3000, 4), ((6, 5, 8), 1000, 8)])
+def test_dense_tiles_are_deterministic(cuda_device, pppm_lib, prec, mesh, n, tile):
+    """Tiles holding more sites than the spread ranks in shared memory (256
+    in the full-tile kernel: the first two cases, ~375 and up to ~270 a tile;
+    512 in the generic kernel: the third, one tile of 1,000) are put in
+    canonical order by ranks counted in global memory: two runs agree bitwise
+    and both match the oracle."""
+    box = (10.0, 11.0, 12.0)
+    pos, q = _random_neutral(n, box, seed=21)
+    tp, tq, pos_r, q_r = _sites(pos, q, prec, cuda_device)
+    plan = _plan(box, mesh, 5, 0.4, precision=prec, tile=tile)
+    r1 = [t.clone() for t in plan.compute(tp, tq)]
+    r2 = [t.clone() for t in plan.compute(tp, tq)]
+    torch.cuda.synchronize()
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)
+    ref = OraclePPPM(box, mesh, 5, 0.4).compute(pos_r, q_r)
+    _check(r1, ref, prec, f"dense {mesh}")
+
+
 def test_nonfinite_positions_flagged(cuda_device, pppm_lib):
     from paper_2504_15508_gb300 import _native as N
     wb, w = make_workload("water64")
