@@ -157,12 +157,14 @@ def test_water_is_neutral():
     for seed in (1, 2, 3):
         wb = make_water(64, 12.42, seed)
         assert abs(wb.q.sum()) < 1e-12
-    wb, _ = make_workload("water4096")
-    assert abs(wb.q.sum()) < 1e-12
+    for name in ("water4096", "water128"):
+        wb, _ = make_workload(name)
+        assert abs(wb.q.sum()) < 1e-12
 
 
-def test_water_geometry():
-    wb = make_water(64, 12.42, 1)
+@pytest.mark.parametrize("n_mol,L,seed", [(64, 12.42, 1), (128, 15.64, 4), (128, 15.64, 7)])
+def test_water_geometry(n_mol, L, seed):
+    wb = make_water(n_mol, L, seed)
     n = wb.n_mol
     o, h, wc = wb.pos[:n], wb.pos[n:3 * n], wb.pos[3 * n:]
     d1 = np.linalg.norm(h[0::2] - o, axis=1)
