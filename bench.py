@@ -165,7 +165,6 @@ def step_algorithmic_bytes(n: int, mesh: int) -> int:
 # entry is removed whenever its kernel changes.
 NCU_TRAFFIC = {
     ("gather", 128): 58.66e6,
-    ("spread", 128): 20.89e6,
     ("fft_z_r2c", 128): 30.71e6,
     ("fft_y", 128): 8.54e6,
     ("fft_x_influence", 128): 12.86e6,
