@@ -224,6 +224,12 @@ int pppm_batch_create(int nbox, const double *boxes, const int *meshes, int orde
 int pppm_batch_set(pppm_batch *batch, double prefactor, int tile, long long spin_limit);
 int pppm_batch_set_dft(pppm_batch *batch, int max_len);
 int pppm_batch_set_quantized(pppm_batch *batch, int group, double scale);
+/* pppm_batch_set_wait_probe: when on (nonzero), the scan stage of box 0 waits
+ * for one binning item more than the box has, so that bounded wait must run
+ * out after the spin limit: the launch ends, pppm_batch_status returns
+ * PPPM_ERR_TIMEOUT and box 0's results are not written.  A test of the
+ * timeout path without any fault; off by default. */
+int pppm_batch_set_wait_probe(pppm_batch *batch, int on);
 int pppm_batch_meshes(const pppm_batch *batch, int *meshes);
 int pppm_batch_tile(const pppm_batch *batch);
 int pppm_compute_batched(pppm_batch *batch, void *stream, const float *pos, const float *q,
@@ -252,7 +258,10 @@ void pppm_batch_destroy(pppm_batch *batch);
  * overlaps on the GPU (other streams or threads) race on it and must be
  * serialized.  The first call on a device looks up the array's device address
  * and uploads the B-spline coefficients, so make it before any stream
- * capture.  Non-finite positions are placed at the origin without a status.
+ * capture.  Every call puts only memsets and kernel launches on the stream
+ * (the fold's cover lists are built on the device, in the scratch array); no
+ * host memory is read after the call returns.  Non-finite positions are
+ * placed at the origin without a status.
  */
 int pppm_spread_noalloc(const double box[3], const int mesh[3], int order, void *stream,
                         const double *pos, const double *q, int64_t n, float *rho);
@@ -279,6 +288,17 @@ int pppm_set_potential(pppm_plan *plan, int on);
  * matches the plan (pppm_graph_launch refuses it).
  */
 int pppm_set_dependent_launch(pppm_plan *plan, int on);
+
+/*
+ * pppm_set_wait_limit -- polls of the gather's bounded wait for each tile's
+ * field copy (default 2^26).  A wait that runs out records PPPM_ERR_TIMEOUT
+ * in the plan's status word and the tile's forces are not written; the block
+ * then waits once more (bounded) so that its copy lands before it exits.
+ * 0 makes every first wait run out: a way to test the timeout path without
+ * any fault.  spins < 0: PPPM_ERR_INVALID_ARG.  A graph captured before the
+ * change no longer matches the plan.  The paper has no counterpart.
+ */
+int pppm_set_wait_limit(pppm_plan *plan, long long spins);
 
 /*
  * Learned coarse-mesh correction.  A coarse-mesh FP32 PPPM is corrected per

@@ -79,6 +79,8 @@ SIGNATURES = {
     "pppm_batch_destroy": (None, [vp]),
     "pppm_set_potential": (cint, [vp, cint]),
     "pppm_set_dependent_launch": (cint, [vp, cint]),
+    "pppm_set_wait_limit": (cint, [vp, ctypes.c_longlong]),
+    "pppm_batch_set_wait_probe": (cint, [vp, cint]),
     "pppm_corr_create": (cint, [vp, ctypes.POINTER(vp)]),
     "pppm_corr_nparams": (cint, []),
     "pppm_corr_set_weights": (cint, [vp, vp, dbl, dbl]),

@@ -297,7 +297,7 @@ int run_sites_to_patches(pppm_plan* P, cudaStream_t s, const In* pos, const In* 
                            need_rec ? (Rec<T>*)P->srec : nullptr, P->scell, P->sorig, (T*)P->swt)); }
     { PROF(K_SPREAD);
       CK(launch_spread<T>(s, g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig, (const T*)P->swt,
-                          (T*)P->patch, P->slot_of)); }
+                          (T*)P->patch, P->slot_of, P->tile_of)); }
     if (rho_out) {
         PROF(K_FOLD);
         CK(launch_fold<T>(s, g, (const T*)P->patch, P->cov_off, P->cov_ent, scale, rho_out));
@@ -377,7 +377,7 @@ int run_compute(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_
         PROF(K_GATHER);
         CK((launch_gather<T, In>(s, P->g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig,
                                  (const T*)P->swt, fl, P->flayout, P->fmap_ok ? (const void*)&P->fmap : nullptr,
-                                 P->opt.prefactor, forces, P->status)));
+                                 P->opt.prefactor, forces, P->status, P->wait_limit)));
     }
     return PPPM_OK;
 }
@@ -695,6 +695,13 @@ int pppm_set_potential(pppm_plan* P, int on) {
     }
     ++P->gen;
     P->potential = on != 0;
+    return PPPM_OK;
+}
+
+int pppm_set_wait_limit(pppm_plan* P, long long spins) {
+    if (!P || spins < 0) return PPPM_ERR_INVALID_ARG;
+    ++P->gen;
+    P->wait_limit = spins;
     return PPPM_OK;
 }
 

@@ -94,6 +94,7 @@ struct Bufs {
     int dft_max;  // lines up to this length take the tensor-core DFT (0: all take the FFT)
     int qgroup;     // node size of the int32-quantised DFT (0: off)
     double qscale;  // its scale
+    int wait_probe;  // 1: box 0's scan waits for one binning item more than exist (its wait runs out)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -276,7 +277,8 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
         }
     }
     __syncwarp();
-    if (dense) rank_dense_tile(B.sorig + sb, c, B.slot_of + sb);  // the slots are dead after the scatter
+    // the slot and tile arrays are dead after the scatter
+    if (dense) rank_dense_tile(B.sorig + sb, c, B.slot_of + sb, B.tile_of + sb, W.u.keys);
     constexpr int NR = (P * P + 31) / 32;
     int roff[NR], riy[NR], riz[NR];
     bool ract[NR];
@@ -923,7 +925,8 @@ k_batched(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, int
         if (threadIdx.x == 0) {
             int ok = 1;
             if (stage > 0) {
-                const int need = boxes[box].nitems[stage - 1];
+                // the probe makes one wait unsatisfiable, so that it must run out
+                const int need = boxes[box].nitems[stage - 1] + ((B.wait_probe && box == 0 && stage == S_SCAN) ? 1 : 0);
                 const volatile int* cnt = done + box * NSTAGE + stage - 1;
                 long long spins = 0;
                 while (*cnt < need) {
@@ -1012,6 +1015,7 @@ struct pppm_batch {
     int dft_max = 0;            // short lines on the tensor cores (off: measured 2 % slower on the batch)
     int quant_group = 0;        // int32-quantised DFT of short lines (an accuracy ablation; off)
     double quant_scale = 1e7;
+    int wait_probe = 0;
     std::vector<double> boxes;  // nbox * 3
     std::vector<int> meshes;    // nbox * 3
     int tile = 0;               // chosen tile edge (0 = not tuned yet)
@@ -1333,6 +1337,7 @@ int enqueue(pppm_batch* P, cudaStream_t s, int li, const float* pos, const float
     B.dft_max = P->dft_max;
     B.qgroup = P->quant_group;
     B.qscale = P->quant_scale;
+    B.wait_probe = P->wait_probe;
     cudaError_t e = cudaErrorInvalidValue;
     const int n = (int)Y.items.size();
     const bool quant = P->quant_group > 0;
@@ -1504,6 +1509,14 @@ int pppm_batch_set(pppm_batch* P, double prefactor, int tile, long long spin_lim
     P->forced_tile = tile;
     P->tile = tile;
     P->spin_limit = spin_limit;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    P->exec = nullptr;
+    return PPPM_OK;
+}
+
+int pppm_batch_set_wait_probe(pppm_batch* P, int on) {
+    if (!P) return PPPM_ERR_INVALID_ARG;
+    P->wait_probe = on != 0;
     if (P->exec) cudaGraphExecDestroy(P->exec);
     P->exec = nullptr;
     return PPPM_OK;

@@ -102,17 +102,78 @@ __device__ __forceinline__ void pdl_enter() {
 }
 
 // Canonical order of a tile that holds more sites than a spread kernel ranks
-// in shared memory: rank of the tile's site i = how many of its sites have a
-// smaller original index, counted over keys[0 .. c) in global memory (O(c^2),
-// only for such tiles; L2 loads, so keys written earlier in the same kernel
-// are seen); order[rank] = i.  One warp, every lane; ends with __syncwarp, after
-// which every lane of the warp may read order[] (with L2 loads).
-__device__ __forceinline__ void rank_dense_tile(const int* keys, int c, int* order) {
-    for (int i = (int)(threadIdx.x & 31); i < c; i += 32) {
-        const int ki = __ldcg(&keys[i]);
-        int r = 0;
-        for (int j = 0; j < c; ++j) r += __ldcg(&keys[j]) < ki;
-        order[r] = i;
+// in shared memory: order[r] = the slot i (0 <= i < c) whose key (original site
+// index, keys[i] >= 0, all distinct) is the r-th smallest.  A stable LSD radix
+// sort of the slots by key, 8-bit digits, as many passes as the largest key
+// has bytes, by one warp: O(c) work per pass whatever the tile's size (a bad
+// frame can put every site into one tile).  tmp holds c more ints of scratch;
+// hist is 256 ints of the warp's own shared memory.  Global buffers are
+// written and re-read by the same warp, with L2 loads and __syncwarp between
+// the phases.  Every lane of the warp must call it; it ends with __syncwarp,
+// after which every lane may read order[] (with L2 loads).
+__device__ __forceinline__ void rank_dense_tile(const int* keys, int c, int* order, int* tmp, int* hist) {
+    const int lane = (int)(threadIdx.x & 31);
+    int kmax = 0;
+    for (int i = lane; i < c; i += 32) kmax = max(kmax, __ldcg(&keys[i]));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    int npass = 1;
+    while (npass < 4 && (kmax >> (8 * npass)) != 0) ++npass;
+    // the last pass must land in order[]: the first writes order[] for an odd
+    // number of passes, tmp[] for an even one
+    int* src = nullptr;
+    int* dst = (npass & 1) ? order : tmp;
+    for (int pass = 0; pass < npass; ++pass) {
+        const int shift = 8 * pass;
+        for (int b = lane; b < 256; b += 32) hist[b] = 0;
+        __syncwarp();
+        for (int i = lane; i < c; i += 32) {
+            const int slot = src ? __ldcg(&src[i]) : i;
+            atomicAdd(&hist[(__ldcg(&keys[slot]) >> shift) & 255], 1);
+        }
+        __syncwarp();
+        {  // exclusive scan of the 256 counts, eight consecutive bins a lane
+            int v[8], sum = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                v[k] = hist[8 * lane + k];
+                sum += v[k];
+            }
+            int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int run = incl - sum;
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                hist[8 * lane + k] = run;
+                run += v[k];
+            }
+        }
+        __syncwarp();
+        // stable scatter: chunks of 32 in order, lanes of a chunk in order
+        for (int base = 0; base < c; base += 32) {
+            const int i = base + lane;
+            const bool act = i < c;
+            const int slot = act ? (src ? __ldcg(&src[i]) : i) : 0;
+            const int d = act ? ((__ldcg(&keys[slot]) >> shift) & 255) : 256 + lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            const int leader = __ffs(peers) - 1;
+            int b0 = 0;
+            if (act) b0 = hist[d];
+            __syncwarp();
+            if (act) {
+                __stcg(&dst[b0 + rank], slot);
+                if (lane == leader) hist[d] = b0 + __popc(peers);
+            }
+            __syncwarp();
+        }
+        src = dst;
+        dst = (dst == order) ? tmp : order;
     }
     __syncwarp();
 }
@@ -183,26 +244,31 @@ template <typename T>
 cudaError_t launch_scatter(cudaStream_t s, const Geo& g, int n, const int* tile_of, const int* slot_of,
                            const int* tile_start, const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell,
                            int* sorig, T* swt);
-// order: n ints of scratch in tile order (the binning's slot array, dead once
-// the scatter has run), used for tiles denser than the shared-memory ranking
+// order, tmp: n ints of scratch each in tile order (the binning's slot and
+// tile arrays, dead once the scatter has run), used to rank tiles denser than
+// the shared-memory ranking
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, T* patch, int* order);
+                          const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp);
 template <typename T>
 cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
                         T scale, T* rho);
 template <typename T, typename Out>
 cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
                           const int* scell, const int* sorig, const T* swt, const T* fields, const FieldLayout& fl,
-                          const void* tmap, double prefactor, Out* forces, int* status);
+                          const void* tmap, double prefactor, Out* forces, int* status, long long wait_limit);
 void upload_bspline_coefficients();
 // full-tile fast paths (cudaErrorNotSupported when the order/tile has none)
 template <typename T>
 cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
-                               const int* sorig, const T* swt, T* patch, int* order);
+                               const int* sorig, const T* swt, T* patch, int* order, int* tmp);
+// wait_limit: spins of the first bounded wait for a tile's field copy (0: it
+// runs out at once, the copy is then waited for once more before the block
+// returns; a test of the timeout path)
 template <typename T, typename Out>
 cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell, const int* sorig,
-                              const T* swt, const void* tmap, double prefactor, Out* forces, int* status);
+                              const T* swt, const void* tmap, double prefactor, Out* forces, int* status,
+                              long long wait_limit);
 
 // fft_kernels.cu
 template <typename T>

@@ -19,10 +19,12 @@
 // first time the entry point runs on a device (with that device current);
 // in host code the array's name is only a host-side stand-in and must never
 // be passed to a kernel.  That first call also uploads the B-spline
-// coefficient table, so it should come before any stream capture.
+// coefficient table, so it should come before any stream capture.  Each call
+// puts only memsets and kernel launches on the caller's stream: the fold's
+// cover lists are built by a kernel inside the scratch array, so nothing is
+// copied from host memory.
 #include <cmath>
 #include <mutex>
-#include <vector>
 
 #include "internal.cuh"
 
@@ -61,6 +63,71 @@ int scratch_address(void** out) {
     }
     *out = g_scratch_addr[dev];
     return PPPM_OK;
+}
+
+// The fold's cover lists, the same lists a plan builds on the host: for axis d
+// and mesh index m, the pairs (tile t, patch coordinate c) with
+// (t T + kmin + c) mod N_d = m, ordered by t and then c; off[d nmax1 + m] is
+// where list m starts in ent (one running index over the three axes) and
+// off[d nmax1 + N_d] where axis d ends.  One block: each thread counts the
+// lists of its indices, a block-wide exclusive scan turns the counts into
+// offsets, then each thread writes its lists.
+constexpr int kCoverThreads = 1024;
+
+__device__ int cover_entries(const Geo& g, int d, int m, int2* out) {
+    const int N = g.N[d], T = g.T;
+    int k = 0;
+    for (int t = 0; t < g.nt[d]; ++t) {
+        int cells = N - t * T;
+        if (cells > g.Tt[d]) cells = g.Tt[d];
+        const int e = cells + g.order - 1;
+        int c = (m - t * T - g.kmin) % N;
+        if (c < 0) c += N;
+        for (; c < e; c += N) {
+            if (out) out[k] = make_int2(t, c);
+            ++k;
+        }
+    }
+    return k;
+}
+
+__global__ void __launch_bounds__(kCoverThreads) k_cover_lists(Geo g, int nmax1, int* off, int2* ent) {
+    __shared__ int wsum[kCoverThreads / 32];
+    const int total = 3 * nmax1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int chunk = (total + kCoverThreads - 1) / kCoverThreads;
+    const int b = tid * chunk, e = min(b + chunk, total);
+    int sum = 0;
+    for (int i = b; i < e; ++i) {
+        const int d = i / nmax1, m = i - d * nmax1;
+        const int c = m < g.N[d] ? cover_entries(g, d, m, nullptr) : 0;
+        off[i] = c;
+        sum += c;
+    }
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += v;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int run = (warp > 0 ? wsum[warp - 1] : 0) + incl - sum;
+    for (int i = b; i < e; ++i) {
+        const int c = off[i];
+        off[i] = run;
+        const int d = i / nmax1, m = i - d * nmax1;
+        if (m < g.N[d]) cover_entries(g, d, m, ent + run);
+        run += c;
+    }
 }
 
 }  // namespace
@@ -104,31 +171,19 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     }
     g.Pz = g.E[2] | 1;
 
-    // fold cover lists (host), copied into the scratch array below
+    // fold cover lists: built on the device, into the scratch array, by k_cover_lists
     int nmax = mesh[0];
     if (mesh[1] > nmax) nmax = mesh[1];
     if (mesh[2] > nmax) nmax = mesh[2];
     const int nmax1 = nmax + 1;
-    std::vector<int> off(3 * (size_t)nmax1, 0);
-    std::vector<int2> ent;
-    for (int d = 0; d < 3; ++d) {
-        const int N = g.N[d];
-        std::vector<std::vector<int2>> lists(N);
+    // entries per axis: every tile contributes (its cells + p - 1) pairs
+    size_t nent = 0;
+    for (int d = 0; d < 3; ++d)
         for (int t = 0; t < g.nt[d]; ++t) {
-            int cells = N - t * T;
+            int cells = g.N[d] - t * T;
             if (cells > g.Tt[d]) cells = g.Tt[d];
-            for (int c = 0; c < cells + order - 1; ++c) {
-                int m = (t * T + g.kmin + c) % N;
-                if (m < 0) m += N;
-                lists[m].push_back(make_int2(t, c));
-            }
+            nent += (size_t)(cells + order - 1);
         }
-        for (int m = 0; m < N; ++m) {
-            off[(size_t)d * nmax1 + m] = (int)ent.size();
-            for (const int2& e : lists[m]) ent.push_back(e);
-        }
-        off[(size_t)d * nmax1 + N] = (int)ent.size();
-    }
 
     // carve the scratch array
     const size_t nn = (size_t)n;
@@ -150,8 +205,8 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     const size_t o_sorig = take(sizeof(int) * nn);
     const size_t o_swt = take(sizeof(float) * wstride(order) * nn);
     const size_t o_patch = take(sizeof(float) * psz * g.ntiles);
-    const size_t o_off = take(sizeof(int) * off.size());
-    const size_t o_ent = take(sizeof(int2) * ent.size());
+    const size_t o_off = take(sizeof(int) * 3 * (size_t)nmax1);
+    const size_t o_ent = take(sizeof(int2) * nent);
     const size_t o_status = take(sizeof(int));
     if (at > kNoAllocScratchBytes) return PPPM_ERR_TOO_LARGE;
     unsigned char* b = static_cast<unsigned char*>(base);
@@ -176,14 +231,14 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     do {                                                \
         if ((x) != cudaSuccess) return PPPM_ERR_CUDA;   \
     } while (0)
-    NA_CK(cudaMemcpyAsync(cov_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
-    NA_CK(cudaMemcpyAsync(cov_ent, ent.data(), sizeof(int2) * ent.size(), cudaMemcpyHostToDevice, s));
+    k_cover_lists<<<1, kCoverThreads, 0, s>>>(g, nmax1, cov_off, cov_ent);
+    NA_CK(cudaGetLastError());
     NA_CK(cudaMemsetAsync(tile_count, 0, sizeof(int) * g.ntiles, s));
     NA_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
     NA_CK((launch_bin<float, double>(s, g, pos, q, (int)n, tile_count, tile_of, slot_of, rec, cell, status)));
     NA_CK(launch_scan(s, tile_count, g.ntiles, tile_start));
     NA_CK(launch_scatter<float>(s, g, (int)n, tile_of, slot_of, tile_start, rec, cell, srec, scell, sorig, swt));
-    NA_CK(launch_spread<float>(s, g, tile_start, srec, scell, sorig, swt, patch, slot_of));
+    NA_CK(launch_spread<float>(s, g, tile_start, srec, scell, sorig, swt, patch, slot_of, tile_of));
     NA_CK(launch_fold<float>(s, g, patch, cov_off, cov_ent, (float)(1.0 / h3), rho));
 #undef NA_CK
     return PPPM_OK;

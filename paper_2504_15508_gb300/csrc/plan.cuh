@@ -31,6 +31,7 @@ struct pppm_plan {
     bool potential = false;  // also produce the mesh potential (padded, planar: phi)
     void* phi = nullptr;     // padded potential mesh, Xp x Yp x Zp (allocated on demand)
     bool pdl = true;         // programmatic dependent launch between the kernels of a solve
+    long long wait_limit = 1ll << 26;  // polls of the gather's bounded wait for its tile copy
     CUtensorMap fmap;        // 4D TMA descriptor of the padded fields
     bool fmap_ok = false;
     void* partial = nullptr;

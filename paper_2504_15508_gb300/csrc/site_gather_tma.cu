@@ -16,12 +16,14 @@ constexpr int kGatherWarps = 4;
 // tile's stencil patch is the box starting at padded coordinates
 // (4 tz T, ty T, tx T), fetched by a single cp.async.bulk.tensor
 // issued by one thread and waited on through an mbarrier.  The wait is
-// bounded: if it runs out the block records PPPM_ERR_TIMEOUT in the status
-// word (bit 2) and returns without touching the patch.
+// bounded (the plan's wait limit, 2^26 polls by default): if it runs out the
+// block records PPPM_ERR_TIMEOUT in the status word (bit 2), waits once more,
+// bounded by kTmaSpinLimit, so that a copy still in flight lands before the
+// block exits, and returns without touching the patch.
 constexpr long long kTmaSpinLimit = 1ll << 26;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
-    for (long long it = 0; it < kTmaSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 6)  // shared memory holds 
 k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
              const int* __restrict__ sorig, const T* __restrict__ swt, const __grid_constant__ CUtensorMap tmap,
              const __grid_constant__ LaneRows lanes, double prefactor, Out* __restrict__ forces,
-             int* __restrict__ status) {
+             int* __restrict__ status, long long wait_limit) {
     pdl_enter();
     // TMA box: [x][y][z][component], z extent EZ points, 4 components a point
     constexpr int E = TILE + P - 1, EZ = gather_box_z(P, TILE), PLANE = E * EZ, PSIZE = E * PLANE;
@@ -182,9 +184,9 @@ k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ 
         }
     };
     fetch(warp * 8);
-    if (!mbar_wait_bounded(mbar_s, 0)) {
+    if (!mbar_wait_bounded(mbar_s, 0, wait_limit)) {
         if (threadIdx.x == 0) atomicOr(status, 2);
-        mbar_wait_bounded(mbar_s, 0);  // give the copy in flight a second bounded chance to land
+        mbar_wait_bounded(mbar_s, 0, kTmaSpinLimit);  // give the copy in flight a second bounded chance to land
         return;
     }
     for (int b = warp * 8; b < nsites; b += kGatherWarps * 8) {
@@ -257,7 +259,7 @@ k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ 
 template <typename T, int P, int TILE, typename Out>
 static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
                               const int* sorig, const T* swt, const void* tmap, double prefactor, Out* forces,
-                              int* status) {
+                              int* status, long long wait_limit) {
     constexpr int E = TILE + P - 1, EZ = gather_box_z(P, TILE), WSP = wstride(P) + 4;
     const size_t smem = (4 * (size_t)E * E * EZ * sizeof(T) + 127) / 128 * 128 +
                         (kGatherWarps * 8 * WSP * sizeof(T) + 31) / 32 * 32 + kGatherWarps * 8 * 2 * sizeof(int) +
@@ -267,7 +269,8 @@ static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_star
     if (e != cudaSuccess) return e;
     static const LaneRows lanes = order_rows(P, EZ);
     return launch_k(k_gather_tma<T, P, TILE, Out>, dim3(g.ntiles), dim3(kGatherWarps * 32), smem, s, g, tile_start,
-                    scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), lanes, prefactor, forces, status);
+                    scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), lanes, prefactor, forces, status,
+                    wait_limit);
 }
 
 #define PPPM_FAST_SWITCH_G(FN, T_, O_, ...)                                                       \
@@ -289,14 +292,16 @@ static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_star
 
 template <typename T, typename Out>
 cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell, const int* sorig,
-                              const T* swt, const void* tmap, double prefactor, Out* forces, int* status) {
-    PPPM_FAST_SWITCH_G(gather_tma, T, Out, s, g, tile_start, scell, sorig, swt, tmap, prefactor, forces, status)
+                              const T* swt, const void* tmap, double prefactor, Out* forces, int* status,
+                              long long wait_limit) {
+    PPPM_FAST_SWITCH_G(gather_tma, T, Out, s, g, tile_start, scell, sorig, swt, tmap, prefactor, forces, status,
+                       wait_limit)
     return cudaErrorNotSupported;
 }
 
 #define PPPM_INST_G(T, O)                                                                                       \
     template cudaError_t launch_gather_tma<T, O>(cudaStream_t, const Geo&, const int*, const int*, const int*,   \
-                                                 const T*, const void*, double, O*, int*);
+                                                 const T*, const void*, double, O*, int*, long long);
 PPPM_INST_G(float, float)
 PPPM_INST_G(float, double)
 PPPM_INST_G(double, float)

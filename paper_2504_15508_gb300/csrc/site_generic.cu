@@ -32,7 +32,8 @@ constexpr int kSpreadCap = 512;
 template <typename T, int P>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
-         const int* __restrict__ scell, const int* __restrict__ sorig, T* __restrict__ patch, int* order) {
+         const int* __restrict__ scell, const int* __restrict__ sorig, T* __restrict__ patch, int* order,
+         int* tmp) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -68,7 +69,7 @@ k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
     }
     __syncwarp();
     const bool dense = c > kSpreadCap;  // ranked from global memory instead
-    if (dense) rank_dense_tile(sorig + s0, c, order + s0);
+    if (dense) rank_dense_tile(sorig + s0, c, order + s0, tmp + s0, reinterpret_cast<int*>(keys));
 
     // lane -> stencil rows (iy, iz); orders above 5 have more rows than lanes
     constexpr int NR = (P * P + 31) / 32;
@@ -111,31 +112,31 @@ k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
 
 template <typename T, int P>
 static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                            const int* scell, const int* sorig, T* patch, int* order) {
+                            const int* scell, const int* sorig, T* patch, int* order, int* tmp) {
     const int psize = g.E[0] * g.E[1] * g.Pz;
     size_t smem = (size_t)kSpreadWarps * psize * sizeof(T) + (size_t)kSpreadWarps * kSpreadCap * sizeof(int2);
     cudaError_t e = cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
     return launch_k(k_spread<T, P>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tile_start, srec, scell, sorig,
-                    patch, order);
+                    patch, order, tmp);
 }
 
 
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, T* patch, int* order) {
+                          const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp) {
     if (fast_tiles(g)) {
-        cudaError_t e = launch_spread_fast<T>(s, g, tile_start, scell, sorig, swt, patch, order);
+        cudaError_t e = launch_spread_fast<T>(s, g, tile_start, scell, sorig, swt, patch, order, tmp);
         if (e != cudaErrorNotSupported) return e;
     }
     switch (g.order) {
-        case 2: return spread_p<T, 2>(s, g, tile_start, srec, scell, sorig, patch, order);
-        case 3: return spread_p<T, 3>(s, g, tile_start, srec, scell, sorig, patch, order);
-        case 4: return spread_p<T, 4>(s, g, tile_start, srec, scell, sorig, patch, order);
-        case 5: return spread_p<T, 5>(s, g, tile_start, srec, scell, sorig, patch, order);
-        case 6: return spread_p<T, 6>(s, g, tile_start, srec, scell, sorig, patch, order);
-        case 7: return spread_p<T, 7>(s, g, tile_start, srec, scell, sorig, patch, order);
+        case 2: return spread_p<T, 2>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
+        case 3: return spread_p<T, 3>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
+        case 4: return spread_p<T, 4>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
+        case 5: return spread_p<T, 5>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
+        case 6: return spread_p<T, 6>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
+        case 7: return spread_p<T, 7>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
     }
     return cudaErrorInvalidValue;
 }
@@ -312,9 +313,10 @@ static cudaError_t gather_p(cudaStream_t s, const Geo& g, const int* tile_start,
 template <typename T, typename Out>
 cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
                           const int* scell, const int* sorig, const T* swt, const T* fields, const FieldLayout& fl,
-                          const void* tmap, double prefactor, Out* forces, int* status) {
+                          const void* tmap, double prefactor, Out* forces, int* status, long long wait_limit) {
     if (fast_tiles(g) && fl.padded && tmap) {
-        cudaError_t e = launch_gather_tma<T, Out>(s, g, tile_start, scell, sorig, swt, tmap, prefactor, forces, status);
+        cudaError_t e = launch_gather_tma<T, Out>(s, g, tile_start, scell, sorig, swt, tmap, prefactor, forces, status,
+                                                  wait_limit);
         if (e != cudaErrorNotSupported) return e;
     }
     switch (g.order) {
@@ -330,14 +332,14 @@ cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, c
 
 #define PPPM_INST_T(T)                                                                                          \
     template cudaError_t launch_spread<T>(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*,       \
-                                          const int*, const T*, T*, int*);                                       \
+                                          const int*, const T*, T*, int*, int*);                                 \
     template cudaError_t launch_fold<T>(cudaStream_t, const Geo&, const T*, const int*, const int2*, T, T*);
 PPPM_INST_T(float)
 PPPM_INST_T(double)
 #define PPPM_INST_TI(T, I)                                                                                       \
     template cudaError_t launch_gather<T, I>(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*,     \
                                              const int*, const T*, const T*, const FieldLayout&, const void*,    \
-                                             double, I*, int*);
+                                             double, I*, int*, long long);
 PPPM_INST_TI(float, float)
 PPPM_INST_TI(float, double)
 PPPM_INST_TI(double, float)

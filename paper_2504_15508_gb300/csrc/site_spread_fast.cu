@@ -52,7 +52,8 @@ struct __align__(16) SpreadWarpSmem {  // 16-byte aligned: staged rows take vect
 template <typename T, int P, int TILE>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
-              const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch, int* order) {
+              const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch, int* order,
+              int* tmp) {
     pdl_enter();
     typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
     typedef typename Vec16T<T>::t V;
@@ -90,7 +91,7 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
     }
     __syncwarp();
     const bool dense = c > kFastCap;  // ranked from global memory instead
-    if (dense) rank_dense_tile(sorig + s0, c, order + s0);
+    if (dense) rank_dense_tile(sorig + s0, c, order + s0, tmp + s0, W.u.keys);
     // lane -> stencil rows (iy, iz); orders above 5 have more rows than lanes
     constexpr int NR = (P * P + 31) / 32;
     int roff[NR], riy[NR], riz[NR];
@@ -162,14 +163,14 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
 
 template <typename T, int P, int TILE>
 static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
-                               const int* sorig, const T* swt, T* patch, int* order) {
+                               const int* sorig, const T* swt, T* patch, int* order, int* tmp) {
     const size_t smem = kSpreadWarps * sizeof(SpreadWarpSmem<T, P, TILE>);
     cudaError_t e = cudaFuncSetAttribute(k_spread_fast<T, P, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
     return launch_k(k_spread_fast<T, P, TILE>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tile_start, scell,
-                    sorig, swt, patch, order);
+                    sorig, swt, patch, order, tmp);
 }
 
 
@@ -192,14 +193,14 @@ static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_sta
 
 template <typename T>
 cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
-                               const int* sorig, const T* swt, T* patch, int* order) {
-    PPPM_FAST_SWITCH(spread_fast, T, s, g, tile_start, scell, sorig, swt, patch, order)
+                               const int* sorig, const T* swt, T* patch, int* order, int* tmp) {
+    PPPM_FAST_SWITCH(spread_fast, T, s, g, tile_start, scell, sorig, swt, patch, order, tmp)
     return cudaErrorNotSupported;
 }
 
 template cudaError_t launch_spread_fast<float>(cudaStream_t, const Geo&, const int*, const int*, const int*,
-                                               const float*, float*, int*);
+                                               const float*, float*, int*, int*);
 template cudaError_t launch_spread_fast<double>(cudaStream_t, const Geo&, const int*, const int*, const int*,
-                                                const double*, double*, int*);
+                                                const double*, double*, int*, int*);
 
 }  // namespace pppm

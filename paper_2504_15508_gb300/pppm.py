@@ -85,6 +85,11 @@ class Plan:
         (default on; off may overlap better with concurrent work)."""
         N.check(self._lib.pppm_set_dependent_launch(self._h, int(bool(on))), "pppm_set_dependent_launch")
 
+    def set_wait_limit(self, spins: int):
+        """Polls of the gather's bounded wait for its tile copies (0: every
+        first wait runs out, the call reports PPPM_ERR_TIMEOUT)."""
+        N.check(self._lib.pppm_set_wait_limit(self._h, int(spins)), "pppm_set_wait_limit")
+
     def reserve(self, n: int):
         N.check(self._lib.pppm_reserve(self._h, int(n)), "pppm_reserve")
 
@@ -281,6 +286,11 @@ class BatchPlan:
 
     def set(self, prefactor: float = 1.0, tile: int = 0, spin_limit: int = 1 << 24):
         N.check(self._lib.pppm_batch_set(self._h, float(prefactor), int(tile), int(spin_limit)), "pppm_batch_set")
+
+    def set_wait_probe(self, on: bool):
+        """When on, the first box's scan waits for one binning item more
+        than exist, so that bounded wait must run out."""
+        N.check(self._lib.pppm_batch_set_wait_probe(self._h, int(bool(on))), "pppm_batch_set_wait_probe")
 
     def set_dft(self, max_len: int):
         """Lines of length <= max_len (0..18, 0 = off) take the tensor-core

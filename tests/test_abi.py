@@ -114,3 +114,8 @@ def test_batch_set_dft_validates(pppm_lib):
 
 def test_batch_set_quantized_validates(pppm_lib):
     assert pppm_lib.pppm_batch_set_quantized(None, 4, 1e7) == N.PPPM_ERR_INVALID_ARG
+
+
+def test_wait_hooks_validate_arguments(pppm_lib):
+    assert pppm_lib.pppm_set_wait_limit(None, 10) == N.PPPM_ERR_INVALID_ARG
+    assert pppm_lib.pppm_batch_set_wait_probe(None, 1) == N.PPPM_ERR_INVALID_ARG

@@ -38,3 +38,13 @@ def test_recorded_traffic_names_real_kernels():
         # the sites or mesh, at most a few times the algorithmic bytes
         alg = bench.algorithmic_bytes(N_SITES, mesh)[kernel]
         assert 0.2 * alg < traffic < 4 * alg, (kernel, mesh, traffic, alg)
+
+
+def test_oracle_pool_on_host_cores():
+    """The CPU baseline's process pool (spawned workers, one thread each)
+    evaluates the frames it is given: two workers, one timed round on the
+    64-water box."""
+    from workloads.water import make_workload
+    wb, w = make_workload("water64")
+    val, rates, workers = bench.oracle_all_cores(wb, w, lambda k: wb.pos + 0.01 * k, rounds=1, workers=2)
+    assert workers == 2 and len(rates) == 1 and val > 0

@@ -75,8 +75,11 @@ def test_batched_graph_replay_and_single_box_equality(cuda_device, pppm_lib):
 
 
 def test_batched_bounded_wait_times_out_cleanly(cuda_device, pppm_lib):
-    """With a spin limit of one iteration the stage waits run out: the launch
-    still ends, reports PPPM_ERR_TIMEOUT, and the next normal run is correct."""
+    """The wait probe makes box 0's scan wait for one binning item more than
+    exist, so that bounded wait must run out: the launch still ends (every
+    other stage's wait is satisfied or skipped), the status is
+    PPPM_ERR_TIMEOUT, the other boxes are still correct, and the next run
+    without the probe is correct for every box."""
     from paper_2504_15508_gb300 import _native as N
     from paper_2504_15508_gb300.pppm import BatchPlan
     specs, boxes, pos, q, offs = _make_batch(4, seed=9)
@@ -84,17 +87,27 @@ def test_batched_bounded_wait_times_out_cleanly(cuda_device, pppm_lib):
     tp = torch.tensor(pos, device=cuda_device)
     tq = torch.tensor(q, device=cuda_device)
     to = torch.tensor(offs, device=cuda_device)
-    bp.set(tile=8, spin_limit=1)
-    bp.compute(tp, tq, to)
-    assert bp.status() in (N.PPPM_ERR_TIMEOUT, N.PPPM_OK)
+    refs = [OraclePPPM(wb.box, bp.meshes[b], 5, 0.4).compute(pos[offs[b]:offs[b + 1]].astype(np.float64),
+                                                              q[offs[b]:offs[b + 1]].astype(np.float64))
+            for b, wb in enumerate(boxes)]
+    bp.set(tile=8, spin_limit=1000)
+    bp.set_wait_probe(True)
+    e, f, v = bp.compute(tp, tq, to)
+    torch.cuda.synchronize()
+    assert bp.status() == N.PPPM_ERR_TIMEOUT
+    assert bp.status() == N.PPPM_OK  # read and cleared
+    for b in range(1, len(boxes)):
+        sl = slice(offs[b], offs[b + 1])
+        assert _rel(f[sl].cpu().numpy(), refs[b]["forces"]) <= 1e-5, b
+    bp.set_wait_probe(False)
     bp.set(tile=8, spin_limit=1 << 24)
     e, f, v = bp.compute(tp, tq, to)
     torch.cuda.synchronize()
     assert bp.status() == N.PPPM_OK
-    wb = boxes[0]
-    sl = slice(offs[0], offs[1])
-    ref = OraclePPPM(wb.box, bp.meshes[0], 5, 0.4).compute(pos[sl].astype(np.float64), q[sl].astype(np.float64))
-    assert _rel(f[sl].cpu().numpy(), ref["forces"]) <= 1e-5
+    for b in range(len(boxes)):
+        sl = slice(offs[b], offs[b + 1])
+        assert _rel(f[sl].cpu().numpy(), refs[b]["forces"]) <= 1e-5, b
+        assert abs(e[b].item() - refs[b]["energy"]) <= 1e-6 * abs(refs[b]["energy"]), b
 
 
 @pytest.mark.parametrize("order,meshes", [
@@ -162,3 +175,56 @@ def test_batched_dense_tiles_are_deterministic(cuda_device, pppm_lib):
     ref = OraclePPPM(box, (12, 12, 12), 5, 0.4).compute(pos.astype(np.float64), q.astype(np.float64))
     assert _rel(r1[1].cpu().numpy(), ref["forces"]) <= 1e-5
     assert abs(r1[0].item() - ref["energy"]) <= 1e-6 * abs(ref["energy"])
+
+
+_FULL = {}
+
+
+def _full_batch():
+    """The 96-box batch as the batched workload states it (seed 5, 64 to 8,192
+    molecules log-uniformly, 29.9 A^3 a molecule, meshes at <= 1.2 A: 12^3 to
+    54^3), with the oracle's result for every box, computed once."""
+    if not _FULL:
+        specs = batched_boxes(nbox=96, seed=5)
+        boxes = [make_water(s["n_mol"], s["L"], s["seed"]) for s in specs]
+        pos = np.concatenate([b.pos for b in boxes]).astype(np.float32)
+        q = np.concatenate([b.q for b in boxes]).astype(np.float32)
+        offs = np.concatenate([[0], np.cumsum([b.n for b in boxes])]).astype(np.int64)
+        refs = []
+        for b, (s, wb) in enumerate(zip(specs, boxes)):
+            sl = slice(offs[b], offs[b + 1])
+            refs.append(OraclePPPM(wb.box, s["mesh"], 5, 0.4).compute(pos[sl].astype(np.float64),
+                                                                       q[sl].astype(np.float64)))
+        _FULL.update(specs=specs, boxes=boxes, pos=pos, q=q, offs=offs, refs=refs)
+    return _FULL
+
+
+@pytest.mark.parametrize("tile,dft", [(4, 0), (8, 0), (4, 18), (8, 18)])
+def test_full_batched96_matches_oracle_per_box(cuda_device, pppm_lib, tile, dft):
+    """All 96 boxes in one launch, the largest (8,192-molecule class) on 54^3
+    meshes, so that the shared-memory layout is sized by the 54-point lines;
+    every box against the FP64 oracle: force RMS 1e-5, energy 1e-6, virial
+    1e-5 relative, for both tile edges and with and without the tensor-core
+    DFT of the short lines."""
+    from paper_2504_15508_gb300.pppm import BatchPlan
+    F = _full_batch()
+    specs, boxes, pos, q, offs, refs = F["specs"], F["boxes"], F["pos"], F["q"], F["offs"], F["refs"]
+    assert max(s["mesh"][0] for s in specs) == 54 and min(s["mesh"][0] for s in specs) == 12
+    bp = BatchPlan(np.array([[s["L"]] * 3 for s in specs]), None, order=5, beta=0.4, tile=tile)
+    bp.set_dft(dft)
+    assert [tuple(m) for m in bp.meshes] == [tuple(s["mesh"]) for s in specs]
+    e, f, v = bp.compute(torch.tensor(pos, device=cuda_device), torch.tensor(q, device=cuda_device),
+                         torch.tensor(offs, device=cuda_device))
+    torch.cuda.synchronize()
+    assert bp.status() == 0 and bp.tile == tile
+    e, f, v = e.cpu().numpy(), f.cpu().numpy(), v.cpu().numpy()
+    worst = (0.0, 0.0, 0.0)
+    for b in range(len(boxes)):
+        sl = slice(offs[b], offs[b + 1])
+        ferr = _rel(f[sl], refs[b]["forces"])
+        eerr = abs(e[b] - refs[b]["energy"]) / abs(refs[b]["energy"])
+        verr = _rel(v[b], refs[b]["virial"])
+        worst = tuple(max(a, c) for a, c in zip(worst, (ferr, eerr, verr)))
+        assert ferr <= 1e-5 and eerr <= 1e-6 and verr <= 1e-5, (b, specs[b]["mesh"], ferr, eerr, verr)
+    print(f"batched96 tile {tile} dft {dft}: worst force {worst[0]:.2e} energy {worst[1]:.2e} "
+          f"virial {worst[2]:.2e}")

@@ -1,8 +1,11 @@
 """Running the force evaluation concurrently with other work on another
-stream (the long/short-range overlap) leaves its results bitwise unchanged."""
+stream (the long/short-range overlap) leaves its results bitwise unchanged,
+and those results match the FP64 oracle within the FP32 tolerances."""
+import numpy as np
 import pytest
 import torch
 
+from oracle.pppm import OraclePPPM
 from workloads.water import make_workload
 
 pytestmark = pytest.mark.gpu
@@ -29,3 +32,10 @@ def test_concurrent_streams_give_identical_results(cuda_device):
     assert torch.equal(out[1], f0) and torch.equal(out[0], e0) and torch.equal(g.out[1], f0)
     assert torch.isfinite(y).all()
     g.close()
+    # the overlapped result itself against the oracle (force RMS 1e-5, energy and virial)
+    ref = OraclePPPM(wb.box, w["mesh"], w["order"], w["beta"]).compute(pos.double().cpu().numpy(),
+                                                                      q.double().cpu().numpy())
+    f = out[1].double().cpu().numpy()
+    assert np.linalg.norm(f - ref["forces"]) <= 1e-5 * np.linalg.norm(ref["forces"])
+    assert abs(out[0].item() - ref["energy"]) <= 1e-6 * abs(ref["energy"])
+    assert np.linalg.norm(out[2].cpu().numpy() - ref["virial"]) <= 1e-5 * np.linalg.norm(ref["virial"])

@@ -277,3 +277,53 @@ def test_prefactor(cuda_device, pppm_lib):
     ref = OraclePPPM(wb.box, w["mesh"], w["order"], w["beta"], prefactor=14.399645).compute(wb.pos, wb.q)
     tp, tq, _, _ = _sites(wb.pos, wb.q, "fp64", cuda_device)
     _check(plan.compute(tp, tq), ref, "fp64", "prefactor")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("mesh", [(36, 36, 36), (30, 30, 30)])
+def test_one_tile_holds_every_site(cuda_device, pppm_lib, prec, mesh):
+    """60,000 charges inside one mesh tile (a clustered or corrupt frame): the
+    canonical order of that tile comes from a radix sort whose cost grows
+    linearly with the tile, so the call ends quickly (a pairwise ranking would
+    take ~1e8 dependent loads a lane).  36^3 runs the full-tile kernels with
+    tile edge 4, 30^3 the generic ones (30 is not a multiple of 4).  Two runs
+    agree bitwise and match the oracle."""
+    import time
+    box = np.array([12.0, 12.0, 12.0])
+    rng = np.random.default_rng(77)
+    n = 60000
+    # u = x N / L stays in [0.5, 3.2) cells: base points 1..3, all in tile 0
+    pos = 0.5 * box / mesh[0] + rng.random((n, 3)) * (2.7 * box / mesh[0])
+    q = rng.normal(size=n)
+    tp, tq, pos_r, q_r = _sites(pos, q, prec, cuda_device)
+    plan = _plan(box, mesh, 5, 0.4, precision=prec)
+    r1 = [t.clone() for t in plan.compute(tp, tq)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r2 = [t.clone() for t in plan.compute(tp, tq)]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    assert dt < 2.0, dt
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)
+    ref = OraclePPPM(box, mesh, 5, 0.4).compute(pos_r, q_r)
+    _check(r1, ref, prec, f"one tile {mesh}")
+
+
+def test_gather_wait_runs_out_cleanly(cuda_device, pppm_lib):
+    """With a wait limit of 0 polls every tile's first wait for its field copy
+    runs out: the call reports PPPM_ERR_TIMEOUT (after the block has waited
+    for its copy once more, bounded), the device stays usable, and the next
+    call with the default limit is correct."""
+    from paper_2504_15508_gb300 import _native as N
+    wb, w = make_workload("water4096")
+    tp, tq, pos_r, q_r = _sites(wb.pos, wb.q, "fp32", cuda_device)
+    plan = _plan(wb.box, w["mesh"], w["order"], w["beta"], precision="fp32")
+    plan.set_wait_limit(0)
+    plan.compute(tp, tq)
+    assert plan.status() == N.PPPM_ERR_TIMEOUT
+    assert plan.status() == N.PPPM_OK  # cleared
+    plan.set_wait_limit(1 << 26)
+    ref = OraclePPPM(wb.box, w["mesh"], w["order"], w["beta"]).compute(pos_r, q_r)
+    _check(plan.compute(tp, tq), ref, "fp32", "after the timeout")
+    assert plan.status() == N.PPPM_OK
