@@ -1,15 +1,24 @@
 """FP64 CPU reference of the coarse-mesh correction network (test infrastructure only).
 
-The network maps per-site features (27 mesh-potential samples around the site,
-a one-hot site type and the site's position inside its mesh cell, padded to 48
-inputs) to 3 outputs through two tanh hidden layers of 64 units:
+The network maps per-site features to 3 outputs through two tanh hidden
+layers of 64 units.  Two feature sets exist:
+
+* "stated": the 27 mesh-potential samples around the site and a one-hot site
+  type, 30 inputs padded with two zeros to 32 (the learned-correction form as
+  stated: local mesh-potential samples plus the site type);
+* "cell" (the default): the same 30, then the site's position inside its mesh
+  cell (sin, cos of 2 pi u per axis), padded with twelve zeros to 48.
+
+The network, for either input width n_in:
 
     h1 = tanh(W1 x + b1),  h2 = tanh(W2 h1 + b2),  y = W3 h2 + b3,
     loss = mean over sites of sum_c (y_c - t_c)^2.
 
 Weights are rounded to BF16 before use (the GPU stores BF16 copies of FP32
 master weights); everything else here is FP64.  The parameter vector is laid
-out as [W1 (64x48, row-major), b1 (64), W2 (64x64), b2 (64), W3 (3x64), b3 (3)].
+out as [W1 (64 x n_in, row-major), b1 (64), W2 (64x64), b2 (64), W3 (3x64),
+b3 (3)]: 7,491 values at n_in = 48, 6,467 at n_in = 32; the width is read off
+the vector's length.
 With ``act_bf16`` the hidden activations are rounded to BF16 as well before
 they enter the next layer: that is how tensor-core inference consumes them
 (BF16 operands, FP32 accumulation); training keeps them unrounded.
@@ -17,12 +26,12 @@ they enter the next layer: that is how tensor-core inference consumes them
 Features (``features``): for each site, the coarse mesh potential phi
 B-spline-interpolated at the 27 points r_i + h (a, b, c), a, b, c in
 {-1, 0, 1} (h = box / mesh per axis), in the order 9 (a+1) + 3 (b+1) + (c+1),
-times a scale s_in; then the one-hot site type (O, H, WC); then
-sin(2 pi u_d), cos(2 pi u_d) for d = x, y, z with u_d = x_d N_d / L_d the
-site's coordinate in mesh units (its offset inside the mesh cell); then
-twelve zeros.  The interpolation is the oracle PPPM's own (the same order-p
-stencil as its charge assignment), evaluated at the shifted points: the
-definition itself.
+times a scale s_in; then the one-hot site type (O, H, WC); then, "stated",
+two zeros, or, "cell", sin(2 pi u_d), cos(2 pi u_d) for d = x, y, z with
+u_d = x_d N_d / L_d the site's coordinate in mesh units (its offset inside
+the mesh cell) and twelve zeros.  The interpolation is the oracle PPPM's own
+(the same order-p stencil as its charge assignment), evaluated at the
+shifted points: the definition itself.
 
 ``adam_step`` is the Adam update (Kingma and Ba, 2015) with bias correction.
 
@@ -33,11 +42,32 @@ from __future__ import annotations
 
 import numpy as np
 
-N_IN, N_H, N_OUT = 48, 64, 3
+N_H, N_OUT = 64, 3
 N_PHI, N_TYPE, N_CELL = 27, 3, 6
-SHAPES = [("W1", (N_H, N_IN)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)),
-          ("W3", (N_OUT, N_H)), ("b3", (N_OUT,))]
-N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+FEATURE_WIDTH = {"stated": 32, "cell": 48}
+
+
+def shapes(n_in: int) -> list:
+    return [("W1", (N_H, n_in)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)),
+            ("W3", (N_OUT, N_H)), ("b3", (N_OUT,))]
+
+
+def n_params(n_in: int) -> int:
+    return sum(int(np.prod(s)) for _, s in shapes(n_in))
+
+
+def width_of(theta) -> int:
+    """Input width n_in of a parameter vector, from its length."""
+    rest = n_params(0)
+    k = len(theta) - rest
+    if k <= 0 or k % N_H:
+        raise ValueError(f"{len(theta)} is not the parameter count of a network of this shape")
+    return k // N_H
+
+
+N_IN = FEATURE_WIDTH["cell"]
+SHAPES = shapes(N_IN)
+N_PARAMS = n_params(N_IN)
 
 
 def bf16_round(x: np.ndarray) -> np.ndarray:
@@ -51,7 +81,7 @@ def bf16_round(x: np.ndarray) -> np.ndarray:
 
 def unpack(theta: np.ndarray) -> dict:
     out, o = {}, 0
-    for name, shape in SHAPES:
+    for name, shape in shapes(width_of(theta)):
         k = int(np.prod(shape))
         out[name] = np.asarray(theta[o:o + k], dtype=np.float64).reshape(shape)
         o += k
@@ -59,7 +89,8 @@ def unpack(theta: np.ndarray) -> dict:
 
 
 def pack(p: dict) -> np.ndarray:
-    return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in SHAPES])
+    return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel()
+                           for name, _ in shapes(np.shape(p["W1"])[1])])
 
 
 def forward(theta: np.ndarray, X: np.ndarray, bf16: bool = True, act_bf16: bool = False):
@@ -109,13 +140,15 @@ def adam_step(theta, m, v, g, step: int, lr: float, b1: float = 0.9, b2: float =
     return np.asarray(theta, np.float64) - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
-def features(phi: np.ndarray, pos: np.ndarray, types: np.ndarray, box, mesh, p: int, s_in: float = 1.0):
-    """Per-site network inputs (n, 48), FP64, from the mesh potential phi."""
+def features(phi: np.ndarray, pos: np.ndarray, types: np.ndarray, box, mesh, p: int, s_in: float = 1.0,
+             kind: str = "cell"):
+    """Per-site network inputs (n, 32) for kind "stated" or (n, 48) for
+    "cell", FP64, from the mesh potential phi."""
     from .pppm import interpolate
     pos = np.asarray(pos, dtype=np.float64)
     h = np.asarray(box, np.float64) / np.asarray(mesh, np.float64)
     n = pos.shape[0]
-    X = np.zeros((n, N_IN))
+    X = np.zeros((n, FEATURE_WIDTH[kind]))
     k = 0
     for a in (-1, 0, 1):
         for b in (-1, 0, 1):
@@ -126,6 +159,8 @@ def features(phi: np.ndarray, pos: np.ndarray, types: np.ndarray, box, mesh, p: 
     t = np.asarray(types).astype(np.int64)
     for j in range(3):
         X[:, 27 + j] = (t == j).astype(np.float64)
+    if kind == "stated":
+        return X
     for d in range(3):
         u = pos[:, d] / h[d]
         X[:, 30 + 2 * d] = np.sin(2.0 * np.pi * u)

@@ -15,15 +15,30 @@ def test_bf16_round_matches_library():
     assert np.array_equal(mlp.bf16_round(x), ref)
 
 
-def test_gradient_matches_central_differences():
+def test_parameter_layout_of_both_widths():
+    assert mlp.n_params(48) == mlp.N_PARAMS == 7491
+    assert mlp.n_params(32) == 6467
+    assert mlp.width_of(np.zeros(7491)) == 48 and mlp.width_of(np.zeros(6467)) == 32
+    with pytest.raises(ValueError):
+        mlp.width_of(np.zeros(7490))
+    # pack inverts unpack, the blocks in the documented order
+    theta = np.arange(6467, dtype=np.float64)
+    p = mlp.unpack(theta)
+    assert p["W1"].shape == (64, 32) and p["W1"][1, 0] == 32 and p["b1"][0] == 2048
+    assert p["W3"].shape == (3, 64) and p["b3"][2] == 6466
+    assert np.array_equal(mlp.pack(p), theta)
+
+
+@pytest.mark.parametrize("n_in", [48, 32])
+def test_gradient_matches_central_differences(n_in):
     rng = np.random.default_rng(1)
-    theta = init_mlp_params(3).astype(np.float64)
-    theta[2048:2112] = rng.normal(size=64) * 0.1  # nonzero b1
-    X = rng.normal(size=(20, mlp.N_IN))
+    theta = init_mlp_params(3, n_in=n_in).astype(np.float64)
+    theta[64 * n_in:64 * n_in + 64] = rng.normal(size=64) * 0.1  # nonzero b1
+    X = rng.normal(size=(20, n_in))
     T = rng.normal(size=(20, 3))
     _, g = mlp.loss_and_grad(theta, X, T, bf16=False)
     h = 1e-6
-    idx = rng.choice(mlp.N_PARAMS, size=120, replace=False)
+    idx = rng.choice(mlp.n_params(n_in), size=120, replace=False)
     fd = np.empty(len(idx))
     for k, j in enumerate(idx):
         tp, tm = theta.copy(), theta.copy()
@@ -33,16 +48,17 @@ def test_gradient_matches_central_differences():
     assert np.max(np.abs(fd - g[idx])) <= 1e-6 * max(1.0, np.max(np.abs(g[idx])))
 
 
-def test_zero_weights_give_bias_and_linear_regime():
-    p = {name: np.zeros(shape) for name, shape in mlp.SHAPES}
+@pytest.mark.parametrize("n_in", [48, 32])
+def test_zero_weights_give_bias_and_linear_regime(n_in):
+    p = {name: np.zeros(shape) for name, shape in mlp.shapes(n_in)}
     p["b3"] = np.array([0.5, -1.0, 2.0])
-    y, _ = mlp.forward(mlp.pack(p), np.ones((4, mlp.N_IN)), bf16=False)
+    y, _ = mlp.forward(mlp.pack(p), np.ones((4, n_in)), bf16=False)
     assert np.allclose(y, p["b3"])
     # small weights: tanh is the identity to third order, so y = W3 W2 W1 x
     rng = np.random.default_rng(2)
-    for name, shape in mlp.SHAPES:
+    for name, shape in mlp.shapes(n_in):
         p[name] = rng.normal(size=shape) * (1e-5 if name.startswith("W") else 0.0)
-    x = rng.normal(size=(5, mlp.N_IN))
+    x = rng.normal(size=(5, n_in))
     y, _ = mlp.forward(mlp.pack(p), x, bf16=False)
     lin = x @ (p["W3"] @ p["W2"] @ p["W1"]).T
     assert np.max(np.abs(y - lin)) <= 1e-6 * np.max(np.abs(lin))
@@ -58,18 +74,37 @@ def test_cardinal_bspline_integer_values():
     assert np.allclose(v, [115 / 192, 19 / 96, 19 / 96, 1 / 384, 1 / 384, 0.0], rtol=0, atol=1e-15)
 
 
-def test_features_constant_mesh_and_one_hot():
+@pytest.mark.parametrize("kind,width,zero_from", [("cell", 48, 36), ("stated", 32, 30)])
+def test_features_constant_mesh_and_one_hot(kind, width, zero_from):
     rng = np.random.default_rng(4)
     box, mesh = np.array([9.0, 10.0, 11.0]), (8, 10, 12)
     phi = np.full(mesh, 2.5)
     pos = rng.uniform(-3.0, 14.0, size=(17, 3))
     types = rng.integers(0, 3, size=17).astype(np.int8)
     for p in (3, 4, 5):
-        X = mlp.features(phi, pos, types, box, mesh, p, s_in=0.5)
-        assert X.shape == (17, 48)
+        X = mlp.features(phi, pos, types, box, mesh, p, s_in=0.5, kind=kind)
+        assert X.shape == (17, width)
         assert np.allclose(X[:, :27], 1.25, rtol=0, atol=1e-13)   # partition of unity
         assert np.array_equal(X[:, 27:30], np.eye(3)[types])
-        assert not X[:, 36:].any()
+        assert not X[:, zero_from:].any()
+
+
+def test_stated_features_are_the_samples_and_type_alone():
+    """The stated set is the first 30 inputs of the cell set (same samples,
+    same type code) and two zeros: no position inside the cell."""
+    rng = np.random.default_rng(12)
+    box, mesh = np.array([7.0, 8.0, 9.0]), (10, 12, 15)
+    phi = rng.normal(size=mesh)
+    pos = rng.uniform(-1.0, 10.0, size=(9, 3))
+    types = rng.integers(0, 3, size=9).astype(np.int8)
+    Xc = mlp.features(phi, pos, types, box, mesh, 5, s_in=0.8, kind="cell")
+    Xs = mlp.features(phi, pos, types, box, mesh, 5, s_in=0.8, kind="stated")
+    assert np.array_equal(Xs[:, :30], Xc[:, :30]) and not Xs[:, 30:].any()
+    # translating the sites by one mesh cell along x and phi by one index
+    # along x gives the same inputs (the samples follow the potential)
+    Xs2 = mlp.features(np.roll(phi, 1, axis=0), pos + np.array([0.7, 0.0, 0.0]), types, box, mesh, 5, s_in=0.8,
+                       kind="stated")
+    assert np.allclose(Xs2, Xs, rtol=0, atol=1e-12)
 
 
 def test_cell_offset_features():
@@ -88,13 +123,14 @@ def test_cell_offset_features():
     assert np.allclose(X2[:, 30:36], X[:, 30:36], atol=1e-12)
 
 
-def test_features_at_mesh_points_are_a_discrete_convolution():
+@pytest.mark.parametrize("kind", ["cell", "stated"])
+def test_features_at_mesh_points_are_a_discrete_convolution(kind):
     rng = np.random.default_rng(5)
     box, mesh = np.array([8.0, 8.0, 8.0]), (8, 8, 8)
     phi = rng.normal(size=mesh)
     m = rng.integers(0, 8, size=(6, 3))
     pos = m * 1.0   # h = 1: the sites sit on mesh points
-    X = mlp.features(phi, pos, np.zeros(6, np.int8), box, mesh, 5)
+    X = mlp.features(phi, pos, np.zeros(6, np.int8), box, mesh, 5, kind=kind)
     w = {0: 115 / 192, 1: 19 / 96, -1: 19 / 96, 2: 1 / 384, -2: 1 / 384}
     for i in range(6):
         k = 0
