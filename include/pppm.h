@@ -309,19 +309,24 @@ int pppm_set_wait_limit(pppm_plan *plan, long long spins);
  * force error of the fine one, which motivates a cheaper coarse solve; the
  * network itself has no counterpart in the paper.
  *
- *   features x_i (48 BF16 values per site, row-major n x 48):
+ *   features x_i (n_in BF16 values per site, row-major n x n_in), n_in = 32
+ *   for the stated feature set (PPPM_CORR_STATED: local potential samples and
+ *   site type) and 48 for the cell set (PPPM_CORR_CELL, the default: the same
+ *   and the site's offset inside its mesh cell):
  *     x_i[9 a + 3 b + c] = s_in * phi(r_i + h * (a-1, b-1, c-1)), a, b, c in
  *     {0, 1, 2}, phi interpolated from the coarse potential mesh with the
  *     plan's order-p B-spline weights (h = box / mesh per axis);
  *     x_i[27 + t] = 1 for the site type t in {0, 1, 2}, 0 otherwise;
- *     x_i[30 + 2 d] = sin(2 pi u_d), x_i[31 + 2 d] = cos(2 pi u_d), d = x, y,
- *     z, with u_d = x_d N_d / L_d (the site's offset inside its mesh cell);
- *     x_i[36..47] = 0.
+ *     stated set: x_i[30..31] = 0;
+ *     cell set: x_i[30 + 2 d] = sin(2 pi u_d), x_i[31 + 2 d] = cos(2 pi u_d),
+ *     d = x, y, z, with u_d = x_d N_d / L_d (the site's offset inside its
+ *     mesh cell); x_i[36..47] = 0.
  *   network  h1 = tanh(W1 x + b1) (64), h2 = tanh(W2 h1 + b2) (64),
  *            y = W3 h2 + b3 (3).  Parameters: one FP32 vector of
- *            pppm_corr_nparams() = 7491 values [W1 64x48 row-major, b1, W2
- *            64x64, b2, W3 3x64, b3].  Inference and training use them rounded
- *            to BF16; accumulation is FP32.
+ *            pppm_corr_param_count() values [W1 64 x n_in row-major, b1, W2
+ *            64x64, b2, W3 3x64, b3]: 7491 for the cell set, 6467 for the
+ *            stated set.  Inference and training use them rounded to BF16;
+ *            accumulation is FP32.
  *   forces   F_i = F_coarse,i + q_i * s_out * y_i.
  *   training target t_i = (F_fine,i - F_coarse,i) / (q_i * s_out) (n x 3
  *            FP32); loss = (1/nb) sum over the nb sites of |y_i - t_i|^2;
@@ -329,17 +334,25 @@ int pppm_set_wait_limit(pppm_plan *plan, long long spins);
  *
  * pppm_corr_create      borrow an FP32 coarse plan (it must outlive the
  *                       corrector; its potential output is switched on);
- *                       parameters start at zero, s_in = s_out = 1.
- * pppm_corr_nparams     7491.
+ *                       parameters start at zero, s_in = s_out = 1; the cell
+ *                       feature set.
+ * pppm_corr_create_features
+ *                       the same with the feature set chosen (PPPM_CORR_CELL
+ *                       or PPPM_CORR_STATED; another value:
+ *                       PPPM_ERR_INVALID_ARG).
+ * pppm_corr_nparams     7491 (the parameter count of the cell set).
+ * pppm_corr_param_count parameters of this corrector (7491 or 6467).
+ * pppm_corr_feature_width
+ *                       n_in of this corrector (48 or 32).
  * pppm_corr_set_weights host FP32 parameters and the scales s_in, s_out (> 0);
  *                       resets the Adam moments and step count.
  * pppm_corr_get_weights host copy of the FP32 master parameters and scales
  *                       (s_in, s_out may be NULL).
  * pppm_corr_features    run the coarse PPPM on (pos, q) (device, FP32, n x 3
  *                       and n), write its forces to forces (device n x 3) and
- *                       the features to feat (device, n x 48 BF16, 96 B per
- *                       row, 16-byte aligned); types is a device array of n
- *                       signed chars.
+ *                       the features to feat (device, n x n_in BF16, 96 or
+ *                       64 B per row, 16-byte aligned); types is a device
+ *                       array of n signed chars.
  * pppm_corr_calibrate   choose the scales from one configuration: runs the
  *                       coarse PPPM and the features with s_in = 1, then sets
  *                       s_in = 1 / rms of the 27 potential samples and
@@ -373,8 +386,12 @@ int pppm_set_wait_limit(pppm_plan *plan, long long spins);
  * inconsistent arguments or an unreadable checkpoint, PPPM_ERR_CUDA.
  */
 typedef struct pppm_corr pppm_corr;
+enum { PPPM_CORR_CELL = 0, PPPM_CORR_STATED = 1 };
 int pppm_corr_create(pppm_plan *coarse, pppm_corr **out);
+int pppm_corr_create_features(pppm_plan *coarse, int features, pppm_corr **out);
 int pppm_corr_nparams(void);
+int pppm_corr_param_count(const pppm_corr *corr);
+int pppm_corr_feature_width(const pppm_corr *corr);
 int pppm_corr_set_weights(pppm_corr *corr, const float *params, double s_in, double s_out);
 int pppm_corr_get_weights(const pppm_corr *corr, float *params, double *s_in, double *s_out);
 int pppm_corr_features(pppm_corr *corr, void *stream, const float *pos, const float *q,

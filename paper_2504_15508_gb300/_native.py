@@ -24,6 +24,8 @@ PPPM_ERR_NONFINITE = -7
 PPPM_ERR_TOO_LARGE = -8
 PPPM_FP32 = 1
 PPPM_FP64 = 2
+PPPM_CORR_CELL = 0
+PPPM_CORR_STATED = 1
 
 
 class PPPMError(RuntimeError):
@@ -83,6 +85,9 @@ SIGNATURES = {
     "pppm_batch_set_wait_probe": (cint, [vp, cint]),
     "pppm_corr_create": (cint, [vp, ctypes.POINTER(vp)]),
     "pppm_corr_nparams": (cint, []),
+    "pppm_corr_create_features": (cint, [vp, cint, ctypes.POINTER(vp)]),
+    "pppm_corr_param_count": (cint, [vp]),
+    "pppm_corr_feature_width": (cint, [vp]),
     "pppm_corr_set_weights": (cint, [vp, vp, dbl, dbl]),
     "pppm_corr_get_weights": (cint, [vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
     "pppm_corr_features": (cint, [vp, vp, vp, vp, vp, i64, vp, vp]),

@@ -4,10 +4,11 @@
 //
 //   features  x_i = [27 samples of the coarse mesh potential phi, interpolated
 //             with the site's order-p B-spline weights at r_i + h (dx, dy, dz),
-//             d in {-1, 0, 1}^3, times s_in; one-hot site type (3);
-//             sin, cos of 2 pi u_d per axis, u = position in mesh units (6);
-//             12 zeros] (BF16, 48 per site)
-//   network   h1 = tanh(W1 x + b1) (48 -> 64), h2 = tanh(W2 h1 + b2) (64 -> 64),
+//             d in {-1, 0, 1}^3, times s_in; one-hot site type (3); then
+//             either 2 zeros (the stated set, 32 per site) or sin, cos of
+//             2 pi u_d per axis, u = position in mesh units (6), and 12 zeros
+//             (the cell set, 48 per site)] (BF16)
+//   network   h1 = tanh(W1 x + b1) (n_in -> 64), h2 = tanh(W2 h1 + b2) (64 -> 64),
 //             y = W3 h2 + b3 (64 -> 3); BF16 weights, FP32 accumulation
 //   forces    F_i = F_coarse,i + q_i s_out y_i
 //   training  target t_i = (F_fine,i - F_coarse,i) / (q_i s_out); loss mean |y - t|^2;
@@ -24,6 +25,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -32,14 +34,23 @@
 namespace pppm {
 namespace corr {
 
-constexpr int NIN = 48, NH = 64, NOUT = 3, NOUT_PAD = 8;
-constexpr int KC1 = NIN / 16;  // k-chunks of the first layer
-constexpr int O_W1 = 0, O_B1 = O_W1 + NH * NIN, O_W2 = O_B1 + NH, O_B2 = O_W2 + NH * NH, O_W3 = O_B2 + NH,
-              O_B3 = O_W3 + NOUT * NH, NPARAM = O_B3 + NOUT;
-// BF16 weight layout for the tensor-core forward: rows padded so that the
-// per-lane B-fragment loads hit distinct banks
-constexpr int K1P = NIN + 8, K2P = NH + 8;
-constexpr int BW1 = 0, BW2 = BW1 + NH * K1P, BW3 = BW2 + NH * K2P, NBF = BW3 + NOUT_PAD * K2P;
+constexpr int NH = 64, NOUT = 3, NOUT_PAD = 8;
+constexpr int K2P = NH + 8;
+// Sizes and offsets of a network with NIN inputs (48: cell set, 32: stated set).
+template <int NIN>
+struct Net {
+    static_assert(NIN == 32 || NIN == 48, "input widths of the two feature sets");
+    static constexpr int KC1 = NIN / 16;  // k-chunks of the first layer
+    static constexpr int O_W1 = 0, O_B1 = O_W1 + NH * NIN, O_W2 = O_B1 + NH, O_B2 = O_W2 + NH * NH,
+                         O_W3 = O_B2 + NH, O_B3 = O_W3 + NOUT * NH, NPARAM = O_B3 + NOUT;
+    // BF16 weight layout for the tensor-core forward: rows padded so that the
+    // per-lane B-fragment loads hit distinct banks (row pitches of 28 and 20
+    // words put the eight row groups of a fragment load on distinct banks)
+    static constexpr int K1P = NIN + 8;
+    static constexpr int BW1 = 0, BW2 = BW1 + NH * K1P, BW3 = BW2 + NH * K2P, NBF = BW3 + NOUT_PAD * K2P;
+    static constexpr int XP = NIN + 1;  // training: padded row of the feature tile
+};
+constexpr int kNinCell = 48, kNinStated = 32;
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -84,7 +95,7 @@ __device__ __forceinline__ void bspline_all(float x0, float w[P]) {
 // Thread t takes site perm[t]: with the solve's tile order as perm, the sites
 // of a warp lie in one tile and their mesh rows overlap, so a warp's loads
 // touch a few rows instead of 32 scattered ones.
-template <int P>
+template <int P, int NIN>
 __global__ void k_features(Geo g, FieldLayout fl, const float* __restrict__ phi, const float* __restrict__ pos,
                            const signed char* __restrict__ types, const int* __restrict__ perm, int n, float s_in,
                            __nv_bfloat16* __restrict__ feat) {
@@ -150,17 +161,23 @@ __global__ void k_features(Geo g, FieldLayout fl, const float* __restrict__ phi,
             }
         }
     }
-    // the row as 24 packed pairs, written with 16-byte stores
+    // the row as NIN / 2 packed pairs, written with 16-byte stores
     float v[NIN];
 #pragma unroll
     for (int k = 0; k < 27; ++k) v[k] = F[k] * s_in;
     const int ty = types[i];
 #pragma unroll
     for (int k = 0; k < 3; ++k) v[27 + k] = ty == k ? 1.f : 0.f;
+    if constexpr (NIN == kNinCell) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) sincospif(2.f * dfrac[d], &v[30 + 2 * d], &v[31 + 2 * d]);
+        for (int d = 0; d < 3; ++d) sincospif(2.f * dfrac[d], &v[30 + 2 * d], &v[31 + 2 * d]);
 #pragma unroll
-    for (int k = 36; k < NIN; ++k) v[k] = 0.f;
+        for (int k = 36; k < NIN; ++k) v[k] = 0.f;
+    } else {
+        (void)dfrac;
+#pragma unroll
+        for (int k = 30; k < NIN; ++k) v[k] = 0.f;
+    }
     uint4* o = reinterpret_cast<uint4*>(feat + (int64_t)i * NIN);
 #pragma unroll
     for (int k = 0; k < NIN / 8; ++k) {
@@ -200,10 +217,14 @@ __device__ __forceinline__ void act_to_a(const float acc[8][4], const float* __r
 
 // One warp per 16 sites (grid-stride).  With forces/q given, adds
 // q_i s_out y_i to forces (the corrected PPPM); else writes y to out.
+template <int NIN>
 __global__ void __launch_bounds__(128)
 k_mlp_forward(const __nv_bfloat16* __restrict__ feat, int n, const __nv_bfloat16* __restrict__ wbf,
               const float* __restrict__ master, float s_out, const float* __restrict__ q, float* __restrict__ forces,
               float* __restrict__ out) {
+    typedef Net<NIN> L;
+    constexpr int NBF = L::NBF, KC1 = L::KC1, K1P = L::K1P, BW1 = L::BW1, BW2 = L::BW2, BW3 = L::BW3;
+    constexpr int O_B1 = L::O_B1, O_B2 = L::O_B2, O_B3 = L::O_B3;
     __shared__ __align__(16) __nv_bfloat16 sw[NBF];
     __shared__ float sb[NH + NH + NOUT_PAD];
     for (int k = threadIdx.x; k < NBF; k += blockDim.x) sw[k] = wbf[k];
@@ -220,7 +241,7 @@ k_mlp_forward(const __nv_bfloat16* __restrict__ feat, int n, const __nv_bfloat16
     const uint32_t* w32 = reinterpret_cast<const uint32_t*>(sw);
     for (int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile * 16 < n; tile += warps) {
         const int r0 = tile * 16 + gid, r1 = r0 + 8;
-        // layer 1: A from the features (16 x 48), three k-chunks
+        // layer 1: A from the features (16 x NIN), NIN / 16 k-chunks
         uint32_t a1[KC1][4];
         const uint32_t* f0 = reinterpret_cast<const uint32_t*>(feat + (int64_t)min(r0, n - 1) * NIN);
         const uint32_t* f1 = reinterpret_cast<const uint32_t*>(feat + (int64_t)min(r1, n - 1) * NIN);
@@ -285,7 +306,11 @@ k_mlp_forward(const __nv_bfloat16* __restrict__ feat, int n, const __nv_bfloat16
 }
 
 // FP32 master -> padded BF16 copy for the forward
+template <int NIN>
 __global__ void k_to_bf16(const float* __restrict__ master, __nv_bfloat16* __restrict__ wbf) {
+    typedef Net<NIN> L;
+    constexpr int NBF = L::NBF, K1P = L::K1P, BW2 = L::BW2, BW3 = L::BW3, O_W1 = L::O_W1, O_W2 = L::O_W2,
+                  O_W3 = L::O_W3;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < NBF; k += gridDim.x * blockDim.x) {
         float v = 0.f;
         if (k < BW2) {
@@ -304,19 +329,23 @@ __global__ void k_to_bf16(const float* __restrict__ master, __nv_bfloat16* __res
 
 // ------------------------------------------------------------------ training
 constexpr int TB = 128;  // sites per training block
-constexpr int XP = NIN + 1, HP = NH + 1;
+constexpr int HP = NH + 1;
 
 __device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // Per block: forward and backward of 128 sites (FP32, weights rounded to BF16
 // as used by inference), per-block gradient sums to partial[block][NPARAM],
 // and the block's share of the loss to lossp[block].
+template <int NIN>
 __global__ void __launch_bounds__(TB)
 k_mlp_grad(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ target, int64_t nrows,
            const int* __restrict__ idx, int nb, float inv_total, const float* __restrict__ master, float* __restrict__ partial,
            float* __restrict__ lossp) {
+    typedef Net<NIN> L;
+    constexpr int XP = L::XP, NPARAM = L::NPARAM, O_W1 = L::O_W1, O_B1 = L::O_B1, O_W2 = L::O_W2, O_B2 = L::O_B2,
+                  O_W3 = L::O_W3, O_B3 = L::O_B3;
     extern __shared__ __align__(16) float sm[];
-    float* W1 = sm;                  // 64 x 48
+    float* W1 = sm;                  // 64 x NIN
     float* W2 = W1 + NH * NIN;       // 64 x 64
     float* W3 = W2 + NH * NH;        // 3 x 64
     float* bb = W3 + NOUT * NH;      // b1 64, b2 64, b3 3 (+1)
@@ -413,28 +442,30 @@ k_mlp_grad(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ tar
         H1[t * HP + k] = dh * (1.f - h * h);
     }
     __syncthreads();
-    // dW1 (thread: columns k0 + 16 c, c < 3, k0 = t % 16; rows j0 + 8 m, m < 8, j0 = t / 16), db1
+    // dW1 (thread: columns k0 + 16 c, c < NIN / 16, k0 = t % 16; rows j0 + 8 m,
+    // m < 8, j0 = t / 16), db1
     {
-        static_assert(NIN == 48 && NH == 64 && TB == 128, "dW1 thread map");
+        static_assert(NIN % 16 == 0 && NH == 64 && TB == 128, "dW1 thread map");
+        constexpr int KC = NIN / 16;
         const int k0 = t & 15, j0 = t >> 4;
-        float acc[3][8];
+        float acc[KC][8];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < KC; ++c)
 #pragma unroll
             for (int m = 0; m < 8; ++m) acc[c][m] = 0.f;
         for (int r = 0; r < TB; ++r) {
-            float xk[3], hj[8];
+            float xk[KC], hj[8];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) xk[c] = X[r * XP + k0 + 16 * c];
+            for (int c = 0; c < KC; ++c) xk[c] = X[r * XP + k0 + 16 * c];
 #pragma unroll
             for (int m = 0; m < 8; ++m) hj[m] = H1[r * HP + j0 + 8 * m];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < KC; ++c)
 #pragma unroll
                 for (int m = 0; m < 8; ++m) acc[c][m] += hj[m] * xk[c];
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < KC; ++c)
 #pragma unroll
             for (int m = 0; m < 8; ++m) g[O_W1 + (j0 + 8 * m) * NIN + k0 + 16 * c] = acc[c][m];
     }
@@ -448,6 +479,7 @@ k_mlp_grad(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ tar
 // Sum the per-block gradients in block order; then either return them or take
 // one Adam step (FP32 master, moments m, v) and refresh nothing else (the BF16
 // copy is rebuilt by k_to_bf16).
+template <int NIN>
 __global__ void k_reduce_adam(const float* __restrict__ partial, const float* __restrict__ lossp, int nblk,
                               float* __restrict__ grad_out, float* __restrict__ loss_out, float* __restrict__ master,
                               float* __restrict__ m1, float* __restrict__ m2, float lr, float b1, float b2, float eps,
@@ -458,6 +490,7 @@ __global__ void k_reduce_adam(const float* __restrict__ partial, const float* __
         for (int b = 0; b < nblk; ++b) l += lossp[b];
         *loss_out = l;
     }
+    constexpr int NPARAM = Net<NIN>::NPARAM;
     if (p >= NPARAM) return;
     float gsum = 0.f;
     for (int b = 0; b < nblk; ++b) gsum += partial[(size_t)b * NPARAM + p];
@@ -484,6 +517,7 @@ __global__ void k_targets(const float* __restrict__ ff, const float* __restrict_
 // [0] sum of squares of the 27 potential samples, [1] sum over sites with
 // q != 0 of |F_fine - F_coarse|^2 / q^2, [2] number of such sites.
 constexpr int kCalBlocks = 256;
+template <int NIN>
 __global__ void __launch_bounds__(256)
 k_calibrate(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ ff, const float* __restrict__ fc,
             const float* __restrict__ q, int n, double* __restrict__ part) {
@@ -527,6 +561,7 @@ using namespace pppm::corr;
 
 struct pppm_corr {
     pppm_plan* plan = nullptr;  // coarse plan (borrowed)
+    int nin = kNinCell;         // input width: 48 (cell set) or 32 (stated set)
     float* master = nullptr;
     float* m1 = nullptr;
     float* m2 = nullptr;
@@ -548,12 +583,22 @@ namespace {
         if ((x) != cudaSuccess) return PPPM_ERR_CUDA;  \
     } while (0)
 
+// Runs f(std::integral_constant<int, NIN>) for the corrector's input width.
+template <typename F>
+auto with_nin(int nin, F&& f) {
+    if (nin == kNinStated) return f(std::integral_constant<int, kNinStated>{});
+    return f(std::integral_constant<int, kNinCell>{});
+}
+
+int nparam_of(int nin) { return nin == kNinStated ? Net<kNinStated>::NPARAM : Net<kNinCell>::NPARAM; }
+int nbf_of(int nin) { return nin == kNinStated ? Net<kNinStated>::NBF : Net<kNinCell>::NBF; }
+
 int ensure_feat(pppm_corr* C, int64_t n) {
     if (n <= C->feat_cap) return PPPM_OK;
     if (C->feat) cudaFree(C->feat);
     C->feat = nullptr;
     C->feat_cap = 0;
-    CC(cudaMalloc((void**)&C->feat, sizeof(__nv_bfloat16) * NIN * (n > 0 ? n : 1)));
+    CC(cudaMalloc((void**)&C->feat, sizeof(__nv_bfloat16) * C->nin * (n > 0 ? n : 1)));
     C->feat_cap = n;
     return PPPM_OK;
 }
@@ -565,14 +610,18 @@ int ensure_partial(pppm_corr* C, int nblk) {
     C->partial = nullptr;
     C->lossp = nullptr;
     C->partial_blocks = 0;
-    CC(cudaMalloc((void**)&C->partial, sizeof(float) * NPARAM * (size_t)nblk));
+    CC(cudaMalloc((void**)&C->partial, sizeof(float) * nparam_of(C->nin) * (size_t)nblk));
     CC(cudaMalloc((void**)&C->lossp, sizeof(float) * nblk));
     C->partial_blocks = nblk;
     return PPPM_OK;
 }
 
 int refresh_bf16(pppm_corr* C, cudaStream_t s) {
-    k_to_bf16<<<(NBF + 255) / 256, 256, 0, s>>>(C->master, C->wbf);
+    const int nbf = nbf_of(C->nin);
+    with_nin(C->nin, [&](auto N) {
+        k_to_bf16<decltype(N)::value><<<(nbf + 255) / 256, 256, 0, s>>>(C->master, C->wbf);
+        return 0;
+    });
     CC(cudaGetLastError());
     return PPPM_OK;
 }
@@ -589,20 +638,23 @@ cudaError_t launch_features(pppm_corr* C, cudaStream_t s, const float* pos, cons
     // in the plan
     const int* perm = n <= P->cap ? P->sorig : nullptr;
     const int blocks = (int)((n + 127) / 128);
-#define PPPM_FEAT(PP)                                                                                      \
-    case PP:                                                                                               \
-        k_features<PP><<<blocks, 128, 0, s>>>(P->g, pl, phi, pos, types, perm, (int)n, C->s_in, feat);         \
+    return with_nin(C->nin, [&](auto N) -> cudaError_t {
+        constexpr int NIN = decltype(N)::value;
+#define PPPM_FEAT(PP)                                                                                           \
+    case PP:                                                                                                    \
+        k_features<PP, NIN><<<blocks, 128, 0, s>>>(P->g, pl, phi, pos, types, perm, (int)n, C->s_in, feat);         \
         break;
-    switch (P->order) {
-        PPPM_FEAT(3)
-        PPPM_FEAT(4)
-        PPPM_FEAT(5)
-        PPPM_FEAT(6)
-        PPPM_FEAT(7)
-        default: return cudaErrorInvalidValue;
-    }
+        switch (P->order) {
+            PPPM_FEAT(3)
+            PPPM_FEAT(4)
+            PPPM_FEAT(5)
+            PPPM_FEAT(6)
+            PPPM_FEAT(7)
+            default: return cudaErrorInvalidValue;
+        }
 #undef PPPM_FEAT
-    return cudaGetLastError();
+        return cudaGetLastError();
+    });
 }
 
 int mlp_forward(pppm_corr* C, cudaStream_t s, const __nv_bfloat16* feat, int64_t n, const float* q, float* forces,
@@ -614,13 +666,20 @@ int mlp_forward(pppm_corr* C, cudaStream_t s, const __nv_bfloat16* feat, int64_t
     const int tiles = (int)((n + 15) / 16);
     int blocks = (tiles + 3) / 4;
     if (blocks > 8 * nsm) blocks = 8 * nsm;
-    k_mlp_forward<<<blocks, 128, 0, s>>>(feat, (int)n, C->wbf, C->master, C->s_out, q, forces, out);
+    with_nin(C->nin, [&](auto N) {
+        k_mlp_forward<decltype(N)::value><<<blocks, 128, 0, s>>>(feat, (int)n, C->wbf, C->master, C->s_out, q,
+                                                                  forces, out);
+        return 0;
+    });
     CC(cudaGetLastError());
     return PPPM_OK;
 }
 
-constexpr size_t kGradSmem =
-    sizeof(float) * (NH * NIN + NH * NH + NOUT * NH + 2 * NH + 4 + TB * XP + 2 * TB * HP + TB * 4 + 32);
+template <int NIN>
+constexpr size_t grad_smem() {
+    return sizeof(float) * (NH * NIN + NH * NH + NOUT * NH + 2 * NH + 4 + TB * Net<NIN>::XP + 2 * TB * HP + TB * 4 +
+                            32);
+}
 
 int grad_step(pppm_corr* C, cudaStream_t s, const __nv_bfloat16* feat, const float* target, int64_t nrows,
               const int* idx, int64_t nb, float* grad_out, float* loss_out, bool adam, float lr) {
@@ -628,19 +687,30 @@ int grad_step(pppm_corr* C, cudaStream_t s, const __nv_bfloat16* feat, const flo
     const int nblk = (int)((nb + TB - 1) / TB);
     int rc = ensure_partial(C, nblk);
     if (rc != PPPM_OK) return rc;
-    CC(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem));
-    k_mlp_grad<<<nblk, TB, kGradSmem, s>>>(feat, target, nrows, idx, (int)nb, 1.f / (float)nb, C->master, C->partial,
-                                          C->lossp);
-    CC(cudaGetLastError());
+    const cudaError_t ge = with_nin(C->nin, [&](auto N) -> cudaError_t {
+        constexpr int NIN = decltype(N)::value;
+        constexpr size_t smem = grad_smem<NIN>();
+        const cudaError_t e = cudaFuncSetAttribute(k_mlp_grad<NIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mlp_grad<NIN><<<nblk, TB, smem, s>>>(feat, target, nrows, idx, (int)nb, 1.f / (float)nb, C->master,
+                                               C->partial, C->lossp);
+        return cudaGetLastError();
+    });
+    CC(ge);
     float bc1 = 1.f, bc2 = 1.f;
     if (adam) {
         C->step += 1;
         bc1 = 1.f - powf(0.9f, (float)C->step);
         bc2 = 1.f - powf(0.999f, (float)C->step);
     }
-    k_reduce_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(C->partial, C->lossp, nblk, grad_out, loss_out,
-                                                       adam ? C->master : nullptr, C->m1, C->m2, lr, 0.9f, 0.999f,
-                                                       1e-8f, bc1, bc2);
+    const int npar = nparam_of(C->nin);
+    with_nin(C->nin, [&](auto N) {
+        k_reduce_adam<decltype(N)::value><<<(npar + 255) / 256, 256, 0, s>>>(
+            C->partial, C->lossp, nblk, grad_out, loss_out, adam ? C->master : nullptr, C->m1, C->m2, lr, 0.9f,
+            0.999f, 1e-8f, bc1, bc2);
+        return 0;
+    });
     CC(cudaGetLastError());
     if (adam) return refresh_bf16(C, s);
     return PPPM_OK;
@@ -650,13 +720,16 @@ int grad_step(pppm_corr* C, cudaStream_t s, const __nv_bfloat16* feat, const flo
 
 extern "C" {
 
-int pppm_corr_create(pppm_plan* coarse, pppm_corr** out) {
+int pppm_corr_create_features(pppm_plan* coarse, int features, pppm_corr** out) {
     if (!out) return PPPM_ERR_INVALID_ARG;
     *out = nullptr;
     if (!coarse || coarse->precision != PPPM_FP32) return PPPM_ERR_INVALID_ARG;
+    if (features != PPPM_CORR_CELL && features != PPPM_CORR_STATED) return PPPM_ERR_INVALID_ARG;
     pppm_corr* C = new (std::nothrow) pppm_corr();
     if (!C) return PPPM_ERR_CUDA;
     C->plan = coarse;
+    C->nin = features == PPPM_CORR_STATED ? kNinStated : kNinCell;
+    const int NPARAM = nparam_of(C->nin), NBF = nbf_of(C->nin);
     auto fail = [&](int code) {
         pppm_corr_destroy(C);
         return code;
@@ -676,6 +749,14 @@ int pppm_corr_create(pppm_plan* coarse, pppm_corr** out) {
     return PPPM_OK;
 }
 
+int pppm_corr_create(pppm_plan* coarse, pppm_corr** out) {
+    return pppm_corr_create_features(coarse, PPPM_CORR_CELL, out);
+}
+
+int pppm_corr_param_count(const pppm_corr* C) { return C ? nparam_of(C->nin) : PPPM_ERR_INVALID_ARG; }
+
+int pppm_corr_feature_width(const pppm_corr* C) { return C ? C->nin : PPPM_ERR_INVALID_ARG; }
+
 void pppm_corr_destroy(pppm_corr* C) {
     if (!C) return;
     cudaDeviceSynchronize();
@@ -685,10 +766,11 @@ void pppm_corr_destroy(pppm_corr* C) {
     delete C;
 }
 
-int pppm_corr_nparams(void) { return NPARAM; }
+int pppm_corr_nparams(void) { return Net<kNinCell>::NPARAM; }
 
 int pppm_corr_set_weights(pppm_corr* C, const float* params, double s_in, double s_out) {
     if (!C || !params || !(s_in > 0.0) || !(s_out > 0.0)) return PPPM_ERR_INVALID_ARG;
+    const int NPARAM = nparam_of(C->nin);
     CC(cudaMemcpy(C->master, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
     CC(cudaMemset(C->m1, 0, sizeof(float) * NPARAM));
     CC(cudaMemset(C->m2, 0, sizeof(float) * NPARAM));
@@ -704,7 +786,7 @@ int pppm_corr_set_weights(pppm_corr* C, const float* params, double s_in, double
 int pppm_corr_get_weights(const pppm_corr* C, float* params, double* s_in, double* s_out) {
     if (!C || !params) return PPPM_ERR_INVALID_ARG;
     CC(cudaDeviceSynchronize());
-    CC(cudaMemcpy(params, C->master, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    CC(cudaMemcpy(params, C->master, sizeof(float) * nparam_of(C->nin), cudaMemcpyDeviceToHost));
     if (s_in) *s_in = C->s_in;
     if (s_out) *s_out = C->s_out;
     return PPPM_OK;
@@ -753,7 +835,10 @@ int pppm_corr_calibrate(pppm_corr* C, void* stream, const float* pos, const floa
     rc = pppm_corr_features(C, stream, pos, q, types, n, C->feat, fc);
     C->s_in = keep_in;
     if (rc != PPPM_OK) return done(rc);
-    k_calibrate<<<kCalBlocks, 256, 0, s>>>(C->feat, f_fine, fc, q, (int)n, part);
+    with_nin(C->nin, [&](auto N) {
+        k_calibrate<decltype(N)::value><<<kCalBlocks, 256, 0, s>>>(C->feat, f_fine, fc, q, (int)n, part);
+        return 0;
+    });
     if (cudaGetLastError() != cudaSuccess) return done(PPPM_ERR_CUDA);
     std::vector<double> h(3 * kCalBlocks);
     if (cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -816,6 +901,7 @@ int pppm_corr_train_step(pppm_corr* C, void* stream, const void* feat, const flo
 // file: magic "PPPMCORR", version 1, nparams, s_in, s_out, step, master, m1, m2
 int pppm_corr_save(const pppm_corr* C, const char* path) {
     if (!C || !path) return PPPM_ERR_INVALID_ARG;
+    const int NPARAM = nparam_of(C->nin);
     std::vector<float> buf(3 * (size_t)NPARAM);
     CC(cudaDeviceSynchronize());
     CC(cudaMemcpy(buf.data(), C->master, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
@@ -835,6 +921,7 @@ int pppm_corr_save(const pppm_corr* C, const char* path) {
 
 int pppm_corr_load(pppm_corr* C, const char* path) {
     if (!C || !path) return PPPM_ERR_INVALID_ARG;
+    const int NPARAM = nparam_of(C->nin);
     FILE* f = fopen(path, "rb");
     if (!f) return PPPM_ERR_INVALID_ARG;
     char magic[8];

@@ -37,7 +37,7 @@ class FrameSpec:
 
 @dataclass
 class Dataset:
-    feat: torch.Tensor     # (frames * n, 48) bf16
+    feat: torch.Tensor     # (frames * n, n_in) bf16, n_in = 48 or 32
     target: torch.Tensor   # (frames * n, 3) f32
     n_sites: int
     n_frames: int
@@ -70,7 +70,7 @@ def build_dataset(corr: Corrector, fine: Plan, spec: FrameSpec, calibrate: bool 
     n = 4 * spec.n_mol
     F = len(spec.base_seeds) * spec.frames_per_base
     dev = torch.device("cuda")
-    feat = torch.empty((F * n, Corrector.N_IN), dtype=torch.bfloat16, device=dev)
+    feat = torch.empty((F * n, corr.n_in), dtype=torch.bfloat16, device=dev)
     target = torch.empty((F * n, 3), dtype=torch.float32, device=dev)
     fc = torch.empty((n, 3), dtype=torch.float32, device=dev)
     for k, (pos, q, types) in enumerate(frames(spec)):
@@ -87,7 +87,7 @@ def train(corr: Corrector, ds: Dataset, steps: int, batch: int = 4096, lr: float
     """Adam on random minibatches with a cosine learning-rate decay."""
     if init_seed is not None:
         s_in, s_out = corr.scales
-        corr.set_weights(init_mlp_params(init_seed), s_in, s_out)
+        corr.set_weights(init_mlp_params(init_seed, n_in=corr.n_in), s_in, s_out)
     dev = ds.feat.device
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(seed))

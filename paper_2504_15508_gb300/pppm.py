@@ -349,24 +349,31 @@ class BatchPlan:
 
 class Corrector:
     """Learned correction of a coarse-mesh FP32 PPPM (see include/pppm.h,
-    pppm_corr_*): per-site features of the coarse mesh potential go through a
-    32-64-64-3 tanh network with BF16 weights; its output, times q_i s_out, is
-    added to the coarse forces.  Training runs on the GPU (forward, backward and
-    Adam in the library's own kernels) against fine-mesh forces.
+    pppm_corr_*): per-site features of the coarse mesh potential go through an
+    n_in-64-64-3 tanh network with BF16 weights; its output, times q_i s_out,
+    is added to the coarse forces.  Training runs on the GPU (forward,
+    backward and Adam in the library's own kernels) against fine-mesh forces.
+
+    features: "cell" (48 inputs: 27 potential samples, site type, offset
+    inside the mesh cell) or "stated" (32 inputs: the samples and the type).
     """
 
-    N_IN = 48
+    WIDTH = {"cell": 48, "stated": 32}
+    N_IN = 48  # width of the default ("cell") set
 
-    def __init__(self, coarse: Plan, params=None, s_in: float = 1.0, s_out: float = 1.0):
+    def __init__(self, coarse: Plan, params=None, s_in: float = 1.0, s_out: float = 1.0, features: str = "cell"):
         if coarse.precision != "fp32":
             raise ValueError("the correction runs on an FP32 coarse plan")
         L = N.lib()
         self._lib = L
         self.coarse = coarse  # keeps the borrowed plan alive
         h = ctypes.c_void_p()
-        N.check(L.pppm_corr_create(coarse.handle, ctypes.byref(h)), "pppm_corr_create")
+        kind = {"cell": N.PPPM_CORR_CELL, "stated": N.PPPM_CORR_STATED}[features]
+        N.check(L.pppm_corr_create_features(coarse.handle, kind, ctypes.byref(h)), "pppm_corr_create_features")
         self._h = h
-        self.nparams = int(L.pppm_corr_nparams())
+        self.features_kind = features
+        self.n_in = int(L.pppm_corr_feature_width(h))
+        self.nparams = int(L.pppm_corr_param_count(h))
         if params is not None:
             self.set_weights(params, s_in, s_out)
 
@@ -418,7 +425,7 @@ class Corrector:
             raise ValueError("types must be a contiguous int8 CUDA tensor of shape (n,)")
 
     def _check_table(self, feat, target, idx):
-        if feat.dtype != torch.bfloat16 or feat.dim() != 2 or feat.shape[1] != self.N_IN or not feat.is_contiguous():
+        if feat.dtype != torch.bfloat16 or feat.dim() != 2 or feat.shape[1] != self.n_in or not feat.is_contiguous():
             raise ValueError("feat must be a contiguous (n, 32) bfloat16 tensor")
         if target.dtype != torch.float32 or tuple(target.shape) != (feat.shape[0], 3) or not target.is_contiguous():
             raise ValueError("target must be a contiguous (n, 3) float32 tensor")
@@ -431,7 +438,7 @@ class Corrector:
         self._sites(pos, q, types)
         n = pos.shape[0]
         if feat is None:
-            feat = torch.empty((n, self.N_IN), dtype=torch.bfloat16, device=pos.device)
+            feat = torch.empty((n, self.n_in), dtype=torch.bfloat16, device=pos.device)
         if forces is None:
             forces = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
         N.check(self._lib.pppm_corr_features(self._h, _stream(stream), _ptr(pos), _ptr(q), _ptr(types), n,
@@ -440,7 +447,7 @@ class Corrector:
 
     def forward(self, feat, out=None, stream=None):
         n = feat.shape[0]
-        assert feat.dtype == torch.bfloat16 and feat.is_contiguous() and feat.shape[1] == self.N_IN
+        assert feat.dtype == torch.bfloat16 and feat.is_contiguous() and feat.shape[1] == self.n_in
         if out is None:
             out = torch.empty((n, 3), dtype=torch.float32, device=feat.device)
         N.check(self._lib.pppm_corr_forward(self._h, _stream(stream), _ptr(feat), n, _ptr(out)),

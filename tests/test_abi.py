@@ -119,3 +119,10 @@ def test_batch_set_quantized_validates(pppm_lib):
 def test_wait_hooks_validate_arguments(pppm_lib):
     assert pppm_lib.pppm_set_wait_limit(None, 10) == N.PPPM_ERR_INVALID_ARG
     assert pppm_lib.pppm_batch_set_wait_probe(None, 1) == N.PPPM_ERR_INVALID_ARG
+
+
+def test_corrector_feature_sets_validate_arguments(pppm_lib):
+    h = ctypes.c_void_p()
+    assert pppm_lib.pppm_corr_create_features(None, N.PPPM_CORR_STATED, ctypes.byref(h)) == N.PPPM_ERR_INVALID_ARG
+    assert pppm_lib.pppm_corr_param_count(None) == N.PPPM_ERR_INVALID_ARG
+    assert pppm_lib.pppm_corr_feature_width(None) == N.PPPM_ERR_INVALID_ARG

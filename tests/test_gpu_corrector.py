@@ -31,11 +31,15 @@ def _mods():
     return Plan, Corrector, learned
 
 
-def _theta(seed, bias_scale=0.1):
+KINDS = ["cell", "stated"]
+
+
+def _theta(seed, bias_scale=0.1, kind="cell"):
+    n_in = mlp.FEATURE_WIDTH[kind]
     rng = np.random.default_rng(seed)
-    t = init_mlp_params(seed).astype(np.float64)
+    t = init_mlp_params(seed, n_in=n_in).astype(np.float64)
     o = 0
-    for name, shape in mlp.SHAPES:
+    for name, shape in mlp.shapes(n_in):
         k = int(np.prod(shape))
         if name.startswith("b"):
             t[o:o + k] = rng.normal(size=k) * bias_scale
@@ -64,12 +68,13 @@ CASES = [  # n_mol, L, mesh, order, seed
 ]
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("n_mol,L,m,p,seed", CASES)
-def test_features_match_oracle(cuda_device, n_mol, L, m, p, seed):
+def test_features_match_oracle(cuda_device, n_mol, L, m, p, seed, kind):
     Plan, Corrector, _ = _mods()
     w = make_water(n_mol, L, seed)
     coarse = Plan((L,) * 3, (m,) * 3, order=p, beta=0.4)
-    corr = Corrector(coarse, params=_theta(0), s_in=0.37, s_out=1.0)
+    corr = Corrector(coarse, params=_theta(0, kind=kind), s_in=0.37, s_out=1.0, features=kind)
     pos, q, types = _sites(w)
     feat, fc = corr.features(pos, q, types)
     torch.cuda.synchronize()
@@ -77,8 +82,9 @@ def test_features_match_oracle(cuda_device, n_mol, L, m, p, seed):
     posf, qf = pos.double().cpu().numpy(), q.double().cpu().numpy()
     orc = OraclePPPM((L,) * 3, (m,) * 3, p, 0.4)
     phi = orc.compute(posf, qf, want_intermediates=True)["phi"]
-    X = mlp.features(phi, posf, w.types, (L,) * 3, (m,) * 3, p, s_in=0.37)
+    X = mlp.features(phi, posf, w.types, (L,) * 3, (m,) * 3, p, s_in=0.37, kind=kind)
     ref = mlp.bf16_round(X.astype(np.float32))
+    assert g.shape == X.shape == (w.n, mlp.FEATURE_WIDTH[kind])
     d = np.abs(g - ref)
     ulp = _bf16_ulp(np.maximum(np.abs(g), np.abs(ref)))
     exact = float(np.mean(d == 0))
@@ -86,8 +92,11 @@ def test_features_match_oracle(cuda_device, n_mol, L, m, p, seed):
     # potential samples: one BF16 step, or the FP32 mesh error near zero
     assert np.all(d[:, :27] <= ulp[:, :27] + 1e-5 * np.max(np.abs(ref[:, :27])))
     # one-hot type and padding exactly; cell-offset terms to one step (+ FP32 location error)
-    assert np.array_equal(g[:, 27:30], X[:, 27:30]) and not g[:, 36:].any()
-    assert np.all(d[:, 30:36] <= ulp[:, 30:36] + 2e-6)
+    if kind == "cell":
+        assert np.array_equal(g[:, 27:30], X[:, 27:30]) and not g[:, 36:].any()
+        assert np.all(d[:, 30:36] <= ulp[:, 30:36] + 2e-6)
+    else:
+        assert np.array_equal(g[:, 27:30], X[:, 27:30]) and not g[:, 30:].any()
     assert exact >= 0.95
 
 
@@ -104,13 +113,14 @@ def test_potential_output_leaves_the_forces_unchanged(cuda_device):
     del corr
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("n", [1, 7, 16, 37, 1000, 16384])
-def test_forward_matches_oracle(cuda_device, n):
+def test_forward_matches_oracle(cuda_device, n, kind):
     Plan, Corrector, _ = _mods()
     w = make_water(4096, 49.7, 2)
     P = Plan((49.7,) * 3, (24,) * 3, order=5, beta=0.4)
-    theta = _theta(3)
-    corr = Corrector(P, params=theta, s_in=0.5, s_out=1.0)
+    theta = _theta(3, kind=kind)
+    corr = Corrector(P, params=theta, s_in=0.5, s_out=1.0, features=kind)
     pos, q, types = _sites(w)
     feat, _ = corr.features(pos, q, types)
     feat = feat[:n].contiguous()
@@ -126,12 +136,13 @@ def test_forward_matches_oracle(cuda_device, n):
     assert np.sqrt(np.mean(err ** 2)) <= 1e-3 * np.sqrt(np.mean(yr ** 2))
 
 
-def test_apply_is_coarse_plus_correction(cuda_device):
+@pytest.mark.parametrize("kind", KINDS)
+def test_apply_is_coarse_plus_correction(cuda_device, kind):
     Plan, Corrector, _ = _mods()
     w = make_water(4096, 49.7, 2)
     P = Plan((49.7,) * 3, (24,) * 3, order=5, beta=0.4)
-    theta = _theta(4)
-    corr = Corrector(P, params=theta, s_in=0.4, s_out=0.05)
+    theta = _theta(4, kind=kind)
+    corr = Corrector(P, params=theta, s_in=0.4, s_out=0.05, features=kind)
     pos, q, types = _sites(w)
     feat, fc = corr.features(pos, q, types)
     y = corr.forward(feat)
@@ -143,7 +154,8 @@ def test_apply_is_coarse_plus_correction(cuda_device):
     posf, qf = pos.double().cpu().numpy(), q.double().cpu().numpy()
     orc = OraclePPPM((49.7,) * 3, (24,) * 3, 5, 0.4)
     r = orc.compute(posf, qf, want_intermediates=True)
-    X = mlp.bf16_round(mlp.features(r["phi"], posf, w.types, (49.7,) * 3, (24,) * 3, 5, 0.4).astype(np.float32))
+    X = mlp.bf16_round(mlp.features(r["phi"], posf, w.types, (49.7,) * 3, (24,) * 3, 5, 0.4,
+                                    kind=kind).astype(np.float32))
     yr, _ = mlp.forward(theta, X, bf16=True, act_bf16=True)
     fr = r["forces"] + qf[:, None] * 0.05 * yr
     corr_part = qf[:, None] * 0.05 * yr
@@ -152,13 +164,14 @@ def test_apply_is_coarse_plus_correction(cuda_device):
     assert err <= 5e-3
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("nb,use_idx", [(1000, True), (128, False), (4099, True)])
-def test_gradient_matches_oracle(cuda_device, nb, use_idx):
+def test_gradient_matches_oracle(cuda_device, nb, use_idx, kind):
     Plan, Corrector, _ = _mods()
     w = make_water(4096, 49.7, 2)
     P = Plan((49.7,) * 3, (24,) * 3, order=5, beta=0.4)
-    theta = _theta(5)
-    corr = Corrector(P, params=theta, s_in=0.5, s_out=1.0)
+    theta = _theta(5, kind=kind)
+    corr = Corrector(P, params=theta, s_in=0.5, s_out=1.0, features=kind)
     pos, q, types = _sites(w)
     feat, _ = corr.features(pos, q, types)
     rng = np.random.default_rng(nb)
@@ -179,18 +192,19 @@ def test_gradient_matches_oracle(cuda_device, nb, use_idx):
     assert abs(loss.item() - lr_) <= 1e-5 * lr_
     # per block of parameters too (no block may hide behind the others)
     o = 0
-    for name, shape in mlp.SHAPES:
+    for name, shape in mlp.shapes(mlp.FEATURE_WIDTH[kind]):
         k = int(np.prod(shape))
         assert np.linalg.norm(gg[o:o + k] - gr[o:o + k]) <= 1e-4 * np.linalg.norm(gr[o:o + k]) + 1e-9, name
         o += k
 
 
-def test_adam_steps_match_oracle(cuda_device):
+@pytest.mark.parametrize("kind", KINDS)
+def test_adam_steps_match_oracle(cuda_device, kind):
     Plan, Corrector, _ = _mods()
     w = make_water(4096, 49.7, 2)
     P = Plan((49.7,) * 3, (24,) * 3, order=5, beta=0.4)
-    theta = _theta(6)
-    corr = Corrector(P, params=theta, s_in=0.5, s_out=1.0)
+    theta = _theta(6, kind=kind)
+    corr = Corrector(P, params=theta, s_in=0.5, s_out=1.0, features=kind)
     pos, q, types = _sites(w)
     feat, _ = corr.features(pos, q, types)
     rng = np.random.default_rng(0)
@@ -210,12 +224,13 @@ def test_adam_steps_match_oracle(cuda_device):
         th = got  # continue from the GPU's FP32 master values
 
 
-def test_training_is_deterministic_and_resumes_bitwise(cuda_device, tmp_path):
+@pytest.mark.parametrize("kind", KINDS)
+def test_training_is_deterministic_and_resumes_bitwise(cuda_device, tmp_path, kind):
     Plan, Corrector, learned = _mods()
     w = make_water(4096, 49.7, 2)
     P = Plan((49.7,) * 3, (24,) * 3, order=5, beta=0.4)
     pos, q, types = _sites(w)
-    theta = _theta(7)
+    theta = _theta(7, kind=kind)
     rng = np.random.default_rng(1)
 
     def run(c, steps, seed):
@@ -229,18 +244,18 @@ def test_training_is_deterministic_and_resumes_bitwise(cuda_device, tmp_path):
             c.train_step(feat, tgt, idx, 1e-3)
         return c.get_weights()[0]
 
-    a = Corrector(P, params=theta, s_in=0.5, s_out=1.0)
+    a = Corrector(P, params=theta, s_in=0.5, s_out=1.0, features=kind)
     run(a, 5, 10)
     ck = str(tmp_path / "corr.bin")
     a.save(ck)
     wa = run(a, 5, 11)
-    b = Corrector(P, params=_theta(8), s_in=2.0, s_out=3.0)
+    b = Corrector(P, params=_theta(8, kind=kind), s_in=2.0, s_out=3.0, features=kind)
     b.load(ck)
     assert b.scales == (0.5, 1.0)
     wb = run(b, 5, 11)
     assert np.array_equal(wa, wb)
     # a fresh run from the same start is bit-identical as well
-    c = Corrector(P, params=theta, s_in=0.5, s_out=1.0)
+    c = Corrector(P, params=theta, s_in=0.5, s_out=1.0, features=kind)
     run(c, 5, 10)
     assert np.array_equal(run(c, 5, 11), wa)
     del rng
@@ -263,6 +278,13 @@ def test_checkpoint_rejects_garbage_and_bad_arguments(cuda_device, tmp_path):
         corr.set_weights(np.zeros(corr.nparams, np.float32), 0.0, 1.0)
     with pytest.raises(ValueError):
         Corrector(Plan((20.0,) * 3, (16,) * 3, order=5, beta=0.4, precision="fp64"))
+    # a checkpoint of one feature set does not load into the other
+    ck = tmp_path / "cell.bin"
+    corr.save(str(ck))
+    other = Corrector(P, params=_theta(0, kind="stated"), features="stated")
+    assert other.nparams == 6467 and other.n_in == 32 and corr.nparams == 7491 and corr.n_in == 48
+    with pytest.raises(N.PPPMError):
+        other.load(str(ck))
     # no sites: the corrected call is the (empty) coarse call
     z = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
     e, f, v = corr.apply(z, torch.zeros(0, device="cuda"), torch.zeros(0, dtype=torch.int8, device="cuda"))
@@ -270,21 +292,28 @@ def test_checkpoint_rejects_garbage_and_bad_arguments(cuda_device, tmp_path):
     assert f.shape == (0, 3) and e.item() == 0.0
 
 
-def test_trained_network_gains_on_held_out_frames(cuda_device):
-    """Train on frames of 8 base configurations, evaluate on 2 others: the
-    corrected coarse mesh must be clearly closer to the fine mesh than the
-    coarse mesh alone."""
+@pytest.mark.parametrize("kind", KINDS)
+def test_trained_network_gains_on_held_out_frames(cuda_device, kind):
+    """Train on frames of 8 base configurations, evaluate on 2 others.  With
+    the cell set the corrected coarse mesh must be clearly closer to the fine
+    mesh than the coarse mesh alone; the stated set (samples and type alone)
+    carries almost nothing of the coarse-mesh error, which depends on where a
+    site sits inside its cell, so for it the test asserts only that the
+    correction does not make the forces worse, and prints the gain."""
     Plan, Corrector, learned = _mods()
     n_mol, L = 4096, 49.7
     coarse = Plan((L,) * 3, (24,) * 3, order=5, beta=0.4)
     fine = Plan((L,) * 3, (60,) * 3, order=5, beta=0.4)
-    corr = Corrector(coarse)
+    corr = Corrector(coarse, features=kind)
     spec = learned.FrameSpec(n_mol=n_mol, L=L, base_seeds=tuple(range(100, 108)), frames_per_base=8, sigma=0.05)
     ds = learned.build_dataset(corr, fine, spec)
     log = learned.train(corr, ds, steps=3000, batch=4096, lr=2e-3, seed=0, init_seed=0)
     held = learned.FrameSpec(n_mol=n_mol, L=L, base_seeds=(200, 201), frames_per_base=2, sigma=0.05, noise_seed=9)
     res = learned.evaluate(corr, fine, held)
-    print(f"held-out force RMS vs fine: coarse {res['coarse']:.4e} corrected {res['corrected']:.4e} "
+    print(f"held-out force RMS vs fine ({kind}): coarse {res['coarse']:.4e} corrected {res['corrected']:.4e} "
           f"gain {res['coarse'] / res['corrected']:.2f}x; loss {log.loss[0][1]:.3e} -> {log.loss[-1][1]:.3e} "
           f"in {log.seconds:.2f} s")
-    assert res["corrected"] < 0.8 * res["coarse"]
+    if kind == "cell":
+        assert res["corrected"] < 0.8 * res["coarse"]
+    else:
+        assert res["corrected"] <= 1.02 * res["coarse"]
