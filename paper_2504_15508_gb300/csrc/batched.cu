@@ -40,7 +40,6 @@ constexpr int kSiteChunk = 1024;  // sites per bin / scatter item
 constexpr int kZPairs = 8;        // row pairs per z-pass item
 constexpr int kSpreadTiles = kWarps;
 constexpr int kGatherTiles = 2;   // four warps per tile
-constexpr int kKeyCap = 256;      // sites per tile ordered by index in the spread
 
 struct BoxDesc {
     Geo g;
@@ -95,6 +94,7 @@ struct Bufs {
     int qgroup;     // node size of the int32-quantised DFT (0: off)
     double qscale;  // its scale
     int wait_probe;  // 1: box 0's scan waits for one binning item more than exist (its wait runs out)
+    RedRows red_rows;  // lane -> stencil row of the spread's shared-memory atomics
 };
 
 // ------------------------------------------------------------------ helpers
@@ -231,110 +231,83 @@ __device__ void st_scatter(const BoxDesc& D, int idx, const Bufs& B) {
     }
 }
 
+// Spread: the item's kSpreadTiles tiles one after another, each by the whole
+// block.  A tile's patch is accumulated in shared memory as 64-bit fixed-point
+// integers with shared-memory atomics (red_scale_exp picks the grid from the
+// tile's sites): integer sums are exact and do not depend on the order in
+// which the warps add their sites, so the result is bitwise reproducible with
+// no ordering of the tile's sites.  The patch keeps the padded pitch and is
+// written out as FP32.
 template <int P, int TILE>
-struct __align__(16) SpreadSmem {  // 16-byte aligned: staged rows take vector stores
+struct SpreadRed {
     static constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
-    static constexpr int WSP = wstride(P) + 4;
-    union {
-        int keys[kKeyCap];     // original indices, while ranking
-        float st_w[32][WSP];   // staged weights, while spreading
-    } u;
-    float pt[PSIZE];
-    int st_cell[32];
-    short perm[kKeyCap];  // canonical position -> slot in the tile
+    static constexpr size_t bytes() { return sizeof(unsigned long long) * PSIZE + sizeof(unsigned) * kWarps; }
 };
 
-// One warp per tile, as the single-box fast spread (canonical site order,
-// conflict-free stencil rows, no atomics); the patch keeps the padded pitch.
 template <int P, int TILE>
 __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
-    typedef SpreadSmem<P, TILE> W_t;
-    constexpr int PZ = W_t::PZ, PLANE = W_t::PLANE, PSIZE = W_t::PSIZE;
+    typedef SpreadRed<P, TILE> L;
+    constexpr int PZ = L::PZ, PLANE = L::PLANE, PSIZE = L::PSIZE;
     constexpr int WS = wstride(P);
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem);
+    unsigned* wmax = reinterpret_cast<unsigned*>(acc + PSIZE);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = idx * kSpreadTiles + warp;
-    if (tile >= D.g.ntiles) return;
-    W_t& W = reinterpret_cast<W_t*>(smem)[warp];
-    constexpr int NV = WS / 4;  // 16-byte vectors per weight row
-    const int s0 = ldcg(&B.tile_start[D.ts0 + tile]);
-    const int c = ldcg(&B.tile_start[D.ts0 + tile + 1]) - s0;
-    const long long sb = D.site0 + s0;
-    // canonical order (by original index) by counting ranks, as the single-box spread
-    const bool ranked = c > 1 && c <= kKeyCap;
-    const bool dense = c > kKeyCap;  // ranked from global memory instead
-    if (ranked) {
-        for (int i = lane; i < c; i += 32) W.u.keys[i] = ldcg(&B.sorig[sb + i]);
-    }
-    for (int i = lane; i < PSIZE; i += 32) W.pt[i] = 0.f;
-    __syncwarp();
-    if (ranked) {
-        // rank of item i = number of items with a smaller original index
-        for (int i = lane; i < c; i += 32) {
-            const int ki = W.u.keys[i];
-            int r = 0;
-            for (int j = 0; j < c; ++j) r += W.u.keys[j] < ki;
-            W.perm[r] = (short)i;
-        }
-    }
-    __syncwarp();
-    // the slot and tile arrays are dead after the scatter
-    if (dense) rank_dense_tile(B.sorig + sb, c, B.slot_of + sb, B.tile_of + sb, W.u.keys);
     constexpr int NR = (P * P + 31) / 32;
     int roff[NR], riy[NR], riz[NR];
     bool ract[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-        const int row = lane + 32 * j;
-        ract[j] = row < P * P;
-        riy[j] = ract[j] ? row / P : 0;
-        riz[j] = ract[j] ? row % P : 0;
+        const int slot = lane + 32 * j;
+        ract[j] = slot < P * P;
+        const int row = ract[j] ? (int)B.red_rows.row[slot] : 0;
+        riy[j] = row / P;
+        riz[j] = row % P;
         roff[j] = riy[j] * PZ + riz[j];
     }
-    // the next batch's weights and cell, in flight while the current one is spread
-    float4 nw[NV];
-    int ncell = 0;
-    auto fetch = [&](int t0) {
-        if (t0 + lane < c) {
-            const long long st = sb + (ranked ? (int)W.perm[t0 + lane] : (dense ? ldcg(&B.slot_of[sb + t0 + lane]) : t0 + lane));
-            const float4* src = reinterpret_cast<const float4*>(B.swt + st * WS);
+    for (int k = 0; k < kSpreadTiles; ++k) {
+        const int tile = idx * kSpreadTiles + k;
+        if (tile >= D.g.ntiles) break;  // uniform across the block
+        const int s0 = ldcg(&B.tile_start[D.ts0 + tile]);
+        const int c = ldcg(&B.tile_start[D.ts0 + tile + 1]) - s0;
+        const long long sb = D.site0 + s0;
+        for (int i = threadIdx.x; i < PSIZE; i += kThreads) acc[i] = 0ull;
+        unsigned mb = 0;  // largest |q Wx| of the tile
+        for (int t = threadIdx.x; t < c; t += kThreads) {
+            const float* w = B.swt + (sb + t) * WS;
 #pragma unroll
-            for (int a = 0; a < NV; ++a) nw[a] = __ldcg(&src[a]);
-            ncell = ldcg(&B.scell[st]);
+            for (int a = 0; a < P; ++a) mb = max(mb, __float_as_uint(fabsf(ldcg(&w[a]))));
         }
-    };
-    fetch(0);
-    for (int t0 = 0; t0 < c; t0 += 32) {
-        const int nb = min(32, c - t0);
-        if (lane < nb) {
-            float4* dst = reinterpret_cast<float4*>(&W.u.st_w[lane][0]);
+        mb = __reduce_max_sync(0xffffffffu, mb);
+        if (lane == 0) wmax[warp] = mb;
+        __syncthreads();
 #pragma unroll
-            for (int a = 0; a < NV; ++a) dst[a] = nw[a];
-            W.st_cell[lane] = ncell;
-        }
-        __syncwarp();
-        fetch(t0 + 32);
-        for (int j = 0; j < nb; ++j) {
-            const int cl = W.st_cell[j];
-            const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+        for (int w = 0; w < kWarps; ++w) mb = max(mb, wmax[w]);
+        const int ks = red_scale_exp(mb, c);
+        const float S = pow2f(ks), invS = pow2f(-ks);
+        for (int t = warp; t < c; t += kWarps) {
+            const float* w = B.swt + (sb + t) * WS;
             float wxq[P];
 #pragma unroll
-            for (int a = 0; a < P; ++a) wxq[a] = W.u.st_w[j][a];
-            float* base0 = W.pt + lx * PLANE + ly * PZ + lz;
+            for (int a = 0; a < P; ++a) wxq[a] = ldcg(&w[a]);
+            const int cl = ldcg(&B.scell[sb + t]);
+            const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+            unsigned long long* base0 = acc + lx * PLANE + ly * PZ + lz;
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr) {
                 if (ract[jr]) {
-                    const float wyz = W.u.st_w[j][P + riy[jr]] * W.u.st_w[j][2 * P + riz[jr]];
-                    float* b = base0 + roff[jr];
+                    const float wyz = ldcg(&w[P + riy[jr]]) * ldcg(&w[2 * P + riz[jr]]);
+                    unsigned long long* b = base0 + roff[jr];
 #pragma unroll
-                    for (int a = 0; a < P; ++a) b[a * PLANE] += wxq[a] * wyz;
+                    for (int a = 0; a < P; ++a)
+                        atomicAdd(b + a * PLANE, (unsigned long long)__float2ll_rn(wxq[a] * wyz * S));
                 }
             }
-            __syncwarp();
         }
-        __syncwarp();
+        __syncthreads();
+        float* dst = B.patch + D.patch0 + (long long)tile * PSIZE;
+        for (int i = threadIdx.x; i < PSIZE; i += kThreads) dst[i] = __ll2float_rn((long long)acc[i]) * invS;
+        __syncthreads();
     }
-    float* dst = B.patch + D.patch0 + (long long)tile * PSIZE;
-    for (int i = lane; i < PSIZE; i += 32) dst[i] = W.pt[i];
 }
 
 // fold of the patches covering (x, y, z): up to four cover slots per axis
@@ -968,7 +941,7 @@ k_batched(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, int
 
 template <int P, int TILE>
 size_t stage_smem(int maxN, int maxB) {
-    size_t m = sizeof(SpreadSmem<P, TILE>) * kWarps;
+    size_t m = SpreadRed<P, TILE>::bytes();
     m = std::max(m, (size_t)kThreads * sizeof(int));
     m = std::max(m, (size_t)(2 * kZPairs * maxN) * sizeof(float2));
     m = std::max(m, (size_t)(2 * maxN * maxB) * sizeof(float2));
@@ -1338,6 +1311,7 @@ int enqueue(pppm_batch* P, cudaStream_t s, int li, const float* pos, const float
     B.qgroup = P->quant_group;
     B.qscale = P->quant_scale;
     B.wait_probe = P->wait_probe;
+    B.red_rows = red_rows(P->order, (Y.T + P->order - 1) | 1);
     cudaError_t e = cudaErrorInvalidValue;
     const int n = (int)Y.items.size();
     const bool quant = P->quant_group > 0;

@@ -178,6 +178,48 @@ __device__ __forceinline__ void rank_dense_tile(const int* keys, int c, int* ord
     __syncwarp();
 }
 
+// Integer (64-bit fixed-point) accumulation of the spread patches of the
+// batched form.
+//
+// Slot (lane + 32 j) -> stencil row iy p + iz, so that the 64-bit accesses of
+// each half-warp (served 16 lanes, 128 bytes, at a time) fall on distinct
+// bank pairs: row (iy, iz) starts at element iy PZ + iz (plus the same site
+// offset for every row), bank pair (iy PZ + iz) mod 16; rows are ordered by
+// (occurrence, bank pair) so that consecutive slots walk the bank pairs
+// round-robin.  Computed on the host, passed to the kernels by value.
+struct RedRows {
+    unsigned char row[64];
+};
+
+inline RedRows red_rows(int p, int pz) {
+    auto grp = [&](int r) { return ((r / p) * pz + r % p) & 15; };
+    int key[64];
+    int seen[16] = {};
+    for (int i = 0; i < p * p; ++i) key[i] = (seen[grp(i)]++) * 16 + grp(i);
+    RedRows rr{};
+    for (int i = 0; i < p * p; ++i) {
+        int pos = 0;
+        for (int j = 0; j < p * p; ++j) pos += key[j] < key[i] || (key[j] == key[i] && j < i);
+        rr.row[pos] = (unsigned char)i;
+    }
+    return rr;
+}
+
+// k of the grid 2^-k for a tile of c sites whose largest |q Wx| is m (as
+// float bits): a patch value sums at most c contributions of at most m each
+// (Wy, Wz <= 1), so |sum| 2^k < 2^61
+__device__ __forceinline__ int red_scale_exp(unsigned m_bits, int c) {
+    const float mq = __uint_as_float(m_bits);
+    if (!(mq > 0.f)) return 60;  // no charge: any scale
+    const float m = mq * (float)max(c, 1);
+    if (!isfinite(m)) return -64;
+    const int e = (int)((__float_as_uint(m) >> 23) & 255u) - 126;  // m < 2^e
+    return min(100, 61 - e);
+}
+
+// 2^k from its exponent bits (-126 <= k <= 127)
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(k + 127) << 23); }
+
 extern thread_local bool g_pdl;  // launches of this host thread use PDL
 
 struct PdlScope {
@@ -234,7 +276,7 @@ inline bool fast_tiles(const Geo& g) {
 }
 
 // ------------------------------------------------------------------ launchers
-// site_kernels.cu
+// site_sort.cu
 template <typename T, typename In>
 cudaError_t launch_bin(cudaStream_t s, const Geo& g, const In* pos, const In* q, int n, int* tile_count,
                        int* tile_of, int* slot_of, Rec<T>* rec, int* cell, int* status);

@@ -218,13 +218,15 @@ def test_full_batched96_matches_oracle_per_box(cuda_device, pppm_lib, tile, dft)
     torch.cuda.synchronize()
     assert bp.status() == 0 and bp.tile == tile
     e, f, v = e.cpu().numpy(), f.cpu().numpy(), v.cpu().numpy()
-    worst = (0.0, 0.0, 0.0)
+    worst, bad = (0.0, 0.0, 0.0), []
     for b in range(len(boxes)):
         sl = slice(offs[b], offs[b + 1])
         ferr = _rel(f[sl], refs[b]["forces"])
         eerr = abs(e[b] - refs[b]["energy"]) / abs(refs[b]["energy"])
         verr = _rel(v[b], refs[b]["virial"])
         worst = tuple(max(a, c) for a, c in zip(worst, (ferr, eerr, verr)))
-        assert ferr <= 1e-5 and eerr <= 1e-6 and verr <= 1e-5, (b, specs[b]["mesh"], ferr, eerr, verr)
+        if not (ferr <= 1e-5 and eerr <= 1e-6 and verr <= 1e-5):
+            bad.append((b, specs[b]["n_mol"], specs[b]["mesh"][0], f"{ferr:.2e}", f"{eerr:.2e}", f"{verr:.2e}"))
     print(f"batched96 tile {tile} dft {dft}: worst force {worst[0]:.2e} energy {worst[1]:.2e} "
-          f"virial {worst[2]:.2e}")
+          f"virial {worst[2]:.2e}; over the bar: {bad}")
+    assert not bad, bad
