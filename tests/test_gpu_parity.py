@@ -51,7 +51,7 @@ def _random_neutral(n, box, seed):
     return pos, q
 
 
-def _check(res, ref, prec, what=""):
+def _check(res, ref, prec, what="", etol=ETOL):
     e, f, v = res
     torch.cuda.synchronize()
     ferr = _rel(f.cpu().numpy(), ref["forces"])
@@ -59,7 +59,7 @@ def _check(res, ref, prec, what=""):
     verr = _rel(v.cpu().numpy(), ref["virial"])
     print(f"{what} {prec}: force {ferr:.3e} energy {eerr:.3e} virial {verr:.3e}")
     assert ferr <= FTOL[prec], (what, ferr)
-    assert eerr <= ETOL, (what, eerr)
+    assert eerr <= etol, (what, eerr)
     assert verr <= max(FTOL[prec], 1e-10), (what, verr)
 
 
@@ -287,7 +287,11 @@ def test_one_tile_holds_every_site(cuda_device, pppm_lib, prec, mesh):
     linearly with the tile, so the call ends quickly (a pairwise ranking would
     take ~1e8 dependent loads a lane).  36^3 runs the full-tile kernels with
     tile edge 4, 30^3 the generic ones (30 is not a multiple of 4).  Two runs
-    agree bitwise and match the oracle."""
+    agree bitwise and match the oracle: forces at the path's tolerance; the
+    FP32 energy to 1e-5, because here every mesh point of the cluster sums
+    ~22,000 FP32 contributions (60,000 sites x 125 points over ~7^3 points)
+    one after another, whose rounding grows like sqrt(22,000) x 2^-24 = 9e-6
+    relative, far beyond the ~100 of a water tile."""
     import time
     box = np.array([12.0, 12.0, 12.0])
     rng = np.random.default_rng(77)
@@ -307,7 +311,7 @@ def test_one_tile_holds_every_site(cuda_device, pppm_lib, prec, mesh):
     for a, b in zip(r1, r2):
         assert torch.equal(a, b)
     ref = OraclePPPM(box, mesh, 5, 0.4).compute(pos_r, q_r)
-    _check(r1, ref, prec, f"one tile {mesh}")
+    _check(r1, ref, prec, f"one tile {mesh}", etol=1e-5 if prec == "fp32" else ETOL)
 
 
 def test_gather_wait_runs_out_cleanly(cuda_device, pppm_lib):
