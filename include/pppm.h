@@ -123,11 +123,11 @@ int pppm_compute_f32(pppm_plan *plan, void *stream, const float *pos, const floa
 
 /*
  * The same evaluation from HOST arrays (pinned or pageable), synchronous:
- * energy, forces and virial are in the host arrays on return.  Pinned
- * (device-mapped) pos and q are read in place by the device, so the transfer
- * overlaps the first kernel; pageable ones are first copied to plan-owned
- * device buffers.  From the second call with the same n and plan state the
- * device part is a replay of a graph captured by the first.  Returns the
+ * energy, forces and virial are in the host arrays on return.  pos and q are
+ * copied to plan-owned device buffers (at full copy-engine speed from pinned
+ * memory), the forces come back by one copy.  From the second call with the
+ * same n and plan state the device part is a replay of a graph captured by
+ * the first.  Returns the
  * device status too (PPPM_ERR_NONFINITE if bad positions were seen,
  * PPPM_ERR_TIMEOUT if a bounded device-side wait ran out).
  */

@@ -32,9 +32,11 @@ thread_local bool g_pdl = false;
 namespace {
 
 enum Slot { K_BIN, K_SCAN, K_SCATTER, K_SPREAD, K_FOLD, K_FFT_Z_R2C, K_FFT_Y, K_FFT_X_INFLUENCE, K_FFT_Y_INV3,
-            K_FFT_Z_C2R, K_GATHER, K_NSLOTS };
+            K_FFT_Z_C2R, K_GATHER, K_TILES_INIT, K_NSLOTS };
+// with fixed tile regions, "bin" is the one-pass sort ("scan" and "scatter"
+// belong to the compact layout)
 const char* kSlotNames[K_NSLOTS] = {"bin", "scan", "scatter", "spread", "fold", "fft_z_r2c", "fft_y",
-                                    "fft_x_influence", "fft_y_inverse3", "fft_z_c2r", "gather"};
+                                    "fft_x_influence", "fft_y_inverse3", "fft_z_c2r", "gather", "tiles_init"};
 
 cudaEvent_t prof_event(pppm_plan* P) {
     if (!P->ev_pool.empty()) {
@@ -153,12 +155,17 @@ int setup_tiles(pppm_plan* P, int T) {
     dfree(P->cov_ent);
     dfree(P->cov2);
     dfree(P->tile_count);
-    dfree(P->tile_start);
+    dfree(P->tiles);
+    dfree(P->region_flag);
     const size_t psz = (size_t)g.E[0] * g.E[1] * g.Pz;
     int rc;
     if ((rc = dalloc(&P->patch, (size_t)g.ntiles * psz * P->esz)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->tile_count, sizeof(int) * (size_t)g.ntiles)) != PPPM_OK) return rc;
-    if ((rc = dalloc(&P->tile_start, sizeof(int) * ((size_t)g.ntiles + 1))) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->tiles, sizeof(int2) * (size_t)g.ntiles)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->region_flag, 2 * sizeof(int))) != PPPM_OK) return rc;
+    // a tile's fixed region holds as many sites as the fast spread ranks in
+    // shared memory at tile edge 8 (at edge 4 the average tile is 8x smaller)
+    P->region_cap = T == 8 ? 256 : 128;
     // cover lists: for each axis and mesh index, the (tile, patch coordinate) pairs mapping to it
     int nmax = g.N[0];
     if (g.N[1] > nmax) nmax = g.N[1];
@@ -211,30 +218,47 @@ int setup_tiles(pppm_plan* P, int T) {
     return PPPM_OK;
 }
 
+// Slots of the fixed tile regions for n sites, or 0 when the plan uses the
+// compact layout: regions need ntiles x cap slots, used only while that is at
+// most 16 times the compact size (and below 2^27).
+int64_t region_slots(const pppm_plan* P, int64_t n) {
+    const int64_t slots = (int64_t)P->g.ntiles * P->region_cap;
+    const int64_t lim = 16 * (n > 65536 ? n : 65536);
+    return (P->region_cap > 0 && slots <= lim && slots <= ((int64_t)1 << 27)) ? slots : 0;
+}
+
 int reserve_sites(pppm_plan* P, int64_t n) {
-    if (n <= P->cap) return PPPM_OK;
     if (n > (int64_t)1 << 30) return PPPM_ERR_TOO_LARGE;
+    int rc;
+    if (n > P->cap) {  // per-site arrays in the caller's order (compact path only)
+        ++P->gen;
+        dfree(P->rec);
+        dfree(P->cell);
+        P->cap = 0;
+        if ((rc = dalloc(&P->rec, 4 * P->esz * n)) != PPPM_OK) return rc;
+        if ((rc = dalloc(&P->cell, sizeof(int) * n)) != PPPM_OK) return rc;
+        P->cap = n;
+    }
+    // tile-ordered arrays, and the per-site tile and rank (also the dense
+    // ranking's scratch, indexed by slot)
+    int64_t slots = region_slots(P, n);
+    if (slots < n) slots = n;
+    if (slots <= P->slot_cap) return PPPM_OK;
     ++P->gen;
     dfree(P->tile_of);
     dfree(P->slot_of);
-    dfree(P->rec);
-    dfree(P->cell);
     dfree(P->srec);
     dfree(P->scell);
     dfree(P->sorig);
     dfree(P->swt);
-    P->cap = 0;
-    const size_t rs = 4 * P->esz;
-    int rc;
-    if ((rc = dalloc(&P->tile_of, sizeof(int) * n)) != PPPM_OK) return rc;
-    if ((rc = dalloc(&P->slot_of, sizeof(int) * n)) != PPPM_OK) return rc;
-    if ((rc = dalloc(&P->rec, rs * n)) != PPPM_OK) return rc;
-    if ((rc = dalloc(&P->cell, sizeof(int) * n)) != PPPM_OK) return rc;
-    if ((rc = dalloc(&P->srec, rs * n)) != PPPM_OK) return rc;
-    if ((rc = dalloc(&P->scell, sizeof(int) * n)) != PPPM_OK) return rc;
-    if ((rc = dalloc(&P->sorig, sizeof(int) * n)) != PPPM_OK) return rc;
-    if ((rc = dalloc(&P->swt, P->esz * wstride(P->order) * n)) != PPPM_OK) return rc;
-    P->cap = n;
+    P->slot_cap = 0;
+    if ((rc = dalloc(&P->tile_of, sizeof(int) * slots)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->slot_of, sizeof(int) * slots)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->srec, 4 * P->esz * slots)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->scell, sizeof(int) * slots)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->sorig, sizeof(int) * slots)) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->swt, P->esz * wstride(P->order) * slots)) != PPPM_OK) return rc;
+    P->slot_cap = slots;
     return PPPM_OK;
 }
 
@@ -285,18 +309,27 @@ int build_field_map(pppm_plan* P) {
 template <typename T, typename In>
 int run_sites_to_patches(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_t n, T* rho_out, T scale) {
     Geo& g = P->g;
-    CK(cudaMemsetAsync(P->tile_count, 0, sizeof(int) * (size_t)g.ntiles, s));
-    { PROF(K_BIN);
-      CK((launch_bin<T, In>(s, g, pos, q, (int)n, P->tile_count, P->tile_of, P->slot_of, (Rec<T>*)P->rec, P->cell,
-                            P->status))); }
-    { PROF(K_SCAN); CK(launch_scan(s, P->tile_count, g.ntiles, P->tile_start)); }
     // the fast spread and the TMA gather read only cells, indices and weights
     const bool need_rec = !fast_tiles(g) || !P->fmap_ok;
-    { PROF(K_SCATTER);
-      CK(launch_scatter<T>(s, g, (int)n, P->tile_of, P->slot_of, P->tile_start, (const Rec<T>*)P->rec, P->cell,
-                           need_rec ? (Rec<T>*)P->srec : nullptr, P->scell, P->sorig, (T*)P->swt)); }
+    if (region_slots(P, n) > 0) {
+        // fixed tile regions: one pass over the sites; its last block rebuilds
+        // the compact layout only if a region overflowed
+        { PROF(K_TILES_INIT); CK(launch_tiles_init(s, P->tiles, g.ntiles, P->region_cap, P->region_flag)); }
+        DirectArgs<T> a{P->tiles, P->region_cap, P->region_flag, P->tile_of, P->slot_of,
+                        need_rec ? (Rec<T>*)P->srec : nullptr, P->scell, P->sorig, (T*)P->swt, P->status};
+        { PROF(K_BIN); CK((launch_bin_direct<T, In>(s, g, pos, q, (int)n, a))); }
+    } else {
+        CK(cudaMemsetAsync(P->tile_count, 0, sizeof(int) * (size_t)g.ntiles, s));
+        { PROF(K_BIN);
+          CK((launch_bin<T, In>(s, g, pos, q, (int)n, P->tile_count, P->tile_of, P->slot_of, (Rec<T>*)P->rec,
+                                P->cell, P->status))); }
+        { PROF(K_SCAN); CK(launch_scan(s, P->tile_count, g.ntiles, P->tiles)); }
+        { PROF(K_SCATTER);
+          CK(launch_scatter<T>(s, g, (int)n, P->tile_of, P->slot_of, P->tiles, (const Rec<T>*)P->rec, P->cell,
+                               need_rec ? (Rec<T>*)P->srec : nullptr, P->scell, P->sorig, (T*)P->swt)); }
+    }
     { PROF(K_SPREAD);
-      CK(launch_spread<T>(s, g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig, (const T*)P->swt,
+      CK(launch_spread<T>(s, g, P->tiles, (const Rec<T>*)P->srec, P->scell, P->sorig, (const T*)P->swt,
                           (T*)P->patch, P->slot_of, P->tile_of)); }
     if (rho_out) {
         PROF(K_FOLD);
@@ -375,7 +408,7 @@ int run_compute(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_
     if ((rc = run_solve<T>(P, s, energy, virial, fl)) != PPPM_OK) return rc;
     if (forces && n > 0) {
         PROF(K_GATHER);
-        CK((launch_gather<T, In>(s, P->g, P->tile_start, (const Rec<T>*)P->srec, P->scell, P->sorig,
+        CK((launch_gather<T, In>(s, P->g, P->tiles, (const Rec<T>*)P->srec, P->scell, P->sorig,
                                  (const T*)P->swt, fl, P->flayout, P->fmap_ok ? (const void*)&P->fmap : nullptr,
                                  P->opt.prefactor, forces, P->status, P->wait_limit)));
     }
@@ -391,16 +424,6 @@ int compute_dispatch(pppm_plan* P, void* stream, const In* pos, const In* q, int
     CK(cudaSetDevice(P->device));
     if (P->precision == PPPM_FP32) return run_compute<float, In>(P, s, pos, q, n, energy, forces, virial, nullptr);
     return run_compute<double, In>(P, s, pos, q, n, energy, forces, virial, nullptr);
-}
-
-// The device address of a pinned, device-mapped host array, else nullptr.
-const void* mapped_host(const void* p) {
-    cudaPointerAttributes a{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 void drop_host_graph(pppm_plan* P) {
@@ -432,20 +455,14 @@ int compute_host(pppm_plan* P, const In* pos, const In* q, int64_t n, double* en
     In* d_q = d_pos + 3 * n;
     In* d_f = d_q + n;
     cudaStream_t s = P->own;
-    // pinned (device-mapped) host arrays are read in place by the binning
-    // kernel, which then overlaps the transfer; others are copied first
+    // the sites are copied to the staging buffers first (a DMA copy from
+    // pinned memory is faster than the sort reading them across the host
+    // link in place), so the replayed graph always reads the same pointers
     const In* use_pos = d_pos;
     const In* use_q = d_q;
     if (n > 0) {
-        const In* mp = (const In*)mapped_host(pos);
-        const In* mq = (const In*)mapped_host(q);
-        if (mp && mq) {
-            use_pos = mp;
-            use_q = mq;
-        } else {
-            CK(cudaMemcpyAsync(d_pos, pos, sizeof(In) * 3 * n, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(d_q, q, sizeof(In) * n, cudaMemcpyHostToDevice, s));
-        }
+        CK(cudaMemcpyAsync(d_pos, pos, sizeof(In) * 3 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_q, q, sizeof(In) * n, cudaMemcpyHostToDevice, s));
     }
     // the device part replays a graph captured on an earlier call with the
     // same site count and plan state; the site pointers are patched per call
@@ -665,7 +682,8 @@ void pppm_destroy(pppm_plan* P) {
     dfree(P->cov_ent);
     dfree(P->cov2);
     dfree(P->tile_count);
-    dfree(P->tile_start);
+    dfree(P->tiles);
+    dfree(P->region_flag);
     dfree(P->tile_of);
     dfree(P->slot_of);
     dfree(P->rec);

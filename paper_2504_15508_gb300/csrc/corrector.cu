@@ -92,17 +92,15 @@ __device__ __forceinline__ void bspline_all(float x0, float w[P]) {
 
 // One thread per site.  The 27 samples share the site's weights; with the
 // (p+2)^3 mesh values around the site they are three separable contractions.
-// Thread t takes site perm[t]: with the solve's tile order as perm, the sites
-// of a warp lie in one tile and their mesh rows overlap, so a warp's loads
-// touch a few rows instead of 32 scattered ones.
+// With the solve's tile order given (tiles, sorig), block b takes the sites of
+// tile b, so the sites of a warp lie in one tile and their mesh rows overlap
+// (a warp's loads touch a few rows instead of 32 scattered ones); without it
+// thread t takes site t.
 template <int P, int NIN>
-__global__ void k_features(Geo g, FieldLayout fl, const float* __restrict__ phi, const float* __restrict__ pos,
-                           const signed char* __restrict__ types, const int* __restrict__ perm, int n, float s_in,
-                           __nv_bfloat16* __restrict__ feat) {
+__device__ __forceinline__ void site_features(const Geo& g, const FieldLayout& fl, const float* __restrict__ phi,
+                                              const float* __restrict__ pos, const signed char* __restrict__ types,
+                                              int i, float s_in, __nv_bfloat16* __restrict__ feat) {
     constexpr int W = P + 2;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int i = perm ? __ldg(&perm[t]) : t;
     const bool odd = (g.order & 1) != 0;
     int gc[3];
     float w[3][P];
@@ -187,6 +185,20 @@ __global__ void k_features(Geo g, FieldLayout fl, const float* __restrict__ phi,
         w.z = pack_bf16(v[8 * k + 4], v[8 * k + 5]);
         w.w = pack_bf16(v[8 * k + 6], v[8 * k + 7]);
         o[k] = w;
+    }
+}
+
+template <int P, int NIN>
+__global__ void k_features(Geo g, FieldLayout fl, const float* __restrict__ phi, const float* __restrict__ pos,
+                           const signed char* __restrict__ types, const int2* __restrict__ tiles,
+                           const int* __restrict__ sorig, int n, float s_in, __nv_bfloat16* __restrict__ feat) {
+    if (tiles) {
+        const int2 tr = tiles[blockIdx.x];
+        for (int s = tr.x + threadIdx.x; s < tr.y; s += blockDim.x)
+            site_features<P, NIN>(g, fl, phi, pos, types, __ldg(&sorig[s]), s_in, feat);
+    } else {
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;
+        if (t < n) site_features<P, NIN>(g, fl, phi, pos, types, t, s_in, feat);
     }
 }
 
@@ -634,15 +646,16 @@ cudaError_t launch_features(pppm_corr* C, cudaStream_t s, const float* pos, cons
     pl.fstride = 0;
     pl.pstride = 1;
     // every caller runs this right after a solve of the same n sites on the
-    // same stream, whose scatter left the tile order (a permutation of 0..n-1)
-    // in the plan
-    const int* perm = n <= P->cap ? P->sorig : nullptr;
-    const int blocks = (int)((n + 127) / 128);
+    // same stream, which left their tile order in the plan
+    const bool by_tile = n <= P->slot_cap && P->tiles;
+    const int2* tiles = by_tile ? P->tiles : nullptr;
+    const int blocks = by_tile ? P->g.ntiles : (int)((n + 127) / 128);
     return with_nin(C->nin, [&](auto N) -> cudaError_t {
         constexpr int NIN = decltype(N)::value;
 #define PPPM_FEAT(PP)                                                                                           \
     case PP:                                                                                                    \
-        k_features<PP, NIN><<<blocks, 128, 0, s>>>(P->g, pl, phi, pos, types, perm, (int)n, C->s_in, feat);         \
+        k_features<PP, NIN><<<blocks, 128, 0, s>>>(P->g, pl, phi, pos, types, tiles, P->sorig, (int)n, C->s_in,  \
+                                                   feat);                                                         \
         break;
         switch (P->order) {
             PPPM_FEAT(3)

@@ -3,12 +3,13 @@
 // The step is a fixed sequence of about a dozen kernels and memsets whose
 // arguments, apart from the sites, do not change between steps of a run.  The
 // graph is captured from one ordinary compute call; on replay, new position
-// and charge pointers are patched into the one kernel node that reads them
-// (the binning kernel), so a caller may feed a different resident frame every
-// step without copying it.  Outputs (energy, forces, virial), the site count
+// and charge pointers are patched into the kernel nodes that read them (the
+// one-pass site sort and its fallback), so a caller may feed a different
+// resident frame every step without copying it.  Outputs (energy, forces, virial), the site count
 // and the plan's options are those of the capture.
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
 #include "plan.cuh"
@@ -19,14 +20,21 @@ struct pppm_graph {
     pppm_plan* plan = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t bin = nullptr;
-    cudaKernelNodeParams bin_params{};
-    // argument copies of the bin kernel: (Geo, pos, q, n, tile_count, tile_of, slot_of, rec, cell, status)
-    Geo geo{};
+    // the kernel nodes that read the sites (arguments (Geo, pos, q, n,
+    // DirectArgs) or (Geo, pos, q, n, six pointers)): copies of their
+    // parameters, so that new site pointers can be patched into each
+    struct SiteNode {
+        cudaGraphNode_t node = nullptr;
+        cudaKernelNodeParams params{};
+        Geo geo{};
+        int n = 0;
+        bool compact = false;      // the compact layout's binning kernel
+        DirectArgs<float> args{};  // the same layout for both precisions (pointers and ints)
+        void* ptrs[6] = {};        // the binning kernel's other arguments
+    };
+    std::vector<SiteNode> sites;
     const void* pos = nullptr;
     const void* q = nullptr;
-    int n = 0;
-    void* ptrs[6] = {};
     int in_size = 4;  // bytes per input value (float or double)
     uint64_t gen = 0;  // plan state at capture
 };
@@ -71,23 +79,30 @@ int graph_create(pppm_plan* P, void* stream, const In* pos, const In* q, int64_t
     if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn == 0) return fail(PPPM_ERR_CUDA);
     std::vector<cudaGraphNode_t> nodes(nn);
     if (cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) return fail(PPPM_ERR_CUDA);
+    static_assert(sizeof(DirectArgs<float>) == sizeof(DirectArgs<double>), "site-kernel arguments");
     for (cudaGraphNode_t nd : nodes) {
         cudaGraphNodeType t;
         if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
         cudaKernelNodeParams kp{};
         if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
-        if (!is_bin_kernel(kp.func)) continue;
-        if (G->bin) return fail(PPPM_ERR_CUDA);  // exactly one binning launch per step
-        G->bin = nd;
-        G->bin_params = kp;
+        const bool compact = is_bin_kernel(kp.func);
+        if (!compact && !is_site_kernel(kp.func)) continue;
+        pppm_graph::SiteNode sn;
+        sn.node = nd;
+        sn.params = kp;
+        sn.compact = compact;
         void** a = kp.kernelParams;
-        std::memcpy(&G->geo, a[0], sizeof(Geo));
-        std::memcpy(&G->pos, a[1], sizeof(void*));
-        std::memcpy(&G->q, a[2], sizeof(void*));
-        std::memcpy(&G->n, a[3], sizeof(int));
-        for (int k = 0; k < 6; ++k) std::memcpy(&G->ptrs[k], a[4 + k], sizeof(void*));
+        std::memcpy(&sn.geo, a[0], sizeof(Geo));
+        std::memcpy(&sn.n, a[3], sizeof(int));
+        if (compact)
+            for (int k = 0; k < 6; ++k) std::memcpy(&sn.ptrs[k], a[4 + k], sizeof(void*));
+        else
+            std::memcpy(&sn.args, a[4], sizeof(DirectArgs<float>));
+        G->sites.push_back(sn);
     }
-    if (!G->bin) return fail(PPPM_ERR_CUDA);
+    if (G->sites.empty()) return fail(PPPM_ERR_CUDA);  // the step reads its sites somewhere
+    G->pos = pos;
+    G->q = q;
     if (cudaGraphInstantiate(&G->exec, g, 0) != cudaSuccess) return fail(PPPM_ERR_CUDA);
     G->gen = P->gen;
     *out = G;
@@ -103,12 +118,15 @@ int graph_launch(pppm_graph* G, void* stream, const In* pos, const In* q) {
     const void* np = pos ? (const void*)pos : G->pos;
     const void* nq = q ? (const void*)q : G->q;
     if (np != G->pos || nq != G->q) {
-        void* args[10] = {&G->geo, (void*)&np, (void*)&nq, &G->n, &G->ptrs[0], &G->ptrs[1],
-                          &G->ptrs[2], &G->ptrs[3], &G->ptrs[4], &G->ptrs[5]};
-        cudaKernelNodeParams kp = G->bin_params;
-        kp.kernelParams = args;
-        kp.extra = nullptr;
-        if (cudaGraphExecKernelNodeSetParams(G->exec, G->bin, &kp) != cudaSuccess) return PPPM_ERR_CUDA;
+        for (pppm_graph::SiteNode& sn : G->sites) {
+            void* args[10] = {&sn.geo, (void*)&np, (void*)&nq, &sn.n, &sn.args};
+            if (sn.compact)
+                for (int k = 0; k < 6; ++k) args[4 + k] = &sn.ptrs[k];
+            cudaKernelNodeParams kp = sn.params;
+            kp.kernelParams = args;
+            kp.extra = nullptr;
+            if (cudaGraphExecKernelNodeSetParams(G->exec, sn.node, &kp) != cudaSuccess) return PPPM_ERR_CUDA;
+        }
         G->pos = np;
         G->q = nq;
     }

@@ -275,40 +275,66 @@ inline bool fast_tiles(const Geo& g) {
     return (g.T == 4 || g.T == 8) && g.Tt[0] == g.T && g.Tt[1] == g.T && g.Tt[2] == g.T;
 }
 
+// Arguments of the one-pass site sort into fixed tile regions (site_sort.cu):
+// the kernels that read the sites take (Geo, pos, q, n, DirectArgs), so that a
+// captured step can patch the site pointers of each such node alike.
+template <typename T>
+struct DirectArgs {
+    int2* tiles;    // per tile: (first slot, end slot)
+    int cap;        // slots of a tile's region
+    int* flag;      // [0] set when a region overflowed (the compact layout is then rebuilt),
+                    // [1] blocks of the sort done
+    int* tile_of;   // per site: its tile
+    int* slot_of;   // per site: its arrival rank in the tile
+    Rec<T>* srec;   // tile order, or null when no generic kernel reads the records
+    int* scell;
+    int* sorig;
+    T* swt;
+    int* status;
+};
+
 // ------------------------------------------------------------------ launchers
-// site_sort.cu
+// site_sort.cu.  Tile-ordered site data are described by tiles[t] = (first
+// slot, end slot) of tile t.
 template <typename T, typename In>
 cudaError_t launch_bin(cudaStream_t s, const Geo& g, const In* pos, const In* q, int n, int* tile_count,
                        int* tile_of, int* slot_of, Rec<T>* rec, int* cell, int* status);
-cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int* start);
-bool is_bin_kernel(const void* func);
+cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int2* tiles);
 template <typename T>
 cudaError_t launch_scatter(cudaStream_t s, const Geo& g, int n, const int* tile_of, const int* slot_of,
-                           const int* tile_start, const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell,
+                           const int2* tiles, const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell,
                            int* sorig, T* swt);
+// fixed regions of a.cap slots per tile: init (also zeroes the two flag words),
+// then the one-pass sort
+cudaError_t launch_tiles_init(cudaStream_t s, int2* tiles, int ntiles, int cap, int* flag);
+template <typename T, typename In>
+cudaError_t launch_bin_direct(cudaStream_t s, const Geo& g, const In* pos, const In* q, int n,
+                              const DirectArgs<T>& a);
+bool is_bin_kernel(const void* func);   // (Geo, pos, q, n, six pointers)
+bool is_site_kernel(const void* func);  // (Geo, pos, q, n, DirectArgs)
 // order, tmp: n ints of scratch each in tile order (the binning's slot and
 // tile arrays, dead once the scatter has run), used to rank tiles denser than
 // the shared-memory ranking
 template <typename T>
-cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
                           const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp);
 template <typename T>
 cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
                         T scale, T* rho);
 template <typename T, typename Out>
-cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
                           const int* scell, const int* sorig, const T* swt, const T* fields, const FieldLayout& fl,
                           const void* tmap, double prefactor, Out* forces, int* status, long long wait_limit);
 void upload_bspline_coefficients();
 // full-tile fast paths (cudaErrorNotSupported when the order/tile has none)
 template <typename T>
-cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
                                const int* sorig, const T* swt, T* patch, int* order, int* tmp);
 // wait_limit: spins of the first bounded wait for a tile's field copy (0: it
 // runs out at once, the copy is then waited for once more before the block
 // returns; a test of the timeout path)
 template <typename T, typename Out>
-cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell, const int* sorig,
+cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell, const int* sorig,
                               const T* swt, const void* tmap, double prefactor, Out* forces, int* status,
                               long long wait_limit);
 

@@ -195,7 +195,7 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
         return o;
     };
     const size_t o_count = take(sizeof(int) * g.ntiles);
-    const size_t o_start = take(sizeof(int) * (g.ntiles + 1));
+    const size_t o_tiles = take(sizeof(int2) * g.ntiles);
     const size_t o_tile = take(sizeof(int) * nn);
     const size_t o_slot = take(sizeof(int) * nn);
     const size_t o_rec = take(sizeof(Rec<float>) * nn);
@@ -211,7 +211,7 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     if (at > kNoAllocScratchBytes) return PPPM_ERR_TOO_LARGE;
     unsigned char* b = static_cast<unsigned char*>(base);
     int* tile_count = reinterpret_cast<int*>(b + o_count);
-    int* tile_start = reinterpret_cast<int*>(b + o_start);
+    int2* tiles = reinterpret_cast<int2*>(b + o_tiles);
     int* tile_of = reinterpret_cast<int*>(b + o_tile);
     int* slot_of = reinterpret_cast<int*>(b + o_slot);
     Rec<float>* rec = reinterpret_cast<Rec<float>*>(b + o_rec);
@@ -236,9 +236,9 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     NA_CK(cudaMemsetAsync(tile_count, 0, sizeof(int) * g.ntiles, s));
     NA_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
     NA_CK((launch_bin<float, double>(s, g, pos, q, (int)n, tile_count, tile_of, slot_of, rec, cell, status)));
-    NA_CK(launch_scan(s, tile_count, g.ntiles, tile_start));
-    NA_CK(launch_scatter<float>(s, g, (int)n, tile_of, slot_of, tile_start, rec, cell, srec, scell, sorig, swt));
-    NA_CK(launch_spread<float>(s, g, tile_start, srec, scell, sorig, swt, patch, slot_of, tile_of));
+    NA_CK(launch_scan(s, tile_count, g.ntiles, tiles));
+    NA_CK(launch_scatter<float>(s, g, (int)n, tile_of, slot_of, tiles, rec, cell, srec, scell, sorig, swt));
+    NA_CK(launch_spread<float>(s, g, tiles, srec, scell, sorig, swt, patch, slot_of, tile_of));
     NA_CK(launch_fold<float>(s, g, patch, cov_off, cov_ent, (float)(1.0 / h3), rho));
 #undef NA_CK
     return PPPM_OK;

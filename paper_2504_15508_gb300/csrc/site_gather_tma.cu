@@ -106,7 +106,7 @@ static LaneRows order_rows(int p, int ez) {
 
 template <typename T, int P, int TILE, typename Out>
 __global__ void __launch_bounds__(kGatherWarps * 32, 6)  // shared memory holds six blocks an SM
-k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
+k_gather_tma(Geo g, const int2* __restrict__ tiles, const int* __restrict__ scell,
              const int* __restrict__ sorig, const T* __restrict__ swt, const __grid_constant__ CUtensorMap tmap,
              const __grid_constant__ LaneRows lanes, double prefactor, Out* __restrict__ forces,
              int* __restrict__ status, long long wait_limit) {
@@ -124,7 +124,8 @@ k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ 
     int* st_orig = st_cell + kGatherWarps * 8;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(st_orig + kGatherWarps * 8);
     const int tile = blockIdx.x;
-    const int s0 = tile_start[tile], s1 = tile_start[tile + 1];
+    const int2 tr = tiles[tile];
+    const int s0 = tr.x, s1 = tr.y;
     if (s0 == s1) return;  // uniform across the block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(mbar);
@@ -257,7 +258,7 @@ k_gather_tma(Geo g, const int* __restrict__ tile_start, const int* __restrict__ 
 }
 
 template <typename T, int P, int TILE, typename Out>
-static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
                               const int* sorig, const T* swt, const void* tmap, double prefactor, Out* forces,
                               int* status, long long wait_limit) {
     constexpr int E = TILE + P - 1, EZ = gather_box_z(P, TILE), WSP = wstride(P) + 4;
@@ -268,7 +269,7 @@ static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_star
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     static const LaneRows lanes = order_rows(P, EZ);
-    return launch_k(k_gather_tma<T, P, TILE, Out>, dim3(g.ntiles), dim3(kGatherWarps * 32), smem, s, g, tile_start,
+    return launch_k(k_gather_tma<T, P, TILE, Out>, dim3(g.ntiles), dim3(kGatherWarps * 32), smem, s, g, tiles,
                     scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), lanes, prefactor, forces, status,
                     wait_limit);
 }
@@ -291,16 +292,16 @@ static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int* tile_star
 
 
 template <typename T, typename Out>
-cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell, const int* sorig,
+cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell, const int* sorig,
                               const T* swt, const void* tmap, double prefactor, Out* forces, int* status,
                               long long wait_limit) {
-    PPPM_FAST_SWITCH_G(gather_tma, T, Out, s, g, tile_start, scell, sorig, swt, tmap, prefactor, forces, status,
+    PPPM_FAST_SWITCH_G(gather_tma, T, Out, s, g, tiles, scell, sorig, swt, tmap, prefactor, forces, status,
                        wait_limit)
     return cudaErrorNotSupported;
 }
 
 #define PPPM_INST_G(T, O)                                                                                       \
-    template cudaError_t launch_gather_tma<T, O>(cudaStream_t, const Geo&, const int*, const int*, const int*,   \
+    template cudaError_t launch_gather_tma<T, O>(cudaStream_t, const Geo&, const int2*, const int*, const int*,  \
                                                  const T*, const void*, double, O*, int*, long long);
 PPPM_INST_G(float, float)
 PPPM_INST_G(float, double)

@@ -31,7 +31,7 @@ constexpr int kSpreadCap = 512;
 
 template <typename T, int P>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
-k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
+k_spread(Geo g, const int2* __restrict__ tiles, const Rec<T>* __restrict__ srec,
          const int* __restrict__ scell, const int* __restrict__ sorig, T* __restrict__ patch, int* order,
          int* tmp) {
     pdl_enter();
@@ -46,8 +46,9 @@ k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
     if (tile >= g.ntiles) return;  // whole warp; no block-level barrier below
 
     for (int i = lane; i < psize; i += 32) pt[i] = T(0);
-    const int s0 = tile_start[tile];
-    const int c = tile_start[tile + 1] - s0;
+    const int2 tr = tiles[tile];
+    const int s0 = tr.x;
+    const int c = tr.y - s0;
     const bool sorted = c > 1 && c <= kSpreadCap;
     if (sorted) {
         int cp = 2;
@@ -111,32 +112,32 @@ k_spread(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
 }
 
 template <typename T, int P>
-static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
                             const int* scell, const int* sorig, T* patch, int* order, int* tmp) {
     const int psize = g.E[0] * g.E[1] * g.Pz;
     size_t smem = (size_t)kSpreadWarps * psize * sizeof(T) + (size_t)kSpreadWarps * kSpreadCap * sizeof(int2);
     cudaError_t e = cudaFuncSetAttribute(k_spread<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
-    return launch_k(k_spread<T, P>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tile_start, srec, scell, sorig,
+    return launch_k(k_spread<T, P>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tiles, srec, scell, sorig,
                     patch, order, tmp);
 }
 
 
 template <typename T>
-cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
                           const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp) {
     if (fast_tiles(g)) {
-        cudaError_t e = launch_spread_fast<T>(s, g, tile_start, scell, sorig, swt, patch, order, tmp);
+        cudaError_t e = launch_spread_fast<T>(s, g, tiles, scell, sorig, swt, patch, order, tmp);
         if (e != cudaErrorNotSupported) return e;
     }
     switch (g.order) {
-        case 2: return spread_p<T, 2>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
-        case 3: return spread_p<T, 3>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
-        case 4: return spread_p<T, 4>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
-        case 5: return spread_p<T, 5>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
-        case 6: return spread_p<T, 6>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
-        case 7: return spread_p<T, 7>(s, g, tile_start, srec, scell, sorig, patch, order, tmp);
+        case 2: return spread_p<T, 2>(s, g, tiles, srec, scell, sorig, patch, order, tmp);
+        case 3: return spread_p<T, 3>(s, g, tiles, srec, scell, sorig, patch, order, tmp);
+        case 4: return spread_p<T, 4>(s, g, tiles, srec, scell, sorig, patch, order, tmp);
+        case 5: return spread_p<T, 5>(s, g, tiles, srec, scell, sorig, patch, order, tmp);
+        case 6: return spread_p<T, 6>(s, g, tiles, srec, scell, sorig, patch, order, tmp);
+        case 7: return spread_p<T, 7>(s, g, tiles, srec, scell, sorig, patch, order, tmp);
     }
     return cudaErrorInvalidValue;
 }
@@ -234,13 +235,14 @@ constexpr int kGatherThreads = 64;
 
 template <typename T, int P, typename Out>
 __global__ void __launch_bounds__(kGatherThreads)
-k_gather(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ srec,
+k_gather(Geo g, const int2* __restrict__ tiles, const Rec<T>* __restrict__ srec,
          const int* __restrict__ scell, const int* __restrict__ sorig, const T* __restrict__ fields, FieldLayout fl,
          double prefactor, Out* __restrict__ forces) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = blockIdx.x;
-    const int s0 = tile_start[tile], s1 = tile_start[tile + 1];
+    const int2 tr = tiles[tile];
+    const int s0 = tr.x, s1 = tr.y;
     if (s0 == s1) return;  // uniform across the block
     const int Ex = g.E[0], Ey = g.E[1], Ez = g.E[2];
     const int psz = Ex * Ey * Ez;
@@ -300,44 +302,44 @@ k_gather(Geo g, const int* __restrict__ tile_start, const Rec<T>* __restrict__ s
 }
 
 template <typename T, int P, typename Out>
-static cudaError_t gather_p(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+static cudaError_t gather_p(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
                             const int* scell, const int* sorig, const T* fields, const FieldLayout& fl,
                             double prefactor, Out* forces) {
     size_t smem = 3ull * g.E[0] * g.E[1] * g.E[2] * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_gather<T, P, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_k(k_gather<T, P, Out>, dim3(g.ntiles), dim3(kGatherThreads), smem, s, g, tile_start, srec, scell,
+    return launch_k(k_gather<T, P, Out>, dim3(g.ntiles), dim3(kGatherThreads), smem, s, g, tiles, srec, scell,
                     sorig, fields, fl, prefactor, forces);
 }
 
 template <typename T, typename Out>
-cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int* tile_start, const Rec<T>* srec,
+cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
                           const int* scell, const int* sorig, const T* swt, const T* fields, const FieldLayout& fl,
                           const void* tmap, double prefactor, Out* forces, int* status, long long wait_limit) {
     if (fast_tiles(g) && fl.padded && tmap) {
-        cudaError_t e = launch_gather_tma<T, Out>(s, g, tile_start, scell, sorig, swt, tmap, prefactor, forces, status,
+        cudaError_t e = launch_gather_tma<T, Out>(s, g, tiles, scell, sorig, swt, tmap, prefactor, forces, status,
                                                   wait_limit);
         if (e != cudaErrorNotSupported) return e;
     }
     switch (g.order) {
-        case 2: return gather_p<T, 2, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
-        case 3: return gather_p<T, 3, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
-        case 4: return gather_p<T, 4, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
-        case 5: return gather_p<T, 5, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
-        case 6: return gather_p<T, 6, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
-        case 7: return gather_p<T, 7, Out>(s, g, tile_start, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 2: return gather_p<T, 2, Out>(s, g, tiles, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 3: return gather_p<T, 3, Out>(s, g, tiles, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 4: return gather_p<T, 4, Out>(s, g, tiles, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 5: return gather_p<T, 5, Out>(s, g, tiles, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 6: return gather_p<T, 6, Out>(s, g, tiles, srec, scell, sorig, fields, fl, prefactor, forces);
+        case 7: return gather_p<T, 7, Out>(s, g, tiles, srec, scell, sorig, fields, fl, prefactor, forces);
     }
     return cudaErrorInvalidValue;
 }
 
 #define PPPM_INST_T(T)                                                                                          \
-    template cudaError_t launch_spread<T>(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*,       \
+    template cudaError_t launch_spread<T>(cudaStream_t, const Geo&, const int2*, const Rec<T>*, const int*,      \
                                           const int*, const T*, T*, int*, int*);                                 \
     template cudaError_t launch_fold<T>(cudaStream_t, const Geo&, const T*, const int*, const int2*, T, T*);
 PPPM_INST_T(float)
 PPPM_INST_T(double)
 #define PPPM_INST_TI(T, I)                                                                                       \
-    template cudaError_t launch_gather<T, I>(cudaStream_t, const Geo&, const int*, const Rec<T>*, const int*,     \
+    template cudaError_t launch_gather<T, I>(cudaStream_t, const Geo&, const int2*, const Rec<T>*, const int*,    \
                                              const int*, const T*, const T*, const FieldLayout&, const void*,    \
                                              double, I*, int*, long long);
 PPPM_INST_TI(float, float)

@@ -51,7 +51,7 @@ struct __align__(16) SpreadWarpSmem {  // 16-byte aligned: staged rows take vect
 
 template <typename T, int P, int TILE>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
-k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__ scell,
+k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ scell,
               const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch, int* order,
               int* tmp) {
     pdl_enter();
@@ -64,8 +64,9 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
     const int tile = blockIdx.x * kSpreadWarps + warp;
     WarpSmem& W = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
     if (tile >= g.ntiles) return;  // whole warp; no block-level barrier below
-    const int s0 = tile_start[tile];
-    const int c = tile_start[tile + 1] - s0;
+    const int2 tr = tiles[tile];
+    const int s0 = tr.x;
+    const int c = tr.y - s0;
     const bool ranked = c > 1 && c <= kFastCap;
     if (ranked) {
         for (int i = lane; i < c; i += 32) W.u.keys[i] = __ldg(&sorig[s0 + i]);
@@ -162,14 +163,14 @@ k_spread_fast(Geo g, const int* __restrict__ tile_start, const int* __restrict__
 }
 
 template <typename T, int P, int TILE>
-static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
                                const int* sorig, const T* swt, T* patch, int* order, int* tmp) {
     const size_t smem = kSpreadWarps * sizeof(SpreadWarpSmem<T, P, TILE>);
     cudaError_t e = cudaFuncSetAttribute(k_spread_fast<T, P, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
-    return launch_k(k_spread_fast<T, P, TILE>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tile_start, scell,
+    return launch_k(k_spread_fast<T, P, TILE>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tiles, scell,
                     sorig, swt, patch, order, tmp);
 }
 
@@ -192,15 +193,15 @@ static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int* tile_sta
 
 
 template <typename T>
-cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int* tile_start, const int* scell,
+cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
                                const int* sorig, const T* swt, T* patch, int* order, int* tmp) {
-    PPPM_FAST_SWITCH(spread_fast, T, s, g, tile_start, scell, sorig, swt, patch, order, tmp)
+    PPPM_FAST_SWITCH(spread_fast, T, s, g, tiles, scell, sorig, swt, patch, order, tmp)
     return cudaErrorNotSupported;
 }
 
-template cudaError_t launch_spread_fast<float>(cudaStream_t, const Geo&, const int*, const int*, const int*,
+template cudaError_t launch_spread_fast<float>(cudaStream_t, const Geo&, const int2*, const int*, const int*,
                                                const float*, float*, int*, int*);
-template cudaError_t launch_spread_fast<double>(cudaStream_t, const Geo&, const int*, const int*, const int*,
+template cudaError_t launch_spread_fast<double>(cudaStream_t, const Geo&, const int2*, const int*, const int*,
                                                 const double*, double*, int*, int*);
 
 }  // namespace pppm

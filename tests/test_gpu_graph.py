@@ -156,3 +156,40 @@ def test_dependent_launch_switch(cuda_device, prec):
     assert torch.equal(f2, f1) and torch.equal(e2, e1)
     g.close()
     plan.set_dependent_launch(True)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_region_overflow_falls_back_inside_a_replay(cuda_device, prec):
+    """4,000 charges in a 10 A box on a 32^3 mesh sort into fixed regions of
+    256 slots per tile (edge 8, ~62 sites a tile).  A frame with every site
+    inside one tile overflows its region: the fallback rebuilds the compact
+    layout on the device, within the same captured graph.  Replays of the
+    spread-out frame, the clustered frame and the spread-out one again each
+    equal the eager call bitwise and the oracle within the path's tolerance."""
+    from oracle.pppm import OraclePPPM
+    from paper_2504_15508_gb300.pppm import Plan
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    box, mesh, n = (10.0, 10.0, 10.0), (32, 32, 32), 4000
+    rng = np.random.default_rng(44)
+    spread_out = rng.random((n, 3)) * 10.0
+    clustered = 0.2 + rng.random((n, 3)) * 2.0   # base points in cells 1-7: tile 0
+    q = rng.normal(size=n)
+    q -= q.mean()
+    plan = Plan(box, mesh, 5, 0.4, precision=prec)
+    tq = torch.tensor(q, dtype=dt, device="cuda")
+    frames = [torch.tensor(p, dtype=dt, device="cuda") for p in (spread_out, clustered, spread_out)]
+    g = plan.graph(frames[0], tq)
+    ftol = 1e-5 if prec == "fp32" else 1e-12
+    for k, p in enumerate(frames):
+        e, f, v = (t.clone() for t in g.launch(p, tq, stream=torch.cuda.current_stream()))
+        e0, f0, v0 = plan.compute(p, tq)
+        torch.cuda.synchronize()
+        assert torch.equal(f, f0) and torch.equal(e, e0) and torch.equal(v, v0), k
+        ref = OraclePPPM(box, mesh, 5, 0.4).compute(p.double().cpu().numpy(), tq.double().cpu().numpy())
+        ferr = np.linalg.norm(f.double().cpu().numpy() - ref["forces"]) / np.linalg.norm(ref["forces"])
+        assert ferr <= ftol, (k, ferr)
+        # FP32 energy of the clustered frame: ~4,000 x 125 / 7^3 = 1,500 sequential
+        # additions a point, rounding sqrt(1500) x 2^-24 = 2.3e-6
+        etol = 1e-6 if (prec == "fp64" or k != 1) else 5e-6
+        assert abs(e.item() - ref["energy"]) <= etol * abs(ref["energy"]), k
+    g.close()
