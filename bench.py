@@ -685,6 +685,19 @@ def run_batched(args):
         return sum(a.elapsed_time(b) for a, b in evs) / K
 
     ms_batched = slowest(timed(lambda: bp.compute(tp, tq, to, out=out, stream=stream)))
+    # the launch form the autotuner chose, then each form forced
+    auto_form = bp.launch
+    ms_form = {}
+    for form in ("persistent", "staged"):
+        bp.set_launch(form)
+        for k in range(3):
+            bp.compute(tp, tq, to, out=out, stream=stream)
+        torch.cuda.synchronize()
+        ms_form[form] = slowest(timed(lambda: bp.compute(tp, tq, to, out=out, stream=stream)))
+    bp.set_launch("auto")
+    for k in range(3):
+        bp.compute(tp, tq, to, out=out, stream=stream)
+    torch.cuda.synchronize()
     energies = gather_by_box(len(all_specs), mine, out[0].cpu().numpy())
     line = {
         "metric": "batched PPPM evals/s, 96 water boxes of 64-8,192 molecules", "value": world * 1e3 / ms_batched,
@@ -695,6 +708,8 @@ def run_batched(args):
                                f"{int(sum(s['n_mol'] for s in specs))} molecules, {n} sites",
                    "tile": bp.tile, "l2": "flushed between timed steps"},
         "energy_sum_all_boxes": float(np.sum(energies)),
+        "launch_form": auto_form, "ms_by_launch_form": ms_form,
+        "staged_speedup_vs_persistent": ms_form["persistent"] / ms_form["staged"],
     }
     if world == 1:
         # the same batch with lines of length <= 18 as a DFT on the tensor cores

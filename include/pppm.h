@@ -224,6 +224,21 @@ int pppm_batch_create(int nbox, const double *boxes, const int *meshes, int orde
 int pppm_batch_set(pppm_batch *batch, double prefactor, int tile, long long spin_limit);
 int pppm_batch_set_dft(pppm_batch *batch, int max_len);
 int pppm_batch_set_quantized(pppm_batch *batch, int group, double scale);
+/* pppm_batch_set_launch: the launch form.  PPPM_BATCH_PERSISTENT runs every
+ * stage of every box in the one persistent launch described above;
+ * PPPM_BATCH_STAGED runs one kernel per stage over that stage's work items of
+ * all boxes (ten launches, recorded in the same graph), stream order taking
+ * the place of the in-kernel waits, so each stage gets its own register and
+ * shared-memory budget; PPPM_BATCH_AUTO (default) lets the autotuner time
+ * both with the tile edges and keep the fastest.  The two forms run the same
+ * stage code but are compiled separately, so results agree to rounding, not
+ * bit for bit; each form is deterministic.  The wait probe and the spin limit
+ * apply to the persistent form only.  Another mode: PPPM_ERR_INVALID_ARG.
+ * pppm_batch_launch: the form in use (the requested one before the first
+ * call).  The paper has no counterpart. */
+enum { PPPM_BATCH_PERSISTENT = 0, PPPM_BATCH_STAGED = 1, PPPM_BATCH_AUTO = 2 };
+int pppm_batch_set_launch(pppm_batch *batch, int mode);
+int pppm_batch_launch(const pppm_batch *batch);
 /* pppm_batch_set_wait_probe: when on (nonzero), the scan stage of box 0 waits
  * for one binning item more than the box has, so that bounded wait must run
  * out after the spin limit: the launch ends, pppm_batch_status returns

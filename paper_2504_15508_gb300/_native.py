@@ -26,6 +26,9 @@ PPPM_FP32 = 1
 PPPM_FP64 = 2
 PPPM_CORR_CELL = 0
 PPPM_CORR_STATED = 1
+PPPM_BATCH_PERSISTENT = 0
+PPPM_BATCH_STAGED = 1
+PPPM_BATCH_AUTO = 2
 
 
 class PPPMError(RuntimeError):
@@ -83,6 +86,8 @@ SIGNATURES = {
     "pppm_set_dependent_launch": (cint, [vp, cint]),
     "pppm_set_wait_limit": (cint, [vp, ctypes.c_longlong]),
     "pppm_batch_set_wait_probe": (cint, [vp, cint]),
+    "pppm_batch_set_launch": (cint, [vp, cint]),
+    "pppm_batch_launch": (cint, [vp]),
     "pppm_corr_create": (cint, [vp, ctypes.POINTER(vp)]),
     "pppm_corr_nparams": (cint, []),
     "pppm_corr_create_features": (cint, [vp, cint, ctypes.POINTER(vp)]),

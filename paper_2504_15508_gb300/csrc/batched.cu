@@ -972,6 +972,84 @@ cudaError_t launch(cudaStream_t s, const BoxDesc* boxes, const int2* items, int 
     return cudaGetLastError();
 }
 
+// Shared memory of one stage alone (the persistent kernel takes the largest).
+template <int P, int TILE>
+size_t stage_smem_of(int stage, int maxN, int maxB) {
+    constexpr int E = TILE + P - 1, PZ = E | 1;
+    size_t m = 0;
+    switch (stage) {
+        case S_BIN: case S_SCATTER: m = 16; break;
+        case S_SCAN: m = (size_t)kThreads * sizeof(int); break;
+        case S_SPREAD: m = SpreadRed<P, TILE>::bytes(); break;
+        case S_ZR2C: m = (size_t)(2 * kZPairs * maxN) * sizeof(float2); break;
+        case S_YFWD: m = (size_t)(2 * maxN * maxB) * sizeof(float2); break;
+        case S_XINF: m = (size_t)(4 * maxN * maxB) * sizeof(float2) + kWarps * 14 * sizeof(float); break;
+        case S_YINV: m = (size_t)(6 * maxN * maxB) * sizeof(float2); break;
+        case S_ZC2R: m = (size_t)(2 * 3 * kZPairs * maxN) * sizeof(float2); break;
+        case S_GATHER:
+            m = (size_t)kGatherTiles * 3 * E * E * PZ * sizeof(float) +
+                (size_t)kWarps * 8 * (wstride(P) + 4) * sizeof(float) + 2 * kWarps * 8 * sizeof(int);
+            break;
+    }
+    return (m + 127) / 128 * 128;
+}
+
+// Staged launch: one kernel per stage over that stage's items of every box
+// (block b takes item b of the stage's contiguous range of the stage-major
+// list); stream order replaces the persistent kernel's waits, and each stage
+// gets its own register and shared-memory budget.
+template <int P, int TILE, bool Q, int STAGE>
+__global__ void __launch_bounds__(kThreads)
+k_stage(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, Bufs B) {
+    pdl_enter();
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(16) BoxDesc sbox;
+    const int2 I = items[blockIdx.x];
+    const int box = I.x & 0xffff, idx = I.y;
+    {
+        const int* src = reinterpret_cast<const int*>(boxes + box);
+        int* dst = reinterpret_cast<int*>(&sbox);
+        for (int w = threadIdx.x; w < (int)(sizeof(BoxDesc) / sizeof(int)); w += kThreads) dst[w] = src[w];
+    }
+    __syncthreads();
+    if constexpr (STAGE == S_BIN) st_bin<P>(sbox, idx, B);
+    if constexpr (STAGE == S_SCAN) st_scan(sbox, B, reinterpret_cast<int*>(smem));
+    if constexpr (STAGE == S_SCATTER) st_scatter<P>(sbox, idx, B);
+    if constexpr (STAGE == S_SPREAD) st_spread<P, TILE>(sbox, idx, B, smem);
+    if constexpr (STAGE == S_ZR2C) st_zr2c<Q>(sbox, idx, B, smem);
+    if constexpr (STAGE == S_YFWD) st_yfwd<Q>(sbox, idx, B, smem);
+    if constexpr (STAGE == S_XINF) st_xinf<Q>(sbox, box, idx, B, smem);
+    if constexpr (STAGE == S_YINV) st_yinv<Q>(sbox, idx, B, smem);
+    if constexpr (STAGE == S_ZC2R) st_zc2r<Q>(sbox, idx, B, smem);
+    if constexpr (STAGE == S_GATHER) st_gather<P, TILE>(sbox, idx, B, smem);
+}
+
+template <int P, int TILE, bool Q, int STAGE>
+cudaError_t launch_one_stage(cudaStream_t s, const BoxDesc* boxes, const int2* items, int start, int count,
+                             const Bufs& B, int maxN, int maxB) {
+    if (count == 0) return cudaSuccess;
+    const size_t smem = stage_smem_of<P, TILE>(STAGE, maxN, maxB);
+    auto kern = k_stage<P, TILE, Q, STAGE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_k(kern, dim3(count), dim3(kThreads), smem, s, boxes, items + start, B);
+}
+
+template <int P, int TILE, bool Q>
+cudaError_t launch_staged(cudaStream_t s, const BoxDesc* boxes, const int2* items, const int* stage_start,
+                          const Bufs& B, int maxN, int maxB) {
+    PdlScope pdl(true);
+    cudaError_t e = cudaSuccess;
+#define PPPM_STAGE(ST)                                                                                      \
+    e = launch_one_stage<P, TILE, Q, ST>(s, boxes, items, stage_start[ST], stage_start[ST + 1] - stage_start[ST], \
+                                         B, maxN, maxB);                                                    \
+    if (e != cudaSuccess) return e;
+    PPPM_STAGE(S_BIN) PPPM_STAGE(S_SCAN) PPPM_STAGE(S_SCATTER) PPPM_STAGE(S_SPREAD) PPPM_STAGE(S_ZR2C)
+    PPPM_STAGE(S_YFWD) PPPM_STAGE(S_XINF) PPPM_STAGE(S_YINV) PPPM_STAGE(S_ZC2R) PPPM_STAGE(S_GATHER)
+#undef PPPM_STAGE
+    return e;
+}
+
 }  // namespace batch
 }  // namespace pppm
 
@@ -989,6 +1067,9 @@ struct pppm_batch {
     int quant_group = 0;        // int32-quantised DFT of short lines (an accuracy ablation; off)
     double quant_scale = 1e7;
     int wait_probe = 0;
+    int launch_mode = PPPM_BATCH_AUTO;  // requested launch form
+    bool staged = false;        // in use: one kernel per stage instead of the persistent launch
+    bool mode_tuned = false;    // the launch form has been chosen for the current layout
     std::vector<double> boxes;  // nbox * 3
     std::vector<int> meshes;    // nbox * 3
     int tile = 0;               // chosen tile edge (0 = not tuned yet)
@@ -1004,6 +1085,7 @@ struct pppm_batch {
         int T = 0;
         std::vector<BoxDesc> desc;
         std::vector<int2> items;
+        int stage_start[NSTAGE + 1] = {};  // each stage's range in the stage-major list
         BoxDesc* d_desc = nullptr;
         int2* d_items = nullptr;
         int4* d_cov2 = nullptr;
@@ -1213,9 +1295,12 @@ int build_layout(pppm_batch* P, int li, int T) {
     std::vector<int> order(P->nbox);
     for (int b = 0; b < P->nbox; ++b) order[b] = b;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return Y.desc[a].g.ntiles > Y.desc[b].g.ntiles; });
-    for (int s = 0; s < NSTAGE; ++s)
+    for (int s = 0; s < NSTAGE; ++s) {
+        Y.stage_start[s] = (int)Y.items.size();
         for (int b : order)
             for (int i = 0; i < Y.desc[b].nitems[s]; ++i) Y.items.push_back(make_int2(b | (s << 16), i));
+    }
+    Y.stage_start[NSTAGE] = (int)Y.items.size();
     Y.ntile_total = tile0;
     Y.ntile_start_total = ts0;
     Y.patch_total = patch0;
@@ -1317,8 +1402,9 @@ int enqueue(pppm_batch* P, cudaStream_t s, int li, const float* pos, const float
     const bool quant = P->quant_group > 0;
 #define BATCH_CASE(PP, TT, QQ)                                                                                   \
     if (P->order == PP && Y.T == TT && quant == QQ)                                                              \
-        e = launch<PP, TT, QQ>(s, Y.d_desc, Y.d_items, n, P->head, P->done, B, P->spin_limit, Y.maxN, Y.maxB,    \
-                               &P->last_grid);
+        e = P->staged ? launch_staged<PP, TT, QQ>(s, Y.d_desc, Y.d_items, Y.stage_start, B, Y.maxN, Y.maxB)     \
+                      : launch<PP, TT, QQ>(s, Y.d_desc, Y.d_items, n, P->head, P->done, B, P->spin_limit, Y.maxN, \
+                                           Y.maxB, &P->last_grid);
     BATCH_CASE(3, 4, false) BATCH_CASE(3, 8, false) BATCH_CASE(5, 4, false) BATCH_CASE(5, 8, false)
     BATCH_CASE(7, 4, false) BATCH_CASE(7, 8, false)
     BATCH_CASE(5, 4, true) BATCH_CASE(5, 8, true)  // the quantised ablation: order 5 only
@@ -1349,7 +1435,9 @@ int prepare(pppm_batch* P, const int64_t* offsets) {
     return PPPM_OK;
 }
 
-// Autotuner: time one warm evaluation per tile edge, keep the faster.
+// Autotuner: time warm evaluations of every candidate tile edge (4 and 8,
+// or the forced one) and launch form (persistent and staged, or the
+// requested one), keep the fastest.
 int autotune(pppm_batch* P, const float* pos, const float* q, double* energies, float* forces, double* virials) {
     cudaStream_t s = nullptr;
     BK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -1357,26 +1445,35 @@ int autotune(pppm_batch* P, const float* pos, const float* q, double* energies, 
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     float best = 1e30f;
-    int best_T = 8;
+    int best_T = P->forced_tile ? P->forced_tile : 8;
+    bool best_staged = P->launch_mode == PPPM_BATCH_STAGED;
     for (int li = 0; li < 2; ++li) {
         if (P->lay[li].T == 0) continue;  // not available for these meshes
-        float ms_sum = 0.f;
-        for (int rep = 0; rep < 3; ++rep) {
-            if (enqueue(P, s, li, pos, q, energies, forces, virials) != PPPM_OK) { ms_sum = 1e30f; break; }
-            cudaEventRecord(a, s);
-            if (enqueue(P, s, li, pos, q, energies, forces, virials) != PPPM_OK) { ms_sum = 1e30f; break; }
-            cudaEventRecord(b, s);
-            cudaEventSynchronize(b);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, a, b);
-            if (rep > 0) ms_sum += ms;
+        if (P->forced_tile && P->lay[li].T != P->forced_tile) continue;
+        for (int m = 0; m < 2; ++m) {
+            const bool staged = m == 1;
+            if (P->launch_mode != PPPM_BATCH_AUTO && staged != (P->launch_mode == PPPM_BATCH_STAGED)) continue;
+            P->staged = staged;
+            float ms_sum = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                if (enqueue(P, s, li, pos, q, energies, forces, virials) != PPPM_OK) { ms_sum = 1e30f; break; }
+                cudaEventRecord(a, s);
+                if (enqueue(P, s, li, pos, q, energies, forces, virials) != PPPM_OK) { ms_sum = 1e30f; break; }
+                cudaEventRecord(b, s);
+                cudaEventSynchronize(b);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0) ms_sum += ms;
+            }
+            if (ms_sum < best) { best = ms_sum; best_T = P->lay[li].T; best_staged = staged; }
         }
-        if (ms_sum < best) { best = ms_sum; best_T = P->lay[li].T; }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaStreamDestroy(s);
     P->tile = best_T;
+    P->staged = best_staged;
+    P->mode_tuned = true;
     return PPPM_OK;
 }
 
@@ -1488,6 +1585,17 @@ int pppm_batch_set(pppm_batch* P, double prefactor, int tile, long long spin_lim
     return PPPM_OK;
 }
 
+int pppm_batch_set_launch(pppm_batch* P, int mode) {
+    if (!P || (mode != PPPM_BATCH_PERSISTENT && mode != PPPM_BATCH_STAGED && mode != PPPM_BATCH_AUTO))
+        return PPPM_ERR_INVALID_ARG;
+    P->launch_mode = mode;
+    P->mode_tuned = false;  // re-tune the launch form (and the tile edge unless forced)
+    P->tile = P->forced_tile;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    P->exec = nullptr;
+    return PPPM_OK;
+}
+
 int pppm_batch_set_wait_probe(pppm_batch* P, int on) {
     if (!P) return PPPM_ERR_INVALID_ARG;
     P->wait_probe = on != 0;
@@ -1524,6 +1632,12 @@ int pppm_batch_meshes(const pppm_batch* P, int* meshes) {
 
 int pppm_batch_tile(const pppm_batch* P) { return P ? P->tile : PPPM_ERR_INVALID_ARG; }
 
+int pppm_batch_launch(const pppm_batch* P) {
+    if (!P) return PPPM_ERR_INVALID_ARG;
+    if (!P->mode_tuned) return P->launch_mode;
+    return P->staged ? PPPM_BATCH_STAGED : PPPM_BATCH_PERSISTENT;
+}
+
 int pppm_compute_batched(pppm_batch* P, void* stream, const float* pos, const float* q, const int64_t* offsets,
                          double* energies, float* forces, double* virials) {
     if (!P || !offsets || !energies || !virials) return PPPM_ERR_INVALID_ARG;
@@ -1533,7 +1647,7 @@ int pppm_compute_batched(pppm_batch* P, void* stream, const float* pos, const fl
     if (n > 0 && (!pos || !q || !forces)) return PPPM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     P->last = s;
-    if (!P->tile) {
+    if (!P->tile || !P->mode_tuned) {
         if ((rc = autotune(P, pos, q, energies, forces, virials)) != PPPM_OK) return rc;
     }
     const int li = P->tile == 4 ? 0 : 1;

@@ -287,6 +287,18 @@ class BatchPlan:
     def set(self, prefactor: float = 1.0, tile: int = 0, spin_limit: int = 1 << 24):
         N.check(self._lib.pppm_batch_set(self._h, float(prefactor), int(tile), int(spin_limit)), "pppm_batch_set")
 
+    def set_launch(self, form: str):
+        """The launch form: "persistent" (one persistent kernel), "staged"
+        (one kernel per stage over all boxes) or "auto" (the autotuner keeps
+        the faster; default)."""
+        mode = {"persistent": N.PPPM_BATCH_PERSISTENT, "staged": N.PPPM_BATCH_STAGED, "auto": N.PPPM_BATCH_AUTO}[form]
+        N.check(self._lib.pppm_batch_set_launch(self._h, mode), "pppm_batch_set_launch")
+
+    @property
+    def launch(self) -> str:
+        m = self._lib.pppm_batch_launch(self._h)
+        return {N.PPPM_BATCH_PERSISTENT: "persistent", N.PPPM_BATCH_STAGED: "staged", N.PPPM_BATCH_AUTO: "auto"}[m]
+
     def set_wait_probe(self, on: bool):
         """When on, the first box's scan waits for one binning item more
         than exist, so that bounded wait must run out."""

@@ -126,3 +126,7 @@ def test_corrector_feature_sets_validate_arguments(pppm_lib):
     assert pppm_lib.pppm_corr_create_features(None, N.PPPM_CORR_STATED, ctypes.byref(h)) == N.PPPM_ERR_INVALID_ARG
     assert pppm_lib.pppm_corr_param_count(None) == N.PPPM_ERR_INVALID_ARG
     assert pppm_lib.pppm_corr_feature_width(None) == N.PPPM_ERR_INVALID_ARG
+
+
+def test_batch_set_launch_validates(pppm_lib):
+    assert pppm_lib.pppm_batch_set_launch(None, N.PPPM_BATCH_STAGED) == N.PPPM_ERR_INVALID_ARG

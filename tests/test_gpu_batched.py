@@ -47,6 +47,34 @@ def test_batched_matches_oracle_per_box(cuda_device, pppm_lib, tile, dft):
         assert ferr <= 1e-5 and eerr <= 1e-6 and verr <= 1e-5, (b, meshes[b], ferr, eerr, verr)
 
 
+def test_staged_launch_agrees_with_persistent(cuda_device, pppm_lib):
+    """The staged form runs the same stage code, compiled separately: each
+    form is bitwise reproducible (first call and graph replay), and the two
+    agree to rounding (1e-6 relative).  The autotuner's choice is one of the
+    two forms."""
+    from paper_2504_15508_gb300.pppm import BatchPlan
+    specs, boxes, pos, q, offs = _make_batch(6, seed=11)
+    tp, tq, to = (torch.tensor(pos, device=cuda_device), torch.tensor(q, device=cuda_device),
+                  torch.tensor(offs, device=cuda_device))
+    res = {}
+    for form in ("persistent", "staged"):
+        bp = BatchPlan(np.array([[s["L"]] * 3 for s in specs]), None, order=5, beta=0.4, tile=8)
+        bp.set_launch(form)
+        r1 = [t.clone() for t in bp.compute(tp, tq, to)]
+        r2 = [t.clone() for t in bp.compute(tp, tq, to)]  # graph replay
+        torch.cuda.synchronize()
+        assert bp.status() == 0 and bp.launch == form
+        for a, b in zip(r1, r2):
+            assert torch.equal(a, b)
+        res[form] = r1
+    for a, b in zip(res["persistent"], res["staged"]):
+        assert torch.linalg.norm((a - b).double()) <= 1e-6 * torch.linalg.norm(a.double())
+    bp = BatchPlan(np.array([[s["L"]] * 3 for s in specs]), None, order=5, beta=0.4)
+    bp.compute(tp, tq, to)
+    torch.cuda.synchronize()
+    assert bp.launch in ("persistent", "staged") and bp.tile in (4, 8)
+
+
 def test_batched_graph_replay_and_single_box_equality(cuda_device, pppm_lib):
     from paper_2504_15508_gb300.pppm import BatchPlan, Plan
     specs, boxes, pos, q, offs = _make_batch(5, seed=7)
@@ -90,6 +118,7 @@ def test_batched_bounded_wait_times_out_cleanly(cuda_device, pppm_lib):
     refs = [OraclePPPM(wb.box, bp.meshes[b], 5, 0.4).compute(pos[offs[b]:offs[b + 1]].astype(np.float64),
                                                               q[offs[b]:offs[b + 1]].astype(np.float64))
             for b, wb in enumerate(boxes)]
+    bp.set_launch("persistent")  # the in-kernel waits belong to the persistent form
     bp.set(tile=8, spin_limit=1000)
     bp.set_wait_probe(True)
     e, f, v = bp.compute(tp, tq, to)
@@ -199,19 +228,22 @@ def _full_batch():
     return _FULL
 
 
-@pytest.mark.parametrize("tile,dft", [(4, 0), (8, 0), (4, 18), (8, 18)])
-def test_full_batched96_matches_oracle_per_box(cuda_device, pppm_lib, tile, dft):
+@pytest.mark.parametrize("tile,dft,staged", [(4, 0, False), (8, 0, False), (4, 18, False), (8, 18, False),
+                                             (8, 0, True), (4, 18, True)])
+def test_full_batched96_matches_oracle_per_box(cuda_device, pppm_lib, tile, dft, staged):
     """All 96 boxes in one launch, the largest (8,192-molecule class) on 54^3
     meshes, so that the shared-memory layout is sized by the 54-point lines;
     every box against the FP64 oracle: force RMS 1e-5, energy 1e-6, virial
-    1e-5 relative, for both tile edges and with and without the tensor-core
-    DFT of the short lines."""
+    1e-5 relative, for both tile edges, with and without the tensor-core DFT
+    of the short lines, in the persistent launch and in the staged one (one
+    kernel per stage)."""
     from paper_2504_15508_gb300.pppm import BatchPlan
     F = _full_batch()
     specs, boxes, pos, q, offs, refs = F["specs"], F["boxes"], F["pos"], F["q"], F["offs"], F["refs"]
     assert max(s["mesh"][0] for s in specs) == 54 and min(s["mesh"][0] for s in specs) == 12
     bp = BatchPlan(np.array([[s["L"]] * 3 for s in specs]), None, order=5, beta=0.4, tile=tile)
     bp.set_dft(dft)
+    bp.set_launch("staged" if staged else "persistent")
     assert [tuple(m) for m in bp.meshes] == [tuple(s["mesh"]) for s in specs]
     e, f, v = bp.compute(torch.tensor(pos, device=cuda_device), torch.tensor(q, device=cuda_device),
                          torch.tensor(offs, device=cuda_device))
@@ -227,6 +259,6 @@ def test_full_batched96_matches_oracle_per_box(cuda_device, pppm_lib, tile, dft)
         worst = tuple(max(a, c) for a, c in zip(worst, (ferr, eerr, verr)))
         if not (ferr <= 1e-5 and eerr <= 1e-6 and verr <= 1e-5):
             bad.append((b, specs[b]["n_mol"], specs[b]["mesh"][0], f"{ferr:.2e}", f"{eerr:.2e}", f"{verr:.2e}"))
-    print(f"batched96 tile {tile} dft {dft}: worst force {worst[0]:.2e} energy {worst[1]:.2e} "
+    print(f"batched96 tile {tile} dft {dft} staged {staged}: worst force {worst[0]:.2e} energy {worst[1]:.2e} "
           f"virial {worst[2]:.2e}; over the bar: {bad}")
     assert not bad, bad
