@@ -393,8 +393,10 @@ __device__ __forceinline__ double div_approx(double a, double b) { return a / b;
 // Per block: B consecutive lines along x, numbered y Hz + kz.
 //   1. forward FFT along x  -> rho_hat(k) up to the 1/h^3 factor;
 //   2. per mode: G, the energy term e = w G |rho_hat|^2 V/(2 N^2) and the virial
-//      terms e (delta_ab - 2 (1 + k^2/(4 beta^2)) k_a k_b / k^2), accumulated per
-//      thread with compensated (TwoSum) sums, reduced per block;
+//      terms e (delta_ab - 2 (1 + k^2/(4 beta^2)) k_a k_b / k^2), summed plainly
+//      over a thread's Nx/16 modes (a relative error of at most Nx/16 roundings
+//      of that short sum), then reduced across threads and blocks with
+//      compensated (TwoSum) pairs;
 //   3. P = G rho_hat / (N h^3) and -i kx' P (kx' = 0 on the Nyquist index);
 //   4. inverse FFT along x of both; P -> S (in place), -i kx' P -> Bx.
 // The last block to finish sums the per-block partials (TwoSum in the mesh
@@ -405,15 +407,6 @@ __device__ __forceinline__ double div_approx(double a, double b) { return a / b;
 // mirrored mode whose x (or y) index is the Nyquist index keeps that component's
 // sign (the index maps to itself, m = +N/2), so a product k_a k_b survives the
 // pairing only when both or neither of its components flip sign.
-template <typename R>
-__device__ __forceinline__ void two_sum_acc(R& hi, R& lo, R v) {
-    R s = hi + v;
-    R bp = s - hi;
-    R err = (hi - (s - bp)) + (v - bp);
-    hi = s;
-    lo += err;
-}
-
 // (h, l) += (h2, l2) with the rounding error of h + h2 carried into l
 template <typename R>
 __device__ __forceinline__ void two_sum_pair(R& h, R& l, R h2, R l2) {
@@ -468,28 +461,18 @@ k_fft_x_influence(Geo g, LineBlocks lb, Eng eng, const R* __restrict__ G, R beta
     const R ky = kfac<R>(g, 1) * my;
     const bool nyq_y = (Ny % 2 == 0) && (yl == Ny / 2);
     const R inv4b2 = R(1) / (R(4) * beta * beta);
-    R acc_hi[7], acc_lo[7];
+    R acc[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) { acc_hi[q] = R(0); acc_lo[q] = R(0); }
-    BUNDLE_LOOP_ROLLED(t, l, Nx, nl) {
-        const int kz = kzl;
+    for (int q = 0; q < 7; ++q) acc[q] = R(0);
+    const int kz = kzl;
+    const R kzv = kfac<R>(g, 2) * kz;
+    const bool plane1 = (kz == 0) || ((Nz % 2 == 0) && (kz == Nz / 2));
+    const R w = plane1 ? R(1) : R(2);
+    auto mode = [&](int t, R gk) {  // mode (t, line lt): energy and virial terms, P and -i kx' P
         const int mx = t <= Nx / 2 ? t : t - Nx;
         const R kx = kfac<R>(g, 0) * mx;
-        const R kzv = kfac<R>(g, 2) * kz;
         const bool nyq_x = (Nx % 2 == 0) && (t == Nx / 2);
-        R gk;
-        if constexpr (Eng::kLen > 0) {
-            // the rows come in the order their values were fetched: take the
-            // first and move the rest down
-            gk = gpre[0];
-#pragma unroll
-            for (int q = 0; q + 1 < NG; ++q) gpre[q] = gpre[q + 1];
-        } else {
-            gk = G[(int64_t)t * es + f0 + l];
-        }
-        const C v = rh[t * B + l];
-        const bool plane1 = (kz == 0) || ((Nz % 2 == 0) && (kz == Nz / 2));
-        const R w = plane1 ? R(1) : R(2);
+        const C v = rh[t * B + lt];
         const R k2 = kx * kx + ky * ky + kzv * kzv;
         if (k2 > R(0)) {
             const R e = w * e_scale * gk * (v.x * v.x + v.y * v.y);
@@ -497,18 +480,28 @@ k_fft_x_influence(Geo g, LineBlocks lb, Eng eng, const R* __restrict__ G, R beta
             const R fxy = (plane1 || (nyq_x == nyq_y)) ? R(1) : R(0);
             const R fxz = (plane1 || !nyq_x) ? R(1) : R(0);
             const R fyz = (plane1 || !nyq_y) ? R(1) : R(0);
-            two_sum_acc(acc_hi[0], acc_lo[0], e);
-            two_sum_acc(acc_hi[1], acc_lo[1], e * (R(1) - c * kx * kx));
-            two_sum_acc(acc_hi[2], acc_lo[2], e * (R(1) - c * ky * ky));
-            two_sum_acc(acc_hi[3], acc_lo[3], e * (R(1) - c * kzv * kzv));
-            two_sum_acc(acc_hi[4], acc_lo[4], -e * c * kx * ky * fxy);
-            two_sum_acc(acc_hi[5], acc_lo[5], -e * c * kx * kzv * fxz);
-            two_sum_acc(acc_hi[6], acc_lo[6], -e * c * ky * kzv * fyz);
+            acc[0] += e;
+            acc[1] += e * (R(1) - c * kx * kx);
+            acc[2] += e * (R(1) - c * ky * ky);
+            acc[3] += e * (R(1) - c * kzv * kzv);
+            acc[4] -= e * c * kx * ky * fxy;
+            acc[5] -= e * c * kx * kzv * fxz;
+            acc[6] -= e * c * ky * kzv * fyz;
         }
         const C P = cscale(v, gk * c_field);
         const R kxd = nyq_x ? R(0) : kx;
-        pbuf[t * B + l] = P;
-        b0[t * B + l] = CT<R>::mk(kxd * P.y, -kxd * P.x);  // -i kx' P
+        pbuf[t * B + lt] = P;
+        b0[t * B + lt] = CT<R>::mk(kxd * P.y, -kxd * P.x);  // -i kx' P
+    };
+    if (lt < nl) {
+        if constexpr (Eng::kLen > 0) {
+            static_assert(Eng::kLen % (kFftThreads / 16) == 0, "a thread's modes are the prefetched ones");
+#pragma unroll
+            for (int i = 0; i < NG; ++i) mode((threadIdx.x >> 4) + i * (kFftThreads / 16), gpre[i]);
+        } else {
+#pragma unroll 1
+            for (int t = threadIdx.x >> 4; t < Nx; t += kFftThreads >> 4) mode(t, G[(int64_t)t * es + f0 + lt]);
+        }
     }
     __syncthreads();
     C* rA = eng.template run<1, true>(pbuf, rh, nl, 1, B);  // rho_hat is no longer needed: scratch
@@ -524,7 +517,7 @@ k_fft_x_influence(Geo g, LineBlocks lb, Eng eng, const R* __restrict__ G, R beta
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-        R h = acc_hi[q], lo = acc_lo[q];
+        R h = acc[q], lo = R(0);
         for (int off = 16; off > 0; off >>= 1) {
             const R h2 = __shfl_down_sync(0xffffffffu, h, off);
             const R l2 = __shfl_down_sync(0xffffffffu, lo, off);

@@ -73,7 +73,14 @@ k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ sce
         // pad to a multiple of 4 with keys larger than every site index
         if (lane < ((c + 3) & ~3) - c) W.u.keys[c + lane] = INT_MAX;
     }
-    for (int i = lane; i < PSIZE; i += 32) W.pt[i] = T(0);
+    // patch rows as 16-byte vectors where the patch size allows
+    constexpr bool kVec = (PSIZE * sizeof(T)) % 16 == 0;
+    constexpr int NV16 = PSIZE * (int)sizeof(T) / 16;
+    if constexpr (kVec) {
+        for (int i = lane; i < NV16; i += 32) reinterpret_cast<float4*>(W.pt)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        for (int i = lane; i < PSIZE; i += 32) W.pt[i] = T(0);
+    }
     __syncwarp();
     if (ranked) {
         // rank of item i = number of items with a smaller original index
@@ -159,7 +166,12 @@ k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ sce
         __syncwarp();
     }
     T* dst = patch + (size_t)tile * PSIZE;  // same padded layout as the shared patch
-    for (int i = lane; i < PSIZE; i += 32) dst[i] = W.pt[i];
+    if constexpr (kVec) {
+        for (int i = lane; i < NV16; i += 32)
+            reinterpret_cast<float4*>(dst)[i] = reinterpret_cast<const float4*>(W.pt)[i];
+    } else {
+        for (int i = lane; i < PSIZE; i += 32) dst[i] = W.pt[i];
+    }
 }
 
 template <typename T, int P, int TILE>
