@@ -232,16 +232,16 @@ __device__ void st_scatter(const BoxDesc& D, int idx, const Bufs& B) {
 }
 
 // Spread: the item's kSpreadTiles tiles one after another, each by the whole
-// block.  A tile's patch is accumulated in shared memory as 64-bit fixed-point
-// integers with shared-memory atomics (red_scale_exp picks the grid from the
-// tile's sites): integer sums are exact and do not depend on the order in
-// which the warps add their sites, so the result is bitwise reproducible with
-// no ordering of the tile's sites.  The patch keeps the padded pitch and is
-// written out as FP32.
+// block.  A tile's patch is accumulated in shared memory exactly, as two
+// int32 words a value (split_scale / split_term: sum of rint(x 2^k) and sum
+// of the remainders at 2^-K) with 32-bit shared-memory atomics: integer sums
+// do not depend on the order in which the warps add their sites, so the
+// result is bitwise reproducible with no ordering of the tile's sites.  The
+// patch keeps the padded pitch and is written out as FP32.
 template <int P, int TILE>
 struct SpreadRed {
     static constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
-    static constexpr size_t bytes() { return sizeof(unsigned long long) * PSIZE + sizeof(unsigned) * kWarps; }
+    static constexpr size_t bytes() { return 2 * sizeof(int) * PSIZE + sizeof(unsigned) * kWarps; }
 };
 
 template <int P, int TILE>
@@ -249,8 +249,9 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
     typedef SpreadRed<P, TILE> L;
     constexpr int PZ = L::PZ, PLANE = L::PLANE, PSIZE = L::PSIZE;
     constexpr int WS = wstride(P);
-    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem);
-    unsigned* wmax = reinterpret_cast<unsigned*>(acc + PSIZE);
+    int* acc_h = reinterpret_cast<int*>(smem);
+    int* acc_l = acc_h + PSIZE;
+    unsigned* wmax = reinterpret_cast<unsigned*>(acc_l + PSIZE);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NR = (P * P + 31) / 32;
     int roff[NR], riy[NR], riz[NR];
@@ -270,7 +271,7 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
         const int s0 = ldcg(&B.tile_start[D.ts0 + tile]);
         const int c = ldcg(&B.tile_start[D.ts0 + tile + 1]) - s0;
         const long long sb = D.site0 + s0;
-        for (int i = threadIdx.x; i < PSIZE; i += kThreads) acc[i] = 0ull;
+        for (int i = threadIdx.x; i < 2 * PSIZE; i += kThreads) acc_h[i] = 0;
         unsigned mb = 0;  // largest |q Wx| of the tile
         for (int t = threadIdx.x; t < c; t += kThreads) {
             const float* w = B.swt + (sb + t) * WS;
@@ -282,8 +283,8 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
         __syncthreads();
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) mb = max(mb, wmax[w]);
-        const int ks = red_scale_exp(mb, c);
-        const float S = pow2f(ks), invS = pow2f(-ks);
+        const SplitScale sc = split_scale(mb, c);
+        const float S = pow2f(sc.k), twoK = pow2f(sc.K);
         for (int t = warp; t < c; t += kWarps) {
             const float* w = B.swt + (sb + t) * WS;
             float wxq[P];
@@ -291,21 +292,29 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
             for (int a = 0; a < P; ++a) wxq[a] = ldcg(&w[a]);
             const int cl = ldcg(&B.scell[sb + t]);
             const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
-            unsigned long long* base0 = acc + lx * PLANE + ly * PZ + lz;
+            const int base0 = lx * PLANE + ly * PZ + lz;
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr) {
                 if (ract[jr]) {
-                    const float wyz = ldcg(&w[P + riy[jr]]) * ldcg(&w[2 * P + riz[jr]]);
-                    unsigned long long* b = base0 + roff[jr];
+                    const float wyzS = ldcg(&w[P + riy[jr]]) * ldcg(&w[2 * P + riz[jr]]) * S;
+                    const int b = base0 + roff[jr];
 #pragma unroll
-                    for (int a = 0; a < P; ++a)
-                        atomicAdd(b + a * PLANE, (unsigned long long)__float2ll_rn(wxq[a] * wyz * S));
+                    for (int a = 0; a < P; ++a) {
+                        int h, l;
+                        split_term(wxq[a] * wyzS, twoK, h, l);
+                        atomicAdd(&acc_h[b + a * PLANE], h);
+                        atomicAdd(&acc_l[b + a * PLANE], l);
+                    }
                 }
             }
         }
         __syncthreads();
         float* dst = B.patch + D.patch0 + (long long)tile * PSIZE;
-        for (int i = threadIdx.x; i < PSIZE; i += kThreads) dst[i] = __ll2float_rn((long long)acc[i]) * invS;
+        const float i1 = pow2f(-sc.k), i2 = pow2f(-sc.K);
+        for (int i = threadIdx.x; i < PSIZE; i += kThreads) {
+            const long long v = (long long)acc_h[i] * (1ll << sc.K) + acc_l[i];
+            dst[i] = sc.finite ? __ll2float_rn(v) * i2 * i1 : __int_as_float(0x7fffffff);
+        }
         __syncthreads();
     }
 }

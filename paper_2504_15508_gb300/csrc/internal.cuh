@@ -205,16 +205,47 @@ inline RedRows red_rows(int p, int pz) {
     return rr;
 }
 
-// k of the grid 2^-k for a tile of c sites whose largest |q Wx| is m (as
-// float bits): a patch value sums at most c contributions of at most m each
-// (Wy, Wz <= 1), so |sum| 2^k < 2^61
-__device__ __forceinline__ int red_scale_exp(unsigned m_bits, int c) {
+// Exact accumulation of a tile patch in two 32-bit integer words a value.
+// Each stencil term x (an FP32 product) is scaled to f = x 2^k and split as
+// f = h + l 2^-K, h = rint(f) and l = rint((f - h) 2^K); the patch keeps
+// sum h and sum l in separate int32 arrays (added with 32-bit shared-memory
+// atomics, so the order of the additions does not matter), and the value is
+// (sum h 2^K + sum l) 2^-(k+K).  For a tile of c sites whose largest |q Wx|
+// is m (Wy, Wz <= 1, so |x| <= m):
+//   k = min(22 - e1, 30 - e), m < 2^e1, m c < 2^e: |f| < 2^22 (h is exact
+//       by the 1.5 2^23 offset) and sum |h| <= c m 2^k + c/2 < 2^31;
+//   K = min(22, 31 - bits(c)): |l| <= 2^(K-1) and sum |l| < 2^30.
+// f itself is the FP32 product scaled by a power of two, and for |f| >= 2 the
+// split is exact, so the patch is the exact sum of the FP32 terms up to
+// 2^-(k+K+1) <= m 2^-45 a term.
+struct SplitScale {
+    int k, K;
+    bool finite;
+};
+
+__device__ __forceinline__ SplitScale split_scale(unsigned m_bits, int c) {
     const float mq = __uint_as_float(m_bits);
-    if (!(mq > 0.f)) return 60;  // no charge: any scale
+    SplitScale r{0, 22, true};
+    if (!(mq > 0.f)) return r;  // no charge: any scale
     const float m = mq * (float)max(c, 1);
-    if (!isfinite(m)) return -64;
-    const int e = (int)((__float_as_uint(m) >> 23) & 255u) - 126;  // m < 2^e
-    return min(100, 61 - e);
+    if (!isfinite(m)) {
+        r.finite = false;
+        return r;
+    }
+    const int e1 = (int)((m_bits >> 23) & 255u) - 126;                  // mq < 2^e1
+    const int e = (int)((__float_as_uint(m) >> 23) & 255u) - 126;       // m < 2^e
+    r.k = min(100, min(22 - e1, 30 - e));
+    r.K = min(22, 31 - (32 - __clz(max(c, 1))));
+    return r;
+}
+
+// the split of f = x 2^k (|f| < 2^22) into h = rint(f) and l = rint((f - h) 2^K)
+__device__ __forceinline__ void split_term(float f, float twoK, int& h, int& l) {
+    constexpr float kMagic = 12582912.f;  // 1.5 2^23: adding it rounds |v| < 2^22 to an integer
+    const float t = f + kMagic;
+    h = __float_as_int(t) - __float_as_int(kMagic);
+    const float r = f - (t - kMagic);
+    l = __float_as_int(fmaf(r, twoK, kMagic)) - __float_as_int(kMagic);
 }
 
 // 2^k from its exponent bits (-126 <= k <= 127)
