@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=20000, help="learned64: Adam steps")
     ap.add_argument("--train-batch", type=int, default=8192, help="learned64: sites per Adam step")
     ap.add_argument("--held-frames", type=int, default=100, help="learned64: held-out frames per base (2 bases)")
+    ap.add_argument("--forward-only", action="store_true",
+                    help="learned64: time only the network forward kernels (mma.sync and tcgen05) on the "
+                         "system's features, seeded random weights, no training")
     return ap.parse_args()
 
 
@@ -793,6 +796,82 @@ def run_batched(args):
 
 
 # --------------------------------------------------------------------- learned form
+def run_forward(args):
+    """The learned correction's network forward alone: the 288,768 sites'
+    features on the 64^3 coarse mesh (both feature sets), seeded random
+    weights, each kernel (warp-level mma.sync, tcgen05 with tensor-memory
+    accumulators) timed as replays of a CUDA graph of the call, L2 flushed
+    before each; the two kernels' outputs are compared."""
+    import torch
+
+    from paper_2504_15508_gb300.pppm import Corrector, Plan
+    from workloads.water import init_mlp_params, make_workload
+
+    dev = torch.device("cuda", 0)
+    wb, w = make_workload("water72192_m64")
+    n = wb.n
+    coarse = Plan(wb.box, (64,) * 3, 5, 0.4, precision="fp32")
+    pos = torch.tensor(wb.pos, dtype=torch.float32, device=dev)
+    q = torch.tensor(wb.q, dtype=torch.float32, device=dev)
+    types = torch.tensor(wb.types, dtype=torch.int8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    K = args.steps
+
+    def graph_timed(fn):
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            for _ in range(max(3, args.warmup)):
+                fn(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            fn(side)
+        torch.cuda.synchronize()
+        cur = torch.cuda.current_stream()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
+            flush.fill_(float(k))
+            evs[k][0].record(cur)
+            g.replay()
+            evs[k][1].record(cur)
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    sampler = ClockSampler(gpu_index_for(0))
+    kinds = {}
+    for kind in ("stated", "cell"):
+        n_in = Corrector.WIDTH[kind]
+        corr = Corrector(coarse, params=init_mlp_params(3, n_in=n_in).astype(np.float32), s_in=0.5, s_out=1.0,
+                         features=kind)
+        feat, _ = corr.features(pos, q, types)
+        flop = 2.0 * n * (n_in * 64 + 64 * 64 + 64 * 3)
+        res, ys = {}, {}
+        for fwd in ("mma_sync", "tcgen05"):
+            corr.set_forward(fwd)
+            y = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            ms = graph_timed(lambda st: corr.forward(feat, out=y, stream=st))
+            res[fwd] = {"us": ms * 1e3, "tflops": flop / (ms * 1e-3) / 1e12}
+            ys[fwd] = y
+        if coarse.status() != 0:
+            raise RuntimeError("forward kernel status set")
+        res["max_abs_diff"] = float((ys["tcgen05"] - ys["mma_sync"]).abs().max())
+        res["inputs"] = n_in
+        kinds[kind] = res
+        corr.close()
+    clocks = sampler.stop()
+    main = kinds["stated"]["mma_sync"]["us"]
+    line = {
+        "metric": "learned-correction network forward, sites/s", "value": n / (main * 1e-6), "unit": "sites/s",
+        "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": main * 1e-3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"water72192 features on the 64^3 mesh ({n} sites), n_in-64-64-3 tanh network, "
+                               f"seeded random weights; the line's value: stated set, mma.sync kernel",
+                   "l2": "flushed between timed steps"},
+        "kernels": kinds, "clocks": clocks, "gpu_launches": K,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """The 216,576-atom system on a coarse 64^3 mesh plus the learned
     correction, trained here on fine-mesh (160^3) forces of seeded perturbed
@@ -878,6 +957,11 @@ def run_learned(args):
         ms_corr = graph_timed(lambda st: corr.apply(pos, q, types, out=o_c, stream=st))
         ms_feat = graph_timed(lambda st: corr.features(pos, q, types, feat=feat, forces=o_c[1], stream=st))
         ms_mlp = graph_timed(lambda st: corr.forward(feat, out=y, stream=st))
+        # the same forward on the tcgen05 kernel, for comparison
+        corr.set_forward("tcgen05")
+        ms_mlp_tc = graph_timed(lambda st: corr.forward(feat, out=y, stream=st))
+        corr.set_forward("mma_sync")
+        mlp_flop = 2.0 * n * (corr.n_in * 64 + 64 * 64 + 64 * 3)
         speedup = ms_plain[eq] / ms_corr if eq is not None else None
         # the plain mesh of exactly the corrected error, by interpolating
         # log(error) and time linearly between the two neighbouring meshes
@@ -896,7 +980,10 @@ def run_learned(args):
             "speedup_vs_plain_at_equal_error": speedup,
             "equal_error_interpolated": interp,
             "gain_in_error_vs_coarse": err["coarse"] / err["corrected"],
-            "ms": {"corrected": ms_corr, "coarse_plus_features": ms_feat, "mlp_forward": ms_mlp},
+            "ms": {"corrected": ms_corr, "coarse_plus_features": ms_feat, "mlp_forward": ms_mlp,
+                   "mlp_forward_tcgen05": ms_mlp_tc},
+            "mlp_forward_tflops": {"mma_sync": mlp_flop / (ms_mlp * 1e-3) / 1e12,
+                                   "tcgen05": mlp_flop / (ms_mlp_tc * 1e-3) / 1e12},
             "train": {"steps": log.steps, "batch": args.train_batch, "seconds": log.seconds,
                       "data_seconds": t_data, "data_gb": data_bytes / 1e9, "loss": log.loss[::4] + log.loss[-1:]},
         }
@@ -1067,7 +1154,10 @@ def main():
         run_batched(args)
         return
     if args.impl == "ours" and args.workload == "learned64":
-        run_learned(args)
+        if args.forward_only:
+            run_forward(args)
+        else:
+            run_learned(args)
         return
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) == 0:

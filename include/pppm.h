@@ -380,7 +380,22 @@ int pppm_set_wait_limit(pppm_plan *plan, long long spins);
  * pppm_corr_targets     training targets t_i = (f_fine,i - f_coarse,i) /
  *                       (q_i s_out), 0 where q_i = 0 (device n x 3 FP32).
  * pppm_corr_forward     y = network(feat) for n feature rows -> out (device
- *                       n x 3 FP32).
+ *                       n x 3 FP32); feat must be 4-byte aligned
+ *                       (PPPM_ERR_INVALID_ARG otherwise, nothing launched).
+ * pppm_corr_set_forward the kernel that runs the network forward (in
+ *                       pppm_corr_forward and pppm_corr_apply):
+ *                       PPPM_FORWARD_MMA_SYNC (the default) runs the
+ *                       warp-level mma.sync kernel, 16 sites a warp, the
+ *                       layers chained in registers; PPPM_FORWARD_TCGEN05
+ *                       runs each layer as tcgen05.mma instructions, 128
+ *                       sites a tile, with the accumulators in tensor memory
+ *                       (a feature pointer that is not 16-byte aligned runs
+ *                       the mma.sync kernel).  Both take BF16 weights and
+ *                       activations and accumulate in FP32; their results
+ *                       agree to rounding (on the workloads, bitwise).  A tcgen05 completion not seen
+ *                       within 2^26 polls sets PPPM_ERR_TIMEOUT in the coarse
+ *                       plan's status word (pppm_status) and the launch ends
+ *                       without writing the remaining rows.
  * pppm_corr_apply       corrected PPPM: coarse compute (energy, virial:
  *                       device doubles, uncorrected) and forces + q s_out y.
  * pppm_corr_grad        loss and its gradient w.r.t. the parameters over the
@@ -402,6 +417,7 @@ int pppm_set_wait_limit(pppm_plan *plan, long long spins);
  */
 typedef struct pppm_corr pppm_corr;
 enum { PPPM_CORR_CELL = 0, PPPM_CORR_STATED = 1 };
+enum { PPPM_FORWARD_TCGEN05 = 0, PPPM_FORWARD_MMA_SYNC = 1 };
 int pppm_corr_create(pppm_plan *coarse, pppm_corr **out);
 int pppm_corr_create_features(pppm_plan *coarse, int features, pppm_corr **out);
 int pppm_corr_nparams(void);
@@ -416,6 +432,7 @@ int pppm_corr_calibrate(pppm_corr *corr, void *stream, const float *pos, const f
 int pppm_corr_get_scales(const pppm_corr *corr, double *s_in, double *s_out);
 int pppm_corr_targets(pppm_corr *corr, void *stream, const float *f_fine, const float *f_coarse,
                       const float *q, int64_t n, float *target);
+int pppm_corr_set_forward(pppm_corr *corr, int kind);
 int pppm_corr_forward(pppm_corr *corr, void *stream, const void *feat, int64_t n, float *out);
 int pppm_corr_apply(pppm_corr *corr, void *stream, const float *pos, const float *q,
                     const signed char *types, int64_t n, double *energy, float *forces,

@@ -26,6 +26,8 @@ PPPM_FP32 = 1
 PPPM_FP64 = 2
 PPPM_CORR_CELL = 0
 PPPM_CORR_STATED = 1
+PPPM_FORWARD_TCGEN05 = 0
+PPPM_FORWARD_MMA_SYNC = 1
 PPPM_BATCH_PERSISTENT = 0
 PPPM_BATCH_STAGED = 1
 PPPM_BATCH_AUTO = 2
@@ -99,6 +101,7 @@ SIGNATURES = {
     "pppm_corr_calibrate": (cint, [vp, vp, vp, vp, vp, i64, vp]),
     "pppm_corr_get_scales": (cint, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
     "pppm_corr_targets": (cint, [vp, vp, vp, vp, vp, i64, vp]),
+    "pppm_corr_set_forward": (cint, [vp, cint]),
     "pppm_corr_forward": (cint, [vp, vp, vp, i64, vp]),
     "pppm_corr_apply": (cint, [vp, vp, vp, vp, vp, i64, vp, vp, vp]),
     "pppm_corr_grad": (cint, [vp, vp, vp, vp, i64, vp, i64, vp, vp]),

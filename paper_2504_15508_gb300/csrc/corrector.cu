@@ -21,6 +21,7 @@
 // gradients reduced in a fixed order before the Adam step.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -317,6 +318,261 @@ k_mlp_forward(const __nv_bfloat16* __restrict__ feat, int n, const __nv_bfloat16
     }
 }
 
+// ------------------------------------------------------------------ tcgen05 forward
+// The same network on the fifth-generation tensor cores: one CTA takes 128
+// sites at a time (M = 128), each layer one chain of tcgen05.mma kind::f16
+// instructions (BF16 operands from shared memory, FP32 accumulators in
+// tensor memory) issued by one thread, N = 64 for the hidden layers and 16
+// (three outputs, zero rows above) for the last, K = 16 per instruction.
+// The accumulators are read back with tcgen05.ld (eight warps: lane t of
+// warp w holds row 32 (w mod 4) + t, warps 0-3 its columns 0-31 and warps 4-7
+// its columns 32-63), biased, passed through tanh, rounded to BF16 and stored
+// as the next layer's A operand; the MMA's completion is signalled through an
+// mbarrier (tcgen05.commit) and waited on with a bounded spin.  Each thread
+// fetches its half of the next tile's feature row while the current tile's
+// layers run.
+//
+// Operands use the no-swizzle K-major canonical layout: 8-row x 16-byte core
+// matrices (8 rows of 8 BF16 values, 128 contiguous bytes), the K-chunks of
+// an 8-row group 128 bytes apart (leading byte offset) and the 8-row groups
+// K/8 * 128 bytes apart (stride byte offset).  One MMA with K = 16 reads two
+// K-chunks, so the k-th MMA of a layer starts 256 k bytes in.
+namespace tc {
+
+constexpr int kRows = 128;             // sites per tile (MMA M)
+constexpr int kThreads = 256;          // warps w and w + 4 share TMEM lanes 32 (w mod 4) + 0..31
+constexpr uint32_t kTmemCols = 64;     // each layer's accumulators in columns 0..63 (outputs: 0..15)
+constexpr int kOutCol = 0, kOutN = 16;
+constexpr long long kSpin = 1ll << 26; // polls of an MMA completion before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) of a K-major operand with K columns
+__host__ __device__ constexpr uint32_t canon(int r, int k, int K) {
+    return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start, leading and stride byte offsets
+// (16-byte units), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this warp's 32 rows: thread t gets row t.
+// The registers are valid only after wait_ld, which takes them as operands so
+// that no use of them can be scheduled ahead of the wait.
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void wait_ld(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+template <int NIN>
+struct Smem {
+    // the second hidden layer's activations replace the first's (A3 = A2):
+    // the layer-2 MMA has completed before they are written
+    static constexpr uint32_t W1 = 0, W2 = W1 + 64 * NIN * 2, W3 = W2 + 64 * 64 * 2, A1 = W3 + kOutN * 64 * 2,
+                              A2 = A1 + kRows * NIN * 2, A3 = A2, BIAS = A2 + kRows * 64 * 2,
+                              MBAR = BIAS + (64 + 64 + kOutN) * 4, TSLOT = MBAR + 8, BYTES = TSLOT + 8;
+};
+
+// hidden activations of this thread's row, columns 32 hf .. 32 hf + 31:
+// tanh(acc + b) -> BF16 -> the next layer's A operand
+__device__ __forceinline__ void hidden_out(uint32_t tmem_row, const float* __restrict__ b, unsigned char* a_op,
+                                           int row, int hf) {
+    uint32_t v[2][16];
+    ld16(tmem_row + 32 * hf, v[0]);  // both loads in flight before the waits
+    ld16(tmem_row + 32 * hf + 16, v[1]);
+    wait_ld(v[0]);
+    wait_ld(v[1]);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int c0 = 32 * hf + 16 * q;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint4 pk;
+            uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = c0 + 8 * h + 2 * e;
+                w[e] = pack_bf16(tanhf(__uint_as_float(v[q][8 * h + 2 * e]) + b[c]),
+                                 tanhf(__uint_as_float(v[q][8 * h + 2 * e + 1]) + b[c + 1]));
+            }
+            *reinterpret_cast<uint4*>(a_op + canon(row, c0 + 8 * h, 64)) = pk;
+        }
+    }
+}
+
+template <int NIN>
+__global__ void __launch_bounds__(kThreads)
+k_mlp_forward_tc(const __nv_bfloat16* __restrict__ feat, int n, const __nv_bfloat16* __restrict__ wbf,
+                 const float* __restrict__ master, float s_out, const float* __restrict__ q,
+                 float* __restrict__ forces, float* __restrict__ out, int* __restrict__ status) {
+    typedef Net<NIN> L;
+    typedef Smem<NIN> S;
+    constexpr int K1P = L::K1P, BW1 = L::BW1, BW2 = L::BW2, BW3 = L::BW3;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int t = threadIdx.x, warp = t >> 5;
+    const int row = 32 * (warp & 3) + (t & 31), hf = warp >> 2;  // tile row and column half of this thread
+    const uint32_t base = smem_u32(sm);
+    const uint32_t mbar = base + S::MBAR;
+    float* bias = reinterpret_cast<float*>(sm + S::BIAS);
+    // weights into the canonical K-major layout (rows are output units)
+    for (int i = t; i < 64 * NIN; i += kThreads) {
+        const int r = i / NIN, k = i - r * NIN;
+        *reinterpret_cast<__nv_bfloat16*>(sm + S::W1 + canon(r, k, NIN)) = wbf[BW1 + r * K1P + k];
+    }
+    for (int i = t; i < 64 * 64; i += kThreads) {
+        const int r = i >> 6, k = i & 63;
+        *reinterpret_cast<__nv_bfloat16*>(sm + S::W2 + canon(r, k, 64)) = wbf[BW2 + r * K2P + k];
+    }
+    for (int i = t; i < kOutN * 64; i += kThreads) {
+        const int r = i >> 6, k = i & 63;
+        *reinterpret_cast<__nv_bfloat16*>(sm + S::W3 + canon(r, k, 64)) =
+            r < NOUT ? wbf[BW3 + r * K2P + k] : __float2bfloat16_rn(0.f);
+    }
+    for (int k = t; k < 64; k += kThreads) {  // biases are BF16 parameters too
+        bias[k] = __bfloat162float(__float2bfloat16_rn(master[L::O_B1 + k]));
+        bias[64 + k] = __bfloat162float(__float2bfloat16_rn(master[L::O_B2 + k]));
+    }
+    if (t < kOutN) bias[128 + t] = t < NOUT ? __bfloat162float(__float2bfloat16_rn(master[L::O_B3 + t])) : 0.f;
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(base + S::TSLOT),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + S::TSLOT);
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's 32 lanes
+    uint32_t phase = 0;
+    bool failed = false;  // the same in every thread (decided at a barrier)
+    // one layer: D[col ..] = A (128 x K) W^T (K x N); false if its completion
+    // was not seen within the spin limit
+    auto layer = [&](uint32_t a_off, uint32_t b_off, int K, int N, uint32_t col) {
+        // every thread's operand stores are done: hand the tile to the tensor cores
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (t == 0) {
+            fence_after();
+            const uint32_t id = idesc(kRows, N);
+            for (int k = 0; k < K / 16; ++k)
+                mma(tmem + col, desc(base + a_off + 256 * k, 128, K / 8 * 128),
+                    desc(base + b_off + 256 * k, 128, K / 8 * 128), id, k > 0);
+            commit(mbar);
+        }
+        const bool ok = wait_bounded(mbar, phase, kSpin);
+        failed = __syncthreads_or(!ok) != 0;
+        if (!failed) phase ^= 1;
+        fence_after();
+        return !failed;
+    };
+    const int ntile = (n + kRows - 1) / kRows;
+    // this thread's half of a feature row (zeros past the end), fetched one
+    // tile ahead so that the loads overlap the current tile's layers
+    constexpr int NCH = NIN / 16;  // 16-byte chunks a thread
+    uint4 nf[NCH];
+    auto fetch = [&](int tile) {
+        const int r = tile * kRows + row;
+        const uint4* src = reinterpret_cast<const uint4*>(feat + (int64_t)min(r, n - 1) * NIN) + hf * NCH;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) nf[c] = r < n ? __ldg(&src[c]) : make_uint4(0, 0, 0, 0);
+    };
+    if (blockIdx.x < ntile) fetch(blockIdx.x);
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int r = tile * kRows + row;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+            *reinterpret_cast<uint4*>(sm + S::A1 + canon(row, 8 * (hf * NCH + c), NIN)) = nf[c];
+        if (tile + (int)gridDim.x < ntile) fetch(tile + gridDim.x);
+        if (!layer(S::A1, S::W1, NIN, 64, 0)) break;
+        hidden_out(trow, bias, sm + S::A2, row, hf);
+        if (!layer(S::A2, S::W2, 64, 64, 0)) break;
+        hidden_out(trow, bias + 64, sm + S::A3, row, hf);
+        if (!layer(S::A3, S::W3, 64, kOutN, kOutCol)) break;
+        uint32_t y[16];
+        ld16(trow + kOutCol, y);  // warp-wide; the second half of the warps drops it
+        wait_ld(y);
+        if (hf == 0 && r < n) {
+#pragma unroll
+            for (int c = 0; c < NOUT; ++c) {
+                const float v = __uint_as_float(y[c]) + bias[128 + c];
+                if (forces) forces[3 * (int64_t)r + c] += q[r] * s_out * v;
+                else out[3 * (int64_t)r + c] = v;
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (failed) {
+        if (t == 0) atomicOr(status, 2);
+        wait_bounded(mbar, phase, kSpin);  // an MMA still in flight lands before the memory is released
+    }
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace tc
+
 // FP32 master -> padded BF16 copy for the forward
 template <int NIN>
 __global__ void k_to_bf16(const float* __restrict__ master, __nv_bfloat16* __restrict__ wbf) {
@@ -586,6 +842,7 @@ struct pppm_corr {
     float s_in = 1.f, s_out = 1.f;
     long long step = 0;
     double* ev = nullptr;  // scratch energy/virial of internal coarse evaluations
+    int forward = PPPM_FORWARD_MMA_SYNC;  // network forward: mma.sync (faster at these widths) or tcgen05
 };
 
 namespace {
@@ -673,9 +930,46 @@ cudaError_t launch_features(pppm_corr* C, cudaStream_t s, const float* pos, cons
 int mlp_forward(pppm_corr* C, cudaStream_t s, const __nv_bfloat16* feat, int64_t n, const float* q, float* forces,
                 float* out) {
     if (n == 0) return PPPM_OK;
+    // both kernels read BF16 pairs as 4-byte words: a feature pointer off the
+    // 4-byte grid is rejected before any launch
+    if (n > (int64_t(1) << 30) || (reinterpret_cast<uintptr_t>(feat) & 3) != 0) return PPPM_ERR_INVALID_ARG;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // the tcgen05 kernel reads a feature row as 16-byte vectors
+    if (C->forward == PPPM_FORWARD_TCGEN05 && (reinterpret_cast<uintptr_t>(feat) & 15) == 0) {
+        cudaError_t e = with_nin(C->nin, [&](auto N) {
+            constexpr int NIN = decltype(N)::value;
+            const size_t smem = tc::Smem<NIN>::BYTES;
+            auto kern = tc::k_mlp_forward_tc<NIN>;
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e2 != cudaSuccess) return e2;
+            // all of the SM's on-chip memory as shared memory, so that as many
+            // CTAs are resident as registers and shared memory allow
+            e2 = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared);
+            if (e2 != cudaSuccess) return e2;
+            // resident CTAs an SM from its registers, shared memory, threads
+            // and tensor memory (512 columns)
+            cudaFuncAttributes fa{};
+            e2 = cudaFuncGetAttributes(&fa, kern);
+            if (e2 != cudaSuccess) return e2;
+            int smem_sm = 0, smem_rsv = 0, regs_sm = 0;
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+            int per_sm = std::min<int>(512 / (int)tc::kTmemCols, 2048 / tc::kThreads);
+            per_sm = std::min<int>(per_sm, smem_sm / (int)(smem + fa.sharedSizeBytes + smem_rsv));
+            if (fa.numRegs > 0) per_sm = std::min<int>(per_sm, regs_sm / (fa.numRegs * tc::kThreads));
+            const int64_t ntile = (n + tc::kRows - 1) / tc::kRows;
+            const int blocks = (int)std::min<int64_t>(ntile, (int64_t)std::max(per_sm, 1) * nsm);
+            kern<<<blocks, tc::kThreads, smem, s>>>(feat, (int)n, C->wbf, C->master, C->s_out, q, forces, out,
+                                                     C->plan->status);
+            return cudaGetLastError();
+        });
+        CC(e);
+        return PPPM_OK;
+    }
     const int tiles = (int)((n + 15) / 16);
     int blocks = (tiles + 3) / 4;
     if (blocks > 8 * nsm) blocks = 8 * nsm;
@@ -876,6 +1170,12 @@ int pppm_corr_get_scales(const pppm_corr* C, double* s_in, double* s_out) {
     if (!C || !s_in || !s_out) return PPPM_ERR_INVALID_ARG;
     *s_in = C->s_in;
     *s_out = C->s_out;
+    return PPPM_OK;
+}
+
+int pppm_corr_set_forward(pppm_corr* C, int kind) {
+    if (!C || (kind != PPPM_FORWARD_TCGEN05 && kind != PPPM_FORWARD_MMA_SYNC)) return PPPM_ERR_INVALID_ARG;
+    C->forward = kind;
     return PPPM_OK;
 }
 

@@ -386,6 +386,7 @@ class Corrector:
         self.features_kind = features
         self.n_in = int(L.pppm_corr_feature_width(h))
         self.nparams = int(L.pppm_corr_param_count(h))
+        self.forward_kind = "mma_sync"
         if params is not None:
             self.set_weights(params, s_in, s_out)
 
@@ -399,6 +400,14 @@ class Corrector:
             self.close()
         except Exception:
             pass
+
+    def set_forward(self, kind: str):
+        """Kernel of the network forward: "mma_sync" (default; warp-level,
+        the layers chained in registers) or "tcgen05" (tensor-memory
+        accumulators, 128 sites a tile)."""
+        k = {"tcgen05": N.PPPM_FORWARD_TCGEN05, "mma_sync": N.PPPM_FORWARD_MMA_SYNC}[kind]
+        N.check(self._lib.pppm_corr_set_forward(self._h, k), "pppm_corr_set_forward")
+        self.forward_kind = kind
 
     # ------------------------------------------------------------ parameters
     def set_weights(self, params, s_in: float, s_out: float):

@@ -113,14 +113,19 @@ def test_potential_output_leaves_the_forces_unchanged(cuda_device):
     del corr
 
 
+FORWARDS = ["tcgen05", "mma_sync"]
+
+
+@pytest.mark.parametrize("fwd", FORWARDS)
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("n", [1, 7, 16, 37, 1000, 16384])
-def test_forward_matches_oracle(cuda_device, n, kind):
+@pytest.mark.parametrize("n", [1, 7, 16, 37, 127, 128, 129, 1000, 16384])
+def test_forward_matches_oracle(cuda_device, n, kind, fwd):
     Plan, Corrector, _ = _mods()
     w = make_water(4096, 49.7, 2)
     P = Plan((49.7,) * 3, (24,) * 3, order=5, beta=0.4)
     theta = _theta(3, kind=kind)
     corr = Corrector(P, params=theta, s_in=0.5, s_out=1.0, features=kind)
+    corr.set_forward(fwd)
     pos, q, types = _sites(w)
     feat, _ = corr.features(pos, q, types)
     feat = feat[:n].contiguous()
@@ -131,9 +136,55 @@ def test_forward_matches_oracle(cuda_device, n, kind):
     yg = y.cpu().numpy()
     err = np.abs(yg - yr)
     scale = np.max(np.abs(yr))
-    print(f"forward n={n}: max {np.max(err) / scale:.2e} rms {np.sqrt(np.mean(err ** 2)) / np.sqrt(np.mean(yr ** 2)):.2e}")
+    print(f"forward {fwd} n={n}: max {np.max(err) / scale:.2e} "
+          f"rms {np.sqrt(np.mean(err ** 2)) / np.sqrt(np.mean(yr ** 2)):.2e}")
     assert np.max(err) <= 4e-3 * scale
     assert np.sqrt(np.mean(err ** 2)) <= 1e-3 * np.sqrt(np.mean(yr ** 2))
+    assert P.status() == 0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_forward_kernels_agree(cuda_device, kind):
+    """The tcgen05 and mma.sync forwards take the same BF16 operands and
+    accumulate in FP32 in different orders: they agree to the rounding of the
+    BF16 activations, and each is reproducible run to run; a feature pointer
+    off the 16-byte grid runs the mma.sync kernel and gives its result."""
+    Plan, Corrector, _ = _mods()
+    w = make_water(4096, 49.7, 2)
+    P = Plan((49.7,) * 3, (24,) * 3, order=5, beta=0.4)
+    corr = Corrector(P, params=_theta(5, kind=kind), s_in=0.5, s_out=1.0, features=kind)
+    pos, q, types = _sites(w)
+    feat, _ = corr.features(pos, q, types)
+    ys = {}
+    for fwd in FORWARDS:
+        corr.set_forward(fwd)
+        a = corr.forward(feat)
+        b = corr.forward(feat)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), fwd
+        ys[fwd] = a
+    d = (ys["tcgen05"] - ys["mma_sync"]).abs()
+    assert float(d.max()) <= 4e-3 * float(ys["mma_sync"].abs().max())
+    # rows 1.. of a copy whose row 1 starts 4 bytes off the 16-byte grid
+    n_in = corr.n_in
+    flat = torch.zeros(feat.numel() + 8, dtype=feat.dtype, device=feat.device)
+    flat[2:2 + feat.numel()] = feat.reshape(-1)
+    shifted = flat[2 + n_in:2 + feat.numel()].view(-1, n_in)
+    assert shifted.data_ptr() % 16 == 4
+    corr.set_forward("tcgen05")
+    y_shift = corr.forward(shifted)
+    corr.set_forward("mma_sync")
+    y_ref = corr.forward(feat[1:].contiguous())
+    torch.cuda.synchronize()
+    assert torch.equal(y_shift, y_ref)
+    # a pointer off the 4-byte grid is refused on the host, for either kernel
+    odd = flat[1 + n_in:1 + n_in + 4 * n_in].view(-1, n_in)
+    assert odd.data_ptr() % 4 == 2
+    for fwd in FORWARDS:
+        corr.set_forward(fwd)
+        with pytest.raises(RuntimeError):
+            corr.forward(odd)
+    assert P.status() == 0
 
 
 @pytest.mark.parametrize("kind", KINDS)
