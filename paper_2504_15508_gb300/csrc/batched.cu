@@ -37,7 +37,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 enum Stage { S_BIN, S_SCAN, S_SCATTER, S_SPREAD, S_ZR2C, S_YFWD, S_XINF, S_YINV, S_ZC2R, S_GATHER, NSTAGE };
 constexpr int kSiteChunk = 1024;  // sites per bin / scatter item
-constexpr int kZPairs = 8;        // row pairs per z-pass item
+constexpr int kZPairs = 8;        // row pairs per z-pass item, at least
+constexpr int kZRows = 512;       // and up to about this many points (pairs x Nz) an item
 constexpr int kSpreadTiles = kWarps;
 constexpr int kGatherTiles = 2;   // four warps per tile
 
@@ -59,6 +60,7 @@ struct BoxDesc {
     int nmax;
     int part0;
     float e_scale, c_field, beta;
+    int zp;  // row pairs per z-pass item
     int nitems[NSTAGE];
 };
 
@@ -380,9 +382,9 @@ __device__ void st_zr2c_quant(const BoxDesc& D, int idx, const Bufs& B, unsigned
     const Geo& g = D.g;
     const int Nz = g.N[2], Hz = g.Hz, rows = g.N[0] * g.N[1];
     float2* a = reinterpret_cast<float2*>(smem);
-    float2* b = a + kZPairs * Nz;
-    const int pair0 = idx * kZPairs;
-    const int np = min(kZPairs, (rows + 1) / 2 - pair0);
+    float2* b = a + D.zp * Nz;
+    const int pair0 = idx * D.zp;
+    const int np = min(D.zp, (rows + 1) / 2 - pair0);
     float2* out = B.cx0 + D.c0;
     for (int half = 0; half < 2; ++half) {
         for (int p = threadIdx.x >> 5; p < np; p += kWarps) {
@@ -414,9 +416,9 @@ __device__ void st_zr2c(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
     const Geo& g = D.g;
     const int Nz = g.N[2], Hz = g.Hz, rows = g.N[0] * g.N[1];
     float2* a = reinterpret_cast<float2*>(smem);
-    float2* b = a + kZPairs * Nz;
-    const int pair0 = idx * kZPairs;
-    const int np = min(kZPairs, (rows + 1) / 2 - pair0);
+    float2* b = a + D.zp * Nz;
+    const int pair0 = idx * D.zp;
+    const int np = min(D.zp, (rows + 1) / 2 - pair0);
     for (int p = threadIdx.x >> 5; p < np; p += kWarps) {
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
         const int x0 = r0 / g.N[1], y0 = r0 - x0 * g.N[1];
@@ -675,11 +677,11 @@ __device__ __forceinline__ void store_field_row(const BoxDesc& D, const Bufs& B,
 __device__ void st_zc2r_quant(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
     const Geo& g = D.g;
     const int Nz = g.N[2], Hz = g.Hz, rows = g.N[0] * g.N[1];
-    const int pair0 = idx * kZPairs;
-    const int np = min(kZPairs, (rows + 1) / 2 - pair0);
+    const int pair0 = idx * D.zp;
+    const int np = min(D.zp, (rows + 1) / 2 - pair0);
     const int nlines = 3 * np;
     float2* a = reinterpret_cast<float2*>(smem);
-    float2* b = a + 3 * kZPairs * Nz;
+    float2* b = a + 3 * D.zp * Nz;
     const float2* srcs[3] = {B.cx1 + D.c0, B.cx2 + D.c0, B.cx0 + D.c0};
     for (int half = 0; half < 2; ++half) {
         for (int line = threadIdx.x >> 5; line < nlines; line += kWarps) {
@@ -711,11 +713,11 @@ __device__ void st_zc2r(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
     if constexpr (Q) chain = quant_chain(D, B);
     const Geo& g = D.g;
     const int Nz = g.N[2], Hz = g.Hz, rows = g.N[0] * g.N[1], Ny = g.N[1], Nx = g.N[0];
-    const int pair0 = idx * kZPairs;
-    const int np = min(kZPairs, (rows + 1) / 2 - pair0);
+    const int pair0 = idx * D.zp;
+    const int np = min(D.zp, (rows + 1) / 2 - pair0);
     const int nlines = 3 * np;
     float2* a = reinterpret_cast<float2*>(smem);
-    float2* b = a + 3 * kZPairs * Nz;
+    float2* b = a + 3 * D.zp * Nz;
     const float2* srcs[3] = {B.cx1 + D.c0, B.cx2 + D.c0, B.cx0 + D.c0};
     const bool even = (Nz % 2) == 0;
     for (int line = threadIdx.x >> 5; line < nlines; line += kWarps) {
@@ -949,14 +951,14 @@ k_batched(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, int
 }
 
 template <int P, int TILE>
-size_t stage_smem(int maxN, int maxB) {
+size_t stage_smem(int maxN, int maxB, int maxZ) {
     size_t m = SpreadRed<P, TILE>::bytes();
     m = std::max(m, (size_t)kThreads * sizeof(int));
-    m = std::max(m, (size_t)(2 * kZPairs * maxN) * sizeof(float2));
+    m = std::max(m, (size_t)(2 * maxZ) * sizeof(float2));
     m = std::max(m, (size_t)(2 * maxN * maxB) * sizeof(float2));
     m = std::max(m, (size_t)(4 * maxN * maxB) * sizeof(float2) + kWarps * 14 * sizeof(float));
     m = std::max(m, (size_t)(6 * maxN * maxB) * sizeof(float2));
-    m = std::max(m, (size_t)(2 * 3 * kZPairs * maxN) * sizeof(float2));
+    m = std::max(m, (size_t)(6 * maxZ) * sizeof(float2));
     constexpr int E = TILE + P - 1, PZ = E | 1;
     m = std::max(m, (size_t)kGatherTiles * 3 * E * E * PZ * sizeof(float) +
                         (size_t)kWarps * 8 * (wstride(P) + 4) * sizeof(float) + 2 * kWarps * 8 * sizeof(int));
@@ -965,8 +967,8 @@ size_t stage_smem(int maxN, int maxB) {
 
 template <int P, int TILE, bool Q>
 cudaError_t launch(cudaStream_t s, const BoxDesc* boxes, const int2* items, int nitems, unsigned int* head, int* done,
-                   const Bufs& B, long long spin_limit, int maxN, int maxB, int* grid_out) {
-    const size_t smem = stage_smem<P, TILE>(maxN, maxB);
+                   const Bufs& B, long long spin_limit, int maxN, int maxB, int maxZ, int* grid_out) {
+    const size_t smem = stage_smem<P, TILE>(maxN, maxB, maxZ);
     cudaError_t e = cudaFuncSetAttribute(k_batched<P, TILE, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;
@@ -983,18 +985,18 @@ cudaError_t launch(cudaStream_t s, const BoxDesc* boxes, const int2* items, int 
 
 // Shared memory of one stage alone (the persistent kernel takes the largest).
 template <int P, int TILE>
-size_t stage_smem_of(int stage, int maxN, int maxB) {
+size_t stage_smem_of(int stage, int maxN, int maxB, int maxZ) {
     constexpr int E = TILE + P - 1, PZ = E | 1;
     size_t m = 0;
     switch (stage) {
         case S_BIN: case S_SCATTER: m = 16; break;
         case S_SCAN: m = (size_t)kThreads * sizeof(int); break;
         case S_SPREAD: m = SpreadRed<P, TILE>::bytes(); break;
-        case S_ZR2C: m = (size_t)(2 * kZPairs * maxN) * sizeof(float2); break;
+        case S_ZR2C: m = (size_t)(2 * maxZ) * sizeof(float2); break;
         case S_YFWD: m = (size_t)(2 * maxN * maxB) * sizeof(float2); break;
         case S_XINF: m = (size_t)(4 * maxN * maxB) * sizeof(float2) + kWarps * 14 * sizeof(float); break;
         case S_YINV: m = (size_t)(6 * maxN * maxB) * sizeof(float2); break;
-        case S_ZC2R: m = (size_t)(2 * 3 * kZPairs * maxN) * sizeof(float2); break;
+        case S_ZC2R: m = (size_t)(6 * maxZ) * sizeof(float2); break;
         case S_GATHER:
             m = (size_t)kGatherTiles * 3 * E * E * PZ * sizeof(float) +
                 (size_t)kWarps * 8 * (wstride(P) + 4) * sizeof(float) + 2 * kWarps * 8 * sizeof(int);
@@ -1035,9 +1037,9 @@ k_stage(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, Bufs 
 
 template <int P, int TILE, bool Q, int STAGE>
 cudaError_t launch_one_stage(cudaStream_t s, const BoxDesc* boxes, const int2* items, int start, int count,
-                             const Bufs& B, int maxN, int maxB) {
+                             const Bufs& B, int maxN, int maxB, int maxZ) {
     if (count == 0) return cudaSuccess;
-    const size_t smem = stage_smem_of<P, TILE>(STAGE, maxN, maxB);
+    const size_t smem = stage_smem_of<P, TILE>(STAGE, maxN, maxB, maxZ);
     auto kern = k_stage<P, TILE, Q, STAGE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1046,12 +1048,12 @@ cudaError_t launch_one_stage(cudaStream_t s, const BoxDesc* boxes, const int2* i
 
 template <int P, int TILE, bool Q>
 cudaError_t launch_staged(cudaStream_t s, const BoxDesc* boxes, const int2* items, const int* stage_start,
-                          const Bufs& B, int maxN, int maxB) {
+                          const Bufs& B, int maxN, int maxB, int maxZ) {
     PdlScope pdl(true);
     cudaError_t e = cudaSuccess;
 #define PPPM_STAGE(ST)                                                                                      \
     e = launch_one_stage<P, TILE, Q, ST>(s, boxes, items, stage_start[ST], stage_start[ST + 1] - stage_start[ST], \
-                                         B, maxN, maxB);                                                    \
+                                         B, maxN, maxB, maxZ);                                              \
     if (e != cudaSuccess) return e;
     PPPM_STAGE(S_BIN) PPPM_STAGE(S_SCAN) PPPM_STAGE(S_SCATTER) PPPM_STAGE(S_SPREAD) PPPM_STAGE(S_ZR2C)
     PPPM_STAGE(S_YFWD) PPPM_STAGE(S_XINF) PPPM_STAGE(S_YINV) PPPM_STAGE(S_ZC2R) PPPM_STAGE(S_GATHER)
@@ -1101,7 +1103,7 @@ struct pppm_batch {
         int ntile_total = 0, ntile_start_total = 0;
         long long patch_total = 0;
         int part_total = 0;
-        int maxN = 0, maxB = 0;
+        int maxN = 0, maxB = 0, maxZ = 0;
     };
     Layout lay[2];  // T = 4, 8
     std::vector<long long> offsets;  // the offsets the layouts were built for
@@ -1291,7 +1293,10 @@ int build_layout(pppm_batch* P, int li, int T) {
         D.nitems[S_SCATTER] = D.nitems[S_BIN];
         D.nitems[S_SPREAD] = (D.g.ntiles + kSpreadTiles - 1) / kSpreadTiles;
         const int npairs = (N[0] * N[1] + 1) / 2;
-        D.nitems[S_ZR2C] = (npairs + kZPairs - 1) / kZPairs;
+        // short z lines: more row pairs an item, so that an item holds ~kZRows points
+        D.zp = std::max(kZPairs, kZRows / N[2]);
+        Y.maxZ = std::max(Y.maxZ, D.zp * N[2]);
+        D.nitems[S_ZR2C] = (npairs + D.zp - 1) / D.zp;
         D.nitems[S_YFWD] = N[0] * D.bd.nb;
         D.nitems[S_XINF] = N[1] * D.bd.nb;
         D.nitems[S_YINV] = N[0] * D.bd.nb;
@@ -1411,9 +1416,10 @@ int enqueue(pppm_batch* P, cudaStream_t s, int li, const float* pos, const float
     const bool quant = P->quant_group > 0;
 #define BATCH_CASE(PP, TT, QQ)                                                                                   \
     if (P->order == PP && Y.T == TT && quant == QQ)                                                              \
-        e = P->staged ? launch_staged<PP, TT, QQ>(s, Y.d_desc, Y.d_items, Y.stage_start, B, Y.maxN, Y.maxB)     \
+        e = P->staged ? launch_staged<PP, TT, QQ>(s, Y.d_desc, Y.d_items, Y.stage_start, B, Y.maxN, Y.maxB,      \
+                                                  Y.maxZ)                                                          \
                       : launch<PP, TT, QQ>(s, Y.d_desc, Y.d_items, n, P->head, P->done, B, P->spin_limit, Y.maxN, \
-                                           Y.maxB, &P->last_grid);
+                                           Y.maxB, Y.maxZ, &P->last_grid);
     BATCH_CASE(3, 4, false) BATCH_CASE(3, 8, false) BATCH_CASE(5, 4, false) BATCH_CASE(5, 8, false)
     BATCH_CASE(7, 4, false) BATCH_CASE(7, 8, false)
     BATCH_CASE(5, 4, true) BATCH_CASE(5, 8, true)  // the quantised ablation: order 5 only
