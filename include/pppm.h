@@ -392,10 +392,16 @@ int pppm_set_wait_limit(pppm_plan *plan, long long spins);
  *                       (a feature pointer that is not 16-byte aligned runs
  *                       the mma.sync kernel).  Both take BF16 weights and
  *                       activations and accumulate in FP32; their results
- *                       agree to rounding (on the workloads, bitwise).  A tcgen05 completion not seen
- *                       within 2^26 polls sets PPPM_ERR_TIMEOUT in the coarse
- *                       plan's status word (pppm_status) and the launch ends
- *                       without writing the remaining rows.
+ *                       agree to rounding (on the workloads, bitwise).
+ * pppm_corr_set_wait_limit polls of the tcgen05 forward's wait for each MMA
+ *                       completion (default 2^26).  A wait that runs out
+ *                       sets PPPM_ERR_TIMEOUT in the coarse plan's status
+ *                       word (pppm_status); the CTA then waits once more
+ *                       (bounded) for the MMA in flight, frees its tensor
+ *                       memory and ends without writing its remaining rows.
+ *                       0 makes every first wait run out: a way to test the
+ *                       timeout path without any fault.  spins < 0:
+ *                       PPPM_ERR_INVALID_ARG.
  * pppm_corr_apply       corrected PPPM: coarse compute (energy, virial:
  *                       device doubles, uncorrected) and forces + q s_out y.
  * pppm_corr_grad        loss and its gradient w.r.t. the parameters over the
@@ -433,6 +439,7 @@ int pppm_corr_get_scales(const pppm_corr *corr, double *s_in, double *s_out);
 int pppm_corr_targets(pppm_corr *corr, void *stream, const float *f_fine, const float *f_coarse,
                       const float *q, int64_t n, float *target);
 int pppm_corr_set_forward(pppm_corr *corr, int kind);
+int pppm_corr_set_wait_limit(pppm_corr *corr, long long spins);
 int pppm_corr_forward(pppm_corr *corr, void *stream, const void *feat, int64_t n, float *out);
 int pppm_corr_apply(pppm_corr *corr, void *stream, const float *pos, const float *q,
                     const signed char *types, int64_t n, double *energy, float *forces,

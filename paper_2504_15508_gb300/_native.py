@@ -102,6 +102,7 @@ SIGNATURES = {
     "pppm_corr_get_scales": (cint, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
     "pppm_corr_targets": (cint, [vp, vp, vp, vp, vp, i64, vp]),
     "pppm_corr_set_forward": (cint, [vp, cint]),
+    "pppm_corr_set_wait_limit": (cint, [vp, ctypes.c_longlong]),
     "pppm_corr_forward": (cint, [vp, vp, vp, i64, vp]),
     "pppm_corr_apply": (cint, [vp, vp, vp, vp, vp, i64, vp, vp, vp]),
     "pppm_corr_grad": (cint, [vp, vp, vp, vp, i64, vp, i64, vp, vp]),

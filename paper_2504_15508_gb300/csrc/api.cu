@@ -769,7 +769,8 @@ int pppm_status(pppm_plan* P) {
     int st = 0;
     CK(cudaMemcpy(&st, P->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st) CK(cudaMemset(P->status, 0, sizeof(int)));
-    // bit 0: a non-finite site; bit 1: the gather's bounded tile-copy wait ran out
+    // bit 0: a non-finite site; bit 1: a bounded wait ran out (the gather's
+    // tile copy, or an MMA completion of the corrector's tcgen05 forward)
     if (st & 2) return PPPM_ERR_TIMEOUT;
     return st ? PPPM_ERR_NONFINITE : PPPM_OK;
 }

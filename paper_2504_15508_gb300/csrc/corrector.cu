@@ -343,7 +343,7 @@ constexpr int kRows = 128;             // sites per tile (MMA M)
 constexpr int kThreads = 256;          // warps w and w + 4 share TMEM lanes 32 (w mod 4) + 0..31
 constexpr uint32_t kTmemCols = 64;     // each layer's accumulators in columns 0..63 (outputs: 0..15)
 constexpr int kOutCol = 0, kOutN = 16;
-constexpr long long kSpin = 1ll << 26; // polls of an MMA completion before giving up
+constexpr long long kSpin = 1ll << 26; // polls of the second wait, after a first one ran out
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -457,7 +457,8 @@ template <int NIN>
 __global__ void __launch_bounds__(kThreads)
 k_mlp_forward_tc(const __nv_bfloat16* __restrict__ feat, int n, const __nv_bfloat16* __restrict__ wbf,
                  const float* __restrict__ master, float s_out, const float* __restrict__ q,
-                 float* __restrict__ forces, float* __restrict__ out, int* __restrict__ status) {
+                 float* __restrict__ forces, float* __restrict__ out, int* __restrict__ status,
+                 long long wait_limit) {
     typedef Net<NIN> L;
     typedef Smem<NIN> S;
     constexpr int K1P = L::K1P, BW1 = L::BW1, BW2 = L::BW2, BW3 = L::BW3;
@@ -518,7 +519,7 @@ k_mlp_forward_tc(const __nv_bfloat16* __restrict__ feat, int n, const __nv_bfloa
                     desc(base + b_off + 256 * k, 128, K / 8 * 128), id, k > 0);
             commit(mbar);
         }
-        const bool ok = wait_bounded(mbar, phase, kSpin);
+        const bool ok = wait_bounded(mbar, phase, wait_limit);
         failed = __syncthreads_or(!ok) != 0;
         if (!failed) phase ^= 1;
         fence_after();
@@ -843,6 +844,7 @@ struct pppm_corr {
     long long step = 0;
     double* ev = nullptr;  // scratch energy/virial of internal coarse evaluations
     int forward = PPPM_FORWARD_MMA_SYNC;  // network forward: mma.sync (faster at these widths) or tcgen05
+    long long wait_limit = 1ll << 26;     // polls of a tcgen05 MMA completion before giving up
 };
 
 namespace {
@@ -964,7 +966,7 @@ int mlp_forward(pppm_corr* C, cudaStream_t s, const __nv_bfloat16* feat, int64_t
             const int64_t ntile = (n + tc::kRows - 1) / tc::kRows;
             const int blocks = (int)std::min<int64_t>(ntile, (int64_t)std::max(per_sm, 1) * nsm);
             kern<<<blocks, tc::kThreads, smem, s>>>(feat, (int)n, C->wbf, C->master, C->s_out, q, forces, out,
-                                                     C->plan->status);
+                                                     C->plan->status, C->wait_limit);
             return cudaGetLastError();
         });
         CC(e);
@@ -1170,6 +1172,12 @@ int pppm_corr_get_scales(const pppm_corr* C, double* s_in, double* s_out) {
     if (!C || !s_in || !s_out) return PPPM_ERR_INVALID_ARG;
     *s_in = C->s_in;
     *s_out = C->s_out;
+    return PPPM_OK;
+}
+
+int pppm_corr_set_wait_limit(pppm_corr* C, long long spins) {
+    if (!C || spins < 0) return PPPM_ERR_INVALID_ARG;
+    C->wait_limit = spins;
     return PPPM_OK;
 }
 

@@ -409,6 +409,11 @@ class Corrector:
         N.check(self._lib.pppm_corr_set_forward(self._h, k), "pppm_corr_set_forward")
         self.forward_kind = kind
 
+    def set_wait_limit(self, spins: int):
+        """Polls of the tcgen05 forward's wait for each MMA completion (0: every
+        first wait runs out, to test the timeout path)."""
+        N.check(self._lib.pppm_corr_set_wait_limit(self._h, int(spins)), "pppm_corr_set_wait_limit")
+
     # ------------------------------------------------------------ parameters
     def set_weights(self, params, s_in: float, s_out: float):
         p = np.ascontiguousarray(params, dtype=np.float32).ravel()

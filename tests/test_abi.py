@@ -130,3 +130,9 @@ def test_corrector_feature_sets_validate_arguments(pppm_lib):
 
 def test_batch_set_launch_validates(pppm_lib):
     assert pppm_lib.pppm_batch_set_launch(None, N.PPPM_BATCH_STAGED) == N.PPPM_ERR_INVALID_ARG
+
+
+def test_corrector_forward_options_validate_arguments(pppm_lib):
+    assert pppm_lib.pppm_corr_set_forward(None, N.PPPM_FORWARD_TCGEN05) == N.PPPM_ERR_INVALID_ARG
+    assert pppm_lib.pppm_corr_set_wait_limit(None, 10) == N.PPPM_ERR_INVALID_ARG
+    assert pppm_lib.pppm_corr_forward(None, None, None, 1, None) == N.PPPM_ERR_INVALID_ARG

@@ -187,6 +187,34 @@ def test_forward_kernels_agree(cuda_device, kind):
     assert P.status() == 0
 
 
+def test_tcgen05_forward_wait_times_out_cleanly(cuda_device):
+    """A completion wait limited to zero polls runs out in every CTA: the plan's
+    status reports PPPM_ERR_TIMEOUT, and the next call with the normal limit
+    (tensor memory freed, nothing left in flight) is correct."""
+    from paper_2504_15508_gb300 import _native as N
+    Plan, Corrector, _ = _mods()
+    w = make_water(4096, 49.7, 2)
+    P = Plan((49.7,) * 3, (24,) * 3, order=5, beta=0.4)
+    corr = Corrector(P, params=_theta(7), s_in=0.5, s_out=1.0)
+    pos, q, types = _sites(w)
+    feat, _ = corr.features(pos, q, types)
+    corr.set_forward("mma_sync")
+    y_ref = corr.forward(feat)
+    corr.set_forward("tcgen05")
+    corr.set_wait_limit(0)
+    corr.forward(feat)
+    torch.cuda.synchronize()
+    assert P.status() == N.PPPM_ERR_TIMEOUT
+    assert P.status() == 0  # read and cleared
+    corr.set_wait_limit(1 << 26)
+    y = corr.forward(feat)
+    torch.cuda.synchronize()
+    assert P.status() == 0
+    assert torch.equal(y, y_ref)
+    with pytest.raises(RuntimeError):
+        corr.set_wait_limit(-1)
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_apply_is_coarse_plus_correction(cuda_device, kind):
     Plan, Corrector, _ = _mods()
