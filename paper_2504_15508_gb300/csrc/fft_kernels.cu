@@ -17,8 +17,8 @@
 // Twiddles come from a table of e^{-2 pi i t / L} built on the device in FP64
 // with sincospi and rounded to the mesh precision.
 //
-// Two FFT engines drive the same kernels: CtEngine<L> for the FP32 mesh sizes
-// the workloads use (every index and radix is a compile-time constant), and
+// Two FFT engines drive the same kernels: CtEngine<L> for the common FP32 mesh
+// lengths (32 to 256: every index and radix is a compile-time constant), and
 // GenEngine for any other 2^a 3^b 5^c length and for FP64 (radix plan read at
 // run time).
 #include <type_traits>
@@ -210,9 +210,20 @@ cudaError_t with_engine(const Radix& r, const typename Cx<T>::t* tw, F&& f) {
     if constexpr (std::is_same<T, float>::value) {
         switch (r.L) {
             case 32: return f(CtEngine<float, 32>{tw});
+            case 48: return f(CtEngine<float, 48>{tw});
             case 64: return f(CtEngine<float, 64>{tw});
+            case 72: return f(CtEngine<float, 72>{tw});
+            case 80: return f(CtEngine<float, 80>{tw});
+            case 90: return f(CtEngine<float, 90>{tw});
+            case 96: return f(CtEngine<float, 96>{tw});
+            case 100: return f(CtEngine<float, 100>{tw});
+            case 108: return f(CtEngine<float, 108>{tw});
+            case 120: return f(CtEngine<float, 120>{tw});
             case 128: return f(CtEngine<float, 128>{tw});
+            case 144: return f(CtEngine<float, 144>{tw});
             case 160: return f(CtEngine<float, 160>{tw});
+            case 192: return f(CtEngine<float, 192>{tw});
+            case 256: return f(CtEngine<float, 256>{tw});
             default: break;
         }
     }
@@ -442,11 +453,12 @@ k_fft_x_influence(Geo g, LineBlocks lb, Eng eng, const R* __restrict__ G, R beta
     C* b0 = a1 + Nx * B;
     C* base = S + f0;
     BUNDLE_LOOP(t, l, Nx, nl) a0[t * B + l] = base[t * es + l];
-    // with a compile-time length, each thread's G values are fetched now so
-    // that their latency hides behind the forward FFT
-    constexpr int NG = Eng::kLen > 0 ? Eng::kLen / (kFftThreads / 16) : 1;
+    // with a compile-time length of whole 16-row passes, each thread's G values
+    // are fetched now so that their latency hides behind the forward FFT
+    constexpr bool kPre = Eng::kLen > 0 && Eng::kLen % (kFftThreads / 16) == 0;
+    constexpr int NG = kPre ? Eng::kLen / (kFftThreads / 16) : 1;
     R gpre[NG];
-    if constexpr (Eng::kLen > 0) {
+    if constexpr (kPre) {
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
             const int t = (threadIdx.x >> 4) + i * (kFftThreads / 16);
@@ -494,8 +506,7 @@ k_fft_x_influence(Geo g, LineBlocks lb, Eng eng, const R* __restrict__ G, R beta
         b0[t * B + lt] = CT<R>::mk(kxd * P.y, -kxd * P.x);  // -i kx' P
     };
     if (lt < nl) {
-        if constexpr (Eng::kLen > 0) {
-            static_assert(Eng::kLen % (kFftThreads / 16) == 0, "a thread's modes are the prefetched ones");
+        if constexpr (kPre) {
 #pragma unroll
             for (int i = 0; i < NG; ++i) mode((threadIdx.x >> 4) + i * (kFftThreads / 16), gpre[i]);
         } else {

@@ -76,7 +76,8 @@ def test_influence_table(cuda_device, pppm_lib, mesh):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("mesh", [(32, 32, 32), (30, 36, 40), (27, 25, 45), (12, 15, 16), (160, 8, 6),
-                                  (64, 128, 32), (128, 160, 64)])
+                                  (64, 128, 32), (128, 160, 64), (72, 96, 120), (48, 80, 90),
+                                  (100, 108, 144), (192, 48, 256)])
 def test_fft_r2c_c2r(cuda_device, pppm_lib, prec, mesh):
     plan = _plan((10.0, 11.0, 12.0), mesh, 5, 0.4, precision=prec)
     rng = np.random.default_rng(sum(mesh))
@@ -136,6 +137,17 @@ def test_water4096(cuda_device, pppm_lib, prec):
     plan = _plan(wb.box, w["mesh"], w["order"], w["beta"], precision=prec)
     ref = OraclePPPM(wb.box, w["mesh"], w["order"], w["beta"]).compute(pos_r, q_r)
     _check(plan.compute(tp, tq), ref, prec, "water4096")
+
+
+@pytest.mark.parametrize("mesh", [(72, 72, 72), (96, 90, 80), (120, 108, 100), (48, 144, 64)])
+def test_water4096_fp32_meshes(cuda_device, pppm_lib, mesh):
+    """The 4,096-water box on meshes whose lengths run the other compile-time
+    FFT engines (and 64 beside them), FP32 against the FP64 oracle."""
+    wb, w = make_workload("water4096")
+    tp, tq, pos_r, q_r = _sites(wb.pos, wb.q, "fp32", cuda_device)
+    plan = _plan(wb.box, mesh, w["order"], w["beta"], precision="fp32")
+    ref = OraclePPPM(wb.box, mesh, w["order"], w["beta"]).compute(pos_r, q_r)
+    _check(plan.compute(tp, tq), ref, "fp32", f"water4096 {mesh}")
 
 
 @pytest.mark.parametrize("mesh", [128, 160])
