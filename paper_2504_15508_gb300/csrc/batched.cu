@@ -409,7 +409,7 @@ __device__ void st_zr2c_quant(const BoxDesc& D, int idx, const Bufs& B, unsigned
     }
 }
 
-template <bool Q>
+template <bool Q, bool CT>
 __device__ void st_zr2c(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
     if constexpr (Q)
         if (qg(D, B, 2) > 0) return st_zr2c_quant(D, idx, B, smem);
@@ -433,7 +433,7 @@ __device__ void st_zr2c(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
             a[p * Nz + t] = make_float2(fold_point_b(D, B, cx0, cy0, t), fold_point_b(D, B, cx1, cy1, t));
     }
     __syncthreads();
-    float2* res = line_transform<Q>(a, b, np, Nz, 1, D.rad[2], B.tw + D.tw0[2], -1.f, false, B.dft_max, qg(D, B, 2), B.qscale, B.status);
+    float2* res = line_transform_t<Q, CT, -1, false>(a, b, np, Nz, 1, D.rad[2], B.tw + D.tw0[2], B.dft_max, qg(D, B, 2), B.qscale, B.status);
     float2* out = B.cx0 + D.c0;
     for (int p = threadIdx.x >> 5; p < np; p += kWarps) {
         const int r0 = 2 * (pair0 + p), r1 = r0 + 1;
@@ -448,7 +448,7 @@ __device__ void st_zr2c(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
 }
 
 // lines along y of the complex spectrum (outer index x), in place
-template <bool Q>
+template <bool Q, bool CT>
 __device__ void st_yfwd(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
     const Geo& g = D.g;
     const int Hz = g.Hz, L = g.N[1], Bw = D.bd.B;
@@ -462,7 +462,7 @@ __device__ void st_yfwd(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
         a[t * Bw + l] = ldcg(&base[(long long)t * Hz + l]);
     }
     __syncthreads();
-    float2* res = line_transform<Q>(a, b, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], -1.f, true, B.dft_max, qg(D, B, 1), B.qscale, B.status);
+    float2* res = line_transform_t<Q, CT, -1, true>(a, b, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], B.dft_max, qg(D, B, 1), B.qscale, B.status);
     for (int i = threadIdx.x; i < L * nl; i += kThreads) {
         const int t = i / nl, l = i - t * nl;
         base[(long long)t * Hz + l] = res[t * Bw + l];
@@ -478,7 +478,7 @@ __device__ __forceinline__ void tsum_pair(float& h, float& l, float h2, float l2
 
 // x FFT, influence multiply with energy/virial, inverse x FFTs; the last item
 // of a box sums that box's partials (compensated FP32, FP64 final)
-template <bool Q>
+template <bool Q, bool CT>
 __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsigned char* smem) {
     const Geo& g = D.g;
     const int Nx = g.N[0], Ny = g.N[1], Nz = g.N[2], Hz = g.Hz, Bw = D.bd.B;
@@ -496,7 +496,7 @@ __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsig
         a0[t * Bw + l] = ldcg(&base[t * es + l]);
     }
     __syncthreads();
-    float2* rh = line_transform<Q>(a0, a1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], -1.f, true, B.dft_max, qg(D, B, 0), B.qscale, B.status);
+    float2* rh = line_transform_t<Q, CT, -1, true>(a0, a1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], B.dft_max, qg(D, B, 0), B.qscale, B.status);
     float2* pbuf = (rh == a0) ? a1 : a0;
     const int my = y <= Ny / 2 ? y : y - Ny;
     const float ky = g.kfac_f[1] * my;
@@ -550,7 +550,7 @@ __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsig
                 }
                 __syncthreads();
             }
-            const float2* r = line_transform<Q>(b0, b1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max,
+            const float2* r = line_transform_t<Q, CT, 1, true>(b0, b1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], B.dft_max,
                                                 qg(D, B, 0), B.qscale, B.status);
             float2* o = d == 0 ? obx : (d == 1 ? oby : base);
             for (int i = threadIdx.x; i < Nx * nl; i += kThreads) {
@@ -560,8 +560,8 @@ __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsig
             __syncthreads();
         }
     } else {
-        float2* rA = line_transform<Q>(pbuf, rh, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max, qg(D, B, 0), B.qscale, B.status);
-        float2* rB = line_transform<Q>(b0, b1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], 1.f, true, B.dft_max, qg(D, B, 0), B.qscale, B.status);
+        float2* rA = line_transform_t<Q, CT, 1, true>(pbuf, rh, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], B.dft_max, qg(D, B, 0), B.qscale, B.status);
+        float2* rB = line_transform_t<Q, CT, 1, true>(b0, b1, nl, 1, Bw, D.rad[0], B.tw + D.tw0[0], B.dft_max, qg(D, B, 0), B.qscale, B.status);
         float2* obx = B.cx1 + D.c0 + (long long)y * Hz + kz0;
         for (int i = threadIdx.x; i < Nx * nl; i += kThreads) {
             const int t = i / nl, l = i - t * nl;
@@ -609,7 +609,7 @@ __device__ void st_xinf(const BoxDesc& D, int box, int idx, const Bufs& B, unsig
     }
 }
 
-template <bool Q>
+template <bool Q, bool CT>
 __device__ void st_yinv(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
     const Geo& g = D.g;
     const int Ny = g.N[1], Hz = g.Hz, Bw = D.bd.B;
@@ -631,9 +631,9 @@ __device__ void st_yinv(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
         buf[4 * sz + t * Bw + l] = ldcg(&B.cx1[off + (long long)t * Hz + l]);
     }
     __syncthreads();
-    float2* rC = line_transform<Q>(buf, buf + sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max, qg(D, B, 1), B.qscale, B.status);
-    float2* rD = line_transform<Q>(buf + 2 * sz, buf + 3 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max, qg(D, B, 1), B.qscale, B.status);
-    float2* rE = line_transform<Q>(buf + 4 * sz, buf + 5 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], 1.f, true, B.dft_max, qg(D, B, 1), B.qscale, B.status);
+    float2* rC = line_transform_t<Q, CT, 1, true>(buf, buf + sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], B.dft_max, qg(D, B, 1), B.qscale, B.status);
+    float2* rD = line_transform_t<Q, CT, 1, true>(buf + 2 * sz, buf + 3 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], B.dft_max, qg(D, B, 1), B.qscale, B.status);
+    float2* rE = line_transform_t<Q, CT, 1, true>(buf + 4 * sz, buf + 5 * sz, nl, 1, Bw, D.rad[1], B.tw + D.tw0[1], B.dft_max, qg(D, B, 1), B.qscale, B.status);
     for (int i = threadIdx.x; i < Ny * nl; i += kThreads) {
         const int t = i / nl, l = i - t * nl;
         B.cx0[off + (long long)t * Hz + l] = rC[t * Bw + l];
@@ -705,7 +705,7 @@ __device__ void st_zc2r_quant(const BoxDesc& D, int idx, const Bufs& B, unsigned
     }
 }
 
-template <bool Q>
+template <bool Q, bool CT>
 __device__ void st_zc2r(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
     if constexpr (Q)
         if (qg(D, B, 2) > 0) return st_zc2r_quant(D, idx, B, smem);
@@ -739,7 +739,7 @@ __device__ void st_zc2r(const BoxDesc& D, int idx, const Bufs& B, unsigned char*
         }
     }
     __syncthreads();
-    float2* res = line_transform<Q>(a, b, nlines, Nz, 1, D.rad[2], B.tw + D.tw0[2], 1.f, false, B.dft_max, qg(D, B, 2), B.qscale, B.status);
+    float2* res = line_transform_t<Q, CT, 1, false>(a, b, nlines, Nz, 1, D.rad[2], B.tw + D.tw0[2], B.dft_max, qg(D, B, 2), B.qscale, B.status);
     const FieldLayout& fl = D.fl;
     const int kmin = g.kmin, zlen = Nz + g.order - 1;
     for (int line = threadIdx.x >> 5; line < nlines; line += kWarps) {
@@ -934,11 +934,11 @@ k_batched(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, int
                 case S_SCAN: st_scan(sbox, B, reinterpret_cast<int*>(smem)); break;
                 case S_SCATTER: st_scatter<P>(sbox, idx, B); break;
                 case S_SPREAD: st_spread<P, TILE>(sbox, idx, B, smem); break;
-                case S_ZR2C: st_zr2c<Q>(sbox, idx, B, smem); break;
-                case S_YFWD: st_yfwd<Q>(sbox, idx, B, smem); break;
-                case S_XINF: st_xinf<Q>(sbox, box, idx, B, smem); break;
-                case S_YINV: st_yinv<Q>(sbox, idx, B, smem); break;
-                case S_ZC2R: st_zc2r<Q>(sbox, idx, B, smem); break;
+                case S_ZR2C: st_zr2c<Q, false>(sbox, idx, B, smem); break;
+                case S_YFWD: st_yfwd<Q, false>(sbox, idx, B, smem); break;
+                case S_XINF: st_xinf<Q, false>(sbox, box, idx, B, smem); break;
+                case S_YINV: st_yinv<Q, false>(sbox, idx, B, smem); break;
+                case S_ZC2R: st_zc2r<Q, false>(sbox, idx, B, smem); break;
                 case S_GATHER: st_gather<P, TILE>(sbox, idx, B, smem); break;
             }
         }
@@ -1010,7 +1010,7 @@ size_t stage_smem_of(int stage, int maxN, int maxB, int maxZ) {
 // list); stream order replaces the persistent kernel's waits, and each stage
 // gets its own register and shared-memory budget.
 template <int P, int TILE, bool Q, int STAGE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)  // four resident blocks an SM: 64 registers
 k_stage(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, Bufs B) {
     pdl_enter();
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1027,11 +1027,11 @@ k_stage(const BoxDesc* __restrict__ boxes, const int2* __restrict__ items, Bufs 
     if constexpr (STAGE == S_SCAN) st_scan(sbox, B, reinterpret_cast<int*>(smem));
     if constexpr (STAGE == S_SCATTER) st_scatter<P>(sbox, idx, B);
     if constexpr (STAGE == S_SPREAD) st_spread<P, TILE>(sbox, idx, B, smem);
-    if constexpr (STAGE == S_ZR2C) st_zr2c<Q>(sbox, idx, B, smem);
-    if constexpr (STAGE == S_YFWD) st_yfwd<Q>(sbox, idx, B, smem);
-    if constexpr (STAGE == S_XINF) st_xinf<Q>(sbox, box, idx, B, smem);
-    if constexpr (STAGE == S_YINV) st_yinv<Q>(sbox, idx, B, smem);
-    if constexpr (STAGE == S_ZC2R) st_zc2r<Q>(sbox, idx, B, smem);
+    if constexpr (STAGE == S_ZR2C) st_zr2c<Q, !Q>(sbox, idx, B, smem);
+    if constexpr (STAGE == S_YFWD) st_yfwd<Q, !Q>(sbox, idx, B, smem);
+    if constexpr (STAGE == S_XINF) st_xinf<Q, !Q>(sbox, box, idx, B, smem);
+    if constexpr (STAGE == S_YINV) st_yinv<Q, !Q>(sbox, idx, B, smem);
+    if constexpr (STAGE == S_ZC2R) st_zc2r<Q, !Q>(sbox, idx, B, smem);
     if constexpr (STAGE == S_GATHER) st_gather<P, TILE>(sbox, idx, B, smem);
 }
 
@@ -1055,8 +1055,15 @@ cudaError_t launch_staged(cudaStream_t s, const BoxDesc* boxes, const int2* item
     e = launch_one_stage<P, TILE, Q, ST>(s, boxes, items, stage_start[ST], stage_start[ST + 1] - stage_start[ST], \
                                          B, maxN, maxB, maxZ);                                              \
     if (e != cudaSuccess) return e;
-    PPPM_STAGE(S_BIN) PPPM_STAGE(S_SCAN) PPPM_STAGE(S_SCATTER) PPPM_STAGE(S_SPREAD) PPPM_STAGE(S_ZR2C)
-    PPPM_STAGE(S_YFWD) PPPM_STAGE(S_XINF) PPPM_STAGE(S_YINV) PPPM_STAGE(S_ZC2R) PPPM_STAGE(S_GATHER)
+    // the FFT stages do not depend on the order or the tile edge: one
+    // instantiation of each serves every batch
+#define PPPM_FFT_STAGE(ST)                                                                                  \
+    e = launch_one_stage<5, 8, Q, ST>(s, boxes, items, stage_start[ST], stage_start[ST + 1] - stage_start[ST], \
+                                      B, maxN, maxB, maxZ);                                                 \
+    if (e != cudaSuccess) return e;
+    PPPM_STAGE(S_BIN) PPPM_STAGE(S_SCAN) PPPM_STAGE(S_SCATTER) PPPM_STAGE(S_SPREAD) PPPM_FFT_STAGE(S_ZR2C)
+    PPPM_FFT_STAGE(S_YFWD) PPPM_FFT_STAGE(S_XINF) PPPM_FFT_STAGE(S_YINV) PPPM_FFT_STAGE(S_ZC2R) PPPM_STAGE(S_GATHER)
+#undef PPPM_FFT_STAGE
 #undef PPPM_STAGE
     return e;
 }

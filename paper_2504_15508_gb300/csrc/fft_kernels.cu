@@ -28,157 +28,6 @@
 
 namespace pppm {
 
-constexpr int kFftThreads = 256;
-
-// ------------------------------------------------------------------ compile-time radix plan
-// Radices 16, 10 and 8 are DFTs in registers (below), so the workload lengths
-// take two Stockham stages: 128 = 16 x 8, 160 = 16 x 10, 64 = 16 x 4, 32 = 16 x 2.
-constexpr int fft_radix(int L, int s) {
-    int m = L, i = 0;
-    const int fs[7] = {16, 10, 8, 4, 2, 3, 5};
-    for (int q = 0; q < 7; ++q)
-        while (m % fs[q] == 0) {
-            if (i == s) return fs[q];
-            m /= fs[q];
-            ++i;
-        }
-    return 1;
-}
-constexpr int fft_nstages(int L) {
-    int n = 0;
-    while (fft_radix(L, n) != 1) ++n;
-    return n;
-}
-constexpr int fft_ns(int L, int s) {
-    int ns = 1;
-    for (int i = 0; i < s; ++i) ns *= fft_radix(L, i);
-    return ns;
-}
-
-// cos and sin of 2 pi m / N for the twiddles inside the register DFTs
-// (N = 8, 10, 16; closed forms of the regular 8-, 10- and 16-gon)
-template <int N>
-__device__ __forceinline__ constexpr double unit_cos(int m) {
-    constexpr double r = 0.70710678118654752440, c8 = 0.92387953251128675613, s8 = 0.38268343236508977173;
-    constexpr double c5 = 0.80901699437494742410, c25 = 0.30901699437494742410;
-    if (N == 16) {
-        const double t[16] = {1, c8, r, s8, 0, -s8, -r, -c8, -1, -c8, -r, -s8, 0, s8, r, c8};
-        return t[m & 15];
-    } else if (N == 8) {
-        const double t[8] = {1, r, 0, -r, -1, -r, 0, r};
-        return t[m & 7];
-    } else {
-        const double t[10] = {1, c5, c25, -c25, -c5, -1, -c5, -c25, c25, c5};
-        return t[m % 10];
-    }
-}
-template <int N>
-__device__ __forceinline__ constexpr double unit_sin(int m) {
-    constexpr double r = 0.70710678118654752440, c8 = 0.92387953251128675613, s8 = 0.38268343236508977173;
-    constexpr double s5 = 0.58778525229247312917, s25 = 0.95105651629515357212;
-    if (N == 16) {
-        const double t[16] = {0, s8, r, c8, 1, c8, r, s8, 0, -s8, -r, -c8, -1, -c8, -r, -s8};
-        return t[m & 15];
-    } else if (N == 8) {
-        const double t[8] = {0, r, 1, r, 0, -r, -1, -r};
-        return t[m & 7];
-    } else {
-        const double t[10] = {0, s5, s25, s25, s5, 0, -s5, -s25, -s25, -s5};
-        return t[m % 10];
-    }
-}
-
-// DFT of N = A B points in registers, X[k] = sum_n x[n] e^{SIGN 2 pi i n k / N}:
-// with n = B n1 + n2 and k = k1 + A k2, a size-A DFT over n1 for each n2, the
-// twiddle e^{SIGN 2 pi i n2 k1 / N}, then a size-B DFT over n2 for each k1.
-template <typename C, typename R, int A, int B, int SIGN>
-__device__ __forceinline__ void dft_ab(C* v) {
-    constexpr int N = A * B;
-    C t[B][A];
-#pragma unroll
-    for (int n2 = 0; n2 < B; ++n2) {
-#pragma unroll
-        for (int n1 = 0; n1 < A; ++n1) t[n2][n1] = v[B * n1 + n2];
-        butterfly<C, R>(t[n2], A, R(SIGN));
-#pragma unroll
-        for (int k1 = 1; k1 < A; ++k1)
-            if (n2 > 0) {
-                const C w = CT<R>::mk(R(unit_cos<N>(n2 * k1)), R(SIGN) * R(unit_sin<N>(n2 * k1)));
-                t[n2][k1] = cmul(t[n2][k1], w);
-            }
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < A; ++k1) {
-        C u[B];
-#pragma unroll
-        for (int n2 = 0; n2 < B; ++n2) u[n2] = t[n2][k1];
-        butterfly<C, R>(u, B, R(SIGN));
-#pragma unroll
-        for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = u[k2];
-    }
-}
-
-template <typename C, typename R, int RDX, int SIGN>
-__device__ __forceinline__ void bfly(C* v) {
-    if constexpr (RDX == 16) dft_ab<C, R, 4, 4, SIGN>(v);
-    else if constexpr (RDX == 10) dft_ab<C, R, 5, 2, SIGN>(v);
-    else if constexpr (RDX == 8) dft_ab<C, R, 4, 2, SIGN>(v);
-    else butterfly<C, R>(v, RDX, R(SIGN));
-}
-
-// One Stockham stage with every size a constant.  Thread mapping: line-fast
-// (bundles, lines adjacent in shared memory) uses 16 lanes per line index and
-// the other threads along the butterflies; otherwise consecutive threads walk
-// the butterflies of a line and then the lines.
-template <typename R, int L, int S, int SIGN, bool LF>
-__device__ __forceinline__ void ct_stage(const typename CT<R>::C* __restrict__ src, typename CT<R>::C* __restrict__ dst,
-                                         int nl, int ls, int ps, const typename CT<R>::C* __restrict__ tw) {
-    typedef typename CT<R>::C C;
-    constexpr int RDX = fft_radix(L, S);
-    constexpr int NS = fft_ns(L, S);
-    constexpr int NBF = L / RDX;
-    constexpr int TSTEP = L / (NS * RDX);
-    auto one = [&](int line, int j) {
-        const int k = j % NS;
-        const C* sp = src + line * ls;
-        C* dp = dst + line * ls;
-        C v[RDX];
-#pragma unroll
-        for (int r = 0; r < RDX; ++r) v[r] = sp[(j + r * NBF) * ps];
-        if (NS > 1) {
-#pragma unroll
-            for (int r = 1; r < RDX; ++r) {
-                C w = __ldg(&tw[k * r * TSTEP]);
-                if (SIGN > 0) w.y = -w.y;
-                v[r] = cmul(v[r], w);
-            }
-        }
-        bfly<C, R, RDX, SIGN>(v);
-        const int d0 = (j / NS) * NS * RDX + k;
-#pragma unroll
-        for (int r = 0; r < RDX; ++r) dp[(d0 + r * NS) * ps] = v[r];
-    };
-    if (LF) {
-        const int tl = threadIdx.x & 15, tj = threadIdx.x >> 4;
-        for (int line = tl; line < nl; line += 16)
-            for (int j = tj; j < NBF; j += kFftThreads >> 4) one(line, j);
-    } else {
-        for (int it = threadIdx.x; it < nl * NBF; it += kFftThreads) one(it / NBF, it % NBF);
-    }
-}
-
-template <typename R, int L, int SIGN, bool LF, int S>
-__device__ __forceinline__ typename CT<R>::C* ct_fft(typename CT<R>::C* a, typename CT<R>::C* b, int nl, int ls,
-                                                     int ps, const typename CT<R>::C* __restrict__ tw) {
-    if constexpr (S == fft_nstages(L)) {
-        return a;
-    } else {
-        ct_stage<R, L, S, SIGN, LF>(a, b, nl, ls, ps, tw);
-        __syncthreads();
-        return ct_fft<R, L, SIGN, LF, S + 1>(b, a, nl, ls, ps, tw);
-    }
-}
-
 template <typename R, int L>
 struct CtEngine {
     typedef typename CT<R>::C C;
