@@ -203,33 +203,55 @@ __device__ void st_scan(const BoxDesc& D, const Bufs& B, int* sh) {
     if (tid == kThreads - 1) B.tile_start[D.ts0 + nt] = sh[kThreads - 1];
 }
 
+// Scatter: a thread's kSiteChunk / kThreads sites, their independent loads
+// (tile, slot, record, cell) issued together before any store, then each
+// site's weight row written as 16-byte vectors.
 template <int P>
 __device__ void st_scatter(const BoxDesc& D, int idx, const Bufs& B) {
     constexpr int WS = wstride(P);
-    for (int k = 0; k < kSiteChunk / kThreads; ++k) {
+    constexpr int KS = kSiteChunk / kThreads;
+    int tt[KS], sl[KS], cl[KS];
+    float4 rr[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+        const int i = idx * kSiteChunk + k * kThreads + threadIdx.x;
+        if (i < D.nsite) {
+            const long long gi = D.site0 + i;
+            tt[k] = ldcg(&B.tile_of[gi]);
+            sl[k] = ldcg(&B.slot_of[gi]);
+            cl[k] = ldcg(&B.cell[gi]);
+            rr[k] = __ldcg(reinterpret_cast<const float4*>(&B.rec[gi]));
+        }
+    }
+    int st[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+        const int i = idx * kSiteChunk + k * kThreads + threadIdx.x;
+        if (i < D.nsite) st[k] = ldcg(&B.tile_start[D.ts0 + tt[k]]);
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
         const int i = idx * kSiteChunk + k * kThreads + threadIdx.x;
         if (i >= D.nsite) continue;
-        const long long gi = D.site0 + i;
-        const int t = ldcg(&B.tile_of[gi]);
-        const long long dst = D.site0 + ldcg(&B.tile_start[D.ts0 + t]) + ldcg(&B.slot_of[gi]);
-        Rec<float> r;
-        r.x0[0] = ldcg(&B.rec[gi].x0[0]);
-        r.x0[1] = ldcg(&B.rec[gi].x0[1]);
-        r.x0[2] = ldcg(&B.rec[gi].x0[2]);
-        r.q = ldcg(&B.rec[gi].q);
-        B.scell[dst] = ldcg(&B.cell[gi]);
+        const long long dst = D.site0 + st[k] + sl[k];
+        B.scell[dst] = cl[k];
         B.sorig[dst] = i;
-        float w[P];
-        float* o = B.swt + dst * WS;
-        bspline_all<P>(r.x0[0], w);
+        float w[WS];
+        float t[P];
+        bspline_all<P>(rr[k].x, t);
 #pragma unroll
-        for (int a = 0; a < P; ++a) o[a] = w[a] * r.q;
-        bspline_all<P>(r.x0[1], w);
+        for (int a = 0; a < P; ++a) w[a] = t[a] * rr[k].w;
+        bspline_all<P>(rr[k].y, t);
 #pragma unroll
-        for (int a = 0; a < P; ++a) o[P + a] = w[a];
-        bspline_all<P>(r.x0[2], w);
+        for (int a = 0; a < P; ++a) w[P + a] = t[a];
+        bspline_all<P>(rr[k].z, t);
 #pragma unroll
-        for (int a = 0; a < P; ++a) o[2 * P + a] = w[a];
+        for (int a = 0; a < P; ++a) w[2 * P + a] = t[a];
+#pragma unroll
+        for (int a = 3 * P; a < WS; ++a) w[a] = 0.f;
+        float4* o = reinterpret_cast<float4*>(B.swt + dst * WS);
+#pragma unroll
+        for (int a = 0; a < WS / 4; ++a) o[a] = make_float4(w[4 * a], w[4 * a + 1], w[4 * a + 2], w[4 * a + 3]);
     }
 }
 
