@@ -142,11 +142,14 @@ def test_batched_bounded_wait_times_out_cleanly(cuda_device, pppm_lib):
 @pytest.mark.parametrize("order,meshes", [
     (3, [(12, 15, 16), (16, 16, 16), (12, 16, 20), (16, 16, 16)]),
     (7, [(15, 16, 18), (16, 16, 16), (15, 16, 20), (16, 16, 16)]),
+    (5, [(18, 75, 24), (16, 16, 16), (81, 20, 25), (16, 16, 16)]),
 ])
 def test_batched_orders_rectangular_empty_and_single_site(cuda_device, pppm_lib, order, meshes):
-    """Orders 3 and 7; in one launch a water box, a box without sites, a
+    """Orders 3, 7 and 5; in one launch a water box, a box without sites, a
     rectangular box of random neutral charges on a mixed mesh and a box with
-    one charge.  Every box equals the oracle; the empty one gives zeros."""
+    one charge.  Every box equals the oracle; the empty one gives zeros.  The
+    order-5 case mixes line lengths with compile-time FFT engines (16-25) and
+    lengths without (75, 81), which take the run-time FFT in the same launch."""
     from paper_2504_15508_gb300.pppm import BatchPlan
     rng = np.random.default_rng(order)
     water = make_water(128, 15.64, 3)
