@@ -86,8 +86,9 @@ int pppm_default_options(pppm_options *opt);
  *   mesh[3]   mesh points per edge, each 2^a 3^b 5^c, >= order, <= 2048
  *   order     B-spline assignment order p in [2, 7] (p^3 stencil points)
  *   beta      splitting parameter of Eq. DPLR:EGt (inverse Angstrom), > 0
- *   precision PPPM_FP32 (spread/FFT/gather in FP32, compensated FP32 energy and
- *             virial partials with an FP64 final sum) or PPPM_FP64
+ *   precision PPPM_FP32 (spread/FFT/gather in FP32; energy and virial terms
+ *             summed per thread in FP32, the partials combined with
+ *             compensated FP32 pairs and an FP64 final sum) or PPPM_FP64
  * The influence function (computed in FP64 on the device) and the FFT twiddles
  * are built here.  The current CUDA device is used and recorded.
  */
