@@ -157,12 +157,15 @@ int setup_tiles(pppm_plan* P, int T) {
     dfree(P->tile_count);
     dfree(P->tiles);
     dfree(P->region_flag);
+    dfree(P->spread_ticket);
     const size_t psz = (size_t)g.E[0] * g.E[1] * g.Pz;
     int rc;
     if ((rc = dalloc(&P->patch, (size_t)g.ntiles * psz * P->esz)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->tile_count, sizeof(int) * (size_t)g.ntiles)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->tiles, sizeof(int2) * (size_t)g.ntiles)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->region_flag, 2 * sizeof(int))) != PPPM_OK) return rc;
+    if ((rc = dalloc(&P->spread_ticket, sizeof(int))) != PPPM_OK) return rc;
+    CK(cudaMemset(P->spread_ticket, 0, sizeof(int)));  // completes before the cover-list uploads below return
     // a tile's fixed region holds as many sites as the fast spread ranks in
     // shared memory at tile edge 8 (at edge 4 the average tile is 8x smaller)
     P->region_cap = T == 8 ? 256 : 128;
@@ -330,7 +333,7 @@ int run_sites_to_patches(pppm_plan* P, cudaStream_t s, const In* pos, const In* 
     }
     { PROF(K_SPREAD);
       CK(launch_spread<T>(s, g, P->tiles, (const Rec<T>*)P->srec, P->scell, P->sorig, (const T*)P->swt,
-                          (T*)P->patch, P->slot_of, P->tile_of)); }
+                          (T*)P->patch, P->slot_of, P->tile_of, P->spread_ticket)); }
     if (rho_out) {
         PROF(K_FOLD);
         CK(launch_fold<T>(s, g, (const T*)P->patch, P->cov_off, P->cov_ent, scale, rho_out));
@@ -684,6 +687,7 @@ void pppm_destroy(pppm_plan* P) {
     dfree(P->tile_count);
     dfree(P->tiles);
     dfree(P->region_flag);
+    dfree(P->spread_ticket);
     dfree(P->tile_of);
     dfree(P->slot_of);
     dfree(P->rec);

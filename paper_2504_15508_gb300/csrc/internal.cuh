@@ -345,10 +345,14 @@ bool is_bin_kernel(const void* func);   // (Geo, pos, q, n, six pointers)
 bool is_site_kernel(const void* func);  // (Geo, pos, q, n, DirectArgs)
 // order, tmp: n ints of scratch each in tile order (the binning's slot and
 // tile arrays, dead once the scatter has run), used to rank tiles denser than
-// the shared-memory ranking
+// the shared-memory ranking.  ticket: one device int, zero before the first
+// launch, which the full-tile spread uses to hand tiles to warps and leaves
+// at zero when it completes (one per plan: two spreads that may run at the
+// same time need two)
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp);
+                          const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp,
+                          int* ticket);
 template <typename T>
 cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
                         T scale, T* rho);
@@ -360,7 +364,7 @@ void upload_bspline_coefficients();
 // full-tile fast paths (cudaErrorNotSupported when the order/tile has none)
 template <typename T>
 cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
-                               const int* sorig, const T* swt, T* patch, int* order, int* tmp);
+                               const int* sorig, const T* swt, T* patch, int* order, int* tmp, int* ticket);
 // wait_limit: spins of the first bounded wait for a tile's field copy (0: it
 // runs out at once, the copy is then waited for once more before the block
 // returns; a test of the timeout path)

@@ -208,6 +208,7 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     const size_t o_off = take(sizeof(int) * 3 * (size_t)nmax1);
     const size_t o_ent = take(sizeof(int2) * nent);
     const size_t o_status = take(sizeof(int));
+    const size_t o_ticket = take(sizeof(int));
     if (at > kNoAllocScratchBytes) return PPPM_ERR_TOO_LARGE;
     unsigned char* b = static_cast<unsigned char*>(base);
     int* tile_count = reinterpret_cast<int*>(b + o_count);
@@ -224,6 +225,7 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     int* cov_off = reinterpret_cast<int*>(b + o_off);
     int2* cov_ent = reinterpret_cast<int2*>(b + o_ent);
     int* status = reinterpret_cast<int*>(b + o_status);
+    int* ticket = reinterpret_cast<int*>(b + o_ticket);
 
     cudaStream_t s = (cudaStream_t)stream;
     const double h3 = (box[0] / mesh[0]) * (box[1] / mesh[1]) * (box[2] / mesh[2]);
@@ -235,10 +237,11 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     NA_CK(cudaGetLastError());
     NA_CK(cudaMemsetAsync(tile_count, 0, sizeof(int) * g.ntiles, s));
     NA_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    NA_CK(cudaMemsetAsync(ticket, 0, sizeof(int), s));
     NA_CK((launch_bin<float, double>(s, g, pos, q, (int)n, tile_count, tile_of, slot_of, rec, cell, status)));
     NA_CK(launch_scan(s, tile_count, g.ntiles, tiles));
     NA_CK(launch_scatter<float>(s, g, (int)n, tile_of, slot_of, tiles, rec, cell, srec, scell, sorig, swt));
-    NA_CK(launch_spread<float>(s, g, tiles, srec, scell, sorig, swt, patch, slot_of, tile_of));
+    NA_CK(launch_spread<float>(s, g, tiles, srec, scell, sorig, swt, patch, slot_of, tile_of, ticket));
     NA_CK(launch_fold<float>(s, g, patch, cov_off, cov_ent, (float)(1.0 / h3), rho));
 #undef NA_CK
     return PPPM_OK;

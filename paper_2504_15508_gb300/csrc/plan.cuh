@@ -47,6 +47,7 @@ struct pppm_plan {
     int2* tiles = nullptr;     // per tile (first slot, end slot) of the tile-ordered site data
     int region_cap = 0;        // slots of a tile's fixed region (0: compact layout only)
     int* region_flag = nullptr;  // device: [0] a region overflowed, [1] blocks of the sort done
+    int* spread_ticket = nullptr;  // device: the spread's tile ticket (zero between launches)
     // sites
     int64_t cap = 0;       // per-site arrays in the caller's order
     int64_t slot_cap = 0;  // tile-ordered arrays (srec, scell, sorig, swt) and tile_of/slot_of

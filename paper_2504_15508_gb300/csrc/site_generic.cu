@@ -126,9 +126,10 @@ static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int2* tiles, con
 
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp) {
+                          const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp,
+                          int* ticket) {
     if (fast_tiles(g)) {
-        cudaError_t e = launch_spread_fast<T>(s, g, tiles, scell, sorig, swt, patch, order, tmp);
+        cudaError_t e = launch_spread_fast<T>(s, g, tiles, scell, sorig, swt, patch, order, tmp, ticket);
         if (e != cudaErrorNotSupported) return e;
     }
     switch (g.order) {
@@ -334,7 +335,7 @@ cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int2* tiles, const
 
 #define PPPM_INST_T(T)                                                                                          \
     template cudaError_t launch_spread<T>(cudaStream_t, const Geo&, const int2*, const Rec<T>*, const int*,      \
-                                          const int*, const T*, T*, int*, int*);                                 \
+                                          const int*, const T*, T*, int*, int*, int*);                           \
     template cudaError_t launch_fold<T>(cudaStream_t, const Geo&, const T*, const int*, const int2*, T, T*);
 PPPM_INST_T(float)
 PPPM_INST_T(double)

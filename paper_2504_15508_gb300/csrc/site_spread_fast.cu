@@ -49,21 +49,19 @@ struct __align__(16) SpreadWarpSmem {  // 16-byte aligned: staged rows take vect
     short perm[kFastCap];  // canonical position -> slot in the tile
 };
 
+// One tile by one warp: rank its sites, spread them in canonical order into
+// the warp's shared patch, write the patch out.  Ends with __syncwarp, after
+// which the warp may start on its next tile.
 template <typename T, int P, int TILE>
-__global__ void __launch_bounds__(kSpreadWarps * 32)
-k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ scell,
-              const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch, int* order,
-              int* tmp) {
-    pdl_enter();
+__device__ __forceinline__ void spread_tile(const Geo& g, int tile, SpreadWarpSmem<T, P, TILE>& W,
+                                            const int2* __restrict__ tiles, const int* __restrict__ scell,
+                                            const int* __restrict__ sorig, const T* __restrict__ swt,
+                                            T* __restrict__ patch, int* order, int* tmp) {
     typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
     typedef typename Vec16T<T>::t V;
-    constexpr int E = WarpSmem::E, PZ = WarpSmem::PZ, PLANE = WarpSmem::PLANE, PSIZE = WarpSmem::PSIZE;
+    constexpr int PZ = WarpSmem::PZ, PLANE = WarpSmem::PLANE, PSIZE = WarpSmem::PSIZE;
     constexpr int WS = wstride(P), NV = WS * (int)sizeof(T) / 16;  // 16-byte vectors per weight row
-    extern __shared__ __align__(32) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * kSpreadWarps + warp;
-    WarpSmem& W = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
-    if (tile >= g.ntiles) return;  // whole warp; no block-level barrier below
+    const int lane = threadIdx.x & 31;
     const int2 tr = tiles[tile];
     const int s0 = tr.x;
     const int c = tr.y - s0;
@@ -172,18 +170,60 @@ k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ sce
     } else {
         for (int i = lane; i < PSIZE; i += 32) dst[i] = W.pt[i];
     }
+    __syncwarp();
+}
+
+// Tiles are handed to warps dynamically: warp w of the (resident-sized) grid
+// first takes tile w, then draws further tiles from a ticket counter until
+// the tiles run out, so that SMs whose warps finish early take more tiles.
+// Every warp draws exactly one ticket past the last tile; the warp drawing the
+// very last ticket (no warp touches the counter after it) sets the counter
+// back to zero for the next launch.  The counter must be zero before the
+// first launch.
+template <typename T, int P, int TILE>
+__global__ void __launch_bounds__(kSpreadWarps * 32)
+k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ scell,
+              const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch, int* order,
+              int* tmp, int* ticket) {
+    pdl_enter();
+    typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem& W = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
+    const int nwarps = (int)gridDim.x * kSpreadWarps;
+    const int dyn = g.ntiles > nwarps ? g.ntiles - nwarps : 0;  // tiles handed out by ticket
+    int tile = (int)blockIdx.x * kSpreadWarps + warp;
+    if (tile >= g.ntiles) tile = -1;
+    for (;;) {
+        if (tile >= 0) spread_tile<T, P, TILE>(g, tile, W, tiles, scell, sorig, swt, patch, order, tmp);
+        int t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= dyn) {
+            if (lane == 0 && t == dyn + nwarps - 1) atomicExch(ticket, 0);
+            return;  // whole warp; no block-level barrier in this kernel
+        }
+        tile = nwarps + t;
+    }
 }
 
 template <typename T, int P, int TILE>
 static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
-                               const int* sorig, const T* swt, T* patch, int* order, int* tmp) {
+                               const int* sorig, const T* swt, T* patch, int* order, int* tmp, int* ticket) {
+    auto kern = k_spread_fast<T, P, TILE>;
     const size_t smem = kSpreadWarps * sizeof(SpreadWarpSmem<T, P, TILE>);
-    cudaError_t e = cudaFuncSetAttribute(k_spread_fast<T, P, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
-    return launch_k(k_spread_fast<T, P, TILE>, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tiles, scell,
-                    sorig, swt, patch, order, tmp);
+    // as many blocks as are resident at once (the tiles beyond them go by ticket)
+    int dev = 0, nsm = 0, per = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSpreadWarps * 32, smem)) != cudaSuccess)
+        return e;
+    int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
+    if (per >= 1 && nsm >= 1 && blocks > per * nsm) blocks = per * nsm;
+    return launch_k(kern, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tiles, scell, sorig, swt, patch, order,
+                    tmp, ticket);
 }
 
 
@@ -206,14 +246,14 @@ static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, 
 
 template <typename T>
 cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
-                               const int* sorig, const T* swt, T* patch, int* order, int* tmp) {
-    PPPM_FAST_SWITCH(spread_fast, T, s, g, tiles, scell, sorig, swt, patch, order, tmp)
+                               const int* sorig, const T* swt, T* patch, int* order, int* tmp, int* ticket) {
+    PPPM_FAST_SWITCH(spread_fast, T, s, g, tiles, scell, sorig, swt, patch, order, tmp, ticket)
     return cudaErrorNotSupported;
 }
 
 template cudaError_t launch_spread_fast<float>(cudaStream_t, const Geo&, const int2*, const int*, const int*,
-                                               const float*, float*, int*, int*);
+                                               const float*, float*, int*, int*, int*);
 template cudaError_t launch_spread_fast<double>(cudaStream_t, const Geo&, const int2*, const int*, const int*,
-                                                const double*, double*, int*, int*);
+                                                const double*, double*, int*, int*, int*);
 
 }  // namespace pppm
