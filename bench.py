@@ -150,8 +150,9 @@ def algorithmic_bytes(n: int, mesh: int) -> dict:
         "fft_y_inverse3": 16 * NH + 24 * NH,
         "fft_z_c2r": 24 * NH + 12 * N,
         # the one-pass sort into fixed tile regions: positions and charges in;
-        # weights (64 B), cell, original index, tile and rank out
-        "bin": 16 * n + 80 * n,
+        # record (16 B: B-spline arguments, charge), cell, original index,
+        # tile and rank out
+        "bin": 16 * n + 32 * n,
         "scatter": 0,  # the region sort's fallback: idle unless a region overflows
         "tiles_init": 8 * ((mesh + 7) // 8) ** 3,
         "fold": 8 * N,
@@ -171,15 +172,16 @@ def step_algorithmic_bytes(n: int, mesh: int) -> int:
 # one ncu --set full capture of the kernel as it stands, on this workload; an
 # entry is removed whenever its kernel changes.
 NCU_TRAFFIC = {
-    ("gather", 128): 59.54e6,
-    ("spread", 128): 21.60e6,
+    ("gather", 128): 44.61e6,
+    ("spread", 128): 7.73e6,
+    ("bin", 128): 4.87e6,
     ("fft_z_r2c", 128): 30.71e6,
     ("fft_y", 128): 8.54e6,
     ("fft_x_influence", 128): 12.86e6,
     ("fft_y_inverse3", 128): 17.08e6,
     ("fft_z_c2r", 128): 25.75e6,
-    ("gather", 160): 96.40e6,
     ("fft_x_influence", 160): 24.98e6,
+    ("gather", 160): 82.63e6,
 }
 
 

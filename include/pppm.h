@@ -266,8 +266,7 @@ void pppm_batch_destroy(pppm_batch *batch);
  *   rho               Nx x Ny x Nz floats, device, written
  * It calls no cudaMalloc/cudaFree: its scratch is one file-scope device array
  * of 32 MiB that every GPU loading this library holds until the process exits.
- * Inputs needing more scratch than that (about 52 B per site plus 4 B per
- * precomputed B-spline weight, 3p rounded up to a multiple of 4 per site, plus
+ * Inputs needing more scratch than that (about 52 B per site plus
  * 4 B x (T+p-1)^3 per tile of T^3 mesh cells, T = 8 or 4) return
  * PPPM_ERR_TOO_LARGE.  All calls share the array and it keeps the last call's
  * contents (the per-tile counters are cleared by each call); calls whose work

@@ -253,14 +253,12 @@ int reserve_sites(pppm_plan* P, int64_t n) {
     dfree(P->srec);
     dfree(P->scell);
     dfree(P->sorig);
-    dfree(P->swt);
     P->slot_cap = 0;
     if ((rc = dalloc(&P->tile_of, sizeof(int) * slots)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->slot_of, sizeof(int) * slots)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->srec, 4 * P->esz * slots)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->scell, sizeof(int) * slots)) != PPPM_OK) return rc;
     if ((rc = dalloc(&P->sorig, sizeof(int) * slots)) != PPPM_OK) return rc;
-    if ((rc = dalloc(&P->swt, P->esz * wstride(P->order) * slots)) != PPPM_OK) return rc;
     P->slot_cap = slots;
     return PPPM_OK;
 }
@@ -312,14 +310,14 @@ int build_field_map(pppm_plan* P) {
 template <typename T, typename In>
 int run_sites_to_patches(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_t n, T* rho_out, T scale) {
     Geo& g = P->g;
-    // the fast spread and the TMA gather read only cells, indices and weights
-    const bool need_rec = !fast_tiles(g) || !P->fmap_ok;
+    // every spread and gather reads the tile-ordered records (the fast ones
+    // evaluate the B-spline weights from them on chip): no weight rows
     if (region_slots(P, n) > 0) {
         // fixed tile regions: one pass over the sites; its last block rebuilds
         // the compact layout only if a region overflowed
         { PROF(K_TILES_INIT); CK(launch_tiles_init(s, P->tiles, g.ntiles, P->region_cap, P->region_flag)); }
         DirectArgs<T> a{P->tiles, P->region_cap, P->region_flag, P->tile_of, P->slot_of,
-                        need_rec ? (Rec<T>*)P->srec : nullptr, P->scell, P->sorig, (T*)P->swt, P->status};
+                        (Rec<T>*)P->srec, P->scell, P->sorig, P->status};
         { PROF(K_BIN); CK((launch_bin_direct<T, In>(s, g, pos, q, (int)n, a))); }
     } else {
         CK(cudaMemsetAsync(P->tile_count, 0, sizeof(int) * (size_t)g.ntiles, s));
@@ -329,11 +327,11 @@ int run_sites_to_patches(pppm_plan* P, cudaStream_t s, const In* pos, const In* 
         { PROF(K_SCAN); CK(launch_scan(s, P->tile_count, g.ntiles, P->tiles)); }
         { PROF(K_SCATTER);
           CK(launch_scatter<T>(s, g, (int)n, P->tile_of, P->slot_of, P->tiles, (const Rec<T>*)P->rec, P->cell,
-                               need_rec ? (Rec<T>*)P->srec : nullptr, P->scell, P->sorig, (T*)P->swt)); }
+                               (Rec<T>*)P->srec, P->scell, P->sorig)); }
     }
     { PROF(K_SPREAD);
-      CK(launch_spread<T>(s, g, P->tiles, (const Rec<T>*)P->srec, P->scell, P->sorig, (const T*)P->swt,
-                          (T*)P->patch, P->slot_of, P->tile_of, P->spread_ticket)); }
+      CK(launch_spread<T>(s, g, P->tiles, (const Rec<T>*)P->srec, P->scell, P->sorig, (T*)P->patch, P->slot_of,
+                          P->tile_of, P->spread_ticket)); }
     if (rho_out) {
         PROF(K_FOLD);
         CK(launch_fold<T>(s, g, (const T*)P->patch, P->cov_off, P->cov_ent, scale, rho_out));
@@ -411,9 +409,9 @@ int run_compute(pppm_plan* P, cudaStream_t s, const In* pos, const In* q, int64_
     if ((rc = run_solve<T>(P, s, energy, virial, fl)) != PPPM_OK) return rc;
     if (forces && n > 0) {
         PROF(K_GATHER);
-        CK((launch_gather<T, In>(s, P->g, P->tiles, (const Rec<T>*)P->srec, P->scell, P->sorig,
-                                 (const T*)P->swt, fl, P->flayout, P->fmap_ok ? (const void*)&P->fmap : nullptr,
-                                 P->opt.prefactor, forces, P->status, P->wait_limit)));
+        CK((launch_gather<T, In>(s, P->g, P->tiles, (const Rec<T>*)P->srec, P->scell, P->sorig, fl, P->flayout,
+                                 P->fmap_ok ? (const void*)&P->fmap : nullptr, P->opt.prefactor, forces, P->status,
+                                 P->wait_limit)));
     }
     return PPPM_OK;
 }
@@ -695,7 +693,6 @@ void pppm_destroy(pppm_plan* P) {
     dfree(P->srec);
     dfree(P->scell);
     dfree(P->sorig);
-    dfree(P->swt);
     drop_host_graph(P);
     dfree(P->phi);
     dfree(P->h_stage);

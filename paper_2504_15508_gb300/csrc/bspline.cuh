@@ -85,6 +85,26 @@ struct BspCoef {
     }
 };
 
+// The per-site weights the spread and the gather use, from a site's record:
+// w[0..p-1] = q W_x, w[p..2p-1] = W_y, w[2p..3p-1] = W_z, zeros up to
+// wstride(p).  Every kernel that needs them evaluates them with this one
+// function, so that they are the same values wherever they are formed.
+template <typename T, int P>
+__device__ __forceinline__ void site_weights(const BspCoef<T, P>& co, const Rec<T>& r, T (&w)[wstride(P)]) {
+    T t[P];
+    co.all(r.x0[0], t);
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[a] = t[a] * r.q;
+    co.all(r.x0[1], t);
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[P + a] = t[a];
+    co.all(r.x0[2], t);
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[2 * P + a] = t[a];
+#pragma unroll
+    for (int a = 3 * P; a < wstride(P); ++a) w[a] = T(0);
+}
+
 // One piece with its coefficients in registers (piece index fixed per thread).
 template <typename T, int P>
 struct BspPiece {

@@ -23,8 +23,9 @@ constexpr int kMaxRadixStages = 16;
 constexpr int kSortCap = 1024;       // sites per tile sorted by index in the spread
 constexpr int kMaxMesh = 2048;
 
-// Values stored per site for the precomputed B-spline weights of order p:
-// 3p weights padded to a multiple of 4.
+// Values in a site's row of B-spline weights of order p (the spread and the
+// gather stage one row a site in shared memory): 3p weights padded to a
+// multiple of 4.
 __host__ __device__ constexpr int wstride(int p) { return (3 * p + 3) & ~3; }
 
 // Radix plan of one FFT length: L = prod(r[0..n-1]), each r in {2, 3, 4, 5, 8}.
@@ -317,10 +318,9 @@ struct DirectArgs {
                     // [1] blocks of the sort done
     int* tile_of;   // per site: its tile
     int* slot_of;   // per site: its arrival rank in the tile
-    Rec<T>* srec;   // tile order, or null when no generic kernel reads the records
+    Rec<T>* srec;   // tile order: records (B-spline arguments, charge)
     int* scell;
     int* sorig;
-    T* swt;
     int* status;
 };
 
@@ -334,7 +334,7 @@ cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int2* tile
 template <typename T>
 cudaError_t launch_scatter(cudaStream_t s, const Geo& g, int n, const int* tile_of, const int* slot_of,
                            const int2* tiles, const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell,
-                           int* sorig, T* swt);
+                           int* sorig);
 // fixed regions of a.cap slots per tile: init (also zeroes the two flag words),
 // then the one-pass sort
 cudaError_t launch_tiles_init(cudaStream_t s, int2* tiles, int ntiles, int cap, int* flag);
@@ -351,26 +351,25 @@ bool is_site_kernel(const void* func);  // (Geo, pos, q, n, DirectArgs)
 // same time need two)
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp,
-                          int* ticket);
+                          const int* scell, const int* sorig, T* patch, int* order, int* tmp, int* ticket);
 template <typename T>
 cudaError_t launch_fold(cudaStream_t s, const Geo& g, const T* patch, const int* cov_off, const int2* cov_ent,
                         T scale, T* rho);
 template <typename T, typename Out>
 cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, const T* fields, const FieldLayout& fl,
+                          const int* scell, const int* sorig, const T* fields, const FieldLayout& fl,
                           const void* tmap, double prefactor, Out* forces, int* status, long long wait_limit);
 void upload_bspline_coefficients();
 // full-tile fast paths (cudaErrorNotSupported when the order/tile has none)
 template <typename T>
 cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
-                               const int* sorig, const T* swt, T* patch, int* order, int* tmp, int* ticket);
+                               const int* sorig, const Rec<T>* srec, T* patch, int* order, int* tmp, int* ticket);
 // wait_limit: spins of the first bounded wait for a tile's field copy (0: it
 // runs out at once, the copy is then waited for once more before the block
 // returns; a test of the timeout path)
 template <typename T, typename Out>
 cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell, const int* sorig,
-                              const T* swt, const void* tmap, double prefactor, Out* forces, int* status,
+                              const Rec<T>* srec, const void* tmap, double prefactor, Out* forces, int* status,
                               long long wait_limit);
 
 // fft_kernels.cu

@@ -203,7 +203,6 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     const size_t o_srec = take(sizeof(Rec<float>) * nn);
     const size_t o_scell = take(sizeof(int) * nn);
     const size_t o_sorig = take(sizeof(int) * nn);
-    const size_t o_swt = take(sizeof(float) * wstride(order) * nn);
     const size_t o_patch = take(sizeof(float) * psz * g.ntiles);
     const size_t o_off = take(sizeof(int) * 3 * (size_t)nmax1);
     const size_t o_ent = take(sizeof(int2) * nent);
@@ -220,7 +219,6 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     Rec<float>* srec = reinterpret_cast<Rec<float>*>(b + o_srec);
     int* scell = reinterpret_cast<int*>(b + o_scell);
     int* sorig = reinterpret_cast<int*>(b + o_sorig);
-    float* swt = reinterpret_cast<float*>(b + o_swt);
     float* patch = reinterpret_cast<float*>(b + o_patch);
     int* cov_off = reinterpret_cast<int*>(b + o_off);
     int2* cov_ent = reinterpret_cast<int2*>(b + o_ent);
@@ -240,8 +238,8 @@ extern "C" int pppm_spread_noalloc(const double box[3], const int mesh[3], int o
     NA_CK(cudaMemsetAsync(ticket, 0, sizeof(int), s));
     NA_CK((launch_bin<float, double>(s, g, pos, q, (int)n, tile_count, tile_of, slot_of, rec, cell, status)));
     NA_CK(launch_scan(s, tile_count, g.ntiles, tiles));
-    NA_CK(launch_scatter<float>(s, g, (int)n, tile_of, slot_of, tiles, rec, cell, srec, scell, sorig, swt));
-    NA_CK(launch_spread<float>(s, g, tiles, srec, scell, sorig, swt, patch, slot_of, tile_of, ticket));
+    NA_CK(launch_scatter<float>(s, g, (int)n, tile_of, slot_of, tiles, rec, cell, srec, scell, sorig));
+    NA_CK(launch_spread<float>(s, g, tiles, srec, scell, sorig, patch, slot_of, tile_of, ticket));
     NA_CK(launch_fold<float>(s, g, patch, cov_off, cov_ent, (float)(1.0 / h3), rho));
 #undef NA_CK
     return PPPM_OK;

@@ -50,7 +50,7 @@ struct pppm_plan {
     int* spread_ticket = nullptr;  // device: the spread's tile ticket (zero between launches)
     // sites
     int64_t cap = 0;       // per-site arrays in the caller's order
-    int64_t slot_cap = 0;  // tile-ordered arrays (srec, scell, sorig, swt) and tile_of/slot_of
+    int64_t slot_cap = 0;  // tile-ordered arrays (srec, scell, sorig) and tile_of/slot_of
     int* tile_of = nullptr;
     int* slot_of = nullptr;
     void* rec = nullptr;
@@ -58,7 +58,6 @@ struct pppm_plan {
     void* srec = nullptr;
     int* scell = nullptr;
     int* sorig = nullptr;
-    void* swt = nullptr;  // per-site B-spline weights in tile order
     // host-API staging
     cudaStream_t own = nullptr;
     void* h_stage = nullptr;  // device buffers of the host-pointer calls

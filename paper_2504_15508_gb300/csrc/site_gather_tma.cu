@@ -1,13 +1,16 @@
 // Force interpolation with TMA-staged field patches (padded field meshes with
 // the three fields of a point interleaved in 16 bytes, compile-time tile edge
-// and order, precomputed per-site weights).
+// and order, per-site weights evaluated on chip from the sites' records).
 #include <climits>
 
 #include <cuda.h>
 
+#include "bspline.cuh"
 #include "internal.cuh"
 
 namespace pppm {
+
+void upload_bspline_gather() { bsp_upload_this_unit(); }
 
 constexpr int kGatherWarps = 4;
 
@@ -107,7 +110,7 @@ static LaneRows order_rows(int p, int ez) {
 template <typename T, int P, int TILE, typename Out>
 __global__ void __launch_bounds__(kGatherWarps * 32, 6)  // shared memory holds six blocks an SM
 k_gather_tma(Geo g, const int2* __restrict__ tiles, const int* __restrict__ scell,
-             const int* __restrict__ sorig, const T* __restrict__ swt, const __grid_constant__ CUtensorMap tmap,
+             const int* __restrict__ sorig, const Rec<T>* __restrict__ srec, const __grid_constant__ CUtensorMap tmap,
              const __grid_constant__ LaneRows lanes, double prefactor, Out* __restrict__ forces,
              int* __restrict__ status, long long wait_limit) {
     pdl_enter();
@@ -165,25 +168,26 @@ k_gather_tma(Geo g, const int2* __restrict__ tiles, const int* __restrict__ scel
     int* wcell = st_cell + warp * 8;
     int* worig = st_orig + warp * 8;
     const int nsites = s1 - s0;
-    // registers holding the next batch of 8 sites (weights, cell, original
-    // index): the first batch is fetched while the TMA copy is in flight, each
-    // later one while the previous batch is being interpolated
-    constexpr int NQ = (8 * WS + 31) / 32;
-    T nw[NQ];
+    // registers holding the next batch of 8 sites (one record entry a lane:
+    // lane 4 j + d holds x0 of axis d of site j, lane 4 j + 3 its charge; the
+    // cell and original index of site j in lane j): the first batch is
+    // fetched while the TMA copy is in flight, each later one while the
+    // previous batch is being interpolated.  At staging, lanes 4 j + d
+    // (d < 3) evaluate the p weights of their axis into the batch's rows.
+    const int sj = lane >> 2, sd = lane & 3;
+    T nrv = T(0);
     int ncell = 0, norig = 0;
     auto fetch = [&](int b) {
         const int nb = min(8, nsites - b);
         if (nb <= 0) return;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int k = lane + 32 * q;
-            if (k < nb * WS) nw[q] = __ldg(&swt[(size_t)(s0 + b) * WS + k]);
-        }
+        if (sj < nb) nrv = __ldg(reinterpret_cast<const T*>(srec + s0 + b + sj) + sd);
         if (lane < nb) {
             ncell = __ldg(&scell[s0 + b + lane]);
             norig = __ldg(&sorig[s0 + b + lane]);
         }
     };
+    BspCoef<T, P> co;
+    co.load();
     fetch(warp * 8);
     if (!mbar_wait_bounded(mbar_s, 0, wait_limit)) {
         if (threadIdx.x == 0) atomicOr(status, 2);
@@ -192,12 +196,17 @@ k_gather_tma(Geo g, const int2* __restrict__ tiles, const int* __restrict__ scel
     }
     for (int b = warp * 8; b < nsites; b += kGatherWarps * 8) {
         const int nb = min(8, nsites - b);
+        {
+            const T qj = __shfl_sync(0xffffffffu, nrv, lane | 3);  // the charge of this lane's site
+            if (sj < nb && sd < 3) {
+                T t[P];
+                co.all(nrv, t);
+                if (sd == 0) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int k = lane + 32 * q;
-            if (k < nb * WS) {
-                const int j = k / WS, a = k - j * WS;
-                ww[j * WSP + a] = nw[q];
+                    for (int a = 0; a < P; ++a) t[a] = t[a] * qj;
+                }
+#pragma unroll
+                for (int a = 0; a < P; ++a) ww[sj * WSP + sd * P + a] = t[a];
             }
         }
         if (lane < nb) {
@@ -259,7 +268,7 @@ k_gather_tma(Geo g, const int2* __restrict__ tiles, const int* __restrict__ scel
 
 template <typename T, int P, int TILE, typename Out>
 static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
-                              const int* sorig, const T* swt, const void* tmap, double prefactor, Out* forces,
+                              const int* sorig, const Rec<T>* srec, const void* tmap, double prefactor, Out* forces,
                               int* status, long long wait_limit) {
     constexpr int E = TILE + P - 1, EZ = gather_box_z(P, TILE), WSP = wstride(P) + 4;
     const size_t smem = (4 * (size_t)E * E * EZ * sizeof(T) + 127) / 128 * 128 +
@@ -270,7 +279,7 @@ static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int2* tiles, c
     if (e != cudaSuccess) return e;
     static const LaneRows lanes = order_rows(P, EZ);
     return launch_k(k_gather_tma<T, P, TILE, Out>, dim3(g.ntiles), dim3(kGatherWarps * 32), smem, s, g, tiles,
-                    scell, sorig, swt, *reinterpret_cast<const CUtensorMap*>(tmap), lanes, prefactor, forces, status,
+                    scell, sorig, srec, *reinterpret_cast<const CUtensorMap*>(tmap), lanes, prefactor, forces, status,
                     wait_limit);
 }
 
@@ -293,16 +302,16 @@ static cudaError_t gather_tma(cudaStream_t s, const Geo& g, const int2* tiles, c
 
 template <typename T, typename Out>
 cudaError_t launch_gather_tma(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell, const int* sorig,
-                              const T* swt, const void* tmap, double prefactor, Out* forces, int* status,
+                              const Rec<T>* srec, const void* tmap, double prefactor, Out* forces, int* status,
                               long long wait_limit) {
-    PPPM_FAST_SWITCH_G(gather_tma, T, Out, s, g, tiles, scell, sorig, swt, tmap, prefactor, forces, status,
+    PPPM_FAST_SWITCH_G(gather_tma, T, Out, s, g, tiles, scell, sorig, srec, tmap, prefactor, forces, status,
                        wait_limit)
     return cudaErrorNotSupported;
 }
 
 #define PPPM_INST_G(T, O)                                                                                       \
     template cudaError_t launch_gather_tma<T, O>(cudaStream_t, const Geo&, const int2*, const int*, const int*,  \
-                                                 const T*, const void*, double, O*, int*, long long);
+                                                 const Rec<T>*, const void*, double, O*, int*, long long);
 PPPM_INST_G(float, float)
 PPPM_INST_G(float, double)
 PPPM_INST_G(double, float)

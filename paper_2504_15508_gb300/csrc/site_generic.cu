@@ -126,10 +126,9 @@ static cudaError_t spread_p(cudaStream_t s, const Geo& g, const int2* tiles, con
 
 template <typename T>
 cudaError_t launch_spread(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, T* patch, int* order, int* tmp,
-                          int* ticket) {
+                          const int* scell, const int* sorig, T* patch, int* order, int* tmp, int* ticket) {
     if (fast_tiles(g)) {
-        cudaError_t e = launch_spread_fast<T>(s, g, tiles, scell, sorig, swt, patch, order, tmp, ticket);
+        cudaError_t e = launch_spread_fast<T>(s, g, tiles, scell, sorig, srec, patch, order, tmp, ticket);
         if (e != cudaErrorNotSupported) return e;
     }
     switch (g.order) {
@@ -315,10 +314,10 @@ static cudaError_t gather_p(cudaStream_t s, const Geo& g, const int2* tiles, con
 
 template <typename T, typename Out>
 cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int2* tiles, const Rec<T>* srec,
-                          const int* scell, const int* sorig, const T* swt, const T* fields, const FieldLayout& fl,
+                          const int* scell, const int* sorig, const T* fields, const FieldLayout& fl,
                           const void* tmap, double prefactor, Out* forces, int* status, long long wait_limit) {
     if (fast_tiles(g) && fl.padded && tmap) {
-        cudaError_t e = launch_gather_tma<T, Out>(s, g, tiles, scell, sorig, swt, tmap, prefactor, forces, status,
+        cudaError_t e = launch_gather_tma<T, Out>(s, g, tiles, scell, sorig, srec, tmap, prefactor, forces, status,
                                                   wait_limit);
         if (e != cudaErrorNotSupported) return e;
     }
@@ -335,13 +334,13 @@ cudaError_t launch_gather(cudaStream_t s, const Geo& g, const int2* tiles, const
 
 #define PPPM_INST_T(T)                                                                                          \
     template cudaError_t launch_spread<T>(cudaStream_t, const Geo&, const int2*, const Rec<T>*, const int*,      \
-                                          const int*, const T*, T*, int*, int*, int*);                           \
+                                          const int*, T*, int*, int*, int*);                                     \
     template cudaError_t launch_fold<T>(cudaStream_t, const Geo&, const T*, const int*, const int2*, T, T*);
 PPPM_INST_T(float)
 PPPM_INST_T(double)
 #define PPPM_INST_TI(T, I)                                                                                       \
     template cudaError_t launch_gather<T, I>(cudaStream_t, const Geo&, const int2*, const Rec<T>*, const int*,    \
-                                             const int*, const T*, const T*, const FieldLayout&, const void*,    \
+                                             const int*, const T*, const FieldLayout&, const void*,              \
                                              double, I*, int*, long long);
 PPPM_INST_TI(float, float)
 PPPM_INST_TI(float, double)

@@ -1,5 +1,6 @@
 // Binning and sort of the sites by mesh tile: location of every site on the
-// mesh and its B-spline weights (order-p stencil, bspline.cuh), evaluated once.
+// mesh (its cell, tile and B-spline arguments, see bspline.cuh), written in
+// tile order as a 16-byte record, a cell and an original index.
 //
 // Two layouts of the tile-ordered site data:
 //   compact   per-tile counts (k_bin), their scan (k_scan), a scatter to tile
@@ -18,17 +19,19 @@
 
 #include <cuda.h>
 
-#include "bspline.cuh"
 #include "internal.cuh"
 
 namespace pppm {
 
 void upload_bspline_generic();
+void upload_bspline_spread();
+void upload_bspline_gather();
 
 // Fills the B-spline piece tables of every translation unit that uses them.
 void upload_bspline_coefficients() {
-    bsp_upload_this_unit();
     upload_bspline_generic();
+    upload_bspline_spread();
+    upload_bspline_gather();
 }
 
 // ------------------------------------------------------------------ binning
@@ -184,78 +187,36 @@ cudaError_t launch_scan(cudaStream_t s, const int* count, int ntiles, int2* tile
     return launch_k(k_scan, dim3(1), dim3(1024), 0, s, count, ntiles, tiles);
 }
 
-// Scatter to tile order.  Each site's B-spline weights are evaluated here,
-// once, one thread per site: swt holds per site {q W_x[0..p-1], W_y[0..p-1],
-// W_z[0..p-1]} padded to wstride(p) values; the fast spread and gather read
-// them instead of re-evaluating the splines in every lane.
-// Site i's data at slot dst of the tile order: record (only the generic spread
-// and gather read it), cell, original index and weights.
-template <typename T, int P>
+// Site i's data at slot dst of the tile order: its record (B-spline
+// arguments and charge; the spread and the gather evaluate the weights from
+// it on chip), cell and original index.
+template <typename T>
 __device__ __forceinline__ void write_site(const Rec<T>& r, int cl, int i, int dst, Rec<T>* __restrict__ srec,
-                                           int* __restrict__ scell, int* __restrict__ sorig, T* __restrict__ swt) {
-    constexpr int WS = wstride(P);
-    if (srec) srec[dst] = r;
+                                           int* __restrict__ scell, int* __restrict__ sorig) {
+    srec[dst] = r;
     scell[dst] = cl;
     sorig[dst] = i;
-    BspCoef<T, P> co;
-    co.load();
-    T w[WS];
-    T t[P];
-    co.all(r.x0[0], t);
-#pragma unroll
-    for (int a = 0; a < P; ++a) w[a] = t[a] * r.q;
-    co.all(r.x0[1], t);
-#pragma unroll
-    for (int a = 0; a < P; ++a) w[P + a] = t[a];
-    co.all(r.x0[2], t);
-#pragma unroll
-    for (int a = 0; a < P; ++a) w[2 * P + a] = t[a];
-#pragma unroll
-    for (int a = 3 * P; a < WS; ++a) w[a] = T(0);
-    T* o = swt + (size_t)dst * WS;
-#pragma unroll
-    for (int a = 0; a < WS; a += 4) {
-        if constexpr (sizeof(T) == 4) {
-            *reinterpret_cast<float4*>(o + a) = make_float4(w[a], w[a + 1], w[a + 2], w[a + 3]);
-        } else {
-            *reinterpret_cast<double2*>(o + a) = make_double2(w[a], w[a + 1]);
-            *reinterpret_cast<double2*>(o + a + 2) = make_double2(w[a + 2], w[a + 3]);
-        }
-    }
 }
 
-template <typename T, int P>
+template <typename T>
 __global__ void k_scatter(int n, const int* __restrict__ tile_of, const int* __restrict__ slot_of,
                           const int2* __restrict__ tiles, const Rec<T>* __restrict__ rec,
                           const int* __restrict__ cell, Rec<T>* __restrict__ srec, int* __restrict__ scell,
-                          int* __restrict__ sorig, T* __restrict__ swt) {
+                          int* __restrict__ sorig) {
     pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    write_site<T, P>(rec[i], cell[i], i, tiles[tile_of[i]].x + slot_of[i], srec, scell, sorig, swt);
+    write_site<T>(rec[i], cell[i], i, tiles[tile_of[i]].x + slot_of[i], srec, scell, sorig);
 }
 
 template <typename T>
 cudaError_t launch_scatter(cudaStream_t s, const Geo& g, int n, const int* tile_of, const int* slot_of,
                            const int2* tiles, const Rec<T>* rec, const int* cell, Rec<T>* srec, int* scell,
-                           int* sorig, T* swt) {
+                           int* sorig) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + 255) / 256;
-#define PPPM_SCATTER_P(PP)                                                                                  \
-    case PP:                                                                                                \
-        return launch_k(k_scatter<T, PP>, dim3(blocks), dim3(256), 0, s, n, tile_of, slot_of, tiles, rec,        \
-                        cell, srec, scell, sorig, swt);
-    switch (g.order) {
-        PPPM_SCATTER_P(2)
-        PPPM_SCATTER_P(3)
-        PPPM_SCATTER_P(4)
-        PPPM_SCATTER_P(5)
-        PPPM_SCATTER_P(6)
-        PPPM_SCATTER_P(7)
-        default: return cudaErrorInvalidValue;
-    }
-#undef PPPM_SCATTER_P
-    return cudaGetLastError();
+    return launch_k(k_scatter<T>, dim3(blocks), dim3(256), 0, s, n, tile_of, slot_of, tiles, rec, cell, srec, scell,
+                    sorig);
 }
 
 // ------------------------------------------------------------------ fixed regions
@@ -274,7 +235,7 @@ __global__ void k_tiles_init(int2* __restrict__ tiles, int ntiles, int cap, int*
 // it rebuilds the compact layout alone (a scan of the counts, then every site
 // again to start + its arrival rank): slow, but only for such inputs, and no
 // extra launch on the normal path.
-template <typename T, typename In, int P>
+template <typename T, typename In>
 __global__ void __launch_bounds__(256)
 k_bin_direct(Geo g, const In* __restrict__ pos, const In* __restrict__ q, int n, DirectArgs<T> a) {
     pdl_enter();
@@ -296,7 +257,7 @@ k_bin_direct(Geo g, const In* __restrict__ pos, const In* __restrict__ q, int n,
         const int slot = base + rank, r0 = t * a.cap;
         a.tile_of[i] = t;
         a.slot_of[i] = slot - r0;  // arrival rank in the tile
-        if (slot < r0 + a.cap) write_site<T, P>(r, cl, i, slot, a.srec, a.scell, a.sorig, a.swt);
+        if (slot < r0 + a.cap) write_site<T>(r, cl, i, slot, a.srec, a.scell, a.sorig);
         else atomicExch(a.flag, 1);  // the region overflowed
     }
     // the block's writes, ordered before its count by the barrier and one
@@ -315,7 +276,7 @@ k_bin_direct(Geo g, const In* __restrict__ pos, const In* __restrict__ q, int n,
         Rec<T> rk;
         int tk = 0, ck = 0;
         site_locate<T, In>(g, pos, q, k, rk, tk, ck);  // the same record, tile and cell as above
-        write_site<T, P>(rk, ck, k, a.tiles[tk].x + __ldcg(&a.slot_of[k]), a.srec, a.scell, a.sorig, a.swt);
+        write_site<T>(rk, ck, k, a.tiles[tk].x + __ldcg(&a.slot_of[k]), a.srec, a.scell, a.sorig);
     }
 }
 
@@ -328,58 +289,26 @@ cudaError_t launch_bin_direct(cudaStream_t s, const Geo& g, const In* pos, const
                               const DirectArgs<T>& a) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + 255) / 256;
-#define PPPM_DIRECT_P(PP) \
-    case PP: return launch_k(k_bin_direct<T, In, PP>, dim3(blocks), dim3(256), 0, s, g, pos, q, n, a);
-    switch (g.order) {
-        PPPM_DIRECT_P(2)
-        PPPM_DIRECT_P(3)
-        PPPM_DIRECT_P(4)
-        PPPM_DIRECT_P(5)
-        PPPM_DIRECT_P(6)
-        PPPM_DIRECT_P(7)
-    }
-#undef PPPM_DIRECT_P
-    return cudaErrorInvalidValue;
+    return launch_k(k_bin_direct<T, In>, dim3(blocks), dim3(256), 0, s, g, pos, q, n, a);
 }
 
 // The kernels that read the sites (the nodes of a captured step whose
 // position and charge pointers are patched on replay): the compact layout's
 // binning kernel, with arguments (Geo, pos, q, n, six pointers), and the
 // region sort, with (Geo, pos, q, n, DirectArgs).
-template <typename T, typename In, int P>
-void add_site_kernels(std::vector<const void*>& v) {
-    v.push_back((const void*)k_bin_direct<T, In, P>);
-}
-
 bool is_bin_kernel(const void* func) {
     return func == (const void*)k_bin<float, float> || func == (const void*)k_bin<float, double> ||
            func == (const void*)k_bin<double, float> || func == (const void*)k_bin<double, double>;
 }
 
 bool is_site_kernel(const void* func) {
-    static std::vector<const void*> all;
-    if (all.empty()) {
-#define PPPM_SK(T, I)                     \
-    add_site_kernels<T, I, 2>(all);       \
-    add_site_kernels<T, I, 3>(all);       \
-    add_site_kernels<T, I, 4>(all);       \
-    add_site_kernels<T, I, 5>(all);       \
-    add_site_kernels<T, I, 6>(all);       \
-    add_site_kernels<T, I, 7>(all);
-        PPPM_SK(float, float)
-        PPPM_SK(float, double)
-        PPPM_SK(double, float)
-        PPPM_SK(double, double)
-#undef PPPM_SK
-    }
-    for (const void* f : all)
-        if (f == func) return true;
-    return false;
+    return func == (const void*)k_bin_direct<float, float> || func == (const void*)k_bin_direct<float, double> ||
+           func == (const void*)k_bin_direct<double, float> || func == (const void*)k_bin_direct<double, double>;
 }
 
 #define PPPM_INST_T(T)                                                                                          \
     template cudaError_t launch_scatter<T>(cudaStream_t, const Geo&, int, const int*, const int*, const int2*,    \
-                                           const Rec<T>*, const int*, Rec<T>*, int*, int*, T*);
+                                           const Rec<T>*, const int*, Rec<T>*, int*, int*);
 PPPM_INST_T(float)
 PPPM_INST_T(double)
 #define PPPM_INST_TI(T, I)                                                                                       \

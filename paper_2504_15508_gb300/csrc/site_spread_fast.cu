@@ -1,13 +1,16 @@
-// Fast charge spread: tile edge and order are compile-time constants, the
-// per-site B-spline weights come precomputed from the scatter, and every axis
-// holds at least one full tile.
+// Fast charge spread: tile edge and order are compile-time constants, each
+// site's B-spline weights are evaluated on chip from its 16-byte record, and
+// every axis holds at least one full tile.
 #include <climits>
 
 #include <cuda.h>
 
+#include "bspline.cuh"
 #include "internal.cuh"
 
 namespace pppm {
+
+void upload_bspline_spread() { bsp_upload_this_unit(); }
 
 constexpr int kSpreadWarps = 4;
 //
@@ -19,9 +22,10 @@ constexpr int kSpreadWarps = 4;
 constexpr int kFastCap = 256;  // sites per tile ordered by index in the fast spread
 constexpr int kStage = 32;     // sites staged per batch (one per lane)
 
-// Spread: as k_spread, with the tile's records staged through shared memory in
-// batches of 32 (the next batch's weights are loaded into registers, as
-// 16-byte vectors, while the current one is spread) and a padded patch pitch
+// Spread: as k_spread, with the tile's sites staged through shared memory in
+// batches of 32 (the next batch's records are loaded into registers while the
+// current one is spread; at staging each lane writes its site's weight row,
+// evaluated from the record) and a padded patch pitch
 // (PZ odd) that keeps the p^2 stencil rows of a site in distinct banks.  The
 // canonical order (by original index) comes from ranking the tile's sites by
 // counting: one pass of broadcast compares, no sorting network.
@@ -35,6 +39,37 @@ template <>
 struct Vec16T<double> {
     typedef double2 t;
 };
+
+// A site record by 16-byte loads, and 16-byte vector a of a row of weights.
+__device__ __forceinline__ Rec<float> load_rec(const Rec<float>* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    Rec<float> r;
+    r.x0[0] = v.x;
+    r.x0[1] = v.y;
+    r.x0[2] = v.z;
+    r.q = v.w;
+    return r;
+}
+__device__ __forceinline__ Rec<double> load_rec(const Rec<double>* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    Rec<double> r;
+    r.x0[0] = a.x;
+    r.x0[1] = a.y;
+    r.x0[2] = b.x;
+    r.q = b.y;
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ typename Vec16T<T>::t vec16(const T* w, int a);
+template <>
+__device__ __forceinline__ float4 vec16<float>(const float* w, int a) {
+    return make_float4(w[4 * a], w[4 * a + 1], w[4 * a + 2], w[4 * a + 3]);
+}
+template <>
+__device__ __forceinline__ double2 vec16<double>(const double* w, int a) {
+    return make_double2(w[2 * a], w[2 * a + 1]);
+}
 
 template <typename T, int P, int TILE>
 struct __align__(16) SpreadWarpSmem {  // 16-byte aligned: staged rows take vector stores
@@ -55,7 +90,7 @@ struct __align__(16) SpreadWarpSmem {  // 16-byte aligned: staged rows take vect
 template <typename T, int P, int TILE>
 __device__ __forceinline__ void spread_tile(const Geo& g, int tile, SpreadWarpSmem<T, P, TILE>& W,
                                             const int2* __restrict__ tiles, const int* __restrict__ scell,
-                                            const int* __restrict__ sorig, const T* __restrict__ swt,
+                                            const int* __restrict__ sorig, const Rec<T>* __restrict__ srec,
                                             T* __restrict__ patch, int* order, int* tmp) {
     typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
     typedef typename Vec16T<T>::t V;
@@ -110,25 +145,29 @@ __device__ __forceinline__ void spread_tile(const Geo& g, int tile, SpreadWarpSm
         riz[j] = ract[j] ? row % P : 0;
         roff[j] = riy[j] * PZ + riz[j];
     }
-    // registers holding the next batch's weights and cell
-    V nw[NV];
+    // registers holding the next batch's records and cells (one site a
+    // lane); a lane turns its site's record into the weight row when the
+    // batch is staged
+    Rec<T> nr;
     int ncell = 0;
     auto fetch = [&](int t0) {
         if (lane < kStage && t0 + lane < c) {
             const int s = s0 + (ranked ? (int)W.perm[t0 + lane] : (dense ? __ldcg(&order[s0 + t0 + lane]) : t0 + lane));
-            const V* src = reinterpret_cast<const V*>(swt + (size_t)s * WS);
-#pragma unroll
-            for (int a = 0; a < NV; ++a) nw[a] = __ldg(&src[a]);
+            nr = load_rec(srec + s);
             ncell = __ldg(&scell[s]);
         }
     };
+    BspCoef<T, P> co;
+    co.load();
     fetch(0);
     for (int t0 = 0; t0 < c; t0 += kStage) {
         const int nb = min(kStage, c - t0);
         if (lane < nb) {
+            T w[WS];
+            site_weights<T, P>(co, nr, w);
             V* dst = reinterpret_cast<V*>(&W.u.st_w[lane][0]);
 #pragma unroll
-            for (int a = 0; a < NV; ++a) dst[a] = nw[a];
+            for (int a = 0; a < NV; ++a) dst[a] = vec16<T>(w, a);
             W.st_cell[lane] = ncell;
         }
         __syncwarp();
@@ -183,7 +222,7 @@ __device__ __forceinline__ void spread_tile(const Geo& g, int tile, SpreadWarpSm
 template <typename T, int P, int TILE>
 __global__ void __launch_bounds__(kSpreadWarps * 32)
 k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ scell,
-              const int* __restrict__ sorig, const T* __restrict__ swt, T* __restrict__ patch, int* order,
+              const int* __restrict__ sorig, const Rec<T>* __restrict__ srec, T* __restrict__ patch, int* order,
               int* tmp, int* ticket) {
     pdl_enter();
     typedef SpreadWarpSmem<T, P, TILE> WarpSmem;
@@ -195,7 +234,7 @@ k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ sce
     int tile = (int)blockIdx.x * kSpreadWarps + warp;
     if (tile >= g.ntiles) tile = -1;
     for (;;) {
-        if (tile >= 0) spread_tile<T, P, TILE>(g, tile, W, tiles, scell, sorig, swt, patch, order, tmp);
+        if (tile >= 0) spread_tile<T, P, TILE>(g, tile, W, tiles, scell, sorig, srec, patch, order, tmp);
         int t = 0;
         if (lane == 0) t = atomicAdd(ticket, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
@@ -209,7 +248,7 @@ k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ sce
 
 template <typename T, int P, int TILE>
 static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
-                               const int* sorig, const T* swt, T* patch, int* order, int* tmp, int* ticket) {
+                               const int* sorig, const Rec<T>* srec, T* patch, int* order, int* tmp, int* ticket) {
     auto kern = k_spread_fast<T, P, TILE>;
     const size_t smem = kSpreadWarps * sizeof(SpreadWarpSmem<T, P, TILE>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -222,7 +261,7 @@ static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, 
         return e;
     int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
     if (per >= 1 && nsm >= 1 && blocks > per * nsm) blocks = per * nsm;
-    return launch_k(kern, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tiles, scell, sorig, swt, patch, order,
+    return launch_k(kern, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tiles, scell, sorig, srec, patch, order,
                     tmp, ticket);
 }
 
@@ -246,14 +285,14 @@ static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, 
 
 template <typename T>
 cudaError_t launch_spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, const int* scell,
-                               const int* sorig, const T* swt, T* patch, int* order, int* tmp, int* ticket) {
-    PPPM_FAST_SWITCH(spread_fast, T, s, g, tiles, scell, sorig, swt, patch, order, tmp, ticket)
+                               const int* sorig, const Rec<T>* srec, T* patch, int* order, int* tmp, int* ticket) {
+    PPPM_FAST_SWITCH(spread_fast, T, s, g, tiles, scell, sorig, srec, patch, order, tmp, ticket)
     return cudaErrorNotSupported;
 }
 
 template cudaError_t launch_spread_fast<float>(cudaStream_t, const Geo&, const int2*, const int*, const int*,
-                                               const float*, float*, int*, int*, int*);
+                                               const Rec<float>*, float*, int*, int*, int*);
 template cudaError_t launch_spread_fast<double>(cudaStream_t, const Geo&, const int2*, const int*, const int*,
-                                                const double*, double*, int*, int*, int*);
+                                                const Rec<double>*, double*, int*, int*, int*);
 
 }  // namespace pppm
