@@ -1,6 +1,7 @@
 // Fast charge spread: tile edge and order are compile-time constants, each
 // site's B-spline weights are evaluated on chip from its 16-byte record, and
 // every axis holds at least one full tile.
+#include <atomic>
 #include <climits>
 
 #include <cuda.h>
@@ -13,6 +14,7 @@ namespace pppm {
 void upload_bspline_spread() { bsp_upload_this_unit(); }
 
 constexpr int kSpreadWarps = 4;
+constexpr int kResidentCacheDevices = 64;
 //
 // The kernels below are the ones the workloads run: tile edge and order are
 // compile-time constants (so every index is constant arithmetic) and every
@@ -253,14 +255,23 @@ static cudaError_t spread_fast(cudaStream_t s, const Geo& g, const int2* tiles, 
     const size_t smem = kSpreadWarps * sizeof(SpreadWarpSmem<T, P, TILE>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // as many blocks as are resident at once (the tiles beyond them go by ticket)
-    int dev = 0, nsm = 0, per = 0;
+    // as many blocks as are resident at once (the tiles beyond them go by
+    // ticket): resident blocks an SM x SMs, queried once per device
+    static std::atomic<int> resident[kResidentCacheDevices];  // 0: not queried yet
+    int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSpreadWarps * 32, smem)) != cudaSuccess)
-        return e;
+    const bool cached = dev >= 0 && dev < kResidentCacheDevices;
+    int cap = cached ? resident[dev].load(std::memory_order_relaxed) : 0;
+    if (cap <= 0) {
+        int nsm = 0, per = 0;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSpreadWarps * 32, smem)) != cudaSuccess)
+            return e;
+        cap = per >= 1 && nsm >= 1 ? per * nsm : 0;
+        if (cached && cap > 0) resident[dev].store(cap, std::memory_order_relaxed);
+    }
     int blocks = (g.ntiles + kSpreadWarps - 1) / kSpreadWarps;
-    if (per >= 1 && nsm >= 1 && blocks > per * nsm) blocks = per * nsm;
+    if (cap > 0 && blocks > cap) blocks = cap;
     return launch_k(kern, dim3(blocks), dim3(kSpreadWarps * 32), smem, s, g, tiles, scell, sorig, srec, patch, order,
                     tmp, ticket);
 }
