@@ -87,8 +87,10 @@ struct BspCoef {
 
 // The per-site weights the spread and the gather use, from a site's record:
 // w[0..p-1] = q W_x, w[p..2p-1] = W_y, w[2p..3p-1] = W_z, zeros up to
-// wstride(p).  Every kernel that needs them evaluates them with this one
-// function, so that they are the same values wherever they are formed.
+// wstride(p).  The fast spread evaluates them with this function; the TMA
+// gather evaluates the same expressions one axis a lane (BspCoef::all, then
+// the x weights times q), so that a site's weights are the same values in
+// both.
 template <typename T, int P>
 __device__ __forceinline__ void site_weights(const BspCoef<T, P>& co, const Rec<T>& r, T (&w)[wstride(P)]) {
     T t[P];
