@@ -90,7 +90,7 @@ struct __align__(16) SpreadWarpSmem {  // 16-byte aligned: staged rows take vect
 // the warp's shared patch, write the patch out.  Ends with __syncwarp, after
 // which the warp may start on its next tile.
 template <typename T, int P, int TILE>
-__device__ __forceinline__ void spread_tile(const Geo& g, int tile, SpreadWarpSmem<T, P, TILE>& W,
+__device__ __forceinline__ void spread_tile(int tile, SpreadWarpSmem<T, P, TILE>& W,
                                             const int2* __restrict__ tiles, const int* __restrict__ scell,
                                             const int* __restrict__ sorig, const Rec<T>* __restrict__ srec,
                                             T* __restrict__ patch, int* order, int* tmp) {
@@ -236,7 +236,7 @@ k_spread_fast(Geo g, const int2* __restrict__ tiles, const int* __restrict__ sce
     int tile = (int)blockIdx.x * kSpreadWarps + warp;
     if (tile >= g.ntiles) tile = -1;
     for (;;) {
-        if (tile >= 0) spread_tile<T, P, TILE>(g, tile, W, tiles, scell, sorig, srec, patch, order, tmp);
+        if (tile >= 0) spread_tile<T, P, TILE>(tile, W, tiles, scell, sorig, srec, patch, order, tmp);
         int t = 0;
         if (lane == 0) t = atomicAdd(ticket, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
