@@ -78,7 +78,7 @@ struct Bufs {
     int* cell;
     int* scell;
     int* sorig;
-    float* swt;
+    Rec<float>* srec;  // tile order: the sites' records (B-spline arguments, charge)
     float* patch;
     float2* cx0;
     float2* cx1;
@@ -205,10 +205,10 @@ __device__ void st_scan(const BoxDesc& D, const Bufs& B, int* sh) {
 
 // Scatter: a thread's kSiteChunk / kThreads sites, their independent loads
 // (tile, slot, record, cell) issued together before any store, then each
-// site's weight row written as 16-byte vectors.
+// site's cell, index and 16-byte record written at its slot of the tile
+// order (the spread and the gather evaluate the weights from the record).
 template <int P>
 __device__ void st_scatter(const BoxDesc& D, int idx, const Bufs& B) {
-    constexpr int WS = wstride(P);
     constexpr int KS = kSiteChunk / kThreads;
     int tt[KS], sl[KS], cl[KS];
     float4 rr[KS];
@@ -236,22 +236,7 @@ __device__ void st_scatter(const BoxDesc& D, int idx, const Bufs& B) {
         const long long dst = D.site0 + st[k] + sl[k];
         B.scell[dst] = cl[k];
         B.sorig[dst] = i;
-        float w[WS];
-        float t[P];
-        bspline_all<P>(rr[k].x, t);
-#pragma unroll
-        for (int a = 0; a < P; ++a) w[a] = t[a] * rr[k].w;
-        bspline_all<P>(rr[k].y, t);
-#pragma unroll
-        for (int a = 0; a < P; ++a) w[P + a] = t[a];
-        bspline_all<P>(rr[k].z, t);
-#pragma unroll
-        for (int a = 0; a < P; ++a) w[2 * P + a] = t[a];
-#pragma unroll
-        for (int a = 3 * P; a < WS; ++a) w[a] = 0.f;
-        float4* o = reinterpret_cast<float4*>(B.swt + dst * WS);
-#pragma unroll
-        for (int a = 0; a < WS / 4; ++a) o[a] = make_float4(w[4 * a], w[4 * a + 1], w[4 * a + 2], w[4 * a + 3]);
+        reinterpret_cast<float4*>(B.srec)[dst] = rr[k];
     }
 }
 
@@ -261,21 +246,44 @@ __device__ void st_scatter(const BoxDesc& D, int idx, const Bufs& B) {
 // of the remainders at 2^-K) with 32-bit shared-memory atomics: integer sums
 // do not depend on the order in which the warps add their sites, so the
 // result is bitwise reproducible with no ordering of the tile's sites.  The
-// patch keeps the padded pitch and is written out as FP32.
+// patch keeps the padded pitch and is written out as FP32.  The sites' weight
+// rows are evaluated from their records into shared memory, kThreads sites
+// at a time (one thread a site), before the warps spread them.
 template <int P, int TILE>
 struct SpreadRed {
     static constexpr int E = TILE + P - 1, PZ = E | 1, PLANE = E * PZ, PSIZE = E * PLANE;
-    static constexpr size_t bytes() { return 2 * sizeof(int) * PSIZE + sizeof(unsigned) * kWarps; }
+    static constexpr int WSR = wstride(P) + 4;  // row pitch: conflict-free 16-byte row stores
+    // accumulators, per-warp maxima, then the rows (16-byte aligned)
+    static constexpr size_t rows_off() { return (2 * sizeof(int) * PSIZE + sizeof(unsigned) * kWarps + 15) / 16 * 16; }
+    static constexpr size_t bytes() { return rows_off() + sizeof(float) * kThreads * WSR; }
 };
+
+// Site t's weight row from its record: q W_x, W_y, W_z (p each), padded.
+template <int P>
+__device__ __forceinline__ void weight_row(const float4& r, float (&w)[wstride(P)]) {
+    float t[P];
+    bspline_all<P>(r.x, t);
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[a] = t[a] * r.w;
+    bspline_all<P>(r.y, t);
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[P + a] = t[a];
+    bspline_all<P>(r.z, t);
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[2 * P + a] = t[a];
+#pragma unroll
+    for (int a = 3 * P; a < wstride(P); ++a) w[a] = 0.f;
+}
 
 template <int P, int TILE>
 __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned char* smem) {
     typedef SpreadRed<P, TILE> L;
-    constexpr int PZ = L::PZ, PLANE = L::PLANE, PSIZE = L::PSIZE;
+    constexpr int PZ = L::PZ, PLANE = L::PLANE, PSIZE = L::PSIZE, WSR = L::WSR;
     constexpr int WS = wstride(P);
     int* acc_h = reinterpret_cast<int*>(smem);
     int* acc_l = acc_h + PSIZE;
     unsigned* wmax = reinterpret_cast<unsigned*>(acc_l + PSIZE);
+    float* rows = reinterpret_cast<float*>(smem + L::rows_off());
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NR = (P * P + 31) / 32;
     int roff[NR], riy[NR], riz[NR];
@@ -298,9 +306,11 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
         for (int i = threadIdx.x; i < 2 * PSIZE; i += kThreads) acc_h[i] = 0;
         unsigned mb = 0;  // largest |q Wx| of the tile
         for (int t = threadIdx.x; t < c; t += kThreads) {
-            const float* w = B.swt + (sb + t) * WS;
+            const float4 r = __ldcg(reinterpret_cast<const float4*>(B.srec + sb + t));
+            float wx[P];
+            bspline_all<P>(r.x, wx);
 #pragma unroll
-            for (int a = 0; a < P; ++a) mb = max(mb, __float_as_uint(fabsf(ldcg(&w[a]))));
+            for (int a = 0; a < P; ++a) mb = max(mb, __float_as_uint(fabsf(wx[a] * r.w)));
         }
         mb = __reduce_max_sync(0xffffffffu, mb);
         if (lane == 0) wmax[warp] = mb;
@@ -309,25 +319,38 @@ __device__ void st_spread(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
         for (int w = 0; w < kWarps; ++w) mb = max(mb, wmax[w]);
         const SplitScale sc = split_scale(mb, c);
         const float S = pow2f(sc.k), twoK = pow2f(sc.K);
-        for (int t = warp; t < c; t += kWarps) {
-            const float* w = B.swt + (sb + t) * WS;
-            float wxq[P];
+        for (int c0 = 0; c0 < c; c0 += kThreads) {  // chunks of kThreads sites (uniform)
+            const int cn = min(kThreads, c - c0);
+            if (c0 > 0) __syncthreads();  // the previous chunk's rows are read no more
+            if ((int)threadIdx.x < cn) {
+                const float4 r = __ldcg(reinterpret_cast<const float4*>(B.srec + sb + c0 + threadIdx.x));
+                float w[WS];
+                weight_row<P>(r, w);
+                float4* o = reinterpret_cast<float4*>(rows + threadIdx.x * WSR);
 #pragma unroll
-            for (int a = 0; a < P; ++a) wxq[a] = ldcg(&w[a]);
-            const int cl = ldcg(&B.scell[sb + t]);
-            const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
-            const int base0 = lx * PLANE + ly * PZ + lz;
+                for (int a = 0; a < WS / 4; ++a) o[a] = make_float4(w[4 * a], w[4 * a + 1], w[4 * a + 2], w[4 * a + 3]);
+            }
+            __syncthreads();
+            for (int t = warp; t < cn; t += kWarps) {
+                const float* w = rows + t * WSR;
+                float wxq[P];
 #pragma unroll
-            for (int jr = 0; jr < NR; ++jr) {
-                if (ract[jr]) {
-                    const float wyzS = ldcg(&w[P + riy[jr]]) * ldcg(&w[2 * P + riz[jr]]) * S;
-                    const int b = base0 + roff[jr];
+                for (int a = 0; a < P; ++a) wxq[a] = w[a];
+                const int cl = ldcg(&B.scell[sb + c0 + t]);
+                const int lx = cl & 255, ly = (cl >> 8) & 255, lz = (cl >> 16) & 255;
+                const int base0 = lx * PLANE + ly * PZ + lz;
 #pragma unroll
-                    for (int a = 0; a < P; ++a) {
-                        int h, l;
-                        split_term(wxq[a] * wyzS, twoK, h, l);
-                        atomicAdd(&acc_h[b + a * PLANE], h);
-                        atomicAdd(&acc_l[b + a * PLANE], l);
+                for (int jr = 0; jr < NR; ++jr) {
+                    if (ract[jr]) {
+                        const float wyzS = w[P + riy[jr]] * w[2 * P + riz[jr]] * S;
+                        const int b = base0 + roff[jr];
+#pragma unroll
+                        for (int a = 0; a < P; ++a) {
+                            int h, l;
+                            split_term(wxq[a] * wyzS, twoK, h, l);
+                            atomicAdd(&acc_h[b + a * PLANE], h);
+                            atomicAdd(&acc_l[b + a * PLANE], l);
+                        }
                     }
                 }
             }
@@ -852,11 +875,22 @@ __device__ void st_gather(const BoxDesc& D, int idx, const Bufs& B, unsigned cha
     int* worig = st_orig + warp * 8;
     const int nsites = s1 - s0;
     const long long sb = D.site0 + s0;
+    const int sj = lane >> 2, sd = lane & 3;  // record entry sd of site sj of a batch
     for (int b = wg * 8; b < nsites; b += 4 * 8) {
         const int nb = min(8, nsites - b);
-        for (int k = lane; k < nb * WS; k += 32) {
-            const int j = k / WS, a = k - j * WS;
-            ww[j * WSP + a] = ldcg(&B.swt[(sb + b + j) * WS + a]);
+        {  // lanes 4 j + d (d < 3) evaluate the p weights of axis d of site j (x times q)
+            const float rv = sj < nb ? ldcg(reinterpret_cast<const float*>(B.srec + sb + b + sj) + sd) : 0.f;
+            const float qj = __shfl_sync(0xffffffffu, rv, lane | 3);
+            if (sj < nb && sd < 3) {
+                float t[P];
+                bspline_all<P>(rv, t);
+                if (sd == 0) {
+#pragma unroll
+                    for (int a = 0; a < P; ++a) t[a] = t[a] * qj;
+                }
+#pragma unroll
+                for (int a = 0; a < P; ++a) ww[sj * WSP + sd * P + a] = t[a];
+            }
         }
         if (lane < nb) {
             wcell[lane] = ldcg(&B.scell[sb + b + lane]);
@@ -1146,7 +1180,7 @@ struct pppm_batch {
     int* cell = nullptr;
     int* scell = nullptr;
     int* sorig = nullptr;
-    float* swt = nullptr;
+    Rec<float>* srec = nullptr;
     float* patch = nullptr;
     long long patch_cap = 0;
     float2* cx[3] = {nullptr, nullptr, nullptr};
@@ -1384,7 +1418,7 @@ int ensure_sites(pppm_batch* P, long long n) {
     bfree(P->cell);
     bfree(P->scell);
     bfree(P->sorig);
-    bfree(P->swt);
+    bfree(P->srec);
     P->cap_sites = 0;
     int rc;
     if ((rc = balloc(&P->tile_of, sizeof(int) * n)) != PPPM_OK) return rc;
@@ -1393,7 +1427,7 @@ int ensure_sites(pppm_batch* P, long long n) {
     if ((rc = balloc(&P->cell, sizeof(int) * n)) != PPPM_OK) return rc;
     if ((rc = balloc(&P->scell, sizeof(int) * n)) != PPPM_OK) return rc;
     if ((rc = balloc(&P->sorig, sizeof(int) * n)) != PPPM_OK) return rc;
-    if ((rc = balloc(&P->swt, sizeof(float) * wstride(P->order) * n)) != PPPM_OK) return rc;
+    if ((rc = balloc(&P->srec, sizeof(Rec<float>) * n)) != PPPM_OK) return rc;
     P->cap_sites = n;
     return PPPM_OK;
 }
@@ -1421,7 +1455,7 @@ int enqueue(pppm_batch* P, cudaStream_t s, int li, const float* pos, const float
     B.cell = P->cell;
     B.scell = P->scell;
     B.sorig = P->sorig;
-    B.swt = P->swt;
+    B.srec = P->srec;
     B.patch = P->patch;
     B.cx0 = P->cx[0];
     B.cx1 = P->cx[1];
@@ -1757,7 +1791,7 @@ void pppm_batch_destroy(pppm_batch* P) {
     bfree(P->cell);
     bfree(P->scell);
     bfree(P->sorig);
-    bfree(P->swt);
+    bfree(P->srec);
     bfree(P->patch);
     for (int c = 0; c < 3; ++c) bfree(P->cx[c]);
     bfree(P->fields);
