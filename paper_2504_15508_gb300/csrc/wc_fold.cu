@@ -33,6 +33,20 @@ k_wc_fold(int64_t n_atoms, int64_t n_wc, const T* __restrict__ f_sites, const in
     for (int64_t grp = (int64_t)blockIdx.x * kFoldWarps + (threadIdx.x >> 5); grp < groups; grp += warps) {
         const int64_t j0 = grp * kFoldAtoms;
         const int na = (int)min((int64_t)kFoldAtoms, n_atoms - j0);
+        // lane r's own terms of atom j0 + r (its site force, its hosted-WC
+        // range), loaded first so that they arrive while the Jacobian runs
+        T f0 = T(0), f1 = T(0), f2 = T(0);
+        int h0 = 0, h1 = 0;
+        if (lane < na) {
+            const int64_t j = j0 + lane;
+            f0 = f_sites[3 * j];
+            f1 = f_sites[3 * j + 1];
+            f2 = f_sites[3 * j + 2];
+            if (host_ptr) {
+                h0 = host_ptr[j];
+                h1 = host_ptr[j + 1];
+            }
+        }
         T acc[kFoldAtoms][3];
 #pragma unroll
         for (int r = 0; r < kFoldAtoms; ++r) acc[r][0] = acc[r][1] = acc[r][2] = T(0);
@@ -77,9 +91,8 @@ k_wc_fold(int64_t n_atoms, int64_t n_wc, const T* __restrict__ f_sites, const in
             if (lane == r) { s0 = acc[r][0]; s1 = acc[r][1]; s2 = acc[r][2]; }
         if (lane < na) {
             const int64_t j = j0 + lane;
-            T f0 = f_sites[3 * j], f1 = f_sites[3 * j + 1], f2 = f_sites[3 * j + 2];
             if (host_ptr) {
-                for (int h = host_ptr[j]; h < host_ptr[j + 1]; ++h) {
+                for (int h = h0; h < h1; ++h) {
                     const int n = host_wc[h];
                     if (n < 0 || n >= n_wc) {
                         bad = true;
